@@ -1,0 +1,390 @@
+"""CPU oracle for the steady state-of-charge problem (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
+import this module. The product path (the CUDA library behind ``include/rfb_soc.h``)
+shares no code with it.
+
+What it computes, in FP64, following the paper (arXiv 2502.08034):
+
+* Kinetics: V_T = RT/F; applied reducing voltage V_ar = -eta (eta = overpotential at
+  s = 1/2 with phi_L = 0, Eq. etat-from-s with s = 1/2); V~ = n_e V_ar / V_T
+  (Eq. Vart-def); s_eq = sigma(V~) (Eq. seq-from-Var); affine rate law
+  R~(s) = e^{alpha V~} (1 - (1 + e^{-V~}) s) (Eq. rate-from-soc-gen).
+* The steady form of Eq. nernst-planck-soc on a voxel lattice, assembled face by face
+  as explicit sparse matrices, the way the paper's explicit proof of concept builds its
+  advection and diffusion operators (Sec. III.C, "explicit sparse matrix
+  representations"): first-order upwind advection by the given face velocities,
+  7-point diffusion, a Dirichlet inlet, zero-gradient outlet, no flux through side walls
+  and fiber faces, and the Butler-Volmer source k0 a_c R~(s_c) with a_c = m_c n_wall/h
+  (n_wall = number of fiber 6-neighbours; the paper's a = A/V of a cut cell).
+  RHS(s) = L s + b.
+* The steady state is the solution of RHS(s) = 0 (a sparse direct solve; the affine rate
+  law makes the problem linear). ``explicit_iterate`` runs the paper's pseudo-time loop
+  s <- s + dt RHS(s) (Algorithm 7's two-buffer loop with F = I + dt(A + D + R)).
+* U_mt (Eq. umt-def): reaction off, s = 0 at the inlet, fluid cells touching a fiber
+  held at 1 (Eq. np-fast-boundary; Algorithm 7 resets s[elec] := 1 every step).
+* Outputs: I_tot (Eq. I-tot-def), F_in / F_out (Eq. electron-flow), mass-balance error
+  (Eq. convergence-bv-flow), utilisation U (Eq. utilization-def, first form), residual
+  (tau/dt)||ds||_RMS = tau RMS(RHS) (Eq. convergence-bv-change) with tau = V_f/Q.
+
+Readings where the paper is silent (stated here once, used throughout):
+* inlet diffusion: the value s_in is imposed on the inlet face, half a cell from the
+  cell centre, so the diffusive term is (2D/h^2)(s_in - s_c); ``inlet_bc='ghost'``
+  gives the alternative (D/h^2)(s_in - s_c);
+* dt = C_CFL / max_c d_c with d_c = -L_cc (the diagonal of -L), so every explicit
+  update is a convex combination for C_CFL <= 1; ``local_dt`` uses dt_c = C_CFL / d_c;
+* tau = V_f / Q with V_f the fluid volume and Q = sum over inlet faces of W h^2;
+* F_in includes the inlet diffusive flux so that I_tot = F_out - F_in holds exactly.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+R_GAS = 8.314462618      # J/(mol K)
+FARADAY = 96485.33212    # C/mol
+
+
+# --------------------------------------------------------------------------------------
+# Kinetics (Sec. II.B-II.D)
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Kinetics:
+    V_T: float        # thermal voltage RT/F
+    V_ar: float       # applied reducing voltage
+    Vt: float         # n_e V_ar / V_T
+    s_eq: float       # sigma(Vt)
+    A: float          # intercept of R~(s): e^{alpha Vt}
+    B: float          # -slope of R~(s): e^{alpha Vt} (1 + e^{-Vt})
+
+
+def kinetics(eta: float, alpha: float = 0.5, n_e: int = 2, T: float = 298.0) -> Kinetics:
+    V_T = R_GAS * T / FARADAY
+    V_ar = -eta
+    Vt = n_e * V_ar / V_T
+    A = math.exp(alpha * Vt)
+    B = A * (1.0 + math.exp(-Vt))
+    s_eq = 1.0 / (1.0 + math.exp(-Vt))
+    return Kinetics(V_T, V_ar, Vt, s_eq, A, B)
+
+
+def rate_affine(s, kin: Kinetics):
+    """R~(s) by Eq. rate-from-soc-gen."""
+    return kin.A * (1.0 - (1.0 + math.exp(-kin.Vt)) * np.asarray(s, dtype=np.float64))
+
+
+def rate_bv(s, Vt: float, alpha: float = 0.5):
+    """R~(s) by Eq. source-term-bv-gen divided by a k0 C_T, with eta~ from
+    Eq. etat-from-s (phi_L = 0)."""
+    s = np.asarray(s, dtype=np.float64)
+    etat = Vt - np.log(s / (1.0 - s))
+    return s ** alpha * (1.0 - s) ** (1.0 - alpha) * (np.exp(alpha * etat) -
+                                                     np.exp((alpha - 1.0) * etat))
+
+
+# --------------------------------------------------------------------------------------
+# Operator assembly
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Problem:
+    """Everything the discrete operator depends on. Arrays in (nz, ny, nx) layout."""
+    solid: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    W: np.ndarray
+    h: float
+    D: float
+    s_in: float
+    k0: float = 0.0
+    alpha: float = 0.5
+    n_e: int = 2
+    T: float = 298.0
+    c0: float = 20.0
+    eta: float = 0.0
+    beta: float = 1.0
+    area_mult: Optional[np.ndarray] = None
+    inlet_bc: str = "face"
+
+    @property
+    def dims(self):
+        nz, ny, nx = self.solid.shape
+        return nx, ny, nz
+
+
+@dataclasses.dataclass
+class Operator:
+    L: sp.csr_matrix          # N x N, rows of solid cells empty
+    b: np.ndarray             # N
+    unknown: np.ndarray       # N bool: cells whose value is solved for
+    fixed: np.ndarray         # N float: values of the non-unknown cells (0 on solid)
+    kappa: np.ndarray         # N: k0 a_c (zero in U_mt mode)
+    kin: Kinetics
+    Q: float                  # volumetric flow rate through the inlet
+    tau: float                # V_f / Q
+    n_fluid: int
+
+
+def n_wall(solid: np.ndarray) -> np.ndarray:
+    """Number of in-domain solid 6-neighbours of each cell (nz, ny, nx)."""
+    s = solid.astype(np.int32)
+    n = np.zeros_like(s)
+    n[:, :, 1:] += s[:, :, :-1]
+    n[:, :, :-1] += s[:, :, 1:]
+    n[:, 1:, :] += s[:, :-1, :]
+    n[:, :-1, :] += s[:, 1:, :]
+    n[1:] += s[:-1]
+    n[:-1] += s[1:]
+    return n
+
+
+def assemble(p: Problem, mode: str = "sbv") -> Operator:
+    """Build RHS(s) = L s + b for every fluid cell.
+
+    mode 'sbv': Eq. nernst-planck-soc with the affine source (Eq. rate-from-soc-gen).
+    mode 'umt': Eqs. np-fast-interior/np-fast-boundary with s_in = 0 and the cells that
+    touch a fiber held at 1 (Eq. umt-def)."""
+    solid = p.solid.astype(bool)
+    nz, ny, nx = solid.shape
+    N = nx * ny * nz
+    h, D = p.h, p.D
+    beta = p.beta
+    s_in = 0.0 if mode == "umt" else p.s_in
+    idx = np.arange(N).reshape(nz, ny, nx)
+    fluid = ~solid
+    rows, cols, vals = [], [], []
+    b = np.zeros(N)
+
+    def add(r, c, v):
+        rows.append(r); cols.append(c); vals.append(v)
+
+    def interior_faces(a, c, u, both):
+        # face between cell a (low side) and c (high side), velocity u along +axis.
+        a, c, u, both = a.ravel(), c.ravel(), u.ravel() * beta, both.ravel()
+        pos = np.maximum(u, 0.0) / h      # flux a -> c carries s_a
+        neg = np.maximum(-u, 0.0) / h     # flux c -> a carries s_c
+        add(a, a, -pos); add(c, a, pos)
+        add(c, c, -neg); add(a, c, neg)
+        dd = np.where(both, D / (h * h), 0.0)
+        add(a, a, -dd); add(a, c, dd)
+        add(c, c, -dd); add(c, a, dd)
+
+    interior_faces(idx[:, :, :-1], idx[:, :, 1:], p.U[:, :, 1:-1],
+                   fluid[:, :, :-1] & fluid[:, :, 1:])
+    interior_faces(idx[:, :-1, :], idx[:, 1:, :], p.V[:, 1:-1, :],
+                   fluid[:, :-1, :] & fluid[:, 1:, :])
+    interior_faces(idx[:-1], idx[1:], p.W[1:-1], fluid[:-1] & fluid[1:])
+
+    # inlet: faces W[0] below plane k = 0 (Dirichlet s_in on the face)
+    cin = idx[0].ravel()
+    fin = fluid[0].ravel()
+    w = p.W[0].ravel() * beta
+    add(cin, cin, -np.maximum(-w, 0.0) / h)
+    np.add.at(b, cin, np.maximum(w, 0.0) / h * s_in)
+    g = 2.0 if p.inlet_bc == "face" else 1.0
+    gd = np.where(fin, g * D / (h * h), 0.0)
+    add(cin, cin, -gd)
+    np.add.at(b, cin, gd * s_in)
+    # outlet: faces W[nz] above plane nz-1, zero-gradient (flux w s_c)
+    cout = idx[-1].ravel()
+    w = p.W[-1].ravel() * beta
+    add(cout, cout, -w / h)
+
+    kin = kinetics(p.eta, p.alpha, p.n_e, p.T)
+    kappa = np.zeros(N)
+    nw = n_wall(solid)
+    if mode == "sbv":
+        m = np.ones(N) if p.area_mult is None else np.asarray(p.area_mult, np.float64).ravel()
+        kappa = np.where(fluid.ravel(), p.k0 * m * nw.ravel() / h, 0.0)
+        add(idx.ravel(), idx.ravel(), -kappa * kin.B)
+        b += kappa * kin.A
+
+    L = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N)).tocsr()
+    L.sum_duplicates()
+    fl = fluid.ravel()
+    # rows and columns of solid cells carry only zero velocities: drop them entirely
+    L = sp.diags(fl.astype(np.float64)) @ L @ sp.diags(fl.astype(np.float64))
+    L = L.tocsr()
+    L.eliminate_zeros()
+    b = np.where(fl, b, 0.0)
+
+    unknown = fl.copy()
+    fixed = np.zeros(N)
+    if mode == "umt":
+        elec = fl & (nw.ravel() > 0)
+        unknown = fl & ~elec
+        fixed[elec] = 1.0
+    Q = h * h * beta * float(np.sum(np.where(fin, p.W[0].ravel(), 0.0)))
+    nf = int(fl.sum())
+    Vf = nf * h ** 3
+    tau = Vf / Q if Q > 0 else (nz * h) ** 2 / D
+    return Operator(L, b, unknown, fixed, kappa, kin, Q, tau, nf)
+
+
+# --------------------------------------------------------------------------------------
+# Steady state, iteration, outputs
+# --------------------------------------------------------------------------------------
+
+def rhs(op: Operator, s: np.ndarray) -> np.ndarray:
+    """RHS(s) = L s + b on all cells (zero on solid cells)."""
+    return op.L @ s + op.b
+
+
+def residual(op: Operator, s: np.ndarray) -> float:
+    """tau * RMS of RHS over the unknown cells (Eq. convergence-bv-change)."""
+    r = rhs(op, s)[op.unknown]
+    return op.tau * math.sqrt(float(np.mean(r * r))) if r.size else 0.0
+
+
+def steady_state(op: Operator, direct_max: int = 40000, rtol: float = 1e-14) -> np.ndarray:
+    """Solve RHS(s) = 0 for the unknown cells; other cells take their fixed values.
+
+    Up to ``direct_max`` unknowns: sparse LU (SuperLU). Larger systems: GMRES on the
+    row-scaled system D^{-1} L (D = diag L) with an incomplete-LU preconditioner, to a
+    relative residual of ``rtol``; both are library linear solvers of the same system."""
+    u = op.unknown
+    s = op.fixed.copy()
+    Luu = op.L[u][:, u].tocsc()
+    rhs_u = -(op.b[u] + op.L[u] @ op.fixed)
+    if Luu.shape[0] <= direct_max:
+        s[u] = spla.spsolve(Luu, rhs_u)
+        return s
+    dinv = sp.diags(1.0 / Luu.diagonal())
+    As = (dinv @ Luu).tocsc()
+    rs = dinv @ rhs_u
+    ilu = spla.spilu(As, drop_tol=1e-5, fill_factor=10)
+    M = spla.LinearOperator(As.shape, ilu.solve)
+    x, info = spla.gmres(As, rs, M=M, rtol=rtol, atol=0.0, restart=200, maxiter=20)
+    if info != 0:
+        raise RuntimeError("oracle GMRES did not reach rtol=%g (info=%d)" % (rtol, info))
+    s[u] = x
+    return s
+
+
+def dt_global(op: Operator, cfl: float) -> float:
+    d = -op.L.diagonal()[op.unknown]
+    return cfl / float(d.max())
+
+
+def explicit_iterate(op: Operator, cfl: float, tol: float, s0: Optional[np.ndarray] = None,
+                     max_steps: int = 10_000_000, check_every: int = 1, local_dt: bool = False):
+    """Explicit pseudo-time stepping to tau*RMS(RHS) < tol, two buffers as in Algorithm 7.
+
+    Returns (s, steps)."""
+    u = op.unknown
+    d = -op.L.diagonal()
+    if local_dt:
+        dt = np.where(u, cfl / np.where(d > 0, d, 1.0), 0.0)
+    else:
+        dt = np.where(u, dt_global(op, cfl), 0.0)
+    s = [op.fixed.copy() if s0 is None else np.array(s0, dtype=np.float64), None]
+    if s0 is None:
+        s[0][u] = 0.0
+    n = 0
+    while n < max_steps:
+        i, j = n % 2, (n + 1) % 2
+        s[j] = s[i] + dt * (op.L @ s[i] + op.b)
+        s[j][~u] = op.fixed[~u]
+        n += 1
+        if n % check_every == 0 and residual(op, s[j]) < tol:
+            break
+    return s[n % 2], n
+
+
+def initial_state(op: Operator, s_in: float) -> np.ndarray:
+    """Cold start: s = s_in on unknown fluid cells (the paper initialises from the inlet
+    value), fixed values elsewhere."""
+    s = op.fixed.copy()
+    s[op.unknown] = s_in
+    return s
+
+
+@dataclasses.dataclass
+class Outputs:
+    I_tot: float
+    F_in: float
+    F_out: float
+    F_in_adv: float
+    mass_balance_rel: float
+    U: float
+    U_outlet_form: float
+    residual: float
+
+
+def outputs(p: Problem, op: Operator, s: np.ndarray) -> Outputs:
+    """Currents, mass balance and utilisation of state s (Sec. II.C)."""
+    solid = p.solid.astype(bool)
+    nz, ny, nx = solid.shape
+    h = p.h
+    scale = p.n_e * FARADAY * p.c0
+    I_tot = scale * h ** 3 * float(np.sum(op.kappa * rate_affine(s, op.kin)))
+    s3 = s.reshape(nz, ny, nx)
+    fin = ~solid[0]
+    fout = ~solid[-1]
+    g = 2.0 if p.inlet_bc == "face" else 1.0
+    w_in = p.beta * p.W[0]
+    w_out = p.beta * p.W[-1]
+    adv_in = float(np.sum(np.where(fin, w_in * p.s_in, 0.0)))
+    dif_in = float(np.sum(np.where(fin, g * p.D / h * (p.s_in - s3[0]), 0.0)))
+    F_in_adv = scale * h * h * adv_in
+    F_in = scale * h * h * (adv_in + dif_in)
+    F_out = scale * h * h * float(np.sum(np.where(fout, w_out * s3[-1], 0.0)))
+    mb = abs(I_tot - (F_out - F_in)) / abs(I_tot) if I_tot != 0 else abs(F_out - F_in)
+    denom = scale * op.Q * (1.0 - p.s_in)
+    U = I_tot / denom if denom != 0 else float("nan")
+    sw = float(np.sum(np.where(fout, w_out, 0.0)))
+    s_out_mean = float(np.sum(np.where(fout, w_out * s3[-1], 0.0))) / sw if sw else float("nan")
+    U_out = (s_out_mean - p.s_in) / (1.0 - p.s_in)
+    return Outputs(I_tot, F_in, F_out, F_in_adv, mb, U, U_out, residual(op, s))
+
+
+def umt(p: Problem, s: Optional[np.ndarray] = None) -> float:
+    """U_mt = sum_out W s_mt / sum_out W (Eq. umt-def) of the U_mt steady state."""
+    op = assemble(p, mode="umt")
+    if s is None:
+        s = steady_state(op)
+    solid = p.solid.astype(bool)
+    nz, ny, nx = solid.shape
+    s3 = s.reshape(nz, ny, nx)
+    fout = ~solid[-1]
+    w = p.W[-1]
+    return float(np.sum(np.where(fout, w * s3[-1], 0.0))) / float(np.sum(np.where(fout, w, 0.0)))
+
+
+# --------------------------------------------------------------------------------------
+# Iterative upsampling (Sec. III.A, "iterative upsampling")
+# --------------------------------------------------------------------------------------
+
+def prolong(s_coarse: np.ndarray, solid_coarse: np.ndarray, solid_fine: np.ndarray,
+            s_in: float) -> np.ndarray:
+    """2x injection: s_f(i,j,k) = s_c(i//2, j//2, k//2). A fine fluid cell whose parent is
+    solid takes the mean over the parent's fluid 6-neighbours, else s_in. Solid -> 0."""
+    sc = s_coarse.reshape(solid_coarse.shape)
+    cfluid = ~solid_coarse.astype(bool)
+    nzc, nyc, nxc = sc.shape
+    acc = np.zeros_like(sc)
+    cnt = np.zeros_like(sc)
+    for axis in range(3):
+        for sh in (-1, 1):
+            vals = np.where(cfluid, sc, 0.0)
+            f = cfluid.astype(np.float64)
+            sl_src = [slice(None)] * 3
+            sl_dst = [slice(None)] * 3
+            if sh == 1:   # neighbour at +1 along axis
+                sl_src[axis] = slice(1, None); sl_dst[axis] = slice(0, -1)
+            else:
+                sl_src[axis] = slice(0, -1); sl_dst[axis] = slice(1, None)
+            acc[tuple(sl_dst)] += vals[tuple(sl_src)]
+            cnt[tuple(sl_dst)] += f[tuple(sl_src)]
+    fill = np.where(cnt > 0, acc / np.where(cnt > 0, cnt, 1.0), s_in)
+    parent = np.where(cfluid, sc, fill)
+    fine = parent.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
+    fine = np.where(solid_fine.astype(bool), 0.0, fine)
+    return fine.ravel()

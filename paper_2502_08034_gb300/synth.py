@@ -1,0 +1,318 @@
+"""Seeded synthetic workloads: fiber voxel lattices and potential-flow face velocities.
+
+This module only *produces inputs*. It holds none of the state-of-charge method's
+arithmetic (no advection, diffusion, kinetics or sweep); both the CUDA library and the
+CPU oracle consume what it returns. Random numbers come from a project-written
+SplitMix64 generator (Steele, Lea & Flood 2014), so the same seed gives the same lattice
+on every machine.
+
+Geometry (the paper's electrodes are fibers of a few-micron diameter resolved at
+h = 1.25 um, Sec. IV): straight cylinders whose axes lie in planes z = z0, at a uniform
+random in-plane angle, added one at a time until the fluid fraction first drops to the
+target porosity. Fluid that is not 6-connected to the inlet plane is then made solid, so
+every fluid cell reaches the inlet Dirichlet condition.
+
+Flow: the paper obtains u from a Navier-Stokes/Chorin solve (Sec. III.A, Algorithm 1).
+Here a discrete potential flow stands in for it: phi = 1 on inlet faces, 0 on outlet
+faces, no flux through fiber faces and side walls, solved by Jacobi-preconditioned FP64
+CG; face velocities are -grad(phi), scaled so that the mean z-velocity over fluid
+z-faces equals the requested mean. The result is discretely divergence-free (to the CG
+tolerance), which the state-of-charge operator's maximum principle relies on.
+
+Layout: arrays are C-ordered (nz, ny, nx), so the flat cell index is
+c = i + nx*(j + ny*k). Face arrays: U (nz, ny, nx+1) with U[k,j,i] on the face between
+cells i-1 and i; V (nz, ny+1, nx); W (nz+1, ny, nx) with W[0] the inlet plane and
+W[nz] the outlet plane. Velocities are in m/s, positive along +x/+y/+z.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+
+_M64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) with 53-bit uniform doubles."""
+
+    def __init__(self, seed: int):
+        self.state = int(seed) & _M64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _M64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+
+    def normal(self) -> float:
+        """Box-Muller; returns one of the pair (the generator is cheap)."""
+        u1 = self.uniform()
+        u2 = self.uniform()
+        u1 = max(u1, 1e-300)
+        return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+@dataclasses.dataclass
+class Fiber:
+    """Infinite cylinder, axis in the plane z = z0 through (x0, y0) at angle theta.
+
+    Coordinates are in cell units of the lattice the fiber was drawn on (``unit``
+    finest-level cells per unit)."""
+
+    z0: float
+    x0: float
+    y0: float
+    theta: float
+    d: float
+
+
+def rasterise(fibers: Sequence[Fiber], dims, scale: float = 1.0) -> np.ndarray:
+    """Solid mask (nz, ny, nx) of the union of fibers; a cell is solid when its centre
+    lies within d/2 of a fiber axis. ``scale`` = fiber-coordinate units per cell."""
+    nx, ny, nz = dims
+    solid = np.zeros((nz, ny, nx), dtype=bool)
+    for f in fibers:
+        _stamp(solid, f, scale)
+    return solid
+
+
+def _stamp(solid: np.ndarray, f: Fiber, scale: float) -> int:
+    """OR one fiber into ``solid``; returns the number of newly solid cells."""
+    nz, ny, nx = solid.shape
+    r = 0.5 * f.d
+    klo = max(0, int(math.floor((f.z0 - r) / scale - 0.5)) - 1)
+    khi = min(nz - 1, int(math.ceil((f.z0 + r) / scale - 0.5)) + 1)
+    if klo > khi:
+        return 0
+    x = (np.arange(nx) + 0.5) * scale
+    y = (np.arange(ny) + 0.5) * scale
+    st, ct = math.sin(f.theta), math.cos(f.theta)
+    dperp = np.abs((x[None, :] - f.x0) * st - (y[:, None] - f.y0) * ct)  # (ny, nx)
+    added = 0
+    for k in range(klo, khi + 1):
+        dz = (k + 0.5) * scale - f.z0
+        inside = dz * dz + dperp * dperp <= r * r
+        if inside.any():
+            plane = solid[k]
+            added += int(np.count_nonzero(inside & ~plane))
+            plane |= inside
+    return added
+
+
+def generate_fibers(seed: int, dims, porosity: float, diameter, max_fibers: int = 1_000_000):
+    """Draw fibers until the fluid fraction first reaches ``porosity`` or below.
+
+    Per fiber the draws are z0 ~ U(0, nz), x0 ~ U(0, nx), y0 ~ U(0, ny),
+    theta ~ U[0, pi) and, when ``diameter`` is a (lo, hi) pair, d ~ U[lo, hi].
+    Returns (fibers, solid mask (nz, ny, nx) bool)."""
+    nx, ny, nz = dims
+    rng = SplitMix64(seed)
+    n = nx * ny * nz
+    target_solid = (1.0 - porosity) * n
+    solid = np.zeros((nz, ny, nx), dtype=bool)
+    nsolid = 0
+    fibers = []
+    while nsolid < target_solid and len(fibers) < max_fibers:
+        z0 = rng.uniform(0.0, nz)
+        x0 = rng.uniform(0.0, nx)
+        y0 = rng.uniform(0.0, ny)
+        th = rng.uniform(0.0, math.pi)
+        if isinstance(diameter, (tuple, list)):
+            d = rng.uniform(diameter[0], diameter[1])
+        else:
+            d = float(diameter)
+        f = Fiber(z0, x0, y0, th, d)
+        fibers.append(f)
+        nsolid += _stamp(solid, f, 1.0)
+    return fibers, solid
+
+
+def remove_unconnected(solid: np.ndarray) -> np.ndarray:
+    """Make solid every fluid cell not 6-connected to the inlet plane k = 0."""
+    from scipy import ndimage
+
+    fluid = ~solid
+    lab, _ = ndimage.label(fluid)  # default structure = 6-connectivity in 3D
+    keep = np.unique(lab[0])
+    keep = keep[keep != 0]
+    connected = np.isin(lab, keep)
+    if not connected[-1].any():
+        raise ValueError("fiber lattice blocks the channel: no fluid path from inlet to outlet")
+    return solid | ~connected
+
+
+# --------------------------------------------------------------------------------------
+# Potential flow fixture
+# --------------------------------------------------------------------------------------
+
+def potential_flow(solid: np.ndarray, h: float, u_mean: float, tol: float = 1e-12,
+                   device: str = "cpu", max_iter: int = 200000, check_every: int = 25):
+    """Discrete potential flow on the fluid cells of ``solid``.
+
+    Returns (U, V, W, info) as float64 numpy arrays in the face layouts of this module;
+    info holds the CG iteration count and the achieved max |div u| / u_mean."""
+    import torch
+
+    dev = torch.device(device)
+    f = torch.from_numpy(~solid).to(dev)
+    nz, ny, nx = f.shape
+    fd = f.double()
+    gx = (f[:, :, 1:] & f[:, :, :-1]).double()
+    gy = (f[:, 1:, :] & f[:, :-1, :]).double()
+    gz = (f[1:] & f[:-1]).double()
+    gin = fd[0]
+    gout = fd[-1]
+    diag = torch.zeros_like(fd)
+    diag[:, :, 1:] += gx
+    diag[:, :, :-1] += gx
+    diag[:, 1:, :] += gy
+    diag[:, :-1, :] += gy
+    diag[1:] += gz
+    diag[:-1] += gz
+    diag[0] += 2.0 * gin
+    diag[-1] += 2.0 * gout
+    inv_diag = torch.where(diag > 0, 1.0 / torch.where(diag > 0, diag, torch.ones_like(diag)),
+                           torch.zeros_like(diag))
+
+    def apply_a(p):
+        out = diag * p
+        t = gx * (p[:, :, 1:]); out[:, :, :-1] -= t
+        t = gx * (p[:, :, :-1]); out[:, :, 1:] -= t
+        t = gy * (p[:, 1:, :]); out[:, :-1, :] -= t
+        t = gy * (p[:, :-1, :]); out[:, 1:, :] -= t
+        t = gz * p[1:]; out[:-1] -= t
+        t = gz * p[:-1]; out[1:] -= t
+        return out
+
+    b = torch.zeros_like(fd)
+    b[0] = 2.0 * gin
+    # initial guess: linear profile in z on fluid cells
+    zc = (torch.arange(nz, device=dev, dtype=torch.float64) + 0.5) / nz
+    x = (1.0 - zc)[:, None, None] * fd
+    r = b - apply_a(x)
+    z = inv_diag * r
+    p = z.clone()
+    rz = torch.sum(r * z)
+
+    def w_mean_unscaled(xv):
+        wz = torch.zeros((nz + 1, ny, nx), dtype=torch.float64, device=dev)
+        wz[0] = 2.0 * (1.0 - xv[0]) * gin / h
+        wz[-1] = 2.0 * xv[-1] * gout / h
+        wz[1:-1] = -(xv[1:] - xv[:-1]) * gz / h
+        cnt = gin.sum() + gout.sum() + gz.sum()
+        return wz, float(wz.sum() / cnt)
+
+    it = 0
+    achieved = float("inf")
+    while it < max_iter:
+        for _ in range(check_every):
+            ap = apply_a(p)
+            alpha = rz / torch.sum(p * ap)
+            x += alpha * p
+            r -= alpha * ap
+            z = inv_diag * r
+            rz_new = torch.sum(r * z)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+            it += 1
+        rtrue = b - apply_a(x)
+        _, wm = w_mean_unscaled(x)
+        achieved = float(rtrue.abs().max()) / (h * wm)
+        if achieved < 0.5 * tol:
+            break
+        if float(r.abs().max()) < 0.05 * tol * h * wm:
+            # recursive residual has drifted below the true one: restart from x
+            r = rtrue
+            z = inv_diag * r
+            p = z.clone()
+            rz = torch.sum(r * z)
+
+    wz, wm = w_mean_unscaled(x)
+    sigma = u_mean / wm
+    U = torch.zeros((nz, ny, nx + 1), dtype=torch.float64, device=dev)
+    V = torch.zeros((nz, ny + 1, nx), dtype=torch.float64, device=dev)
+    U[:, :, 1:-1] = -(x[:, :, 1:] - x[:, :, :-1]) * gx / h * sigma
+    V[:, 1:-1, :] = -(x[:, 1:, :] - x[:, :-1, :]) * gy / h * sigma
+    W = wz * sigma
+    div = (U[:, :, 1:] - U[:, :, :-1]) + (V[:, 1:, :] - V[:, :-1, :]) + (W[1:] - W[:-1])
+    div = div * fd
+    info = {"cg_iters": it, "max_div_rel": float(div.abs().max()) / u_mean,
+            "superficial_q": float(W[0].sum()) / (nx * ny)}
+    return U.cpu().numpy(), V.cpu().numpy(), W.cpu().numpy(), info
+
+
+# --------------------------------------------------------------------------------------
+# Workload recipes
+# --------------------------------------------------------------------------------------
+
+H_PAPER = 1.25e-6          # m, the paper's finest resolution (Sec. IV)
+D_SOC = 4e-10              # m^2/s, AQDS / H2AQDS diffusivity (parameter table)
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    dims: tuple            # (nx, ny, nz)
+    h: float
+    solid: np.ndarray      # (nz, ny, nx) uint8, 1 = fiber
+    U: np.ndarray
+    V: np.ndarray
+    W: np.ndarray
+    D: float
+    k0: float
+    alpha: float
+    T: float
+    n_e: int
+    c0: float
+    s_in: float
+    eta: float             # overpotential in volts (negative = reducing)
+    tol: float
+    u_mean: float
+    info: dict
+
+    @property
+    def n(self) -> int:
+        return int(self.dims[0] * self.dims[1] * self.dims[2])
+
+    @property
+    def porosity(self) -> float:
+        return 1.0 - float(self.solid.mean())
+
+
+def build_case(name: str, dims, porosity: float, diameter, seed: int, u_mean: float,
+               eta: float, s_in: float, tol: float, h: float = H_PAPER,
+               flow_device: str = "cpu", k0: float = 1e-7, flow_tol: float = 1e-12) -> Case:
+    fibers, solid = generate_fibers(seed, dims, porosity, diameter)
+    solid = remove_unconnected(solid)
+    U, V, W, info = potential_flow(solid, h, u_mean, tol=flow_tol, device=flow_device)
+    info = dict(info)
+    info["n_fibers"] = len(fibers)
+    if not info["max_div_rel"] < 1e3 * flow_tol:
+        raise RuntimeError("potential flow did not converge: %r" % (info,))
+    return Case(name=name, dims=tuple(int(d) for d in dims), h=h,
+                solid=solid.astype(np.uint8), U=U, V=V, W=W, D=D_SOC, k0=k0, alpha=0.5,
+                T=298.0, n_e=2, c0=20.0, s_in=s_in, eta=eta, tol=tol, u_mean=u_mean,
+                info=info)
+
+
+def fiber_channel_case(dims=(48, 48, 96), porosity=0.80, diameter=8.0, seed=1,
+                       u_mean=0.01, eta=-0.10, s_in=0.5, tol=1e-10, **kw) -> Case:
+    """Plain FP64 workload: 48x48x96, d = 8 cells, porosity 0.80, 1 cm/s, eta = -0.10 V,
+    s_in = 0.5 (defaults); smaller dims give the same recipe at test size."""
+    return build_case("fiber48x48x96" if tuple(dims) == (48, 48, 96) else
+                      "fiber%dx%dx%d" % tuple(dims), dims, porosity, diameter, seed,
+                      u_mean, eta, s_in, tol, **kw)
+
+
+def large_mixed_case(dims=(256, 256, 512), seed=2, **kw) -> Case:
+    """Mixed-precision workload: 256x256x512, porosity 0.85, d ~ U[6, 10] cells,
+    0.5 cm/s, eta = -0.05 V, s_in = 0.3, residual 1e-8."""
+    return build_case("fiber%dx%dx%d_mixed" % tuple(dims), dims, 0.85, (6.0, 10.0), seed,
+                      0.005, -0.05, 0.3, 1e-8, **kw)

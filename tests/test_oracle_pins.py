@@ -1,0 +1,329 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks oracle/soc.py against something other than itself: numbers the paper
+prints, closed forms, exact discrete identities, symmetries, bounds, limits and brute
+force, chosen so that a dropped term, a wrong sign or index, or a transposed operand in
+the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import soc
+from tests._cases import channel_1d, fiber_case, problem_from_case
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            out[parts[0]] = (float(parts[1]), float(parts[2]))
+    return out
+
+
+# ---------------------------------------------------------------- kinetics (Sec. II.B-D)
+
+def test_kinetics_values_printed_in_paper():
+    g = _golden("kinetics_paper.txt")
+    kin = soc.kinetics(0.0, 0.5, 2, 298.0)
+    v, tol = g["V_T_volts"]
+    assert abs(kin.V_T - v) < tol
+    # Nernst overpotential (V_T/n_e) logit(s) at s = 0.99: invert s_eq(V_ar) = 0.99
+    v, tol = g["nernst_overpotential_s099_V"]
+    # s_eq = sigma(n_e V_ar / V_T) -> V_ar = V_T/n_e * logit(s_eq); check via kinetics()
+    var = kin.V_T / 2 * math.log(0.99 / 0.01)
+    assert abs(soc.kinetics(-var).s_eq - 0.99) < 1e-12
+    assert abs(var - v) < tol
+    v, tol = g["s_eq_at_Var_0"]
+    assert abs(kin.s_eq - v) <= tol
+
+
+@pytest.mark.parametrize("eta", [-0.2, -0.1, -0.05, -0.02, 0.0, 0.03])
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.7])
+def test_affine_rate_law_matches_butler_volmer_form(eta, alpha):
+    """Eq. rate-from-soc-gen equals Eq. source-term-bv-gen / (a k0 C_T) with eta~ from
+    Eq. etat-from-s, pointwise in s."""
+    kin = soc.kinetics(eta, alpha)
+    s = np.linspace(1e-3, 1 - 1e-3, 201)
+    a = soc.rate_affine(s, kin)
+    b = soc.rate_bv(s, kin.Vt, alpha)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12 * kin.A)
+    # zero at s_eq = sigma(V~) (Eq. seq-from-Var)
+    assert abs(soc.rate_affine(kin.s_eq, kin)) < 1e-12 * kin.A
+
+
+def test_alpha_half_reduces_to_cosh_form():
+    """Eq. rate-from-soc: R~ = e^{V~/2} - 2 cosh(V~/2) s at alpha = 1/2."""
+    for eta in (-0.1, -0.05, 0.02):
+        kin = soc.kinetics(eta, 0.5)
+        s = np.linspace(0, 1, 11)
+        ref = math.exp(kin.Vt / 2) - 2 * math.cosh(kin.Vt / 2) * s
+        assert np.allclose(soc.rate_affine(s, kin), ref, rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------- exact 1D discrete closed form
+
+def _closed_form_1d(n, a, d, K, g, E_in):
+    """e_k = s_k - s* of the 1D channel: rows
+    k=0:   (a + d + g d + K) e0 - d e1 = (a + g d) E_in
+    0<k<n-1: a(e_{k-1}-e_k) + d(e_{k+1} - 2e_k + e_{k-1}) - K e_k = 0
+    k=n-1: -(a + d) e_{n-2} + (a + d + K) e_{n-1} = 0,
+    solved through the roots of d r^2 - (a + 2d + K) r + (a + d) = 0."""
+    k = np.arange(n, dtype=np.float64)
+    if d == 0.0:
+        return E_in * (a / (a + K)) ** (k + 1)
+    disc = math.sqrt((a + K) ** 2 + 4 * d * K)
+    rs = ((a + 2 * d + K) - disc) / (2 * d)   # small root
+    rl = ((a + 2 * d + K) + disc) / (2 * d)   # large root, normalised at the outlet
+    phi_s = rs ** k
+    phi_l = rl ** (k - (n - 1))
+
+    def row0(v):
+        return (a + d + g * d + K) * v[0] - d * v[1]
+
+    def rowN(v):
+        return -(a + d) * v[n - 2] + (a + d + K) * v[n - 1]
+
+    M = np.array([[row0(phi_s), row0(phi_l)], [rowN(phi_s), rowN(phi_l)]])
+    P, Q = np.linalg.solve(M, np.array([(a + g * d) * E_in, 0.0]))
+    return P * phi_s + Q * phi_l
+
+
+@pytest.mark.parametrize("D", [4e-10, 0.0, 4e-9])
+@pytest.mark.parametrize("inlet_bc", ["face", "ghost"])
+@pytest.mark.parametrize("k0,m", [(1e-7, 1.0), (1e-6, 0.7), (0.0, 1.0)])
+def test_1d_channel_exact_discrete_closed_form(D, inlet_bc, k0, m):
+    n, w = 40, 0.01
+    solid, U, V, W, h = channel_1d(n, w)
+    eta, s_in = -0.08, 0.2
+    area = np.full(solid.shape, m)
+    p = soc.Problem(solid, U, V, W, h, D, s_in, k0=k0, eta=eta, area_mult=area,
+                    inlet_bc=inlet_bc)
+    op = soc.assemble(p)
+    s = soc.steady_state(op).reshape(solid.shape)[:, 1, 1]
+    kin = soc.kinetics(eta)
+    K = k0 * m * 4 / h * kin.B
+    s_star = kin.A / kin.B if K > 0 else s_in
+    g = 2.0 if inlet_bc == "face" else 1.0
+    e = _closed_form_1d(n, w / h, D / h ** 2, K, g, s_in - s_star)
+    assert np.allclose(s - s_star, e, rtol=0, atol=1e-12 * max(abs(s_in - s_star), 0.1))
+    if k0 == 0.0:
+        assert np.allclose(s, s_in, atol=1e-13)
+
+
+def test_plug_flow_continuum_limit_first_order():
+    """With D = 0 and a fixed area per volume (a = 4/h0, via m = h/h0) the discrete
+    solution approaches the plug-flow exponential s(z) = s_eq + (s_in - s_eq)
+    exp(-K z / w) at first order in h (first-order upwinding)."""
+    L, w, eta, s_in, k0, h0 = 50e-6, 0.01, -0.05, 0.1, 1e-5, 1.25e-6
+    kin = soc.kinetics(eta)
+    K = k0 * 4 / h0 * kin.B
+    errs = []
+    for n in (20, 40, 80, 160):
+        h = L / n
+        solid, U, V, W, _ = channel_1d(n, w, h)
+        p = soc.Problem(solid, U, V, W, h, 0.0, s_in, k0=k0, eta=eta,
+                        area_mult=np.full(solid.shape, h / h0))
+        s = soc.steady_state(soc.assemble(p)).reshape(solid.shape)[:, 1, 1]
+        z = (np.arange(n) + 1.0) * h     # outflow face of each cell
+        exact = kin.s_eq + (s_in - kin.s_eq) * np.exp(-K * z / w)
+        errs.append(np.max(np.abs(s - exact)))
+    assert errs[0] > 1e-3
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in ratios), ratios
+
+
+# --------------------------------------------------- structure of the 3D operator
+
+def _p3(dims=(16, 16, 32), **over):
+    return problem_from_case(fiber_case(dims), soc, **over)
+
+
+def test_m_matrix_sign_structure_and_monotone_step():
+    """Upwinding + diffusion + a decreasing source give an M-matrix: off-diagonals >= 0,
+    diagonal < 0; I + dt L is non-negative for C_CFL <= 1 (monotone update)."""
+    p = _p3()
+    op = soc.assemble(p)
+    L = op.L.tocoo()
+    off = L.row != L.col
+    assert np.all(L.data[off] >= 0.0)
+    fl = p.solid.ravel() == 0
+    assert np.all(op.L.diagonal()[fl] < 0.0)
+    dt = soc.dt_global(op, 1.0)
+    F = (dt * op.L).tocsr()
+    F.setdiag(F.diagonal() + 1.0)
+    Fd = F[fl][:, fl]
+    assert Fd.min() >= -1e-15
+    # the flow really has transverse components on this lattice
+    assert np.abs(p.U).max() > 0.2 * np.abs(p.W).max()
+    assert np.abs(p.V).max() > 0.2 * np.abs(p.W).max()
+
+
+def test_uniform_state_is_steady_without_reaction():
+    """k0 = 0 and s = s_in everywhere: every face flux balances for a divergence-free
+    velocity field, so RHS vanishes (needs each face velocity on the right face)."""
+    p = _p3(k0=0.0, s_in=0.37)
+    op = soc.assemble(p)
+    s = np.where(p.solid.ravel() == 0, 0.37, 0.0)
+    r = soc.rhs(op, s)
+    scale = 0.37 * np.abs(p.W).max() / p.h
+    assert np.abs(r).max() < 1e-10 * scale
+
+
+def test_conservation_identity_any_state():
+    """sum_c h^3 RHS_c = (F_in - F_out + I_tot) / (n_e F c0) for any s (telescoping)."""
+    p = _p3()
+    op = soc.assemble(p)
+    rng = np.random.default_rng(0)
+    s = np.where(p.solid.ravel() == 0, rng.uniform(0, 1, p.solid.size), 0.0)
+    o = soc.outputs(p, op, s)
+    lhs = p.h ** 3 * float(np.sum(soc.rhs(op, s)))
+    rhs_ = (o.F_in - o.F_out + o.I_tot) / (p.n_e * soc.FARADAY * p.c0)
+    assert abs(lhs - rhs_) < 1e-11 * (o.F_in + o.F_out) / (p.n_e * soc.FARADAY * p.c0)
+
+
+def test_steady_state_mass_balance_and_bounds():
+    """At steady state I_tot = F_out - F_in (Eq. convergence-bv-flow) and
+    min(s_in, s_eq) <= s <= max(s_in, s_eq) (discrete maximum principle)."""
+    p = _p3()
+    op = soc.assemble(p)
+    s = soc.steady_state(op)
+    o = soc.outputs(p, op, s)
+    assert o.mass_balance_rel < 1e-9
+    fl = p.solid.ravel() == 0
+    lo, hi = min(p.s_in, op.kin.s_eq), max(p.s_in, op.kin.s_eq)
+    assert s[fl].min() >= lo - 1e-11 and s[fl].max() <= hi + 1e-11
+    assert o.residual < 1e-12
+    # the two printed utilisation expressions agree once the second is corrected for
+    # s_in != 0 and for the inlet diffusive flux
+    U_corr = o.U_outlet_form - (o.F_in - o.F_in_adv) / (
+        p.n_e * soc.FARADAY * p.c0 * op.Q * (1 - p.s_in))
+    assert abs(o.U - U_corr) < 1e-9 * abs(o.U)
+
+
+def test_inlet_at_equilibrium_is_steady():
+    p = _p3()
+    kin = soc.kinetics(p.eta)
+    p2 = _p3(s_in=kin.s_eq)
+    op = soc.assemble(p2)
+    s = soc.steady_state(op)
+    fl = p.solid.ravel() == 0
+    assert np.allclose(s[fl], kin.s_eq, atol=1e-11)
+
+
+def test_xy_transposition_symmetry():
+    """Swapping the x and y axes of the geometry and the flow transposes the solution."""
+    p = _p3()
+    s = soc.steady_state(soc.assemble(p)).reshape(p.solid.shape)
+    solid_t = np.ascontiguousarray(p.solid.transpose(0, 2, 1))
+    U_t = np.ascontiguousarray(p.V.transpose(0, 2, 1))
+    V_t = np.ascontiguousarray(p.U.transpose(0, 2, 1))
+    W_t = np.ascontiguousarray(p.W.transpose(0, 2, 1))
+    pt = soc.Problem(solid_t, U_t, V_t, W_t, p.h, p.D, p.s_in, k0=p.k0, eta=p.eta)
+    st = soc.steady_state(soc.assemble(pt)).reshape(solid_t.shape)
+    assert np.allclose(st, s.transpose(0, 2, 1), rtol=0, atol=1e-13)
+
+
+def test_x_mirror_symmetry():
+    """Mirroring x (i -> nx-1-i) with U negated on mirrored faces mirrors the solution."""
+    p = _p3()
+    s = soc.steady_state(soc.assemble(p)).reshape(p.solid.shape)
+    pm = soc.Problem(p.solid[:, :, ::-1].copy(), -p.U[:, :, ::-1].copy(),
+                     p.V[:, :, ::-1].copy(), p.W[:, :, ::-1].copy(), p.h, p.D, p.s_in,
+                     k0=p.k0, eta=p.eta)
+    sm = soc.steady_state(soc.assemble(pm)).reshape(p.solid.shape)
+    assert np.allclose(sm, s[:, :, ::-1], rtol=0, atol=1e-13)
+
+
+# --------------------------------------------- iteration and solver (brute force)
+
+def test_dense_lu_brute_force_small_lattice():
+    p = problem_from_case(fiber_case((6, 6, 10), diameter=2.0, porosity=0.8), soc)
+    for mode in ("sbv", "umt"):
+        op = soc.assemble(p, mode)
+        u = op.unknown
+        A = op.L[u][:, u].toarray()
+        rhs_u = -(op.b[u] + op.L[u] @ op.fixed)
+        x = np.linalg.solve(A, rhs_u)
+        s = soc.steady_state(op)
+        assert np.allclose(s[u], x, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("local_dt", [False, True])
+def test_explicit_iteration_reaches_the_steady_state(local_dt):
+    """The paper's pseudo-time loop (Algorithm 7 with dt from a CFL bound) converges to
+    the solution of RHS = 0; a per-cell dt changes only the path, not the fixed point."""
+    p = problem_from_case(fiber_case((8, 8, 12), diameter=3.0), soc)
+    op = soc.assemble(p)
+    ref = soc.steady_state(op)
+    s, n = soc.explicit_iterate(op, 0.4, 1e-13, s0=soc.initial_state(op, p.s_in),
+                                check_every=50, local_dt=local_dt)
+    assert n < 10_000_000
+    assert np.abs(s - ref).max() < 1e-11
+
+
+def test_grid_fits_gmres_matches_direct():
+    """The large-system solver path agrees with SuperLU on a mid-size lattice."""
+    p = _p3((16, 16, 32))
+    op = soc.assemble(p)
+    a = soc.steady_state(op, direct_max=10 ** 9)
+    b = soc.steady_state(op, direct_max=0)
+    assert np.abs(a - b).max() < 1e-12
+
+
+# ------------------------------------------------------------------------- U_mt
+
+def test_umt_bounds_and_upper_bound_on_utilisation():
+    """0 <= U_mt <= 1 and U <= U_mt for s_in = 0 (Eq. umt-def and the text after it)."""
+    for eta in (-0.2, -0.1, -0.02):
+        p = _p3(s_in=0.0, eta=eta)
+        op = soc.assemble(p)
+        s = soc.steady_state(op)
+        o = soc.outputs(p, op, s)
+        u = soc.umt(p)
+        assert 0.0 <= u <= 1.0
+        assert o.U <= u + 1e-12
+
+
+def test_umt_is_the_fast_kinetics_limit():
+    """k0 -> infinity with s_eq -> 1 and s_in = 0 drives the SBV state to the U_mt state
+    (Eqs. np-fast-interior/np-fast-boundary)."""
+    p = _p3(s_in=0.0, eta=-0.35, k0=10.0)
+    op = soc.assemble(p)
+    s = soc.steady_state(op)
+    o = soc.outputs(p, op, s)
+    u = soc.umt(p)
+    assert abs(o.U_outlet_form - u) < 1e-5
+    s_mt = soc.steady_state(soc.assemble(p, "umt"))
+    fl = p.solid.ravel() == 0
+    assert np.abs(s[fl] - s_mt[fl]).max() < 1e-5
+
+
+def test_umt_independent_of_kinetics_and_inlet():
+    a = soc.umt(_p3(s_in=0.3, eta=-0.1, k0=1e-7))
+    b = soc.umt(_p3(s_in=0.9, eta=-0.02, k0=5e-6))
+    assert a == b
+
+
+# ------------------------------------------------------------------ prolongation
+
+def test_prolongation_injection():
+    rng = np.random.default_rng(3)
+    solid_c = np.zeros((4, 3, 3), dtype=np.uint8)
+    solid_c[1, 1, 1] = 1
+    sc = rng.uniform(size=solid_c.size) * (solid_c.ravel() == 0)
+    solid_f = solid_c.repeat(2, 0).repeat(2, 1).repeat(2, 2).copy()
+    solid_f[2, 2, 2] = 0   # fine fluid cell under the solid coarse parent
+    sf = soc.prolong(sc, solid_c, solid_f, 0.5).reshape(solid_f.shape)
+    scr = sc.reshape(solid_c.shape)
+    assert sf[0, 0, 0] == scr[0, 0, 0] and sf[7, 5, 5] == scr[3, 2, 2]
+    nb = [scr[0, 1, 1], scr[2, 1, 1], scr[1, 0, 1], scr[1, 2, 1], scr[1, 1, 0], scr[1, 1, 2]]
+    assert abs(sf[2, 2, 2] - np.mean(nb)) < 1e-15
+    assert sf[3, 3, 3] == 0.0
