@@ -1,0 +1,207 @@
+/*
+ * rfb_soc.h - C ABI of the GB300 steady state-of-charge solver.
+ *
+ * The library computes the steady state of the state-of-charge PDE of Emanuel & Rycroft,
+ * "Digital Twin for Porous Electrodes in Redox Flow Batteries" (arXiv 2502.08034),
+ * Eq. nernst-planck-soc (Sec. II.D):
+ *     ds/dt = -u . grad s + D lap s + k0 a R~(s),
+ * with the affine rate law R~(s) = e^{alpha V~} (1 - (1 + e^{-V~}) s)
+ * (Eq. rate-from-soc-gen), V~ = n_e V_ar / V_T (Eq. Vart-def), by explicit pseudo-time
+ * stepping on a voxel lattice (the explicit reformulation of Sec. III.C), plus the
+ * mass-transport utilisation U_mt (Eq. umt-def, Algorithm 7).
+ *
+ * Discretisation (identical in every entry point):
+ *   - lattice nx * ny * nz, cell size dx; flow enters through the low-z face of plane
+ *     k = 0 (inlet) and leaves through the high-z face of plane k = nz-1 (outlet);
+ *     cell index c = i + nx*(j + ny*k);
+ *   - first-order upwind advection by the given face velocities (times the velocity
+ *     scale beta), 7-point diffusion between fluid cells, no flux through side walls and
+ *     fiber faces, inlet value s_in imposed on the inlet face (diffusive term
+ *     (2D/dx^2)(s_in - s_c); RFB_INLET_GHOST gives (D/dx^2)(s_in - s_c)), zero-gradient
+ *     outlet;
+ *   - reaction k0 a_c R~(s_c) with a_c = m_c n_wall(c) / dx, n_wall = number of fiber
+ *     6-neighbours (the voxel form of the cut-cell specific area a = A/V, Sec. III.B),
+ *     m_c an optional per-cell area multiplier (default 1);
+ *   - "overpotential" eta [V] is the activation overpotential at s = 1/2 with
+ *     phi_L = 0 (Eq. etat-from-s), i.e. V_ar = -eta; eta < 0 is reducing.
+ *   - residual r = tau * RMS over unknown cells of RHS(s) = (tau/dt) ||ds||_RMS
+ *     (Eq. convergence-bv-change), tau = V_fluid / Q, Q = beta * sum_inlet W dx^2.
+ *
+ * Conventions: every call returns rfb_status; nothing throws across the ABI. A handle
+ * is not thread-safe; distinct handles are independent. All work is queued on the
+ * handle's CUDA stream (rfb_soc_set_stream); calls that return host values synchronise
+ * that stream. Pointers marked "host or device" are interpreted per the rfb_mem_kind
+ * argument; device pointers must be on the handle's device.
+ */
+#ifndef RFB_SOC_H
+#define RFB_SOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rfb_status {
+    RFB_OK = 0,
+    RFB_ERR_INVALID_ARG = 1,   /* bad size, value, pointer or option; nothing changed */
+    RFB_ERR_CUDA = 2,          /* a CUDA call failed; see rfb_soc_last_error */
+    RFB_ERR_OOM = 3,           /* device allocation failed */
+    RFB_ERR_NOT_CONVERGED = 4, /* max_sweeps reached; the state is valid and readable */
+    RFB_ERR_NONFINITE = 5,     /* a non-finite value appeared in the state or residual */
+    RFB_ERR_STATE = 6,         /* call needs a state that is not there (e.g. no solve) */
+    RFB_ERR_UNSUPPORTED = 7    /* option not built into this library */
+} rfb_status;
+
+typedef enum rfb_mem_kind { RFB_MEM_HOST = 0, RFB_MEM_DEVICE = 1 } rfb_mem_kind;
+
+typedef enum rfb_precision {
+    RFB_PREC_FP64 = 0,   /* FP64 sweeps and reductions */
+    RFB_PREC_MIXED = 1   /* FP32 correction sweeps, FP64 defect / reductions / state */
+} rfb_precision;
+
+typedef enum rfb_inlet_bc { RFB_INLET_FACE = 0, RFB_INLET_GHOST = 1 } rfb_inlet_bc;
+
+typedef enum rfb_dt_mode {
+    RFB_DT_GLOBAL = 0,   /* dt = cfl / max_c d_c, d_c the diagonal of -L */
+    RFB_DT_LOCAL = 1     /* dt_c = cfl / d_c per cell (same fixed point, fewer sweeps) */
+} rfb_dt_mode;
+
+/* Butler-Volmer kinetics (Sec. II.B, parameter table). */
+typedef struct rfb_kinetics {
+    double k0;      /* rate constant [m/s] */
+    double alpha;   /* charge-transfer coefficient, 0 < alpha < 1 */
+    int32_t n_e;    /* electrons per reaction (2 for AQDS) */
+    int32_t pad_;
+    double T;       /* temperature [K] */
+    double c0;      /* total concentration of redox species C_T [mol/m^3] */
+} rfb_kinetics;
+
+typedef struct rfb_solve_opts {
+    int32_t precision;      /* rfb_precision (default RFB_PREC_FP64) */
+    int32_t inlet_bc;       /* rfb_inlet_bc (default RFB_INLET_FACE) */
+    int32_t dt_mode;        /* rfb_dt_mode (default RFB_DT_GLOBAL) */
+    int32_t check_every;    /* sweeps between FP64 residual checks (0 = automatic) */
+    double cfl;             /* C_CFL in (0, 1] (default 0.4) */
+    double velocity_scale;  /* beta >= 0: every face velocity is multiplied by it (1) */
+    int64_t max_sweeps;     /* give up after this many sweeps (0 = 50,000,000) */
+    int32_t reserved[8];    /* must be zero */
+} rfb_solve_opts;
+
+typedef struct rfb_solve_result {
+    int64_t sweeps;          /* explicit sweeps applied by this call */
+    int64_t checks;          /* FP64 residual evaluations */
+    double residual;         /* tau * RMS(RHS) at the returned state */
+    double I_tot;            /* total current [A], Eq. I-tot-def */
+    double F_in;             /* inlet electron flow [A], advective + diffusive */
+    double F_out;            /* outlet electron flow [A], Eq. electron-flow */
+    double F_in_adv;         /* advective part of F_in (the paper's F_in) */
+    double mass_balance_rel; /* |I_tot - (F_out - F_in)| / |I_tot|, Eq. convergence-bv-flow */
+    double U;                /* utilisation I_tot / (n_e F c0 Q (1 - s_in)), Eq. utilization-def */
+    double outlet_mean;      /* sum_out W s / sum_out W */
+    double dt;               /* global pseudo-time step [s] (RFB_DT_LOCAL: the minimum) */
+    double tau;              /* V_fluid / Q [s] */
+    double time_ms;          /* wall time of the call */
+    int64_t nonfinite;       /* non-finite RHS values seen at the last check */
+} rfb_solve_result;
+
+typedef struct rfb_soc_handle rfb_soc_handle;
+
+/* Fill opts with the defaults listed above. */
+void rfb_solve_opts_default(rfb_solve_opts* opts);
+
+/* Static string for a status code (never NULL). */
+const char* rfb_status_string(rfb_status st);
+
+/* Last error detail recorded on the handle (empty string if none; never NULL). */
+const char* rfb_soc_last_error(const rfb_soc_handle* h);
+
+/*
+ * Create a solver for one lattice (Sec. III.C: the explicit operators are built once
+ * per geometry and flow field).
+ *   dims          nx, ny, nz >= 1 (nz >= 2)
+ *   dx            cell size [m] > 0
+ *   fiber_mask    N bytes, 1 = fiber (solid), 0 = fluid; layout c = i + nx*(j + ny*k)
+ *   U, V, W       face velocities [m/s]: U (nx+1)*ny*nz with U[i + (nx+1)*(j + ny*k)] on
+ *                 the face between cells i-1 and i; V nx*(ny+1)*nz; W nx*ny*(nz+1) with
+ *                 plane 0 = inlet faces, plane nz = outlet faces. Must be finite, zero on
+ *                 side walls and on every face touching a fiber cell; inlet and outlet
+ *                 W must be >= 0.
+ *   D             diffusivity [m^2/s] > 0
+ *   kin           kinetics (k0 >= 0, 0 < alpha < 1, n_e >= 1, T > 0, c0 > 0)
+ *   area_mult     nullable; N doubles > 0 (the per-cell multiplier m_c)
+ *   kind          whether the array pointers are host or device memory
+ *   cuda_stream   cudaStream_t to queue work on (NULL = legacy default stream)
+ *   out           receives the handle
+ * The library copies every input into device memory it owns; the caller may free its
+ * arrays on return. Invalid inputs return RFB_ERR_INVALID_ARG with a message on *out
+ * left NULL (read it with rfb_soc_last_error(NULL)).
+ */
+rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber_mask,
+                          const double* U, const double* V, const double* W, double D,
+                          const rfb_kinetics* kin, const double* area_mult,
+                          rfb_mem_kind kind, void* cuda_stream, rfb_soc_handle** out);
+
+/* Release every resource of the handle. NULL-safe. */
+rfb_status rfb_soc_destroy(rfb_soc_handle* h);
+
+/* Queue subsequent work of the handle on this cudaStream_t (NULL = default stream). */
+rfb_status rfb_soc_set_stream(rfb_soc_handle* h, void* cuda_stream);
+
+/*
+ * Drive the state to residual <= tol by explicit pseudo-time sweeps
+ * s <- s + dt RHS(s) (Eq. nernst-planck-soc stepped to dt-independent steady state).
+ *   s_in   inlet state of charge, 0 <= s_in <= 1
+ *   eta    overpotential [V] (see above)
+ *   tol    residual tolerance > 0
+ *   opts   nullable (defaults)
+ *   res    nullable; filled on return (also on NOT_CONVERGED / NONFINITE)
+ * Starts from the current state if one is set (previous solve, rfb_soc_set_state or
+ * rfb_soc_upsample), otherwise from s = s_in on every fluid cell.
+ * Returns RFB_OK, RFB_ERR_NOT_CONVERGED (state valid) or RFB_ERR_NONFINITE.
+ */
+rfb_status rfb_soc_solve(rfb_soc_handle* h, double s_in, double eta, double tol,
+                         const rfb_solve_opts* opts, rfb_solve_result* res);
+
+/*
+ * Apply exactly n_sweeps explicit sweeps to the current state (FP64 or, with
+ * RFB_PREC_MIXED, FP32 sweeps on a correction that is added to the FP64 state), then
+ * evaluate the outputs into res (nullable). Starts from s = s_in if no state is set.
+ */
+rfb_status rfb_soc_step(rfb_soc_handle* h, double s_in, double eta, int64_t n_sweeps,
+                        const rfb_solve_opts* opts, rfb_solve_result* res);
+
+/*
+ * Evaluate residual, I_tot, F_in, F_out, mass balance and U (Sec. II.C) in FP64 on the
+ * current state at the operating point of the last solve/step. RFB_ERR_STATE if none.
+ */
+rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res);
+
+/*
+ * Mass-transport utilisation U_mt (Eq. umt-def): the steady state of advection and
+ * diffusion with s = 0 at the inlet and every fluid cell that touches a fiber held at 1
+ * (Eqs. np-fast-interior/np-fast-boundary, Algorithm 7), then sum_out W s / sum_out W.
+ * Independent of the kinetics and of s_in. Uses its own state buffer (the SOC state is
+ * untouched). opts nullable; res (nullable) receives sweeps and residual.
+ */
+rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts,
+                       double* umt, rfb_solve_result* res);
+
+/* Copy the FP64 state (N doubles, solid cells 0) out to host or device memory. */
+rfb_status rfb_soc_get_state(rfb_soc_handle* h, double* s, rfb_mem_kind kind);
+
+/* Set the FP64 state (N doubles; solid-cell values are ignored). Must be finite. */
+rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind kind);
+
+/* Lattice size N and fluid-cell count of the handle (either pointer nullable). */
+rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fluid);
+
+/* Number of CUDA kernels this handle has launched since creation (graph replays count
+ * every kernel inside the graph). */
+int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFB_SOC_H */

@@ -1,0 +1,744 @@
+// Host side of the C ABI declared in include/rfb_soc.h: device buffers, the solve driver
+// (pseudo-time loop with periodic FP64 residual checks, FP32 defect correction), state
+// management. All kernels live in soc_kernels.cuh.
+#include "rfb_soc.h"
+#include "soc_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace rfb;
+
+namespace {
+
+constexpr double R_GAS = 8.314462618;
+constexpr double FARADAY = 96485.33212;
+
+thread_local std::string g_create_error;
+
+struct OpPoint {
+    bool valid = false;
+    double s_in = 0, eta = 0, beta = 1, cfl = 0.4;
+    int inlet_bc = 0, dt_mode = 1, umt = 0;
+    double A = 0, B = 0;      // affine rate law intercept / -slope
+    double dt = 0;            // global step
+    double dmin = 0;          // smallest diagonal (local-dt bookkeeping)
+};
+
+}  // namespace
+
+struct rfb_soc_handle {
+    int nx = 0, ny = 0, nz = 0, nxny = 0;
+    int64_t N = 0;
+    double h = 0, D = 0;
+    rfb_kinetics kin{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    uint8_t* d_flags = nullptr;
+    double *d_u = nullptr, *d_v = nullptr, *d_w = nullptr;      // m/s, cell aligned
+    double *d_us = nullptr, *d_vs = nullptr, *d_ws = nullptr;   // * beta / h
+    float *d_u32 = nullptr, *d_v32 = nullptr, *d_w32 = nullptr; // * beta / h, FP32
+    double* d_m = nullptr;
+    float* d_m32 = nullptr;
+    double* d_s[2] = {nullptr, nullptr};
+    double* d_t[2] = {nullptr, nullptr};   // U_mt state
+    float* d_delta[2] = {nullptr, nullptr};
+    float* d_r32 = nullptr;
+    float* d_dtc = nullptr;
+    double* d_partials = nullptr;
+    double* d_red = nullptr;
+    double* h_red = nullptr;                // pinned, NRED doubles
+    unsigned long long* d_err = nullptr;
+    int s_cur = 0, t_cur = 0;
+    bool have_state = false;
+    bool have_umt_state = false;
+    double scaled_beta = NAN;
+
+    int64_t n_fluid = 0, n_elec = 0;
+    double sum_w_in = 0, sum_w_out = 0;     // unscaled sums of inlet / outlet W
+    OpPoint op;
+    int64_t launches = 0;
+    std::string err;
+
+    int kchunk = 8;
+    dim3 grid, block;
+    int64_t nblocks = 0;
+};
+
+namespace {
+
+struct Fail {
+    rfb_status st;
+};
+
+void set_err(rfb_soc_handle* h, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+}
+
+#define CK(h, call)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            set_err((h), "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                    __FILE__, __LINE__);                                               \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? RFB_ERR_OOM : RFB_ERR_CUDA};  \
+        }                                                                              \
+    } while (0)
+
+#define LAUNCHED(h)                                                                     \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            set_err((h), "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),   \
+                    __FILE__, __LINE__);                                               \
+            throw Fail{RFB_ERR_CUDA};                                                  \
+        }                                                                              \
+        ++(h)->launches;                                                               \
+    } while (0)
+
+template <typename T>
+void dalloc(rfb_soc_handle* h, T** p, size_t n) {
+    CK(h, cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)));
+}
+
+int flat_grid(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
+}
+
+Lattice lattice(const rfb_soc_handle* h) {
+    return Lattice{h->nx, h->ny, h->nz, h->nxny, h->d_flags};
+}
+
+void kinetics_AB(const rfb_kinetics& k, double eta, double* A, double* B) {
+    const double VT = R_GAS * k.T / FARADAY;
+    const double Vt = k.n_e * (-eta) / VT;
+    *A = std::exp(k.alpha * Vt);
+    *B = *A * (1.0 + std::exp(-Vt));
+}
+
+template <typename T>
+Coef<T> make_coef(const rfb_soc_handle* h, const OpPoint& op, bool correction, bool local) {
+    Coef<T> C{};
+    if constexpr (sizeof(T) == 8) {
+        C.u = h->d_us; C.v = h->d_vs; C.w = h->d_ws; C.m = h->d_m;
+    } else {
+        C.u = h->d_u32; C.v = h->d_v32; C.w = h->d_w32; C.m = h->d_m32;
+    }
+    C.dtc = local ? h->d_dtc : nullptr;
+    C.s_in = correction ? T(0) : T(op.s_in);
+    C.Dh = T(h->D / (h->h * h->h));
+    C.gDh = T((op.inlet_bc == RFB_INLET_GHOST ? 1.0 : 2.0) * h->D / (h->h * h->h));
+    C.dt = T(op.dt);
+    for (int n = 0; n < 8; ++n) {
+        const double kap = op.umt ? 0.0 : h->kin.k0 * n / h->h;
+        C.rA[n] = (correction || op.umt) ? T(0) : T(kap * op.A);
+        C.rB[n] = T(kap * op.B);
+    }
+    C.umt = op.umt;
+    return C;
+}
+
+void reduce_readback(rfb_soc_handle* h, int min_slot0) {
+    finalize_kernel<<<1, 256, 0, h->stream>>>(h->d_partials, h->nblocks, h->d_red, min_slot0);
+    LAUNCHED(h);
+    CK(h, cudaMemcpyAsync(h->h_red, h->d_red, NRED * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+}
+
+// Prepare velocities, tables and dt for an operating point.
+void prepare(rfb_soc_handle* h, OpPoint& op) {
+    if (!(h->scaled_beta == op.beta)) {
+        const double sc = op.beta / h->h;
+        const int64_t N = h->N;
+        scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_u, h->d_us, h->d_u32, sc, N);
+        LAUNCHED(h);
+        scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_v, h->d_vs, h->d_v32, sc, N);
+        LAUNCHED(h);
+        scale_kernel<<<flat_grid(N + h->nxny), 256, 0, h->stream>>>(h->d_w, h->d_ws, h->d_w32,
+                                                                    sc, N + h->nxny);
+        LAUNCHED(h);
+        h->scaled_beta = op.beta;
+    }
+    kinetics_AB(h->kin, op.eta, &op.A, &op.B);
+    Coef<double> C = make_coef<double>(h, op, false, false);
+    const bool local = op.dt_mode == RFB_DT_LOCAL;
+    diag_kernel<<<h->grid, h->block, 0, h->stream>>>(lattice(h), C, op.cfl,
+                                                     local ? h->d_dtc : nullptr,
+                                                     h->d_partials, h->kchunk);
+    LAUNCHED(h);
+    reduce_readback(h, 1);
+    const double dmax = h->h_red[NRED - 1];
+    op.dmin = h->h_red[0];
+    op.dt = dmax > 0 ? op.cfl / dmax : 0.0;
+    op.valid = true;
+}
+
+void fill_result(const rfb_soc_handle* h, const OpPoint& op, rfb_solve_result* r,
+                 int64_t n_unknown) {
+    const double* v = h->h_red;
+    const double h3 = h->h * h->h * h->h;
+    const double scale = h->kin.n_e * FARADAY * h->kin.c0 * h3;
+    // Q = beta * sum_in W h^2 ; tau = V_f / Q = N_f h / (beta sum_in W)
+    const double Q = op.beta * h->sum_w_in * h->h * h->h;
+    const double tau = Q > 0 ? (double)h->n_fluid * h3 / Q
+                             : std::pow(h->nz * h->h, 2) / h->D;
+    r->residual = n_unknown > 0 ? tau * std::sqrt(v[0] / (double)n_unknown) : 0.0;
+    r->I_tot = scale * v[1];
+    r->F_in_adv = scale * v[3];
+    r->F_in = scale * (v[2] + v[3]);
+    r->F_out = scale * v[4];
+    const double net = r->F_out - r->F_in;
+    r->mass_balance_rel = r->I_tot != 0 ? std::fabs(r->I_tot - net) / std::fabs(r->I_tot)
+                                        : std::fabs(net);
+    const double denom = h->kin.n_e * FARADAY * h->kin.c0 * Q * (1.0 - op.s_in);
+    r->U = denom != 0 ? r->I_tot / denom : NAN;
+    r->outlet_mean = v[5] != 0 ? v[4] / v[5] : NAN;
+    r->dt = op.dt;
+    r->tau = tau;
+    r->nonfinite = (int64_t)v[6];
+}
+
+// FP64 check on buffer set (s/t). fuse: add delta and write the other buffer.
+void check(rfb_soc_handle* h, const OpPoint& op, bool umt, bool fuse, bool write_r) {
+    double** buf = umt ? h->d_t : h->d_s;
+    int& cur = umt ? h->t_cur : h->s_cur;
+    Coef<double> C = make_coef<double>(h, op, false, false);
+    Lattice L = lattice(h);
+    if (fuse) {
+        if (write_r)
+            check_kernel<true, true><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, buf[cur], h->d_delta[0], buf[cur ^ 1], h->d_r32, h->d_partials,
+                h->kchunk);
+        else
+            check_kernel<true, false><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, buf[cur], h->d_delta[0], buf[cur ^ 1], nullptr, h->d_partials,
+                h->kchunk);
+        LAUNCHED(h);
+        cur ^= 1;
+    } else {
+        if (write_r)
+            check_kernel<false, true><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, buf[cur], nullptr, nullptr, h->d_r32, h->d_partials, h->kchunk);
+        else
+            check_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, buf[cur], nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
+        LAUNCHED(h);
+    }
+    reduce_readback(h, 0);
+}
+
+// n FP64 sweeps on s (or t for U_mt), ping-pong
+void sweeps64(rfb_soc_handle* h, const OpPoint& op, bool umt, int64_t n) {
+    double** buf = umt ? h->d_t : h->d_s;
+    int& cur = umt ? h->t_cur : h->s_cur;
+    Coef<double> C = make_coef<double>(h, op, false, op.dt_mode == RFB_DT_LOCAL);
+    Lattice L = lattice(h);
+    for (int64_t q = 0; q < n; ++q) {
+        sweep_kernel<double, false><<<h->grid, h->block, 0, h->stream>>>(
+            L, C, buf[cur], buf[cur ^ 1], nullptr, h->kchunk);
+        LAUNCHED(h);
+        cur ^= 1;
+    }
+}
+
+// n FP32 correction sweeps delta <- delta + dt (L delta + r), starting from delta = 0.
+// The result is left in d_delta[0].
+void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n) {
+    const size_t bytes = (size_t)h->N * sizeof(float);
+    CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->d_delta[1], 0, bytes, h->stream));
+    Coef<float> C = make_coef<float>(h, op, true, op.dt_mode == RFB_DT_LOCAL);
+    Lattice L = lattice(h);
+    int cur = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        sweep_kernel<float, true><<<h->grid, h->block, 0, h->stream>>>(
+            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->kchunk);
+        LAUNCHED(h);
+        cur ^= 1;
+    }
+    if (cur == 1) std::swap(h->d_delta[0], h->d_delta[1]);
+}
+
+void init_state(rfb_soc_handle* h, bool umt, double s_in) {
+    double** buf = umt ? h->d_t : h->d_s;
+    init_state_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(h->d_flags, buf[0], buf[1],
+                                                              s_in, umt ? 1 : 0, h->N);
+    LAUNCHED(h);
+    if (umt) { h->t_cur = 0; h->have_umt_state = true; }
+    else { h->s_cur = 0; h->have_state = true; }
+}
+
+bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
+    rfb_solve_opts_default(o);
+    if (in) *o = *in;
+    if (o->precision != RFB_PREC_FP64 && o->precision != RFB_PREC_MIXED) {
+        set_err(h, "opts.precision must be RFB_PREC_FP64 or RFB_PREC_MIXED");
+        return false;
+    }
+    if (o->inlet_bc != RFB_INLET_FACE && o->inlet_bc != RFB_INLET_GHOST) {
+        set_err(h, "opts.inlet_bc invalid");
+        return false;
+    }
+    if (o->dt_mode != RFB_DT_GLOBAL && o->dt_mode != RFB_DT_LOCAL) {
+        set_err(h, "opts.dt_mode invalid");
+        return false;
+    }
+    if (!(o->cfl > 0 && o->cfl <= 1.0)) { set_err(h, "opts.cfl must be in (0, 1]"); return false; }
+    if (!(o->velocity_scale >= 0 && std::isfinite(o->velocity_scale))) {
+        set_err(h, "opts.velocity_scale must be finite and >= 0");
+        return false;
+    }
+    if (o->check_every < 0 || o->max_sweeps < 0) {
+        set_err(h, "opts.check_every / max_sweeps must be >= 0");
+        return false;
+    }
+    for (int q = 0; q < 8; ++q)
+        if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
+    if (o->max_sweeps == 0) o->max_sweeps = 50000000;
+    return true;
+}
+
+OpPoint make_op(const rfb_solve_opts& o, double s_in, double eta, bool umt) {
+    OpPoint op;
+    op.s_in = umt ? 0.0 : s_in;
+    op.eta = eta;
+    op.beta = o.velocity_scale;
+    op.cfl = o.cfl;
+    op.inlet_bc = o.inlet_bc;
+    op.dt_mode = o.dt_mode;
+    op.umt = umt ? 1 : 0;
+    return op;
+}
+
+int64_t default_check_every(const rfb_soc_handle* h, int precision) {
+    // one FP64 check per ~this many sweeps: cheap for small lattices (launch bound),
+    // negligible for large ones
+    (void)h;
+    return precision == RFB_PREC_MIXED ? 200 : 100;
+}
+
+// Core driver shared by solve / step / umt. Returns the status; fills res.
+rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool umt,
+                 double tol, int64_t fixed_sweeps, rfb_solve_result* res) {
+    auto t0 = std::chrono::steady_clock::now();
+    prepare(h, op);
+    const int64_t n_unknown = umt ? h->n_fluid - h->n_elec : h->n_fluid;
+    bool& have = umt ? h->have_umt_state : h->have_state;
+    if (!have) init_state(h, umt, op.s_in);
+    const bool mixed = o.precision == RFB_PREC_MIXED;
+    const int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, o.precision);
+    rfb_solve_result r{};
+    rfb_status st = RFB_OK;
+    int64_t done = 0;
+    const int64_t limit = fixed_sweeps >= 0 ? fixed_sweeps : o.max_sweeps;
+    // first check: residual of the starting state (mixed: also the FP32 forcing)
+    check(h, op, umt, false, mixed);
+    ++r.checks;
+    fill_result(h, op, &r, n_unknown);
+    while (true) {
+        if (r.nonfinite > 0) { st = RFB_ERR_NONFINITE; break; }
+        if (fixed_sweeps < 0 && r.residual <= tol) break;
+        if (done >= limit) {
+            st = fixed_sweeps >= 0 ? RFB_OK : RFB_ERR_NOT_CONVERGED;
+            break;
+        }
+        const int64_t n = std::min(every, limit - done);
+        if (mixed) {
+            sweeps32(h, op, n);
+            check(h, op, umt, true, true);
+        } else {
+            sweeps64(h, op, umt, n);
+            check(h, op, umt, false, false);
+        }
+        done += n;
+        ++r.checks;
+        fill_result(h, op, &r, n_unknown);
+    }
+    r.sweeps = done;
+    r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                    .count();
+    if (res) *res = r;
+    return st;
+}
+
+rfb_status guard(rfb_soc_handle* h) {
+    if (!h) return RFB_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) {
+        set_err(h, "cudaSetDevice: %s", cudaGetErrorString(e));
+        return RFB_ERR_CUDA;
+    }
+    h->err.clear();
+    return RFB_OK;
+}
+
+void free_all(rfb_soc_handle* h) {
+    void* ptrs[] = {h->d_flags, h->d_u,  h->d_v,   h->d_w,     h->d_us,   h->d_vs,
+                    h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
+                    h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
+                    h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_red) cudaFreeHost(h->h_red);
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void rfb_solve_opts_default(rfb_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = RFB_PREC_FP64;
+    o->inlet_bc = RFB_INLET_FACE;
+    o->dt_mode = RFB_DT_LOCAL;
+    o->check_every = 0;
+    o->cfl = 0.4;
+    o->velocity_scale = 1.0;
+    o->max_sweeps = 0;
+}
+
+const char* rfb_status_string(rfb_status st) {
+    switch (st) {
+        case RFB_OK: return "ok";
+        case RFB_ERR_INVALID_ARG: return "invalid argument";
+        case RFB_ERR_CUDA: return "CUDA error";
+        case RFB_ERR_OOM: return "out of device memory";
+        case RFB_ERR_NOT_CONVERGED: return "not converged (state valid)";
+        case RFB_ERR_NONFINITE: return "non-finite value in state or residual";
+        case RFB_ERR_STATE: return "required state missing";
+        case RFB_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char* rfb_soc_last_error(const rfb_soc_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber_mask,
+                          const double* U, const double* V, const double* W, double D,
+                          const rfb_kinetics* kin, const double* area_mult,
+                          rfb_mem_kind kind, void* cuda_stream, rfb_soc_handle** out) {
+    g_create_error.clear();
+    if (!out) { set_err(nullptr, "out is NULL"); return RFB_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!dims || !fiber_mask || !U || !V || !W || !kin) {
+        set_err(nullptr, "NULL input pointer");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) {
+        set_err(nullptr, "kind must be RFB_MEM_HOST or RFB_MEM_DEVICE");
+        return RFB_ERR_INVALID_ARG;
+    }
+    const int nx = dims[0], ny = dims[1], nz = dims[2];
+    if (nx < 1 || ny < 1 || nz < 2) {
+        set_err(nullptr, "dims must be >= (1, 1, 2)");
+        return RFB_ERR_INVALID_ARG;
+    }
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N + (int64_t)nx * ny >= ((int64_t)1 << 31)) {
+        set_err(nullptr, "lattice too large: N + nx*ny must be < 2^31");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (!(dx > 0 && std::isfinite(dx)) || !(D > 0 && std::isfinite(D))) {
+        set_err(nullptr, "dx and D must be finite and > 0");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (!(kin->k0 >= 0 && std::isfinite(kin->k0)) || !(kin->alpha > 0 && kin->alpha < 1) ||
+        kin->n_e < 1 || !(kin->T > 0 && std::isfinite(kin->T)) ||
+        !(kin->c0 > 0 && std::isfinite(kin->c0))) {
+        set_err(nullptr, "kinetics out of range (k0 >= 0, 0 < alpha < 1, n_e >= 1, T > 0, c0 > 0)");
+        return RFB_ERR_INVALID_ARG;
+    }
+    rfb_soc_handle* h = new rfb_soc_handle();
+    try {
+        h->nx = nx; h->ny = ny; h->nz = nz; h->nxny = nx * ny; h->N = N;
+        h->h = dx; h->D = D; h->kin = *kin;
+        h->stream = (cudaStream_t)cuda_stream;
+        CK(h, cudaGetDevice(&h->device));
+        const int64_t nxny = h->nxny;
+        const int64_t nU = (int64_t)(nx + 1) * ny * nz, nV = (int64_t)nx * (ny + 1) * nz,
+                      nW = nxny * (nz + 1);
+        dalloc(h, &h->d_flags, N);
+        dalloc(h, &h->d_u, N); dalloc(h, &h->d_v, N); dalloc(h, &h->d_w, N + nxny);
+        dalloc(h, &h->d_us, N); dalloc(h, &h->d_vs, N); dalloc(h, &h->d_ws, N + nxny);
+        dalloc(h, &h->d_u32, N); dalloc(h, &h->d_v32, N); dalloc(h, &h->d_w32, N + nxny);
+        for (int q = 0; q < 2; ++q) {
+            dalloc(h, &h->d_s[q], N); dalloc(h, &h->d_t[q], N); dalloc(h, &h->d_delta[q], N);
+        }
+        dalloc(h, &h->d_r32, N); dalloc(h, &h->d_dtc, N);
+        dalloc(h, &h->d_err, 4);
+        CK(h, cudaMallocHost((void**)&h->h_red, NRED * sizeof(double)));
+        dalloc(h, &h->d_red, NRED);
+        // launch geometry: 32 x 8 column tiles, z chunks so that there are >= ~8 blocks
+        // per SM
+        h->block = dim3(BX, BY, 1);
+        const int gx = (nx + BX - 1) / BX, gy = (ny + BY - 1) / BY;
+        int kc = nz;
+        while (kc > 4 && (int64_t)gx * gy * ((nz + kc - 1) / kc) < 152 * 8) kc = (kc + 1) / 2;
+        h->kchunk = kc;
+        h->grid = dim3(gx, gy, (nz + kc - 1) / kc);
+        h->nblocks = (int64_t)h->grid.x * h->grid.y * h->grid.z;
+        dalloc(h, &h->d_partials, (size_t)h->nblocks * NRED);
+
+        // staging: the inputs on the device (copied when they are host arrays)
+        uint8_t* d_mask = nullptr;
+        double *dU = nullptr, *dV = nullptr, *dW = nullptr, *dm = nullptr;
+        std::vector<void*> tmp;
+        auto stage = [&](const void* src, size_t bytes, void** dst) {
+            if (kind == RFB_MEM_DEVICE) { *dst = const_cast<void*>(src); return; }
+            CK(h, cudaMalloc(dst, std::max<size_t>(bytes, 1)));
+            tmp.push_back(*dst);
+            CK(h, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+        };
+        try {
+            stage(fiber_mask, N, (void**)&d_mask);
+            stage(U, nU * 8, (void**)&dU);
+            stage(V, nV * 8, (void**)&dV);
+            stage(W, nW * 8, (void**)&dW);
+            if (area_mult) stage(area_mult, N * 8, (void**)&dm);
+            CK(h, cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned long long), h->stream));
+            CK(h, cudaMemsetAsync(h->d_u, 0, N * 8, h->stream));
+            CK(h, cudaMemsetAsync(h->d_v, 0, N * 8, h->stream));
+            flags_kernel<<<flat_grid(N), 256, 0, h->stream>>>(d_mask, h->d_flags, nx, ny, nz);
+            LAUNCHED(h);
+            repack_kernel<<<flat_grid(nU), 256, 0, h->stream>>>(dU, d_mask, h->d_u, nx, ny, nz,
+                                                                0, h->d_err);
+            LAUNCHED(h);
+            repack_kernel<<<flat_grid(nV), 256, 0, h->stream>>>(dV, d_mask, h->d_v, nx, ny, nz,
+                                                                1, h->d_err);
+            LAUNCHED(h);
+            repack_kernel<<<flat_grid(nW), 256, 0, h->stream>>>(dW, d_mask, h->d_w, nx, ny, nz,
+                                                                2, h->d_err);
+            LAUNCHED(h);
+            if (area_mult) {
+                dalloc(h, &h->d_m, N);
+                dalloc(h, &h->d_m32, N);
+                scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(dm, h->d_m, h->d_m32, 1.0, N);
+                LAUNCHED(h);
+            }
+            unsigned long long herr[4];
+            CK(h, cudaMemcpyAsync(herr, h->d_err, sizeof herr, cudaMemcpyDeviceToHost,
+                                  h->stream));
+            std::vector<uint8_t> flags(N);
+            CK(h, cudaMemcpyAsync(flags.data(), h->d_flags, N, cudaMemcpyDeviceToHost,
+                                  h->stream));
+            std::vector<double> w_in(nxny), w_out(nxny);
+            CK(h, cudaMemcpyAsync(w_in.data(), h->d_w, nxny * 8, cudaMemcpyDeviceToHost,
+                                  h->stream));
+            CK(h, cudaMemcpyAsync(w_out.data(), h->d_w + N, nxny * 8, cudaMemcpyDeviceToHost,
+                                  h->stream));
+            std::vector<double> mh;
+            if (area_mult) {
+                mh.resize(N);
+                CK(h, cudaMemcpyAsync(mh.data(), h->d_m, N * 8, cudaMemcpyDeviceToHost,
+                                      h->stream));
+            }
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (void* p : tmp) cudaFree(p);
+            tmp.clear();
+            if (herr[0]) { set_err(nullptr, "%llu non-finite face velocities", herr[0]); throw Fail{RFB_ERR_INVALID_ARG}; }
+            if (herr[1]) { set_err(nullptr, "%llu nonzero velocities on side-wall or fiber faces", herr[1]); throw Fail{RFB_ERR_INVALID_ARG}; }
+            if (herr[2]) { set_err(nullptr, "%llu negative inlet/outlet velocities", herr[2]); throw Fail{RFB_ERR_INVALID_ARG}; }
+            for (int64_t c = 0; c < N; ++c) {
+                if (flags[c] & F_FLUID) {
+                    ++h->n_fluid;
+                    if (flags[c] & F_ELEC) ++h->n_elec;
+                }
+            }
+            for (int64_t q = 0; q < nxny; ++q) {
+                if (flags[q] & F_FLUID) h->sum_w_in += w_in[q];
+                if (flags[N - nxny + q] & F_FLUID) h->sum_w_out += w_out[q];
+            }
+            for (size_t c = 0; c < mh.size(); ++c)
+                if (!(mh[c] > 0 && std::isfinite(mh[c]))) {
+                    set_err(nullptr, "area_mult must be finite and > 0 (cell %zu)", c);
+                    throw Fail{RFB_ERR_INVALID_ARG};
+                }
+            if (h->n_fluid == 0) { set_err(nullptr, "no fluid cells"); throw Fail{RFB_ERR_INVALID_ARG}; }
+        } catch (...) {
+            for (void* p : tmp) cudaFree(p);
+            throw;
+        }
+    } catch (Fail f) {
+        if (!h->err.empty()) g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return f.st;
+    }
+    *out = h;
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_destroy(rfb_soc_handle* h) {
+    if (!h) return RFB_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_set_stream(rfb_soc_handle* h, void* s) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    h->stream = (cudaStream_t)s;
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_solve(rfb_soc_handle* h, double s_in, double eta, double tol,
+                         const rfb_solve_opts* opts, rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    if (!(s_in >= 0 && s_in <= 1)) { set_err(h, "s_in must be in [0, 1]"); return RFB_ERR_INVALID_ARG; }
+    if (!std::isfinite(eta)) { set_err(h, "eta must be finite"); return RFB_ERR_INVALID_ARG; }
+    if (!(tol > 0)) { set_err(h, "tol must be > 0"); return RFB_ERR_INVALID_ARG; }
+    try {
+        OpPoint op = make_op(o, s_in, eta, false);
+        rfb_status st = drive(h, o, op, false, tol, -1, res);
+        h->op = op;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_step(rfb_soc_handle* h, double s_in, double eta, int64_t n_sweeps,
+                        const rfb_solve_opts* opts, rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    if (!(s_in >= 0 && s_in <= 1)) { set_err(h, "s_in must be in [0, 1]"); return RFB_ERR_INVALID_ARG; }
+    if (!std::isfinite(eta)) { set_err(h, "eta must be finite"); return RFB_ERR_INVALID_ARG; }
+    if (n_sweeps < 0) { set_err(h, "n_sweeps must be >= 0"); return RFB_ERR_INVALID_ARG; }
+    try {
+        OpPoint op = make_op(o, s_in, eta, false);
+        if (o.check_every == 0) o.check_every = (int32_t)std::min<int64_t>(std::max<int64_t>(n_sweeps, 1), 1 << 30);
+        rfb_status st = drive(h, o, op, false, 0.0, n_sweeps, res);
+        h->op = op;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (!h->have_state || !h->op.valid) {
+        set_err(h, "no state / operating point: call rfb_soc_solve or rfb_soc_step first");
+        return RFB_ERR_STATE;
+    }
+    try {
+        OpPoint op = h->op;
+        check(h, op, false, false, false);
+        rfb_solve_result r{};
+        r.checks = 1;
+        fill_result(h, op, &r, h->n_fluid);
+        if (res) *res = r;
+        return r.nonfinite ? RFB_ERR_NONFINITE : RFB_OK;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts, double* umt,
+                       rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    if (!(tol > 0)) { set_err(h, "tol must be > 0"); return RFB_ERR_INVALID_ARG; }
+    try {
+        OpPoint op = make_op(o, 0.0, 0.0, true);
+        h->have_umt_state = false;   // always a cold start: s = 0, electrode cells = 1
+        rfb_solve_result r{};
+        rfb_status st = drive(h, o, op, true, tol, -1, &r);
+        if (umt) *umt = r.outlet_mean;
+        if (res) *res = r;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_get_state(rfb_soc_handle* h, double* s, rfb_mem_kind kind) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (!s) { set_err(h, "s is NULL"); return RFB_ERR_INVALID_ARG; }
+    if (!h->have_state) { set_err(h, "no state"); return RFB_ERR_STATE; }
+    try {
+        CK(h, cudaMemcpyAsync(s, h->d_s[h->s_cur], h->N * 8,
+                              kind == RFB_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                   : cudaMemcpyDeviceToDevice,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind kind) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (!s) { set_err(h, "s is NULL"); return RFB_ERR_INVALID_ARG; }
+    if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
+    try {
+        const double* src = s;
+        double* tmp = nullptr;
+        if (kind == RFB_MEM_HOST) {
+            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
+            CK(h, cudaMemcpyAsync(tmp, s, h->N * 8, cudaMemcpyHostToDevice, h->stream));
+            src = tmp;
+        }
+        CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned long long), h->stream));
+        set_state_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(h->d_flags, src, h->d_s[0],
+                                                                 h->d_s[1], h->d_err, h->N);
+        LAUNCHED(h);
+        unsigned long long bad = 0;
+        CK(h, cudaMemcpyAsync(&bad, h->d_err, sizeof bad, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (tmp) cudaFree(tmp);
+        h->s_cur = 0;
+        h->have_state = true;
+        if (bad) { set_err(h, "%llu non-finite state values (set to 0)", bad); return RFB_ERR_INVALID_ARG; }
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fluid) {
+    if (!h) return RFB_ERR_INVALID_ARG;
+    if (n_cells) *n_cells = h->N;
+    if (n_fluid) *n_fluid = h->n_fluid;
+    return RFB_OK;
+}
+
+int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,478 @@
+// Device code of the steady state-of-charge solver (sm_103a).
+//
+// One explicit pseudo-time sweep of Eq. nernst-planck-soc on a voxel lattice:
+//   s'_c = s_c + dt * RHS_c,  RHS_c = adv_c + diff_c + k0 a_c R~(s_c)  (+ forcing)
+// with first-order upwind advection by face velocities, 7-point diffusion, a Dirichlet
+// inlet face and a zero-gradient outlet (Sec. III.C explicit operators), and the affine
+// rate law R~(s) = A - B s (Eq. rate-from-soc-gen).
+//
+// Layout (structure of arrays, x fastest, c = i + nx*(j + ny*k)):
+//   flags[c]  uint8: bit0 fluid, bits1..6 fluid neighbour at -x,+x,-y,+y,-z,+z,
+//             bit7 electrode (fluid cell with at least one fiber neighbour)
+//   u[c]      (beta/h) * velocity on the low-x face of cell c (0 for i = 0)
+//   v[c]      (beta/h) * velocity on the low-y face
+//   w[c]      (beta/h) * velocity on the low-z face; w[c + nx*ny] is the high face,
+//             so w has N + nx*ny entries and its last plane holds the outlet faces.
+// The high-x face of cell c is u[c+1] (zero at i = nx-1, a side wall), likewise y.
+//
+// Threads own one (i, j) column of a 32 x 8 tile and march a chunk of z planes,
+// carrying s at k-1, k, k+1 and the shared z face in registers (2.5D streaming);
+// x/y neighbours come through L1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfb {
+
+enum : unsigned {
+    F_FLUID = 1u, F_XM = 2u, F_XP = 4u, F_YM = 8u, F_YP = 16u, F_ZM = 32u, F_ZP = 64u,
+    F_ELEC = 128u
+};
+constexpr unsigned F_NBRS = 0x7Eu;
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int NRED = 8;   // reduction slots of the FP64 check
+
+struct Lattice {
+    int nx, ny, nz, nxny;
+    const uint8_t* __restrict__ flags;
+};
+
+template <typename T>
+struct Coef {
+    const T* __restrict__ u;
+    const T* __restrict__ v;
+    const T* __restrict__ w;
+    const T* __restrict__ m;       // per-cell area multiplier, nullptr = 1
+    const float* __restrict__ dtc; // per-cell step (local dt), nullptr = global dt
+    T s_in;    // inlet value (0 in correction sweeps and U_mt)
+    T Dh;      // D / h^2
+    T gDh;     // inlet diffusion coefficient: 2 D/h^2 (face) or D/h^2 (ghost)
+    T dt;      // global pseudo-time step
+    T rA[8];   // k0 n_wall / h * A     by n_wall (zero in correction sweeps / U_mt)
+    T rB[8];   // k0 n_wall / h * B     by n_wall (zero in U_mt)
+    int umt;   // electrode cells are Dirichlet (value untouched), no reaction
+};
+
+// q > 0 for an FP64 q, decided on the integer pipe (the FP64 pipe of GB300 is narrow);
+// identical to the floating-point comparison for every non-NaN q, including -0.0.
+__device__ __forceinline__ bool positive(double q) { return __double_as_longlong(q) > 0; }
+__device__ __forceinline__ bool positive(float q) { return q > 0.0f; }
+
+__device__ __forceinline__ int n_wall_of(unsigned f, int i, int j, int k, int nx, int ny,
+                                         int nz) {
+    int dom = 6 - (i == 0) - (i == nx - 1) - (j == 0) - (j == ny - 1) - (k == 0) -
+              (k == nz - 1);
+    return dom - __popc(f & F_NBRS);
+}
+
+// Right-hand side at one fluid cell. Neighbour values of non-fluid / out-of-domain
+// neighbours must be passed as sc (their faces carry zero velocity and no diffusion).
+// szm_adv: value carried in through the low-z face (s_in at the inlet).
+// z_lo_dif: whether the low-z diffusion term is the inlet face term.
+template <typename T>
+__device__ __forceinline__ T cell_rhs(const Coef<T>& C, const T* tA, const T* tB, T sc, T sxm,
+                                      T sxp, T sym, T syp, T szm, T szp, T uL, T uH, T vL,
+                                      T vH, T wL, T wH, bool inlet, bool outlet, int nw,
+                                      T mult) {
+    // upwind advection: inflow through low faces, outflow through high faces
+    T adv = uL * (positive(uL) ? sxm : sc);
+    adv -= uH * (positive(uH) ? sc : sxp);
+    adv += vL * (positive(vL) ? sym : sc);
+    adv -= vH * (positive(vH) ? sc : syp);
+    T zin = inlet ? C.s_in : szm;
+    adv += wL * (positive(wL) ? zin : sc);
+    T zout = outlet ? sc : szp;
+    adv -= wH * (positive(wH) ? sc : zout);
+    // 7-point diffusion between fluid cells (non-fluid neighbours enter as sc)
+    T zmd = inlet ? sc : szm;
+    T nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
+    T dif = C.Dh * nsum - (T(6) * C.Dh) * sc;
+    if (inlet) dif += C.gDh * (C.s_in - sc);
+    // Butler-Volmer source k0 a_c (A - B s)
+    T rea = mult * (tA[nw] - tB[nw] * sc);
+    return (adv + dif) + rea;
+}
+
+// Diagonal d_c of -L at one fluid cell (outflow + diffusion + reaction), FP64.
+template <typename T>
+__device__ __forceinline__ T cell_diag(const Coef<T>& C, const T* tB, unsigned f, T uL, T uH,
+                                       T vL, T vH, T wL, T wH, bool inlet, int nw, T mult) {
+    T d = (uH > T(0) ? uH : T(0)) + (uL < T(0) ? -uL : T(0));
+    d += (vH > T(0) ? vH : T(0)) + (vL < T(0) ? -vL : T(0));
+    d += (wH > T(0) ? wH : T(0)) + (wL < T(0) ? -wL : T(0));
+    d += C.Dh * T(__popc(f & F_NBRS));
+    if (inlet) d += C.gDh;
+    d += mult * tB[nw];
+    return d;
+}
+
+// The per-n_wall reaction coefficients, copied once per block into shared memory
+// (dynamic indexing of kernel-parameter arrays would go through local memory).
+#define RFB_LOAD_TABLES(T, C)                                                         \
+    __shared__ T tA[8], tB[8];                                                         \
+    {                                                                                  \
+        const int t_ = threadIdx.y * BX + threadIdx.x;                                 \
+        if (t_ < 8) { tA[t_] = (C).rA[t_]; tB[t_] = (C).rB[t_]; }                      \
+        __syncthreads();                                                               \
+    }
+
+// ---------------------------------------------------------------------------------
+// Sweep: s_out = s + dt (RHS(s) [+ force]) on every unknown fluid cell. Cells that are
+// solid (or pinned electrode cells in U_mt mode) are not written: both buffers hold
+// the same fixed value there.
+// ---------------------------------------------------------------------------------
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(BX * BY)
+sweep_kernel(Lattice L, Coef<T> C, const T* __restrict__ s, T* __restrict__ s_out,
+             const float* __restrict__ force, int kchunk) {
+    RFB_LOAD_TABLES(T, C)
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= L.nx || j >= L.ny) return;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, L.nz);
+    const int nx = L.nx, nxny = L.nxny;
+    int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+    T s_prev = kb > 0 ? s[c - nxny] : T(0);
+    T s_cur = s[c];
+    T wL = C.w[c];
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const bool outlet = (k == L.nz - 1);
+        T s_next = outlet ? T(0) : s[c + nxny];
+        T wH = C.w[c + nxny];
+        const unsigned f = L.flags[c];
+        const bool upd = (f & F_FLUID) && !(C.umt && (f & F_ELEC));
+        if (upd) {
+            T sxm = (f & F_XM) ? s[c - 1] : s_cur;
+            T sxp = (f & F_XP) ? s[c + 1] : s_cur;
+            T sym = (f & F_YM) ? s[c - nx] : s_cur;
+            T syp = (f & F_YP) ? s[c + nx] : s_cur;
+            T szm = (f & F_ZM) ? s_prev : s_cur;
+            T szp = (f & F_ZP) ? s_next : s_cur;
+            T uL = C.u[c];
+            T uH = (i + 1 < nx) ? C.u[c + 1] : T(0);
+            T vL = C.v[c];
+            T vH = (j + 1 < L.ny) ? C.v[c + nx] : T(0);
+            const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+            T mult = C.m ? C.m[c] : T(1);
+            T r = cell_rhs<T>(C, tA, tB, s_cur, sxm, sxp, sym, syp, szm, szp, uL, uH, vL, vH, wL, wH,
+                              k == 0, outlet, nw, mult);
+            if (FORCE) r += T(force[c]);
+            T dt = C.dtc ? T(C.dtc[c]) : C.dt;
+            s_out[c] = s_cur + dt * r;
+        }
+        s_prev = s_cur;
+        s_cur = s_next;
+        wL = wH;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Block reduction helpers (fixed order => deterministic)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max(double x) {
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// slots 0..NRED-2 are sums, slot NRED-1 is a max
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NRED], double* out) {
+    __shared__ double sh[BX * BY / 32][NRED];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED - 1; ++q) acc[q] = warp_sum(acc[q]);
+    acc[NRED - 1] = warp_max(acc[NRED - 1]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) sh[wid][q] = acc[q];
+    }
+    __syncthreads();
+    if (tid < NRED) {
+        double r = sh[0][tid];
+        for (int w = 1; w < BX * BY / 32; ++w)
+            r = (tid == NRED - 1) ? fmax(r, sh[w][tid]) : r + sh[w][tid];
+        out[tid] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 check: RHS64 at every fluid cell and the reductions
+//   0 sum RHS^2 (unknown cells)        4 sum_outlet wH s
+//   1 sum m kappa R~(s) (fluid cells)  5 sum_outlet wH
+//   2 sum_inlet gDh (s_in - s)         6 count of non-finite RHS
+//   3 sum_inlet wL s_in                7 max |RHS|
+// FUSE: the state is s_old + delta (FP32 correction); it is written to s_new.
+// WRITE_R: RHS is stored as FP32 forcing for the next correction sweeps.
+// ---------------------------------------------------------------------------------
+template <bool FUSE, bool WRITE_R>
+__global__ void __launch_bounds__(BX * BY)
+check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
+             const float* __restrict__ delta, double* __restrict__ s_new,
+             float* __restrict__ r_out, double* __restrict__ partials, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        auto val = [&](int64_t cc) -> double {
+            return FUSE ? s[cc] + (double)delta[cc] : s[cc];
+        };
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double s_prev = kb > 0 ? val(c - nxny) : 0.0;
+        double s_cur = val(c);
+        double wL = C.w[c];
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const bool outlet = (k == L.nz - 1);
+            double s_next = outlet ? 0.0 : val(c + nxny);
+            double wH = C.w[c + nxny];
+            const unsigned f = L.flags[c];
+            if (FUSE) s_new[c] = s_cur;
+            if (f & F_FLUID) {
+                const bool pinned = C.umt && (f & F_ELEC);
+                double sxm = (f & F_XM) ? val(c - 1) : s_cur;
+                double sxp = (f & F_XP) ? val(c + 1) : s_cur;
+                double sym = (f & F_YM) ? val(c - nx) : s_cur;
+                double syp = (f & F_YP) ? val(c + nx) : s_cur;
+                double szm = (f & F_ZM) ? s_prev : s_cur;
+                double szp = (f & F_ZP) ? s_next : s_cur;
+                double uL = C.u[c];
+                double uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
+                double vL = C.v[c];
+                double vH = (j + 1 < L.ny) ? C.v[c + nx] : 0.0;
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                double mult = C.m ? C.m[c] : 1.0;
+                double r = cell_rhs<double>(C, tA, tB, s_cur, sxm, sxp, sym, syp, szm, szp, uL, uH,
+                                            vL, vH, wL, wH, k == 0, outlet, nw, mult);
+                if (!pinned) {
+                    if (isfinite(r)) {
+                        acc[0] += r * r;
+                        acc[7] = fmax(acc[7], fabs(r));
+                    } else {
+                        acc[6] += 1.0;
+                    }
+                    if (WRITE_R) r_out[c] = (float)r;
+                } else if (WRITE_R) {
+                    r_out[c] = 0.0f;
+                }
+                acc[1] += mult * (tA[nw] - tB[nw] * s_cur);
+                if (k == 0) {
+                    acc[2] += C.gDh * (C.s_in - s_cur);
+                    acc[3] += wL * C.s_in;
+                }
+                if (outlet) {
+                    acc[4] += wH * s_cur;
+                    acc[5] += wH;
+                }
+            }
+            s_prev = s_cur;
+            s_cur = s_next;
+            wL = wH;
+        }
+    }
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+}
+
+// Largest diagonal of -L over unknown fluid cells (for dt = cfl / max d), and the
+// per-cell local step dtc = cfl / d_c (rounded toward zero in FP32) when requested.
+__global__ void __launch_bounds__(BX * BY)
+diag_kernel(Lattice L, Coef<double> C, double cfl, float* __restrict__ dtc,
+            double* __restrict__ partials, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const unsigned f = L.flags[c];
+            if (!(f & F_FLUID) || (C.umt && (f & F_ELEC))) {
+                if (dtc) dtc[c] = 0.0f;
+                continue;
+            }
+            double uL = C.u[c];
+            double uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
+            double vL = C.v[c];
+            double vH = (j + 1 < L.ny) ? C.v[c + nx] : 0.0;
+            double wL = C.w[c], wH = C.w[c + nxny];
+            const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+            double mult = C.m ? C.m[c] : 1.0;
+            double d = cell_diag<double>(C, tB, f, uL, uH, vL, vH, wL, wH, k == 0, nw, mult);
+            acc[7] = fmax(acc[7], d);
+            acc[0] = (acc[0] == 0.0 || d < acc[0]) ? d : acc[0];
+            if (dtc) dtc[c] = d > 0.0 ? __double2float_rz(cfl / d) : 0.0f;
+        }
+    }
+    // slot 0 carries a min: reduce it as -max(-x) by negating around the max slot
+    __shared__ double mins[BX * BY];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    mins[tid] = acc[0] == 0.0 ? 1e300 : acc[0];
+    acc[0] = 0.0;
+    __syncthreads();
+    for (int sft = BX * BY / 2; sft > 0; sft >>= 1) {
+        if (tid < sft) mins[tid] = fmin(mins[tid], mins[tid + sft]);
+        __syncthreads();
+    }
+    const double bmin = mins[0];
+    __syncthreads();
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+    if (tid == 0) partials[bid * NRED + 0] = bmin;
+}
+
+// Sum (slots 0..6) / max (slot 7) of the per-block partials, in a fixed order.
+// min_slot0: slot 0 is reduced with min instead of a sum (diag_kernel).
+__global__ void __launch_bounds__(256)
+finalize_kernel(const double* __restrict__ partials, int64_t nblocks, double* __restrict__ out,
+                int min_slot0) {
+    __shared__ double sh[256];
+    for (int q = 0; q < NRED; ++q) {
+        const bool is_max = (q == NRED - 1);
+        const bool is_min = (q == 0 && min_slot0);
+        double a = is_min ? 1e300 : 0.0;
+        for (int64_t b = threadIdx.x; b < nblocks; b += 256) {
+            double x = partials[b * NRED + q];
+            a = is_max ? fmax(a, x) : is_min ? fmin(a, x) : a + x;
+        }
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int sft = 128; sft > 0; sft >>= 1) {
+            if (threadIdx.x < sft) {
+                double x = sh[threadIdx.x + sft];
+                sh[threadIdx.x] = is_max ? fmax(sh[threadIdx.x], x)
+                                         : is_min ? fmin(sh[threadIdx.x], x)
+                                                  : sh[threadIdx.x] + x;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = sh[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Setup kernels
+// ---------------------------------------------------------------------------------
+
+// flags from the solid mask (1 = fiber)
+__global__ void flags_kernel(const uint8_t* __restrict__ solid, uint8_t* __restrict__ flags,
+                             int nx, int ny, int nz) {
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((int64_t)nx * ny));
+        const int64_t nxny = (int64_t)nx * ny;
+        if (solid[c]) { flags[c] = 0; continue; }
+        unsigned f = F_FLUID;
+        int dom = 0, fl = 0;
+        if (i > 0) { ++dom; if (!solid[c - 1]) { f |= F_XM; ++fl; } }
+        if (i + 1 < nx) { ++dom; if (!solid[c + 1]) { f |= F_XP; ++fl; } }
+        if (j > 0) { ++dom; if (!solid[c - nx]) { f |= F_YM; ++fl; } }
+        if (j + 1 < ny) { ++dom; if (!solid[c + nx]) { f |= F_YP; ++fl; } }
+        if (k > 0) { ++dom; if (!solid[c - nxny]) { f |= F_ZM; ++fl; } }
+        if (k + 1 < nz) { ++dom; if (!solid[c + nxny]) { f |= F_ZP; ++fl; } }
+        if (dom > fl) f |= F_ELEC;
+        flags[c] = (uint8_t)f;
+    }
+}
+
+// Validate one face array against the mask and repack it cell aligned (low faces).
+// axis 0: U (nx+1, ny, nz); 1: V (nx, ny+1, nz); 2: W (nx, ny, nz+1) -> N + nxny out.
+// err[0]: non-finite; err[1]: nonzero on a wall/fiber face; err[2]: negative inlet or
+// outlet velocity.
+__global__ void repack_kernel(const double* __restrict__ in, const uint8_t* __restrict__ solid,
+                              double* __restrict__ out, int nx, int ny, int nz, int axis,
+                              unsigned long long* __restrict__ err) {
+    const int ex = nx + (axis == 0), ey = ny + (axis == 1), ez = nz + (axis == 2);
+    const int64_t M = (int64_t)ex * ey * ez;
+    const int64_t nxny = (int64_t)nx * ny;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < M;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(q % ex);
+        const int b = (int)((q / ex) % ey);
+        const int k = (int)(q / ((int64_t)ex * ey));
+        const double val = in[q];
+        if (!isfinite(val)) atomicAdd(&err[0], 1ull);
+        // the two cells sharing the face (either may be outside the domain)
+        int i0 = a, j0 = b, k0 = k, i1 = a, j1 = b, k1 = k;
+        int n_axis = axis == 0 ? nx : axis == 1 ? ny : nz;
+        int pos = axis == 0 ? a : axis == 1 ? b : k;
+        if (axis == 0) i0 = a - 1; else if (axis == 1) j0 = b - 1; else k0 = k - 1;
+        bool lo_in = pos > 0, hi_in = pos < n_axis;
+        bool lo_solid = lo_in && solid[i0 + nx * (int64_t)j0 + nxny * k0];
+        bool hi_solid = hi_in && solid[i1 + nx * (int64_t)j1 + nxny * k1];
+        bool wall = (axis != 2) && (!lo_in || !hi_in);
+        if ((wall || lo_solid || hi_solid) && val != 0.0) atomicAdd(&err[1], 1ull);
+        if (axis == 2 && (!lo_in || !hi_in) && val < 0.0) atomicAdd(&err[2], 1ull);
+        if (axis == 0) {
+            if (a < nx) out[a + nx * (int64_t)b + nxny * k] = val;
+        } else if (axis == 1) {
+            if (b < ny) out[a + nx * (int64_t)b + nxny * k] = val;
+        } else {
+            out[a + nx * (int64_t)b + nxny * k] = val;
+        }
+    }
+}
+
+// out64 = scale * in; out32 = (float) out64
+__global__ void scale_kernel(const double* __restrict__ in, double* __restrict__ out64,
+                             float* __restrict__ out32, double scale, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double x = scale * in[q];
+        out64[q] = x;
+        out32[q] = (float)x;
+    }
+}
+
+// Initial state: s_in on unknown fluid cells, 1 on pinned electrode cells (U_mt), 0 on
+// solid cells; written to both buffers.
+__global__ void init_state_kernel(const uint8_t* __restrict__ flags, double* __restrict__ a,
+                                  double* __restrict__ b, double s_in, int umt, int64_t n) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = flags[c];
+        double x = 0.0;
+        if (f & F_FLUID) x = (umt && (f & F_ELEC)) ? 1.0 : s_in;
+        a[c] = x;
+        if (b) b[c] = x;
+    }
+}
+
+// s (both buffers) from a caller array; solid cells forced to 0 (pinned U_mt cells 1).
+__global__ void set_state_kernel(const uint8_t* __restrict__ flags, const double* __restrict__ in,
+                                 double* __restrict__ a, double* __restrict__ b,
+                                 unsigned long long* __restrict__ err, int64_t n) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = flags[c];
+        double x = (f & F_FLUID) ? in[c] : 0.0;
+        if (!isfinite(x)) { atomicAdd(err, 1ull); x = 0.0; }
+        a[c] = x;
+        b[c] = x;
+    }
+}
+
+}  // namespace rfb

@@ -1,0 +1,248 @@
+"""Python binding of the C ABI in include/rfb_soc.h (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library ``librfbsoc.so`` built in-tree by
+``_build.build()``; if the library is missing this module raises instead of falling
+back to anything else. Inputs may be numpy arrays (host memory) or CUDA torch tensors
+(device memory, used in place for the copy into library-owned buffers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+RFB_OK, RFB_ERR_INVALID_ARG, RFB_ERR_CUDA, RFB_ERR_OOM = 0, 1, 2, 3
+RFB_ERR_NOT_CONVERGED, RFB_ERR_NONFINITE, RFB_ERR_STATE, RFB_ERR_UNSUPPORTED = 4, 5, 6, 7
+MEM_HOST, MEM_DEVICE = 0, 1
+PREC = {"fp64": 0, "mixed": 1}
+INLET = {"face": 0, "ghost": 1}
+DT = {"global": 0, "local": 1}
+
+
+class Kinetics(ctypes.Structure):
+    _fields_ = [("k0", c_double), ("alpha", c_double), ("n_e", c_int32), ("pad_", c_int32),
+                ("T", c_double), ("c0", c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("inlet_bc", c_int32), ("dt_mode", c_int32),
+                ("check_every", c_int32), ("cfl", c_double), ("velocity_scale", c_double),
+                ("max_sweeps", c_int64), ("reserved", c_int32 * 8)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("sweeps", c_int64), ("checks", c_int64), ("residual", c_double),
+                ("I_tot", c_double), ("F_in", c_double), ("F_out", c_double),
+                ("F_in_adv", c_double), ("mass_balance_rel", c_double), ("U", c_double),
+                ("outlet_mean", c_double), ("dt", c_double), ("tau", c_double),
+                ("time_ms", c_double), ("nonfinite", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("librfbsoc.so is not built (run __graft_entry__.build()); "
+                               "there is no fallback implementation")
+        L = ctypes.CDLL(path)
+        H = c_void_p
+        L.rfb_solve_opts_default.argtypes = [POINTER(SolveOpts)]
+        L.rfb_solve_opts_default.restype = None
+        L.rfb_status_string.argtypes = [c_int]
+        L.rfb_status_string.restype = c_char_p
+        L.rfb_soc_last_error.argtypes = [H]
+        L.rfb_soc_last_error.restype = c_char_p
+        L.rfb_soc_create.argtypes = [POINTER(c_int32), c_double, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_double, POINTER(Kinetics), c_void_p, c_int,
+                                     c_void_p, POINTER(H)]
+        L.rfb_soc_destroy.argtypes = [H]
+        L.rfb_soc_set_stream.argtypes = [H, c_void_p]
+        L.rfb_soc_solve.argtypes = [H, c_double, c_double, c_double, POINTER(SolveOpts),
+                                    POINTER(SolveResult)]
+        L.rfb_soc_step.argtypes = [H, c_double, c_double, c_int64, POINTER(SolveOpts),
+                                   POINTER(SolveResult)]
+        L.rfb_soc_current.argtypes = [H, POINTER(SolveResult)]
+        L.rfb_soc_umt.argtypes = [H, c_double, POINTER(SolveOpts), POINTER(c_double),
+                                  POINTER(SolveResult)]
+        L.rfb_soc_get_state.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_set_state.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_info.argtypes = [H, POINTER(c_int64), POINTER(c_int64)]
+        L.rfb_soc_kernel_launches.argtypes = [H]
+        L.rfb_soc_kernel_launches.restype = c_int64
+        for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
+                     "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
+                     "rfb_soc_set_state", "rfb_soc_info"):
+            getattr(L, name).restype = c_int
+        _LIB = L
+    return _LIB
+
+
+class RfbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (lib().rfb_status_string(status).decode(), msg))
+        self.status = status
+
+
+def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
+              velocity_scale=1.0, max_sweeps=0) -> SolveOpts:
+    o = SolveOpts()
+    lib().rfb_solve_opts_default(byref(o))
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.inlet_bc = INLET[inlet_bc] if isinstance(inlet_bc, str) else int(inlet_bc)
+    o.dt_mode = DT[dt_mode] if isinstance(dt_mode, str) else int(dt_mode)
+    o.check_every = int(check_every)
+    o.cfl = float(cfl)
+    o.velocity_scale = float(velocity_scale)
+    o.max_sweeps = int(max_sweeps)
+    return o
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive, kind) of a numpy array or CUDA torch tensor."""
+    if x is None:
+        return None, None, None
+    if _is_torch(x):
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            import torch
+            tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+            if x.dtype != tdt or not x.is_contiguous():
+                x = x.to(tdt).contiguous()
+            return c_void_p(x.data_ptr()), x, MEM_DEVICE
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(c_void_p), a, MEM_HOST
+
+
+class Solver:
+    """One lattice + flow field on the GPU (a ``rfb_soc_handle``)."""
+
+    def __init__(self, dims, dx, solid, U, V, W, D, k0, alpha=0.5, n_e=2, T=298.0, c0=20.0,
+                 area_mult=None, stream=None):
+        L = lib()
+        self.dims = tuple(int(d) for d in dims)
+        d = (c_int32 * 3)(*self.dims)
+        kin = Kinetics(float(k0), float(alpha), int(n_e), 0, float(T), float(c0))
+        ptrs = [_ptr(solid, np.uint8), _ptr(U, np.float64), _ptr(V, np.float64),
+                _ptr(W, np.float64), _ptr(area_mult, np.float64)]
+        kinds = {p[2] for p in ptrs if p[2] is not None}
+        if len(kinds) != 1:
+            raise ValueError("all arrays must be host (numpy) or all CUDA tensors")
+        kind = kinds.pop()
+        self._keep = [p[1] for p in ptrs]
+        h = c_void_p()
+        st = L.rfb_soc_create(d, float(dx), ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0],
+                              float(D), byref(kin), ptrs[4][0], kind, _stream_ptr(stream),
+                              byref(h))
+        self._keep = None
+        if st != RFB_OK:
+            raise RfbError(st, L.rfb_soc_last_error(None).decode())
+        self.h = h
+        n, nf = c_int64(), c_int64()
+        L.rfb_soc_info(h, byref(n), byref(nf))
+        self.n_cells, self.n_fluid = n.value, nf.value
+
+    @classmethod
+    def from_case(cls, case, area_mult=None, stream=None, device_inputs=False):
+        arrays = [case.solid, case.U, case.V, case.W]
+        if device_inputs:
+            import torch
+            arrays = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+            if area_mult is not None:
+                area_mult = torch.from_numpy(np.ascontiguousarray(area_mult)).cuda()
+        return cls(case.dims, case.h, *arrays, case.D, case.k0, case.alpha, case.n_e, case.T,
+                   case.c0, area_mult=area_mult, stream=stream)
+
+    def _check(self, st, ok=(RFB_OK,)):
+        if st not in ok:
+            raise RfbError(st, lib().rfb_soc_last_error(self.h).decode())
+        return st
+
+    def solve(self, s_in, eta, tol, allow_not_converged=False, **opts) -> dict:
+        r = SolveResult()
+        o = make_opts(**opts)
+        st = lib().rfb_soc_solve(self.h, float(s_in), float(eta), float(tol), byref(o), byref(r))
+        self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
+        out = r.as_dict()
+        out["status"] = st
+        return out
+
+    def step(self, s_in, eta, n, **opts) -> dict:
+        r = SolveResult()
+        o = make_opts(**opts)
+        self._check(lib().rfb_soc_step(self.h, float(s_in), float(eta), int(n), byref(o), byref(r)))
+        return r.as_dict()
+
+    def current(self) -> dict:
+        r = SolveResult()
+        self._check(lib().rfb_soc_current(self.h, byref(r)))
+        return r.as_dict()
+
+    def umt(self, tol, **opts):
+        r = SolveResult()
+        u = c_double()
+        o = make_opts(**opts)
+        self._check(lib().rfb_soc_umt(self.h, float(tol), byref(o), byref(u), byref(r)))
+        return u.value, r.as_dict()
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.n_cells, dtype=np.float64)
+        p, keep, kind = _ptr(out, np.float64)
+        if kind == MEM_HOST and keep is not out:
+            raise ValueError("out must be a contiguous float64 array")
+        self._check(lib().rfb_soc_get_state(self.h, p, kind))
+        return out
+
+    def set_state(self, s):
+        p, keep, kind = _ptr(s, np.float64)
+        self._check(lib().rfb_soc_set_state(self.h, p, kind))
+
+    def set_stream(self, stream):
+        self._check(lib().rfb_soc_set_stream(self.h, _stream_ptr(stream)))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().rfb_soc_kernel_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rfb_soc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(int(stream.cuda_stream))

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every symbol its header declares (no GPU
+work: only host-side entry points are called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2502_08034_gb300 import _build, rfb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(inc, fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rfb_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return rfb.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"rfb_soc_create", "rfb_soc_solve", "rfb_soc_umt", "rfb_soc_current"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_default_opts(lib):
+    for st in range(8):
+        assert lib.rfb_status_string(st)
+    o = rfb.make_opts()
+    assert o.cfl == 0.4 and o.velocity_scale == 1.0 and o.precision == 0
+    assert o.dt_mode == rfb.DT["local"]
+
+
+def test_create_rejects_bad_dims_before_touching_a_device(lib):
+    import numpy as np
+    dims = (ctypes.c_int32 * 3)(4, 4, 1)       # nz must be >= 2
+    kin = rfb.Kinetics(1e-7, 0.5, 2, 0, 298.0, 20.0)
+    a = np.zeros(64)
+    h = ctypes.c_void_p()
+    p = a.ctypes.data_as(ctypes.c_void_p)
+    st = lib.rfb_soc_create(dims, 1e-6, p, p, p, p, 4e-10, ctypes.byref(kin), None, 0, None,
+                            ctypes.byref(h))
+    assert st == rfb.RFB_ERR_INVALID_ARG
+    assert b"dims" in lib.rfb_soc_last_error(None)
+    dims = (ctypes.c_int32 * 3)(4, 4, 4)
+    kin = rfb.Kinetics(1e-7, 1.5, 2, 0, 298.0, 20.0)   # alpha out of range
+    st = lib.rfb_soc_create(dims, 1e-6, p, p, p, p, 4e-10, ctypes.byref(kin), None, 0, None,
+                            ctypes.byref(h))
+    assert st == rfb.RFB_ERR_INVALID_ARG
+    assert lib.rfb_soc_destroy(None) == 0
