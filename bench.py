@@ -1,0 +1,348 @@
+"""Benchmark: steady state-of-charge solve on one GB300 (replicas for --gpus N > 1).
+
+Step = one cold-start solve (s = s_in everywhere) to residual 1e-8 of the 256x256x512
+fiber lattice (porosity 0.85, d ~ U[6,10] cells, potential flow at 0.5 cm/s,
+eta = -0.05 V, s_in = 0.3) in mixed precision: FP32 correction sweeps with FP64 defect
+checks. value = lattice cells x sweeps / step time (GCell-updates/s), whole job.
+
+Prints one JSON line. ``--impl reference`` times the CPU oracle instead (explicit FP64
+CSR sweeps of the same workload on a bounded sample of it).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCell-updates/s + time-to-steady (res 1e-8) of SOC sweep, % HBM peak, vs FP64"
+UNIT = "GCell-updates/s"
+# algorithmic bytes per cell of one FP32 correction sweep: delta in + out (8), FP32
+# forcing r (4), three FP32 face velocities (12), one mask bit (1/8)
+SWEEP_BYTES_PER_CELL = 4 + 4 + 4 + 12 + 0.125
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dims", default="256,256,512")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_case(dims, device):
+    from paper_2502_08034_gb300 import synth
+    return synth.large_mixed_case(dims=dims, flow_device=device)
+
+
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(n_cells):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", "soc_kernels.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    p = os.path.join(ROOT, "profiles", "sweep_fp32_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("source_sha") == digest and "dram_bytes_per_cell" in parts:
+            return float(parts["dram_bytes_per_cell"]) * n_cells
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(case, n_planes=16, sweeps=40, repeats=1):
+    """Time the CPU oracle's explicit FP64 sweeps (Algorithm 7 style, scipy CSR matvec,
+    one core) on the first ``n_planes`` z-planes of the workload."""
+    import numpy as np
+
+    from oracle import soc
+    nz = n_planes
+    p = soc.Problem(np.ascontiguousarray(case.solid[:nz]), case.U[:nz], case.V[:nz],
+                    case.W[:nz + 1], case.h, case.D, case.s_in, k0=case.k0, eta=case.eta)
+    op = soc.assemble(p)
+    s0 = soc.initial_state(op, case.s_in)
+    n = case.dims[0] * case.dims[1] * nz
+    best = float("inf")
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        soc.explicit_iterate(op, 0.4, 0.0, s0=s0, max_steps=sweeps, check_every=sweeps + 1,
+                             local_dt=True)
+        best = min(best, time.perf_counter() - t0)
+    return n * sweeps / best / 1e9, best, n, sweeps
+
+
+def run_reference(args, dims):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    t0 = time.time()
+    case = make_case(dims, "cuda" if _cuda() else "cpu")
+    setup_s = time.time() - t0
+    import numpy as np  # noqa: F401
+    for _ in range(args.warmup):
+        oracle_sample(case, sweeps=5)
+    times, rates = [], []
+    n = sweeps = 0
+    for _ in range(args.steps):
+        rate, sec, n, sweeps = oracle_sample(case, sweeps=20)
+        times.append(sec)
+        rates.append(rate)
+    total = sum(times)
+    value = n * sweeps * len(times) / total / 1e9
+    sample = ("explicit FP64 CSR sweeps (scipy, 1 thread) of the first 16 z-planes "
+              "(%dx%dx16 = %d cells) of the workload, %d sweeps per step" %
+              (dims[0], dims[1], n, sweeps))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "fiber%dx%dx%d_mixed" % dims, "sample": "16 z-planes"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "setup_s": setup_s}
+    print(json.dumps(out), flush=True)
+
+
+def _cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def main():
+    args = parse()
+    dims = tuple(int(x) for x in args.dims.split(","))
+    if args.impl == "reference":
+        run_reference(args, dims)
+        return
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2502_08034_gb300 import _build, rfb
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    t0 = time.time()
+    case = make_case(dims, "cuda:%d" % local)
+    setup_case_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    sv = rfb.Solver.from_case(case, device_inputs=True, stream=stream)
+    torch.cuda.synchronize()
+    create_s = time.time() - t0
+    N = sv.n_cells
+
+    def step(precision="mixed", tol=args.tol):
+        sv.reset_state()
+        return sv.solve(case.s_in, case.eta, tol, precision=precision)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = sv.kernel_launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    results = []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = sv.kernel_launches - launches0
+    t_local = torch.tensor([elapsed_ms], device="cuda")
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t_local.item())
+    sweeps = sum(r["sweeps"] for r in results)
+    value = world * N * sweeps / (elapsed_ms / 1e3) / 1e9
+    sweep_ms = sum(r["sweep_ms"] for r in results)
+    peak, peak_kind = peak_hbm()
+    achieved = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
+    traffic = kernel_traffic(N)
+    last = results[-1]
+
+    extras = {}
+    e2e = None
+    cpu = None
+    if not args.no_extras:
+        # FP64 path on the same workload and tolerance ("vs FP64")
+        r64 = step("fp64")
+        # accuracy of the mixed state against the FP64 one (both at the same tol)
+        s64 = sv.get_state()
+        r32 = step("mixed")
+        s32 = sv.get_state()
+        fluid = case.solid.ravel() == 0
+        extras["fp64"] = {"time_to_steady_ms": r64["time_ms"], "sweeps": r64["sweeps"],
+                          "GCell_updates_per_s": N * r64["sweeps"] / r64["time_ms"] / 1e6,
+                          "sweep_kernel_GCell_per_s": N * r64["sweeps"] / r64["sweep_ms"] / 1e6}
+        extras["mixed_vs_fp64_speedup"] = r64["time_ms"] / r32["time_ms"]
+        extras["mixed_minus_fp64_maxabs_s"] = float(np.abs(s32[fluid] - s64[fluid]).max())
+        u, ru = sv.umt(args.tol, precision="mixed")
+        extras["U_mt"] = u
+        extras["U_mt_time_ms"] = ru["time_ms"]
+        extras["U_mt_sweeps"] = ru["sweeps"]
+        # end to end through the C ABI with host buffers: create from host arrays, solve,
+        # read the state back to host memory
+        h2d = case.solid.nbytes + case.U.nbytes + case.V.nbytes + case.W.nbytes
+        d2h = N * 8
+        host_s = np.empty(N)
+        e2e_t, e2e_sw = 0.0, 0
+        for _ in range(max(1, min(args.steps, 2))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with rfb.Solver.from_case(case) as sh:
+                rr = sh.solve(case.s_in, case.eta, args.tol, precision="mixed")
+                sh.get_state(host_s)
+            e2e_t += time.perf_counter() - t0
+            e2e_sw += rr["sweeps"]
+        e2e = {"value": world * N * e2e_sw / e2e_t / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h + 8 * 16)}
+        if rank == 0 and world == 1:
+            rate, sec, n_s, sw = oracle_sample(case, sweeps=40)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "explicit FP64 CSR sweeps (scipy, 1 thread) on the first 16 "
+                             "z-planes (%d cells) of the workload, %d sweeps, %.1f s" %
+                             (n_s, sw, sec)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+               "data": "synthetic",
+               "config": {"workload": "fiber%dx%dx%d_mixed" % dims, "dims": list(dims),
+                          "porosity": round(case.porosity, 4), "fiber_d": "U[6,10] cells",
+                          "u_mean_m_s": case.u_mean, "eta_V": case.eta, "s_in": case.s_in,
+                          "tol": args.tol, "precision": "mixed", "dt_mode": "local",
+                          "parallelism": "replicas" if world > 1 else "1 GPU",
+                          "l2": "inputs larger than L2 (%.0f MB of fields)" %
+                                (N * 28 / 1e6)},
+               "time_to_steady_ms": elapsed_ms / args.steps,
+               "sweeps_per_step": sweeps / args.steps,
+               "residual": last["residual"], "I_tot_A": last["I_tot"], "U": last["U"],
+               "mass_balance_rel": last["mass_balance_rel"],
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                            "kernel": "sweep_kernel<float, FORCE> (FP32 correction sweep)",
+                            "bytes_per_cell": SWEEP_BYTES_PER_CELL,
+                            "peak_kind": peak_kind},
+               "sweep_kernel_ms": sweep_ms / sweeps,
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": launches,
+               "setup_s": {"case": setup_case_s, "create": create_s}}
+        out.update(extras)
+        print(json.dumps(out), flush=True)
+    sv.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

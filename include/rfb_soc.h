@@ -80,7 +80,7 @@ typedef struct rfb_kinetics {
 typedef struct rfb_solve_opts {
     int32_t precision;      /* rfb_precision (default RFB_PREC_FP64) */
     int32_t inlet_bc;       /* rfb_inlet_bc (default RFB_INLET_FACE) */
-    int32_t dt_mode;        /* rfb_dt_mode (default RFB_DT_GLOBAL) */
+    int32_t dt_mode;        /* rfb_dt_mode (default RFB_DT_LOCAL) */
     int32_t check_every;    /* sweeps between FP64 residual checks (0 = automatic) */
     double cfl;             /* C_CFL in (0, 1] (default 0.4) */
     double velocity_scale;  /* beta >= 0: every face velocity is multiplied by it (1) */
@@ -103,6 +103,9 @@ typedef struct rfb_solve_result {
     double tau;              /* V_fluid / Q [s] */
     double time_ms;          /* wall time of the call */
     int64_t nonfinite;       /* non-finite RHS values seen at the last check */
+    double sweep_ms;         /* device time of the sweep kernels (CUDA events on the
+                                handle's stream around each batch of sweeps) */
+    double check_ms;         /* device time of the FP64 checks (kernel + reduction) */
 } rfb_solve_result;
 
 typedef struct rfb_soc_handle rfb_soc_handle;
@@ -186,6 +189,9 @@ rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res);
  */
 rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts,
                        double* umt, rfb_solve_result* res);
+
+/* Forget the current state: the next solve/step starts from s = s_in (cold start). */
+rfb_status rfb_soc_reset_state(rfb_soc_handle* h);
 
 /* Copy the FP64 state (N doubles, solid cells 0) out to host or device memory. */
 rfb_status rfb_soc_get_state(rfb_soc_handle* h, double* s, rfb_mem_kind kind);

@@ -12,10 +12,14 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-LIB = os.path.join(HERE, "librfbsoc.so")
-SOURCES = [os.path.join(HERE, "csrc", "rfb_soc.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "soc_kernels.cuh"),
-                  os.path.join(ROOT, "include", "rfb_soc.h")]
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "librfbsoc.so")            # the solver (C ABI of include/rfb_soc.h)
+SYNTH_LIB = os.path.join(HERE, "librfbsynth.so")    # potential-flow input generator
+TARGETS = {
+    LIB: ([os.path.join(CSRC, "rfb_soc.cu")],
+          [os.path.join(CSRC, "soc_kernels.cuh"), os.path.join(ROOT, "include", "rfb_soc.h")]),
+    SYNTH_LIB: ([os.path.join(CSRC, "synth_flow.cu")], []),
+}
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -34,31 +38,44 @@ def cuda_lib_dir() -> str:
     return os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
 
 
-def command(out: str = LIB, extra=()):
+def command(out: str = LIB, extra=(), target: str = LIB):
+    sources = TARGETS[target][0]
     return [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
             "-cudart", "shared", "-I", os.path.join(ROOT, "include"),
-            "-Xlinker", "-rpath," + cuda_lib_dir(), *extra, "-o", out, *SOURCES]
+            "-Xlinker", "-rpath," + cuda_lib_dir(), *extra, "-o", out, *sources]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(target: str) -> bool:
+    if not os.path.exists(target):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in DEPS)
+    t = os.path.getmtime(target)
+    srcs, deps = TARGETS[target]
+    return all(os.path.getmtime(d) <= t for d in srcs + deps)
+
+
+def _build_one(target: str, force: bool, verbose: bool):
+    if not force and up_to_date(target):
+        return None
+    tmp = target + ".tmp"
+    cmd = command(tmp, target=target)
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    return target, tmp, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                         text=True)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    cmd = command()
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    tmp = LIB + ".tmp"
-    cmd[-1 - len(SOURCES)] = tmp
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
+    """Compile both libraries (in parallel); returns the solver library path."""
+    jobs = [j for j in (_build_one(t, force, verbose) for t in TARGETS) if j]
+    errors = []
+    for target, tmp, proc in jobs:
+        out, err = proc.communicate()
+        if proc.returncode != 0:
+            errors.append("nvcc failed for %s:\n%s%s" % (os.path.basename(target), out, err))
+        else:
+            os.replace(tmp, target)
+    if errors:
+        raise RuntimeError("\n".join(errors))
     return LIB
 
 

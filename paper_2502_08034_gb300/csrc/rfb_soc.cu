@@ -72,6 +72,7 @@ struct rfb_soc_handle {
     int kchunk = 8;
     dim3 grid, block;
     int64_t nblocks = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -346,6 +347,7 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     rfb_solve_result r{};
     rfb_status st = RFB_OK;
     int64_t done = 0;
+    double sweep_ms = 0.0, check_ms = 0.0;
     const int64_t limit = fixed_sweeps >= 0 ? fixed_sweeps : o.max_sweeps;
     // first check: residual of the starting state (mixed: also the FP32 forcing)
     check(h, op, umt, false, mixed);
@@ -359,18 +361,25 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
             break;
         }
         const int64_t n = std::min(every, limit - done);
-        if (mixed) {
-            sweeps32(h, op, n);
-            check(h, op, umt, true, true);
-        } else {
-            sweeps64(h, op, umt, n);
-            check(h, op, umt, false, false);
-        }
+        CK(h, cudaEventRecord(h->ev[0], h->stream));
+        if (mixed) sweeps32(h, op, n);
+        else sweeps64(h, op, umt, n);
+        CK(h, cudaEventRecord(h->ev[1], h->stream));
+        check(h, op, umt, mixed, mixed);
+        CK(h, cudaEventRecord(h->ev[2], h->stream));   // check() synchronised the stream
+        CK(h, cudaEventSynchronize(h->ev[2]));
+        float ms_s = 0.f, ms_c = 0.f;
+        CK(h, cudaEventElapsedTime(&ms_s, h->ev[0], h->ev[1]));
+        CK(h, cudaEventElapsedTime(&ms_c, h->ev[1], h->ev[2]));
+        sweep_ms += ms_s;
+        check_ms += ms_c;
         done += n;
         ++r.checks;
         fill_result(h, op, &r, n_unknown);
     }
     r.sweeps = done;
+    r.sweep_ms = sweep_ms;
+    r.check_ms = check_ms;
     r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                     .count();
     if (res) *res = r;
@@ -396,6 +405,8 @@ void free_all(rfb_soc_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -500,6 +511,7 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         h->grid = dim3(gx, gy, (nz + kc - 1) / kc);
         h->nblocks = (int64_t)h->grid.x * h->grid.y * h->grid.z;
         dalloc(h, &h->d_partials, (size_t)h->nblocks * NRED);
+        for (cudaEvent_t& e : h->ev) CK(h, cudaEventCreate(&e));
 
         // staging: the inputs on the device (copied when they are host arrays)
         uint8_t* d_mask = nullptr;
@@ -683,6 +695,14 @@ rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts
     } catch (Fail f) {
         return f.st;
     }
+}
+
+rfb_status rfb_soc_reset_state(rfb_soc_handle* h) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    h->have_state = false;
+    h->op.valid = false;
+    return RFB_OK;
 }
 
 rfb_status rfb_soc_get_state(rfb_soc_handle* h, double* s, rfb_mem_kind kind) {

@@ -40,7 +40,8 @@ class SolveResult(ctypes.Structure):
                 ("I_tot", c_double), ("F_in", c_double), ("F_out", c_double),
                 ("F_in_adv", c_double), ("mass_balance_rel", c_double), ("U", c_double),
                 ("outlet_mean", c_double), ("dt", c_double), ("tau", c_double),
-                ("time_ms", c_double), ("nonfinite", c_int64)]
+                ("time_ms", c_double), ("nonfinite", c_int64), ("sweep_ms", c_double),
+                ("check_ms", c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -79,12 +80,13 @@ def lib():
                                   POINTER(SolveResult)]
         L.rfb_soc_get_state.argtypes = [H, c_void_p, c_int]
         L.rfb_soc_set_state.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_reset_state.argtypes = [H]
         L.rfb_soc_info.argtypes = [H, POINTER(c_int64), POINTER(c_int64)]
         L.rfb_soc_kernel_launches.argtypes = [H]
         L.rfb_soc_kernel_launches.restype = c_int64
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
-                     "rfb_soc_set_state", "rfb_soc_info"):
+                     "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -214,6 +216,9 @@ class Solver:
     def set_state(self, s):
         p, keep, kind = _ptr(s, np.float64)
         self._check(lib().rfb_soc_set_state(self.h, p, kind))
+
+    def reset_state(self):
+        self._check(lib().rfb_soc_reset_state(self.h))
 
     def set_stream(self, stream):
         self._check(lib().rfb_soc_set_stream(self.h, _stream_ptr(stream)))

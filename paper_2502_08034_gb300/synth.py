@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -157,7 +158,11 @@ def potential_flow(solid: np.ndarray, h: float, u_mean: float, tol: float = 1e-1
     """Discrete potential flow on the fluid cells of ``solid``.
 
     Returns (U, V, W, info) as float64 numpy arrays in the face layouts of this module;
-    info holds the CG iteration count and the achieved max |div u| / u_mean."""
+    info holds the CG iteration count and the achieved max |div u| / u_mean.
+    On a CUDA device the native fixture solver (librfbsynth.so) runs; on the CPU a torch
+    CG of the same equations."""
+    if str(device).startswith("cuda"):
+        return _potential_flow_native(solid, h, u_mean, tol, max_iter, device)
     import torch
 
     dev = torch.device(device)
@@ -246,6 +251,38 @@ def potential_flow(solid: np.ndarray, h: float, u_mean: float, tol: float = 1e-1
     info = {"cg_iters": it, "max_div_rel": float(div.abs().max()) / u_mean,
             "superficial_q": float(W[0].sum()) / (nx * ny)}
     return U.cpu().numpy(), V.cpu().numpy(), W.cpu().numpy(), info
+
+
+def _potential_flow_native(solid, h, u_mean, tol, max_iter, device):
+    import ctypes
+
+    import torch
+
+    from . import _build
+
+    if not os.path.exists(_build.SYNTH_LIB):
+        raise RuntimeError("librfbsynth.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.SYNTH_LIB)
+    f = lib.rfb_synth_potential_flow
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [ctypes.c_int] * 2 + \
+        [ctypes.c_void_p] * 5 + [ctypes.c_void_p]
+    nz, ny, nx = solid.shape
+    dev = torch.device(device)
+    d_solid = torch.from_numpy(np.ascontiguousarray(solid, dtype=np.uint8)).to(dev)
+    U = torch.empty((nz, ny, nx + 1), dtype=torch.float64, device=dev)
+    V = torch.empty((nz, ny + 1, nx), dtype=torch.float64, device=dev)
+    W = torch.empty((nz + 1, ny, nx), dtype=torch.float64, device=dev)
+    info = (ctypes.c_double * 4)()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    rc = f(nx, ny, nz, h, u_mean, tol, max_iter, 200, d_solid.data_ptr(), U.data_ptr(),
+           V.data_ptr(), W.data_ptr(), ctypes.cast(info, ctypes.c_void_p), stream)
+    torch.cuda.synchronize(dev)
+    if rc not in (0, 3):
+        raise RuntimeError("native potential-flow solver failed (code %d)" % rc)
+    out = {"cg_iters": int(info[0]), "max_div_rel": float(info[1]),
+           "true_residual_rel": float(info[2]), "superficial_q": float(info[3])}
+    return U.cpu().numpy(), V.cpu().numpy(), W.cpu().numpy(), out
 
 
 # --------------------------------------------------------------------------------------
