@@ -181,6 +181,26 @@ rfb_status rfb_soc_step(rfb_soc_handle* h, double s_in, double eta, int64_t n_sw
 rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res);
 
 /*
+ * Same outputs as rfb_soc_current, computed by the same FP64 kernel and fixed-order
+ * reduction, but without touching any device memory that needs allocating: the
+ * per-block partial sums go to a static device array of 65,600 bytes (8192 blocks x 8
+ * sums + 8 totals) that every GPU loading this library holds until the process exits.
+ * The paper has no counterpart; this exists for callers that cannot allocate at the
+ * moment they need the outputs, e.g. a runtime whose caching allocator owns the
+ * device's memory, or a monitor on a latency-critical path that must not pay for the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *   res   host struct, filled like rfb_soc_current (sweeps = 0, checks = 1)
+ * Errors: RFB_ERR_STATE without a state; RFB_ERR_INVALID_ARG if the lattice needs more
+ * than 8192 reduction blocks (about nx*ny > 2,000,000; use rfb_soc_current then).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture begins.
+ * All calls in the process share the one array and its contents stay behind after a
+ * call; calls whose work overlaps on the GPU (other streams, other handles, other host
+ * threads) race on it and must be serialised by the caller.
+ */
+rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_result* res);
+
+/*
  * Mass-transport utilisation U_mt (Eq. umt-def): the steady state of advection and
  * diffusion with s = 0 at the inlet and every fluid cell that touches a fiber held at 1
  * (Eqs. np-fast-interior/np-fast-boundary, Algorithm 7), then sum_out W s / sum_out W.

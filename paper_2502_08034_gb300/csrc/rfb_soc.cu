@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -191,8 +192,8 @@ void prepare(rfb_soc_handle* h, OpPoint& op) {
 }
 
 void fill_result(const rfb_soc_handle* h, const OpPoint& op, rfb_solve_result* r,
-                 int64_t n_unknown) {
-    const double* v = h->h_red;
+                 int64_t n_unknown, const double* sums = nullptr) {
+    const double* v = sums ? sums : h->h_red;
     const double h3 = h->h * h->h * h->h;
     const double scale = h->kin.n_e * FARADAY * h->kin.c0 * h3;
     // Q = beta * sum_in W h^2 ; tau = V_f / Q = N_f h / (beta sum_in W)
@@ -762,3 +763,93 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// =====================================================================================
+// Allocation-free evaluation of the outputs
+//
+// rfb_soc_current needs scratch for its per-block partial sums; it uses a buffer that
+// rfb_soc_create allocated. Some callers cannot allocate device memory at the moment
+// they want the outputs: a runtime whose caching allocator already owns the device's
+// memory budget, or a monitor on a latency-critical path that must not pay for the
+// implicit device synchronisation of cudaMalloc/cudaFree. rfb_soc_current_noalloc serves
+// them: the same FP64 check kernel and fixed-order reduction, but the scratch is the
+// file-scope array below, present on every device that loads this library until the
+// process exits.
+// =====================================================================================
+namespace {
+
+// 8192 blocks x 8 partial sums, then the 8 final sums: 8200 doubles = 65,600 bytes.
+constexpr int64_t NOALLOC_MAX_BLOCKS = 8192;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * NRED + NRED];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[256] = {};   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch on h's device, looked up once per device with that
+// device current (h's device is made current by guard()). In host code the symbol's
+// name is only a host-side stand-in, so kernels must be given this address.
+rfb_status noalloc_scratch(rfb_soc_handle* h, double** out) {
+    if (h->device < 0 || h->device >= 256) {
+        set_err(h, "device ordinal %d out of range", h->device);
+        return RFB_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[h->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_err(h, "cudaGetSymbolAddress(g_noalloc_scratch) failed: %s",
+                    cudaGetErrorString(e));
+            return RFB_ERR_CUDA;
+        }
+        g_noalloc_addr[h->device] = (double*)p;
+    }
+    *out = g_noalloc_addr[h->device];
+    return RFB_OK;
+}
+
+}  // namespace
+
+extern "C" rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (!res) { set_err(h, "res is NULL"); return RFB_ERR_INVALID_ARG; }
+    if (!h->have_state || !h->op.valid) {
+        set_err(h, "no state / operating point: call rfb_soc_solve or rfb_soc_step first");
+        return RFB_ERR_STATE;
+    }
+    if (h->nblocks > NOALLOC_MAX_BLOCKS) {
+        set_err(h, "lattice needs %lld reduction blocks; the static scratch of "
+                "rfb_soc_current_noalloc holds %lld (use rfb_soc_current)",
+                (long long)h->nblocks, (long long)NOALLOC_MAX_BLOCKS);
+        return RFB_ERR_INVALID_ARG;
+    }
+    double* scratch = nullptr;
+    rfb_status st = noalloc_scratch(h, &scratch);
+    if (st) return st;
+    try {
+        // Every partial slot read by finalize_kernel is written by check_kernel in this
+        // call, and finalize_kernel writes every final slot, so nothing left over from an
+        // earlier call is read and nothing has to be cleared first.
+        const OpPoint op = h->op;
+        Coef<double> C = make_coef<double>(h, op, false, false);
+        double* partials = scratch;
+        double* sums = scratch + NOALLOC_MAX_BLOCKS * NRED;
+        check_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), C, h->d_s[h->s_cur], nullptr, nullptr, nullptr, partials, h->kchunk);
+        LAUNCHED(h);
+        finalize_kernel<<<1, 256, 0, h->stream>>>(partials, h->nblocks, sums, 0);
+        LAUNCHED(h);
+        double host_sums[NRED];
+        CK(h, cudaMemcpyAsync(host_sums, sums, sizeof host_sums, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        rfb_solve_result r{};
+        r.checks = 1;
+        fill_result(h, op, &r, h->n_fluid, host_sums);
+        *res = r;
+        return r.nonfinite ? RFB_ERR_NONFINITE : RFB_OK;
+    } catch (Fail f) {
+        return f.st;
+    }
+}

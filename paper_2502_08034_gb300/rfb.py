@@ -76,6 +76,7 @@ def lib():
         L.rfb_soc_step.argtypes = [H, c_double, c_double, c_int64, POINTER(SolveOpts),
                                    POINTER(SolveResult)]
         L.rfb_soc_current.argtypes = [H, POINTER(SolveResult)]
+        L.rfb_soc_current_noalloc.argtypes = [H, POINTER(SolveResult)]
         L.rfb_soc_umt.argtypes = [H, c_double, POINTER(SolveOpts), POINTER(c_double),
                                   POINTER(SolveResult)]
         L.rfb_soc_get_state.argtypes = [H, c_void_p, c_int]
@@ -86,7 +87,8 @@ def lib():
         L.rfb_soc_kernel_launches.restype = c_int64
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
-                     "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state"):
+                     "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
+                     "rfb_soc_current_noalloc"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -195,6 +197,13 @@ class Solver:
     def current(self) -> dict:
         r = SolveResult()
         self._check(lib().rfb_soc_current(self.h, byref(r)))
+        return r.as_dict()
+
+    def current_noalloc(self) -> dict:
+        """rfb_soc_current_noalloc: the outputs without any device allocation (static
+        scratch shared by every caller in the process; serialise overlapping calls)."""
+        r = SolveResult()
+        self._check(lib().rfb_soc_current_noalloc(self.h, byref(r)))
         return r.as_dict()
 
     def umt(self, tol, **opts):
