@@ -73,6 +73,8 @@ struct rfb_soc_handle {
     int kchunk = 8;
     dim3 grid, block;
     int64_t nblocks = 0;
+    int vkchunk = 8;          // vectorised FP32 sweep (nx % 4 == 0)
+    dim3 vgrid, vblock;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -265,12 +267,24 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n) {
     const size_t bytes = (size_t)h->N * sizeof(float);
     CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
     CK(h, cudaMemsetAsync(h->d_delta[1], 0, bytes, h->stream));
-    Coef<float> C = make_coef<float>(h, op, true, op.dt_mode == RFB_DT_LOCAL);
+    const bool local = op.dt_mode == RFB_DT_LOCAL;
+    const bool vec = (h->nx % 4) == 0;
+    // the vectorised kernel computes the local step on the fly; the scalar one reads dtc
+    Coef<float> C = make_coef<float>(h, op, true, local && !vec);
     Lattice L = lattice(h);
     int cur = 0;
     for (int64_t q = 0; q < n; ++q) {
-        sweep_kernel<float, true><<<h->grid, h->block, 0, h->stream>>>(
-            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->kchunk);
+        if (vec && local)
+            sweep32v_kernel<true><<<h->vgrid, h->vblock, 0, h->stream>>>(
+                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl,
+                h->vkchunk);
+        else if (vec)
+            sweep32v_kernel<false><<<h->vgrid, h->vblock, 0, h->stream>>>(
+                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl,
+                h->vkchunk);
+        else
+            sweep_kernel<float, true><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->kchunk);
         LAUNCHED(h);
         cur ^= 1;
     }
@@ -511,6 +525,14 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         h->kchunk = kc;
         h->grid = dim3(gx, gy, (nz + kc - 1) / kc);
         h->nblocks = (int64_t)h->grid.x * h->grid.y * h->grid.z;
+        {
+            h->vblock = dim3(VBX, VBY, 1);
+            const int vx = (nx / 4 + VBX - 1) / VBX, vy = (ny + VBY - 1) / VBY;
+            int vk = nz;
+            while (vk > 4 && (int64_t)vx * vy * ((nz + vk - 1) / vk) < 152 * 16) vk = (vk + 1) / 2;
+            h->vkchunk = vk;
+            h->vgrid = dim3(vx, vy, (nz + vk - 1) / vk);
+        }
         dalloc(h, &h->d_partials, (size_t)h->nblocks * NRED);
         for (cudaEvent_t& e : h->ev) CK(h, cudaEventCreate(&e));
 

@@ -171,6 +171,123 @@ sweep_kernel(Lattice L, Coef<T> C, const T* __restrict__ s, T* __restrict__ s_ou
 }
 
 // ---------------------------------------------------------------------------------
+// FP32 correction sweep, vectorised: delta_out = delta + dt (L delta + r) with the
+// homogeneous operator (no inlet value, no intercept), 4 consecutive x cells per thread
+// (128-bit loads/stores, nx % 4 == 0). Every load of a plane is issued before any
+// arithmetic (addresses are clamped at the domain edges instead of predicated on the
+// flags), and the local step dt_c = cfl / d_c is computed on the fly from the FP32
+// face velocities. Threads march a chunk of z planes keeping delta at k-1, k, k+1 and
+// the shared z faces in registers.
+// ---------------------------------------------------------------------------------
+constexpr int VBX = 32;   // threads along x (128 cells)
+constexpr int VBY = 8;
+
+struct __align__(16) F4 { float x, y, z, w; };
+__device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float el(const float4& v, int e) {
+    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+}
+
+template <bool LOCAL_DT>
+__global__ void __launch_bounds__(VBX * VBY)
+sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
+                float* __restrict__ s_out, const float* __restrict__ force, float cfl,
+                int kchunk) {
+    __shared__ float tB[8];
+    {
+        const int t_ = threadIdx.y * VBX + threadIdx.x;
+        if (t_ < 8) tB[t_] = C.rB[t_];
+        __syncthreads();
+    }
+    const int i0 = 4 * (blockIdx.x * VBX + threadIdx.x);
+    const int j = blockIdx.y * VBY + threadIdx.y;
+    if (i0 >= L.nx || j >= L.ny) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, nz);
+    const bool has_xm = i0 > 0, has_xp = i0 + 4 < nx;
+    const bool has_ym = j > 0, has_yp = j + 1 < ny;
+    const int64_t off_xm = has_xm ? -1 : 0, off_xp = has_xp ? 4 : 3;
+    const int64_t off_ym = has_ym ? -nx : 0, off_yp = has_yp ? nx : 0;
+    int64_t c = (int64_t)i0 + (int64_t)nx * j + (int64_t)nxny * kb;
+    float4 d_prev = kb > 0 ? ldg4(s + c - nxny) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 d_cur = ldg4(s + c);
+    float4 wL = ldg4(C.w + c);
+    const float Dh = C.Dh, gDh = C.gDh;
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const bool outlet = (k == nz - 1);
+        const bool inlet = (k == 0);
+        // ---- all loads of this plane
+        const float4 d_next = outlet ? d_cur : ldg4(s + c + nxny);
+        const float4 wH = ldg4(C.w + c + nxny);
+        const float4 d_ym = ldg4(s + c + off_ym);
+        const float4 d_yp = ldg4(s + c + off_yp);
+        const float d_xm = __ldg(s + c + off_xm);
+        const float d_xp = __ldg(s + c + off_xp);
+        const float4 u4 = ldg4(C.u + c);
+        const float u_nx = has_xp ? __ldg(C.u + c + 4) : 0.f;
+        const float4 v4 = ldg4(C.v + c);
+        const float4 vH4 = has_yp ? ldg4(C.v + c + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 r4 = ldg4(force + c);
+        const uint32_t f4 = __ldg(reinterpret_cast<const unsigned int*>(L.flags + c));
+        const float4 m4 = C.m ? ldg4(C.m + c) : make_float4(1.f, 1.f, 1.f, 1.f);
+        // ---- arithmetic
+        float out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned f = (f4 >> (8 * e)) & 0xffu;
+            const float sc = el(d_cur, e);
+            const bool upd = (f & F_FLUID) && !(C.umt && (f & F_ELEC));
+            const float xm_raw = e == 0 ? d_xm : el(d_cur, e - 1);
+            const float xp_raw = e == 3 ? d_xp : el(d_cur, e + 1);
+            const float sxm = (f & F_XM) ? xm_raw : sc;
+            const float sxp = (f & F_XP) ? xp_raw : sc;
+            const float sym = (f & F_YM) ? el(d_ym, e) : sc;
+            const float syp = (f & F_YP) ? el(d_yp, e) : sc;
+            const float szm = (f & F_ZM) ? el(d_prev, e) : sc;
+            const float szp = (f & F_ZP) ? el(d_next, e) : sc;
+            const float uL = el(u4, e);
+            const float uH = e == 3 ? u_nx : el(u4, e + 1);
+            const float vL = el(v4, e), vH = el(vH4, e);
+            const float wl = el(wL, e), wh = el(wH, e);
+            // upwind advection (the inlet carries the correction's zero boundary value)
+            float adv = uL * (uL > 0.f ? sxm : sc);
+            adv -= uH * (uH > 0.f ? sc : sxp);
+            adv += vL * (vL > 0.f ? sym : sc);
+            adv -= vH * (vH > 0.f ? sc : syp);
+            adv += wl * (wl > 0.f ? (inlet ? 0.f : szm) : sc);
+            adv -= wh * ((wh > 0.f || outlet) ? sc : szp);
+            // diffusion between fluid cells; inlet face term with zero boundary value
+            const float zmd = inlet ? sc : szm;
+            const float nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
+            float dif = Dh * nsum - (6.f * Dh) * sc;
+            if (inlet) dif -= gDh * sc;
+            const int ii = i0 + e;
+            const int nw = n_wall_of(f, ii, j, k, nx, ny, nz);
+            const float mult = el(m4, e);
+            const float rb = mult * tB[nw];
+            const float rhs = (adv + dif) - rb * sc + el(r4, e);
+            float dt;
+            if (LOCAL_DT) {
+                float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
+                          fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
+                d += Dh * (float)__popc(f & F_NBRS) + (inlet ? gDh : 0.f) + rb;
+                dt = d > 0.f ? __fdividef(cfl, d) : 0.f;
+            } else {
+                dt = C.dt;
+            }
+            out[e] = upd ? sc + dt * rhs : sc;
+        }
+        *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
+        d_prev = d_cur;
+        d_cur = d_next;
+        wL = wH;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Block reduction helpers (fixed order => deterministic)
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double x) {

@@ -115,6 +115,20 @@ def test_mixed_precision_parity_small_large_recipe():
     assert r["mass_balance_rel"] < 1e-6
 
 
+@pytest.mark.parametrize("dims,dt_mode", [((37, 21, 19), "local"), ((36, 20, 24), "global"),
+                                          ((36, 20, 24), "local")])
+def test_mixed_precision_parity_vector_and_scalar_kernels(dims, dt_mode):
+    """nx % 4 != 0 runs the scalar FP32 sweep, nx % 4 == 0 the 4-cells-per-thread one."""
+    case = fiber_case(dims, diameter=4.0)
+    p, op = _oracle(case)
+    s_ref = soc.steady_state(op)
+    with _solver(case) as sv:
+        r = sv.solve(case.s_in, case.eta, 1e-11, precision="mixed", dt_mode=dt_mode)
+        s = sv.get_state()
+    assert r["residual"] <= 1e-11
+    assert np.abs(s - s_ref).max() < 1e-7
+
+
 def test_umt_parity():
     case = fiber_case((16, 16, 32))
     p, _ = _oracle(case)
