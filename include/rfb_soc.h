@@ -210,6 +210,55 @@ rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_result* res);
 rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts,
                        double* umt, rfb_solve_result* res);
 
+/*
+ * Iterative upsampling (Sec. III.A, "iterative upsampling"; the paper solves coarse to
+ * steady state and initialises the refined problem from it by coarse-to-fine
+ * interpolation). Sets fine's state to the 2x prolongation of coarse's state:
+ * injection s_f(i,j,k) = s_c(i/2, j/2, k/2) for fine fluid cells with a fluid parent
+ * (the coarse-to-fine comparison rule of Sec. IV); a fine fluid cell whose parent is
+ * solid takes the mean of the parent's fluid 6-neighbours, else the coarse handle's
+ * last s_in. The next rfb_soc_solve on fine warm-starts from it; the fixed point does
+ * not depend on the start. Requires fine dims = 2 x coarse dims, fine dx = coarse dx / 2,
+ * both handles on one device, and a coarse state (RFB_ERR_STATE otherwise). Synchronises
+ * both handles' streams.
+ */
+rfb_status rfb_soc_upsample(const rfb_soc_handle* coarse, rfb_soc_handle* fine);
+
+/*
+ * Replace the per-cell reactive-area multiplier m_c (N doubles > 0, host or device;
+ * NULL = all ones). The state is kept as a warm start for the next solve.
+ */
+rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kind kind);
+
+typedef enum rfb_objective {
+    RFB_OBJ_I_TOT = 0,   /* total current I_tot [A], Eq. I-tot-def */
+    RFB_OBJ_U = 1,       /* utilisation U, Eq. utilization-def (first form) */
+    RFB_OBJ_U_MT = 2     /* mass-transport utilisation U_mt, Eq. umt-def */
+} rfb_objective;
+
+/*
+ * Discrete adjoint of the steady state. The steady state solves RHS(s) = L s + b = 0
+ * (linear in s by Eq. rate-from-soc-gen), so for an objective J the adjoint lam solves
+ * L^T lam = -dJ/ds (transposed explicit sweeps, the downwind gather of the upwind
+ * operator, same pseudo-time steps as the forward solve, to ||L^T lam + dJ/ds|| /
+ * ||dJ/ds|| <= tol), and
+ *   dJ/dm_c  = dJ/dm_c|explicit + lam_c k0 n_wall(c)/dx R~(s_c)
+ *   dJ/dbeta = dJ/dbeta|explicit + lam . (advective part of RHS(s)) / beta.
+ * I_TOT and U need a converged rfb_soc_solve at the current operating point (and area
+ * multipliers); U_MT needs a converged rfb_soc_umt. dU_mt/dm is identically zero (the
+ * U_mt problem has no kinetics) and is returned as zeros. velocity_scale must be > 0.
+ *   opts             nullable; dt_mode / cfl / check_every / max_sweeps are used
+ *   d_area_mult      nullable; N doubles (host or device per kind) receiving dJ/dm_c
+ *                    (zero on solid cells and cells without fiber neighbours)
+ *   d_velocity_scale nullable; host double receiving dJ/dbeta
+ *   res              nullable; sweeps, checks, residual (relative adjoint residual), and
+ *                    the objective's forward values I_tot / U / outlet_mean
+ */
+rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
+                           const rfb_solve_opts* opts, double* d_area_mult,
+                           double* d_velocity_scale, rfb_mem_kind kind,
+                           rfb_solve_result* res);
+
 /* Forget the current state: the next solve/step starts from s = s_in (cold start). */
 rfb_status rfb_soc_reset_state(rfb_soc_handle* h);
 

@@ -359,6 +359,73 @@ def umt(p: Problem, s: Optional[np.ndarray] = None) -> float:
 
 
 # --------------------------------------------------------------------------------------
+# Discrete adjoint of the steady state
+# --------------------------------------------------------------------------------------
+#
+# The steady state solves RHS(s; m, beta) = L(m, beta) s + b(m, beta) = 0 (linear in s,
+# Eq. rate-from-soc-gen). For an objective J(s, m, beta):
+#   L^T lam = -dJ/ds,   dJ/dp = dJ/dp|explicit + lam . dRHS/dp
+# with dRHS_c/dm_c = k0 n_wall(c)/h R~(s_c) (only row c) and dRHS/dbeta = the advective
+# part of RHS divided by beta (every face velocity carries beta). Objectives:
+#   'I_tot' : J = n_e F c0 h^3 sum_c k0 m_c n_wall/h R~(s_c)              (Eq. I-tot-def)
+#   'U'     : J = I_tot / (n_e F c0 Q (1 - s_in)), Q = beta h^2 sum_in W  (Eq. utilization-def)
+#   'U_mt'  : J = sum_out W s / sum_out W on the U_mt state (Eq. umt-def); independent of m.
+
+def _advection_only(p: Problem, mode: str) -> Operator:
+    """Operator with D = 0 and no reaction: L_adv s + b_adv is the advective part."""
+    q = dataclasses.replace(p, D=0.0, k0=0.0)
+    return assemble(q, mode=mode)
+
+
+def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
+    """Adjoint state and gradients at the steady state s (solved here if None)."""
+    mode = "umt" if objective == "U_mt" else "sbv"
+    op = assemble(p, mode)
+    if s is None:
+        s = steady_state(op)
+    u = op.unknown
+    N = s.size
+    h = p.h
+    scale = p.n_e * FARADAY * p.c0 * h ** 3
+    nw = n_wall(p.solid.astype(bool)).ravel().astype(np.float64)
+    m = np.ones(N) if p.area_mult is None else np.asarray(p.area_mult, np.float64).ravel()
+    fl = p.solid.ravel() == 0
+    kap0 = np.where(fl, p.k0 * nw / h, 0.0)             # dkappa/dm
+    g = np.zeros(N)
+    if objective in ("I_tot", "U"):
+        g = -scale * kap0 * m * op.kin.B                # dI_tot/ds
+        denom = p.n_e * FARADAY * p.c0 * op.Q * (1.0 - p.s_in)
+        if objective == "U":
+            g = g / denom
+    elif objective == "U_mt":
+        nz, ny, nx = p.solid.shape
+        w_out = np.zeros(N)
+        w_out[(nz - 1) * nx * ny:] = np.where(fl[(nz - 1) * nx * ny:], p.beta * p.W[-1].ravel(),
+                                              0.0)
+        g = np.where(u, w_out / w_out.sum(), 0.0)
+    else:
+        raise ValueError(objective)
+    Luu = op.L[u][:, u]
+    lam = np.zeros(N)
+    lam[u] = spla.spsolve(Luu.T.tocsc(), -g[u])
+    # gradients
+    R = rate_affine(s, op.kin)
+    dm = np.zeros(N)
+    if objective == "I_tot":
+        dm = (scale + lam) * kap0 * R
+    elif objective == "U":
+        dm = (scale / denom + lam) * kap0 * R
+    dm = np.where(fl, dm, 0.0)
+    adv = _advection_only(p, mode)
+    adv_rhs = (adv.L @ s + adv.b)
+    dbeta = float(np.dot(lam[u], adv_rhs[u])) / p.beta if p.beta != 0 else float("nan")
+    if objective == "U":
+        J = outputs(p, op, s).U
+        dbeta -= J / p.beta
+    return {"lam": lam, "d_area_mult": dm, "d_beta": dbeta, "g": g, "s": s}
+
+
+# --------------------------------------------------------------------------------------
 # Iterative upsampling (Sec. III.A, "iterative upsampling")
 # --------------------------------------------------------------------------------------
 

@@ -62,6 +62,12 @@ struct rfb_soc_handle {
     int s_cur = 0, t_cur = 0;
     bool have_state = false;
     bool have_umt_state = false;
+    bool s_converged = false;     // state is a converged solve at op (adjoint precondition)
+    bool t_converged = false;     // U_mt state converged at umt_op
+    OpPoint umt_op;
+    double* d_lam[2] = {nullptr, nullptr};   // adjoint state (allocated on first use)
+    double* d_g = nullptr;
+    double* d_grad = nullptr;
     double scaled_beta = NAN;
 
     int64_t n_fluid = 0, n_elec = 0;
@@ -416,7 +422,8 @@ void free_all(rfb_soc_handle* h) {
     void* ptrs[] = {h->d_flags, h->d_u,  h->d_v,   h->d_w,     h->d_us,   h->d_vs,
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
-                    h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err};
+                    h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
+                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -654,6 +661,7 @@ rfb_status rfb_soc_solve(rfb_soc_handle* h, double s_in, double eta, double tol,
         OpPoint op = make_op(o, s_in, eta, false);
         rfb_status st = drive(h, o, op, false, tol, -1, res);
         h->op = op;
+        h->s_converged = (st == RFB_OK);
         return st;
     } catch (Fail f) {
         return f.st;
@@ -672,6 +680,7 @@ rfb_status rfb_soc_step(rfb_soc_handle* h, double s_in, double eta, int64_t n_sw
     try {
         OpPoint op = make_op(o, s_in, eta, false);
         if (o.check_every == 0) o.check_every = (int32_t)std::min<int64_t>(std::max<int64_t>(n_sweeps, 1), 1 << 30);
+        h->s_converged = false;
         rfb_status st = drive(h, o, op, false, 0.0, n_sweeps, res);
         h->op = op;
         return st;
@@ -712,6 +721,8 @@ rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts
         h->have_umt_state = false;   // always a cold start: s = 0, electrode cells = 1
         rfb_solve_result r{};
         rfb_status st = drive(h, o, op, true, tol, -1, &r);
+        h->umt_op = op;
+        h->t_converged = (st == RFB_OK);
         if (umt) *umt = r.outlet_mean;
         if (res) *res = r;
         return st;
@@ -724,6 +735,7 @@ rfb_status rfb_soc_reset_state(rfb_soc_handle* h) {
     rfb_status g = guard(h);
     if (g) return g;
     h->have_state = false;
+    h->s_converged = false;
     h->op.valid = false;
     return RFB_OK;
 }
@@ -768,11 +780,220 @@ rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind ki
         if (tmp) cudaFree(tmp);
         h->s_cur = 0;
         h->have_state = true;
+        h->s_converged = false;
         if (bad) { set_err(h, "%llu non-finite state values (set to 0)", bad); return RFB_ERR_INVALID_ARG; }
     } catch (Fail f) {
         return f.st;
     }
     return RFB_OK;
+}
+
+rfb_status rfb_soc_upsample(const rfb_soc_handle* coarse, rfb_soc_handle* fine) {
+    if (!coarse) { set_err(fine, "coarse is NULL"); return RFB_ERR_INVALID_ARG; }
+    rfb_status g = guard(fine);
+    if (g) return g;
+    if (coarse->device != fine->device) {
+        set_err(fine, "coarse and fine handles are on different devices");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (fine->nx != 2 * coarse->nx || fine->ny != 2 * coarse->ny || fine->nz != 2 * coarse->nz) {
+        set_err(fine, "fine dims (%d,%d,%d) must be twice the coarse dims (%d,%d,%d)", fine->nx,
+                fine->ny, fine->nz, coarse->nx, coarse->ny, coarse->nz);
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (std::fabs(2.0 * fine->h - coarse->h) > 1e-12 * coarse->h) {
+        set_err(fine, "fine dx must be half the coarse dx");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (!coarse->have_state) {
+        set_err(fine, "coarse handle has no state to prolong");
+        return RFB_ERR_STATE;
+    }
+    try {
+        // the coarse state is read on the fine handle's stream: order it after the
+        // coarse handle's queued work
+        CK(fine, cudaStreamSynchronize(coarse->stream));
+        const double fill = coarse->op.valid ? coarse->op.s_in : 0.0;
+        prolong_kernel<<<flat_grid(fine->N), 256, 0, fine->stream>>>(
+            coarse->d_flags, coarse->d_s[coarse->s_cur], coarse->nx, coarse->ny, coarse->nz,
+            fine->d_flags, fine->d_s[0], fine->d_s[1], fill);
+        LAUNCHED(fine);
+        CK(fine, cudaStreamSynchronize(fine->stream));
+        fine->s_cur = 0;
+        fine->have_state = true;
+        fine->s_converged = false;
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kind kind) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
+    try {
+        if (!h->d_m) {
+            dalloc(h, &h->d_m, h->N);
+            dalloc(h, &h->d_m32, h->N);
+        }
+        double* src = nullptr;
+        double* tmp = nullptr;
+        std::vector<double> host;
+        if (m) {
+            if (kind == RFB_MEM_HOST) {
+                host.assign(m, m + h->N);
+            } else {
+                host.resize(h->N);
+                CK(h, cudaMemcpyAsync(host.data(), m, h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+                CK(h, cudaStreamSynchronize(h->stream));
+            }
+            for (int64_t c = 0; c < h->N; ++c)
+                if (!(host[c] > 0 && std::isfinite(host[c]))) {
+                    set_err(h, "area_mult must be finite and > 0 (cell %lld)", (long long)c);
+                    return RFB_ERR_INVALID_ARG;
+                }
+            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
+            CK(h, cudaMemcpyAsync(tmp, host.data(), h->N * 8, cudaMemcpyHostToDevice, h->stream));
+            src = tmp;
+        } else {
+            host.assign(h->N, 1.0);
+            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
+            CK(h, cudaMemcpyAsync(tmp, host.data(), h->N * 8, cudaMemcpyHostToDevice, h->stream));
+            src = tmp;
+        }
+        scale_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(src, h->d_m, h->d_m32, 1.0, h->N);
+        LAUNCHED(h);
+        CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(tmp);
+        h->s_converged = false;   // the operator changed; the state stays as a warm start
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
+                           const rfb_solve_opts* opts, double* d_area_mult,
+                           double* d_velocity_scale, rfb_mem_kind kind,
+                           rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (obj != RFB_OBJ_I_TOT && obj != RFB_OBJ_U && obj != RFB_OBJ_U_MT) {
+        set_err(h, "unknown objective");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (!(tol > 0)) { set_err(h, "tol must be > 0"); return RFB_ERR_INVALID_ARG; }
+    if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
+    const bool umt = obj == RFB_OBJ_U_MT;
+    if (umt ? !(h->have_umt_state && h->t_converged) : !(h->have_state && h->s_converged)) {
+        set_err(h, umt ? "adjoint of U_mt needs a converged rfb_soc_umt first"
+                       : "adjoint needs a converged rfb_soc_solve at the current operating point");
+        return RFB_ERR_STATE;
+    }
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    OpPoint op = umt ? h->umt_op : h->op;
+    if (!(op.beta > 0)) { set_err(h, "the adjoint needs velocity_scale > 0"); return RFB_ERR_INVALID_ARG; }
+    op.dt_mode = o.dt_mode;
+    op.cfl = o.cfl;
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        const int64_t N = h->N;
+        if (!h->d_lam[0]) {
+            dalloc(h, &h->d_lam[0], N);
+            dalloc(h, &h->d_lam[1], N);
+            dalloc(h, &h->d_g, N);
+            dalloc(h, &h->d_grad, N);
+        }
+        prepare(h, op);   // dt / local dt: L and L^T share their diagonal
+        const double* s = umt ? h->d_t[h->t_cur] : h->d_s[h->s_cur];
+        // objective value (for the explicit beta term of U) and the scales
+        rfb_solve_result fwd{};
+        {
+            Coef<double> C = make_coef<double>(h, op, false, false);
+            check_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
+                lattice(h), C, s, nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
+            LAUNCHED(h);
+            reduce_readback(h, 0);
+            fill_result(h, op, &fwd, umt ? h->n_fluid - h->n_elec : h->n_fluid);
+        }
+        const double h3 = h->h * h->h * h->h;
+        const double scale = h->kin.n_e * FARADAY * h->kin.c0 * h3;
+        const double Q = op.beta * h->sum_w_in * h->h * h->h;
+        double jscale = 1.0;
+        if (obj == RFB_OBJ_I_TOT) jscale = scale;
+        if (obj == RFB_OBJ_U) {
+            const double denom = h->kin.n_e * FARADAY * h->kin.c0 * Q * (1.0 - op.s_in);
+            if (!(denom != 0)) { set_err(h, "U undefined (Q = 0 or s_in = 1)"); return RFB_ERR_INVALID_ARG; }
+            jscale = scale / denom;
+        }
+        // outlet flux sum (beta-scaled velocities / h) for U_mt's dJ/ds
+        const double w_out_sum = op.beta / h->h * h->sum_w_out;
+        Coef<double> C = make_coef<double>(h, op, false, op.dt_mode == RFB_DT_LOCAL);
+        const double kB1 = h->kin.k0 / h->h * op.B;
+        adjoint_source_kernel<<<flat_grid(N), 256, 0, h->stream>>>(lattice(h), C, umt ? 2 : 0,
+                                                                   w_out_sum, kB1, h->d_g);
+        LAUNCHED(h);
+        CK(h, cudaMemsetAsync(h->d_lam[0], 0, N * 8, h->stream));
+        CK(h, cudaMemsetAsync(h->d_lam[1], 0, N * 8, h->stream));
+        int cur = 0;
+        const int64_t every = o.check_every > 0 ? o.check_every : 100;
+        rfb_solve_result r{};
+        rfb_status st = RFB_OK;
+        double rel = INFINITY;
+        int64_t done = 0;
+        while (true) {
+            adjoint_kernel<1><<<h->grid, h->block, 0, h->stream>>>(
+                lattice(h), C, h->d_lam[cur], nullptr, h->d_g, h->d_partials, h->kchunk);
+            LAUNCHED(h);
+            reduce_readback(h, 0);
+            ++r.checks;
+            rel = h->h_red[1] > 0 ? std::sqrt(h->h_red[0] / h->h_red[1]) : 0.0;
+            if (h->h_red[6] > 0) { st = RFB_ERR_NONFINITE; break; }
+            if (rel <= tol) break;
+            if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            const int64_t n = std::min(every, o.max_sweeps - done);
+            for (int64_t q = 0; q < n; ++q) {
+                adjoint_kernel<0><<<h->grid, h->block, 0, h->stream>>>(
+                    lattice(h), C, h->d_lam[cur], h->d_lam[cur ^ 1], h->d_g, nullptr, h->kchunk);
+                LAUNCHED(h);
+                cur ^= 1;
+            }
+            done += n;
+        }
+        // gradients
+        const double kap0A = umt ? 0.0 : h->kin.k0 / h->h * op.A;
+        const double kap0B = umt ? 0.0 : h->kin.k0 / h->h * op.B;
+        gradient_kernel<<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), C, s, h->d_lam[cur], kap0A, kap0B, jscale, 1.0,
+            umt ? nullptr : h->d_grad, h->d_partials, h->kchunk);
+        LAUNCHED(h);
+        reduce_readback(h, 0);
+        double dbeta = jscale * h->h_red[0] / op.beta;
+        if (obj == RFB_OBJ_U) dbeta -= fwd.U / op.beta;
+        if (umt) CK(h, cudaMemsetAsync(h->d_grad, 0, N * 8, h->stream));
+        if (d_area_mult) {
+            CK(h, cudaMemcpyAsync(d_area_mult, h->d_grad, N * 8,
+                                  kind == RFB_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                       : cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (d_velocity_scale) *d_velocity_scale = dbeta;
+        r.sweeps = done;
+        r.residual = rel;
+        r.I_tot = fwd.I_tot;
+        r.U = fwd.U;
+        r.outlet_mean = fwd.outlet_mean;
+        r.dt = op.dt;
+        r.tau = fwd.tau;
+        r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (res) *res = r;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
 }
 
 rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fluid) {

@@ -592,4 +592,233 @@ __global__ void set_state_kernel(const uint8_t* __restrict__ flags, const double
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Discrete adjoint of the steady state (FP64).
+//
+// The steady state solves L s + b = 0. For an objective J the adjoint solves
+// L^T lam = -g with g = dJ/ds. Column c of L collects what cell c sends to its
+// neighbours: through a face with outward velocity q > 0 the upwind flux q s_c leaves c
+// and enters the neighbour, so
+//   (L^T lam)_c = sum_{faces, q > 0} q (lam_nb - lam_c)      (outlet face: lam_nb = 0)
+//               + D/h^2 sum_{fluid nbrs} (lam_nb - lam_c) - [inlet] gD/h^2 lam_c
+//               - m_c kappa0(n_wall) B lam_c,
+// i.e. the advection part gathers from downwind neighbours. The pseudo-time iteration
+// lam <- lam + dt_c (L^T lam + g) uses the same dt_c as the forward one (L and L^T
+// share their diagonal). Pinned U_mt cells are not unknowns: lam = 0 there.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double adjoint_rhs(const Coef<double>& C, const double* tB, double lc,
+                                              double lxm, double lxp, double lym, double lyp,
+                                              double lzm, double lzp, double uL, double uH,
+                                              double vL, double vH, double wL, double wH,
+                                              bool inlet, bool outlet, int nw, double mult) {
+    double a = 0.0;
+    if (positive(uH)) a += uH * (lxp - lc);
+    if (positive(-uL)) a -= uL * (lxm - lc);
+    if (positive(vH)) a += vH * (lyp - lc);
+    if (positive(-vL)) a -= vL * (lym - lc);
+    if (positive(wH)) a += wH * ((outlet ? 0.0 : lzp) - lc);
+    if (positive(-wL)) a -= wL * (lzm - lc);
+    const double zmd = inlet ? lc : lzm;
+    const double nsum = ((lxm + lxp) + (lym + lyp)) + (zmd + lzp);
+    double d = C.Dh * nsum - (6.0 * C.Dh) * lc;
+    if (inlet) d -= C.gDh * lc;
+    return (a + d) - mult * tB[nw] * lc;
+}
+
+// MODE 0: sweep  lam_out = lam + dt (L^T lam + g)
+// MODE 1: check  reductions of r = L^T lam + g over unknown cells:
+//                0 sum r^2, 1 sum g^2, 6 non-finite count, 7 max |r|
+template <int MODE>
+__global__ void __launch_bounds__(BX * BY)
+adjoint_kernel(Lattice L, Coef<double> C, const double* __restrict__ lam,
+               double* __restrict__ lam_out, const double* __restrict__ g,
+               double* __restrict__ partials, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double l_prev = kb > 0 ? lam[c - nxny] : 0.0;
+        double l_cur = lam[c];
+        double wL = C.w[c];
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const bool outlet = (k == L.nz - 1);
+            double l_next = outlet ? 0.0 : lam[c + nxny];
+            double wH = C.w[c + nxny];
+            const unsigned f = L.flags[c];
+            if ((f & F_FLUID) && !(C.umt && (f & F_ELEC))) {
+                double lxm = (f & F_XM) ? lam[c - 1] : l_cur;
+                double lxp = (f & F_XP) ? lam[c + 1] : l_cur;
+                double lym = (f & F_YM) ? lam[c - nx] : l_cur;
+                double lyp = (f & F_YP) ? lam[c + nx] : l_cur;
+                double lzm = (f & F_ZM) ? l_prev : l_cur;
+                double lzp = (f & F_ZP) ? l_next : l_cur;
+                double uL = C.u[c];
+                double uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
+                double vL = C.v[c];
+                double vH = (j + 1 < L.ny) ? C.v[c + nx] : 0.0;
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                const double mult = C.m ? C.m[c] : 1.0;
+                const double r = adjoint_rhs(C, tB, l_cur, lxm, lxp, lym, lyp, lzm, lzp, uL,
+                                             uH, vL, vH, wL, wH, k == 0, outlet, nw, mult) +
+                                 g[c];
+                if (MODE == 0) {
+                    const double dt = C.dtc ? (double)C.dtc[c] : C.dt;
+                    lam_out[c] = l_cur + dt * r;
+                } else {
+                    if (isfinite(r)) {
+                        acc[0] += r * r;
+                        acc[7] = fmax(acc[7], fabs(r));
+                    } else {
+                        acc[6] += 1.0;
+                    }
+                    acc[1] += g[c] * g[c];
+                }
+            }
+            l_prev = l_cur;
+            l_cur = l_next;
+            wL = wH;
+        }
+    }
+    if (MODE == 1) {
+        const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                            ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+        block_reduce_store(acc, partials + bid * NRED);
+    }
+}
+
+// g~ = dJ/ds / jscale on unknown fluid cells (0 elsewhere):
+//   OBJ 0 (I_tot, U): -m_c kappa0(n_wall) B;   OBJ 2 (U_mt): [outlet] w_c / w_out_sum
+__global__ void adjoint_source_kernel(Lattice L, Coef<double> C, int obj, double w_out_sum,
+                                      double kB1, double* __restrict__ g) {
+    const int64_t N = (int64_t)L.nxny * L.nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = L.flags[c];
+        double x = 0.0;
+        if ((f & F_FLUID) && !(C.umt && (f & F_ELEC))) {
+            const int i = (int)(c % L.nx);
+            const int j = (int)((c / L.nx) % L.ny);
+            const int k = (int)(c / L.nxny);
+            if (obj == 2) {
+                if (k == L.nz - 1) x = C.w[c + L.nxny] / w_out_sum;
+            } else {
+                const int nw = n_wall_of(f, i, j, k, L.nx, L.ny, L.nz);
+                x = -(C.m ? C.m[c] : 1.0) * kB1 * nw;   // kB1 = k0 B / h per fiber face
+            }
+        }
+        g[c] = x;
+    }
+}
+
+// Gradients at the steady state s with adjoint lam~ = lam / jscale:
+//   dm[c] = jscale (mscale + lam~_c) kappa0(n_wall) R~(s_c)   (fluid cells, OBJ 0)
+//   slot 0 of the reduction: sum over unknown cells of lam~_c adv_c(s) (beta-scaled
+//   velocities, so d/dbeta of RHS is adv/beta).
+__global__ void __launch_bounds__(BX * BY)
+gradient_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
+                const double* __restrict__ lam, double kap0A, double kap0B, double jscale,
+                double mscale, double* __restrict__ dm, double* __restrict__ partials,
+                int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    __shared__ double tZ[8];
+    if (threadIdx.y * BX + threadIdx.x < 8) tZ[threadIdx.y * BX + threadIdx.x] = 0.0;
+    __syncthreads();
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        // advection only: no diffusion, no reaction
+        Coef<double> A = C;
+        A.Dh = 0.0;
+        A.gDh = 0.0;
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double s_prev = kb > 0 ? s[c - nxny] : 0.0;
+        double s_cur = s[c];
+        double wL = C.w[c];
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const bool outlet = (k == L.nz - 1);
+            double s_next = outlet ? 0.0 : s[c + nxny];
+            double wH = C.w[c + nxny];
+            const unsigned f = L.flags[c];
+            double dmv = 0.0;
+            if (f & F_FLUID) {
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                dmv = jscale * (mscale + lam[c]) * nw * (kap0A - kap0B * s_cur);
+                if (!(C.umt && (f & F_ELEC))) {
+                    double sxm = (f & F_XM) ? s[c - 1] : s_cur;
+                    double sxp = (f & F_XP) ? s[c + 1] : s_cur;
+                    double sym = (f & F_YM) ? s[c - nx] : s_cur;
+                    double syp = (f & F_YP) ? s[c + nx] : s_cur;
+                    double szm = (f & F_ZM) ? s_prev : s_cur;
+                    double szp = (f & F_ZP) ? s_next : s_cur;
+                    double uL = C.u[c];
+                    double uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
+                    double vL = C.v[c];
+                    double vH = (j + 1 < L.ny) ? C.v[c + nx] : 0.0;
+                    const double adv = cell_rhs<double>(A, tZ, tZ, s_cur, sxm, sxp, sym, syp,
+                                                        szm, szp, uL, uH, vL, vH, wL, wH,
+                                                        k == 0, outlet, 0, 0.0);
+                    acc[0] += lam[c] * adv;
+                }
+            }
+            if (dm) dm[c] = dmv;
+            s_prev = s_cur;
+            s_cur = s_next;
+            wL = wH;
+        }
+    }
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+}
+
+// 2x prolongation for iterative upsampling: a fine fluid cell takes its coarse parent's
+// value (injection); if the parent is solid, the mean over the parent's fluid
+// 6-neighbours (order -z, +z, -y, +y, -x, +x); if there are none, s_fill. Fine solid
+// cells get 0. Written to both buffers of the fine state.
+__global__ void prolong_kernel(const uint8_t* __restrict__ cflags, const double* __restrict__ sc,
+                               int cnx, int cny, int cnz, const uint8_t* __restrict__ fflags,
+                               double* __restrict__ fa, double* __restrict__ fb, double s_fill) {
+    const int fnx = 2 * cnx, fny = 2 * cny;
+    const int64_t fN = (int64_t)fnx * fny * (2 * cnz);
+    const int64_t cnxny = (int64_t)cnx * cny;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < fN;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        double x = 0.0;
+        if (fflags[q] & F_FLUID) {
+            const int i = (int)(q % fnx);
+            const int j = (int)((q / fnx) % fny);
+            const int k = (int)(q / ((int64_t)fnx * fny));
+            const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
+            const int64_t p = ci + (int64_t)cnx * cj + cnxny * ck;
+            if (cflags[p] & F_FLUID) {
+                x = sc[p];
+            } else {
+                double acc = 0.0;
+                int cnt = 0;
+                if (ck > 0 && (cflags[p - cnxny] & F_FLUID)) { acc += sc[p - cnxny]; ++cnt; }
+                if (ck + 1 < cnz && (cflags[p + cnxny] & F_FLUID)) { acc += sc[p + cnxny]; ++cnt; }
+                if (cj > 0 && (cflags[p - cnx] & F_FLUID)) { acc += sc[p - cnx]; ++cnt; }
+                if (cj + 1 < cny && (cflags[p + cnx] & F_FLUID)) { acc += sc[p + cnx]; ++cnt; }
+                if (ci > 0 && (cflags[p - 1] & F_FLUID)) { acc += sc[p - 1]; ++cnt; }
+                if (ci + 1 < cnx && (cflags[p + 1] & F_FLUID)) { acc += sc[p + 1]; ++cnt; }
+                x = cnt ? acc / cnt : s_fill;
+            }
+        }
+        fa[q] = x;
+        fb[q] = x;
+    }
+}
+
 }  // namespace rfb

@@ -22,6 +22,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 PREC = {"fp64": 0, "mixed": 1}
 INLET = {"face": 0, "ghost": 1}
 DT = {"global": 0, "local": 1}
+OBJECTIVES = {"I_tot": 0, "U": 1, "U_mt": 2}
 
 
 class Kinetics(ctypes.Structure):
@@ -82,13 +83,18 @@ def lib():
         L.rfb_soc_get_state.argtypes = [H, c_void_p, c_int]
         L.rfb_soc_set_state.argtypes = [H, c_void_p, c_int]
         L.rfb_soc_reset_state.argtypes = [H]
+        L.rfb_soc_upsample.argtypes = [H, H]
+        L.rfb_soc_set_area_mult.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_adjoint.argtypes = [H, c_int, c_double, POINTER(SolveOpts), c_void_p,
+                                      POINTER(c_double), c_int, POINTER(SolveResult)]
         L.rfb_soc_info.argtypes = [H, POINTER(c_int64), POINTER(c_int64)]
         L.rfb_soc_kernel_launches.argtypes = [H]
         L.rfb_soc_kernel_launches.restype = c_int64
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
-                     "rfb_soc_current_noalloc"):
+                     "rfb_soc_current_noalloc", "rfb_soc_upsample", "rfb_soc_set_area_mult",
+                     "rfb_soc_adjoint"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -225,6 +231,31 @@ class Solver:
     def set_state(self, s):
         p, keep, kind = _ptr(s, np.float64)
         self._check(lib().rfb_soc_set_state(self.h, p, kind))
+
+    def set_area_mult(self, m):
+        """rfb_soc_set_area_mult (None = all ones)."""
+        if m is None:
+            self._check(lib().rfb_soc_set_area_mult(self.h, None, MEM_HOST))
+            return
+        p, keep, kind = _ptr(m, np.float64)
+        self._check(lib().rfb_soc_set_area_mult(self.h, p, kind))
+
+    def adjoint(self, objective="I_tot", tol=1e-12, out=None, **opts):
+        """rfb_soc_adjoint: returns (dJ/dm (N), dJ/dbeta, result dict)."""
+        obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+        if out is None:
+            out = np.empty(self.n_cells, dtype=np.float64)
+        p, keep, kind = _ptr(out, np.float64)
+        db = c_double()
+        r = SolveResult()
+        o = make_opts(**opts)
+        self._check(lib().rfb_soc_adjoint(self.h, obj, float(tol), byref(o), p, byref(db), kind,
+                                          byref(r)))
+        return out, db.value, r.as_dict()
+
+    def upsample_from(self, coarse: "Solver"):
+        """rfb_soc_upsample: this (fine) handle's state := 2x prolongation of coarse's."""
+        self._check(lib().rfb_soc_upsample(coarse.h, self.h))
 
     def reset_state(self):
         self._check(lib().rfb_soc_reset_state(self.h))

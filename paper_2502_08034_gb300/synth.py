@@ -339,6 +339,58 @@ def build_case(name: str, dims, porosity: float, diameter, seed: int, u_mean: fl
                 info=info)
 
 
+def multilevel_cases(fine_dims, levels: int, porosity: float, diameter, seed: int,
+                     u_mean: float, eta: float, s_in: float, tol: float,
+                     h_fine: float = H_PAPER, flow_device: str = "cpu", k0: float = 1e-7,
+                     name: str = "fiber"):
+    """The same analytic fibers rasterised at ``levels`` resolutions, coarsest first.
+
+    Fibers are drawn once in finest-level cell units (porosity target at the finest
+    level); level l has dims fine_dims / 2^(levels-1-l) and cell size h_fine times the
+    same factor. Each level gets its own flood fill and potential flow."""
+    fibers, solid_f = generate_fibers(seed, fine_dims, porosity, diameter)
+    out = []
+    for lev in range(levels):
+        f = 2 ** (levels - 1 - lev)
+        dims = tuple(int(d) // f for d in fine_dims)
+        solid = solid_f if f == 1 else rasterise(fibers, dims, scale=float(f))
+        solid = remove_unconnected(solid)
+        U, V, W, info = potential_flow(solid, h_fine * f, u_mean, device=flow_device)
+        info = dict(info)
+        info["n_fibers"] = len(fibers)
+        out.append(Case(name="%s%dx%dx%d" % ((name,) + dims), dims=dims, h=h_fine * f,
+                        solid=solid.astype(np.uint8), U=U, V=V, W=W, D=D_SOC, k0=k0,
+                        alpha=0.5, T=298.0, n_e=2, c0=20.0, s_in=s_in, eta=eta, tol=tol,
+                        u_mean=u_mean, info=info))
+    return out
+
+
+def lognormal_area_mult(solid: np.ndarray, sigma: float = 0.3, seed: int = 40) -> np.ndarray:
+    """Per-cell reactive-area multiplier: exp(sigma Z), Z standard normal (numpy PCG64
+    with ``seed``), on fluid cells with at least one fiber 6-neighbour (median 1); 1 on
+    every other cell. Shape (nz, ny, nx)."""
+    s = solid.astype(bool)
+    touch = np.zeros_like(s)
+    touch[:, :, 1:] |= s[:, :, :-1]
+    touch[:, :, :-1] |= s[:, :, 1:]
+    touch[:, 1:, :] |= s[:, :-1, :]
+    touch[:, :-1, :] |= s[:, 1:, :]
+    touch[1:] |= s[:-1]
+    touch[:-1] |= s[1:]
+    wall = touch & ~s
+    z = np.random.default_rng(seed).standard_normal(int(wall.sum()))
+    m = np.ones(s.shape)
+    m[wall] = np.exp(sigma * z)
+    return m
+
+
+def adjoint_case(dims=(128, 128, 256), seed=4, **kw) -> Case:
+    """Differentiation workload: 128x128x256, porosity 0.8, d = 8, 1 cm/s, -0.10 V,
+    s_in = 0.5."""
+    return build_case("fiber%dx%dx%d_adjoint" % tuple(dims), dims, 0.80, 8.0, seed, 0.01,
+                      -0.10, 0.5, 1e-12, **kw)
+
+
 def fiber_channel_case(dims=(48, 48, 96), porosity=0.80, diameter=8.0, seed=1,
                        u_mean=0.01, eta=-0.10, s_in=0.5, tol=1e-10, **kw) -> Case:
     """Plain FP64 workload: 48x48x96, d = 8 cells, porosity 0.80, 1 cm/s, eta = -0.10 V,

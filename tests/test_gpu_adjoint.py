@@ -1,0 +1,174 @@
+"""Discrete adjoint on the GPU: parity with the oracle's CSR-transpose adjoint, central
+finite differences of GPU solves, and the torch.autograd bridge."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import soc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_08034_gb300 import _build
+    _build.build()
+
+
+@functools.lru_cache(maxsize=None)
+def _small():
+    from paper_2502_08034_gb300 import synth
+    case = synth.build_case("adj24", (24, 24, 48), 0.80, 4.0, 4, 0.01, -0.10, 0.5, 1e-12)
+    return case, synth.lognormal_area_mult(case.solid, 0.3, 40)
+
+
+def _problem(case, m, **over):
+    kw = dict(k0=case.k0, eta=case.eta, area_mult=m)
+    kw.update(over)
+    return soc.Problem(case.solid, case.U, case.V, case.W, case.h, case.D, case.s_in, **kw)
+
+
+@pytest.mark.parametrize("objective", ["I_tot", "U", "U_mt"])
+def test_adjoint_matches_oracle(objective):
+    from paper_2502_08034_gb300 import rfb
+    case, m = _small()
+    with rfb.Solver.from_case(case, area_mult=m) as sv:
+        sv.solve(case.s_in, case.eta, 1e-14, precision="fp64", max_sweeps=2_000_000)
+        sv.umt(1e-14, precision="fp64")
+        dm, db, r = sv.adjoint(objective, 1e-13)
+    ref = soc.adjoint(_problem(case, m), None, objective)
+    scale = np.abs(ref["d_area_mult"]).max()
+    if objective == "U_mt":
+        assert np.all(dm == 0.0)
+    else:
+        assert np.abs(dm - ref["d_area_mult"]).max() <= 1e-9 * scale
+    assert abs(db - ref["d_beta"]) <= 1e-9 * abs(ref["d_beta"])
+    assert r["residual"] <= 1e-13
+
+
+def _current_cellwise(case, m, s_p, s_m, m_p, m_m):
+    """(I_tot(+) - I_tot(-)) summed cell by cell (the two states differ only near the
+    perturbed voxel, so the difference is formed before the sum)."""
+    kin = soc.kinetics(case.eta)
+    nw = soc.n_wall(case.solid.astype(bool)).ravel()
+    kap = case.k0 * nw / case.h
+    scale = case.n_e * soc.FARADAY * case.c0 * case.h ** 3
+    d = m_p * kap * soc.rate_affine(s_p, kin) - m_m * kap * soc.rate_affine(s_m, kin)
+    return scale * float(np.sum(d))
+
+
+def _fd_voxels(sv, case, m, s0, voxels, eps_rel, sweeps):
+    out = []
+    for c in voxels:
+        res = []
+        for sign in (1, -1):
+            mm = m.ravel().copy()
+            mm[c] += sign * eps_rel * mm[c]
+            sv.set_area_mult(mm)
+            sv.set_state(s0)
+            sv.step(case.s_in, case.eta, sweeps, precision="fp64")
+            res.append((sv.get_state(), mm))
+        (sp, mp), (sm, mmn) = res
+        fd = _current_cellwise(case, m, sp, sm, mp, mmn) / (2 * eps_rel * m.ravel()[c])
+        out.append(fd)
+    sv.set_area_mult(m)
+    return np.array(out)
+
+
+def test_adjoint_matches_central_differences_small():
+    from paper_2502_08034_gb300 import rfb
+    case, m = _small()
+    fl = case.solid.ravel() == 0
+    nw = soc.n_wall(case.solid.astype(bool)).ravel()
+    rng = np.random.default_rng(41)
+    voxels = rng.choice(np.flatnonzero(fl & (nw > 0)), 6, replace=False)
+    with rfb.Solver.from_case(case, area_mult=m) as sv:
+        sv.solve(case.s_in, case.eta, 1e-14, precision="fp64")
+        s0 = sv.get_state()
+        dm, db, _ = sv.adjoint("I_tot", 1e-13)
+        fd = _fd_voxels(sv, case, m, s0, voxels, 1e-6, 6000)
+        # velocity scale: central difference of the solve
+        vals = []
+        for b in (1 + 1e-6, 1 - 1e-6):
+            sv.set_state(s0)
+            vals.append(sv.solve(case.s_in, case.eta, 1e-14, precision="fp64",
+                                 velocity_scale=b)["I_tot"])
+        fd_b = (vals[0] - vals[1]) / 2e-6
+    # a one-voxel change at step 1e-6 moves the solution by ~1e-12: the difference of
+    # two FP64 solves resolves it to ~1e-5
+    assert np.all(np.abs(fd - dm[voxels]) <= 1e-4 * np.abs(fd)), (fd, dm[voxels])
+    assert abs(fd_b - db) <= 1e-6 * abs(fd_b)
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    from paper_2502_08034_gb300 import rfb
+    from paper_2502_08034_gb300.autograd import soc_objective
+    case, m = _small()
+    with rfb.Solver.from_case(case) as sv:
+        mt = torch.tensor(m.ravel(), dtype=torch.float64, device="cuda", requires_grad=True)
+        beta = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+        I, U, Umt = soc_objective(sv, mt, beta, case.s_in, case.eta, 1e-14)
+        (I * 3.0 + U * 0.5 + Umt * 2.0).backward()
+        ref_i = soc.adjoint(_problem(case, m), None, "I_tot")
+        ref_u = soc.adjoint(_problem(case, m), None, "U")
+        ref_mt = soc.adjoint(_problem(case, m), None, "U_mt")
+    want_m = 3.0 * ref_i["d_area_mult"] + 0.5 * ref_u["d_area_mult"]
+    want_b = 3.0 * ref_i["d_beta"] + 0.5 * ref_u["d_beta"] + 2.0 * ref_mt["d_beta"]
+    got_m = mt.grad.cpu().numpy()
+    assert np.abs(got_m - want_m).max() <= 1e-8 * np.abs(want_m).max()
+    assert abs(float(beta.grad) - want_b) <= 1e-8 * abs(want_b)
+
+
+def test_adjoint_requires_a_converged_state():
+    from paper_2502_08034_gb300 import rfb
+    case, m = _small()
+    with rfb.Solver.from_case(case, area_mult=m) as sv:
+        sv.step(case.s_in, case.eta, 10)
+        with pytest.raises(rfb.RfbError) as e:
+            sv.adjoint("I_tot", 1e-10)
+        assert e.value.status == rfb.RFB_ERR_STATE
+        with pytest.raises(rfb.RfbError):
+            sv.adjoint("U_mt", 1e-10)
+
+
+def test_differentiation_workload_128x128x256_full_size():
+    """Differentiation workload at full size (128x128x256, porosity 0.8, d = 8, lognormal
+    sigma = 0.3 area multipliers on wall cells): adjoint gradients of I_tot and U_mt
+    against central differences on 64 random wall voxels (I_tot) and on the velocity
+    scale (both, step 1e-6). Voxel steps: 1e-3 (tight check) and 1e-6 on 16 of them,
+    where the single-voxel response is only ~3 orders above the FP64 rounding floor of
+    the 4M-cell state, so the bound is loose."""
+    from paper_2502_08034_gb300 import rfb, synth
+    case = synth.adjoint_case(flow_device="cuda")
+    m = synth.lognormal_area_mult(case.solid, 0.3, 40)
+    fl = case.solid.ravel() == 0
+    nw = soc.n_wall(case.solid.astype(bool)).ravel()
+    rng = np.random.default_rng(41)
+    voxels = rng.choice(np.flatnonzero(fl & (nw > 0)), 64, replace=False)
+    with rfb.Solver.from_case(case, area_mult=m, device_inputs=True) as sv:
+        r0 = sv.solve(case.s_in, case.eta, 1e-13, precision="fp64")
+        s0 = sv.get_state()
+        dm, db, ra = sv.adjoint("I_tot", 1e-12)
+        sv.umt(1e-13, precision="fp64")
+        dmt, dbmt, _ = sv.adjoint("U_mt", 1e-12)
+        sweeps = max(3000, 2 * r0["sweeps"])
+        fd3 = _fd_voxels(sv, case, m, s0, voxels, 1e-3, sweeps)
+        fd6 = _fd_voxels(sv, case, m, s0, voxels[:16], 1e-6, sweeps)
+        vals, vmt = [], []
+        for b in (1 + 1e-6, 1 - 1e-6):
+            sv.set_state(s0)
+            vals.append(sv.solve(case.s_in, case.eta, 1e-13, precision="fp64",
+                                 velocity_scale=b)["I_tot"])
+            vmt.append(sv.umt(1e-13, precision="fp64", velocity_scale=b)[0])
+    assert np.all(dmt == 0.0)
+    rel3 = np.abs(fd3 - dm[voxels]) / np.abs(fd3)
+    rel6 = np.abs(fd6 - dm[voxels[:16]]) / np.abs(fd6)
+    print("FD rel err: step 1e-3 max %.2e, step 1e-6 max %.2e" % (rel3.max(), rel6.max()))
+    assert rel3.max() <= 1e-5, rel3.max()
+    assert rel6.max() <= 1e-2, rel6.max()
+    assert abs((vals[0] - vals[1]) / 2e-6 - db) <= 1e-5 * abs(db)
+    assert abs((vmt[0] - vmt[1]) / 2e-6 - dbmt) <= 1e-5 * abs(dbmt)

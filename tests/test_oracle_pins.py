@@ -327,3 +327,46 @@ def test_prolongation_injection():
     nb = [scr[0, 1, 1], scr[2, 1, 1], scr[1, 0, 1], scr[1, 2, 1], scr[1, 1, 0], scr[1, 1, 2]]
     assert abs(sf[2, 2, 2] - np.mean(nb)) < 1e-15
     assert sf[3, 3, 3] == 0.0
+
+
+# ---------------------------------------------------------------- adjoint (FD pinned)
+
+def _fd_objective(p, objective):
+    if objective == "U_mt":
+        return soc.umt(p)
+    op = soc.assemble(p)
+    o = soc.outputs(p, op, soc.steady_state(op))
+    return o.I_tot if objective == "I_tot" else o.U
+
+
+@pytest.mark.parametrize("objective", ["I_tot", "U", "U_mt"])
+def test_oracle_adjoint_matches_central_differences(objective):
+    """The adjoint gradients equal central finite differences of the steady-state solve
+    with respect to the per-voxel area multiplier and the velocity scale."""
+    import dataclasses
+    base = _p3((8, 8, 12))
+    rng = np.random.default_rng(40)
+    nw = soc.n_wall(base.solid.astype(bool)).ravel()
+    fl = base.solid.ravel() == 0
+    m = np.where(fl & (nw > 0), np.exp(0.3 * rng.standard_normal(base.solid.size)), 1.0)
+    p = dataclasses.replace(base, area_mult=m.reshape(base.solid.shape), k0=2e-6)
+    adj = soc.adjoint(p, None, objective)
+    walls = np.flatnonzero(fl & (nw > 0))
+    pick = rng.choice(walls, 5, replace=False)
+    for c in pick:
+        eps = 1e-6 * m[c]
+        mp, mm = m.copy(), m.copy()
+        mp[c] += eps
+        mm[c] -= eps
+        jp = _fd_objective(dataclasses.replace(p, area_mult=mp.reshape(p.solid.shape)), objective)
+        jm = _fd_objective(dataclasses.replace(p, area_mult=mm.reshape(p.solid.shape)), objective)
+        fd = (jp - jm) / (2 * eps)
+        if objective == "U_mt":
+            assert fd == 0.0 and adj["d_area_mult"][c] == 0.0
+        else:
+            assert abs(fd - adj["d_area_mult"][c]) <= 1e-5 * abs(fd), (c, fd, adj["d_area_mult"][c])
+    eps = 1e-6
+    jp = _fd_objective(dataclasses.replace(p, beta=1 + eps), objective)
+    jm = _fd_objective(dataclasses.replace(p, beta=1 - eps), objective)
+    fd = (jp - jm) / (2 * eps)
+    assert abs(fd - adj["d_beta"]) <= 1e-6 * abs(fd), (fd, adj["d_beta"])
