@@ -268,6 +268,53 @@ rfb_status rfb_soc_get_state(rfb_soc_handle* h, double* s, rfb_mem_kind kind);
 /* Set the FP64 state (N doubles; solid-cell values are ignored). Must be finite. */
 rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind kind);
 
+/*
+ * Batches: many lattices of uneven size and operating points (the paper's design
+ * question, how utilisation varies with geometry, flow rate and voltage, Sec. V)
+ * advanced together. Each sweep over all lattices is one persistent launch whose
+ * resident blocks walk a list of work items (128 x 8 column tiles times a chunk of z
+ * planes, from every lattice); one correction cycle (zeroing, sweeps, fused FP64 check
+ * of every lattice, convergence bookkeeping) is captured once as a CUDA graph and
+ * replayed until every lattice has converged; converged lattices drop out of the work
+ * list on the device. Mixed precision only (FP32 correction sweeps, FP64 checks and
+ * state). The z-chunk of the work items and the sweeps per cycle are picked by a
+ * built-in autotuner on the first solve (timed with CUDA events).
+ */
+typedef struct rfb_batch rfb_batch;
+
+typedef struct rfb_batch_info {
+    int32_t kchunk;            /* z planes per work item (autotuned) */
+    int32_t sweeps_per_cycle;  /* sweeps between FP64 checks (autotuned or opts) */
+    int32_t n_items;           /* work items over all lattices */
+    int32_t grid_blocks;       /* resident blocks of the persistent launch */
+    double sweep_ms;           /* autotuner: device time of one sweep of the batch */
+    double check_ms;           /* autotuner: device time of one FP64 check of the batch */
+    int64_t cycles;            /* graph replays of this solve */
+    double time_ms;            /* wall time of this solve */
+    int64_t launches;          /* kernels launched by this batch so far */
+} rfb_batch_info;
+
+/* hs: n handles (distinct, same device, nx % 4 == 0), not owned; they must outlive the
+ * batch. Work is queued on hs[0]'s stream. */
+rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** out);
+
+/* Solve every lattice q to residual <= tol[q] at (s_in[q], eta[q]) (host arrays of n).
+ * opts (nullable) must select RFB_PREC_MIXED (the default of this call is still the
+ * opts default, so pass opts with precision = RFB_PREC_MIXED); velocity_scale, cfl,
+ * dt_mode, inlet_bc, max_sweeps (per lattice) and check_every (0 = autotuned) apply to
+ * all. Each handle warm-starts from its state if it has one. res (nullable, n entries)
+ * and info (nullable) are filled. Returns RFB_ERR_NOT_CONVERGED if max_sweeps ran out
+ * first; the states of every handle are valid either way. */
+rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* eta,
+                               const double* tol, const rfb_solve_opts* opts,
+                               rfb_solve_result* res, rfb_batch_info* info);
+
+/* Last error detail of the batch (b = NULL: of the last failed rfb_soc_batch_create). */
+const char* rfb_soc_batch_last_error(const rfb_batch* b);
+
+/* Release the batch (not its handles). NULL-safe. */
+rfb_status rfb_soc_batch_destroy(rfb_batch* b);
+
 /* Lattice size N and fluid-cell count of the handle (either pointer nullable). */
 rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fluid);
 

@@ -409,6 +409,7 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
 
 rfb_status guard(rfb_soc_handle* h) {
     if (!h) return RFB_ERR_INVALID_ARG;
+    (void)cudaGetLastError();   // drop a stale error left by an earlier failed runtime call
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) {
         set_err(h, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -1096,3 +1097,372 @@ extern "C" rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_resul
         return f.st;
     }
 }
+
+// =====================================================================================
+// Batches (many lattices, one persistent launch per sweep, one CUDA graph per cycle)
+// =====================================================================================
+struct rfb_batch {
+    std::vector<rfb_soc_handle*> hs;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    BatchInst* d_insts = nullptr;
+    BatchCtl* d_ctl = nullptr;
+    BatchCtl* h_ctl = nullptr;          // pinned
+    BatchItem* d_items = nullptr;
+    int* d_item_begin = nullptr;
+    double* d_partials = nullptr;
+    int n_items = 0;
+    int items_kchunk = -1;
+    std::vector<int> item_begin;
+    int grid_blocks = 0;
+    // autotuner results
+    int tuned_kchunk = 0;
+    int tuned_every = 0;
+    double tuned_sweep_ms = 0, tuned_check_ms = 0;
+    cudaGraphExec_t exec = nullptr;
+    int exec_every = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::string err;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void bset_err(rfb_batch* b, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->err = buf;
+}
+
+#define BCK(b, call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            bset_err((b), "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                     __FILE__, __LINE__);                                              \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? RFB_ERR_OOM : RFB_ERR_CUDA};  \
+        }                                                                              \
+    } while (0)
+
+#define BLAUNCHED(b)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            bset_err((b), "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),  \
+                     __FILE__, __LINE__);                                              \
+            throw Fail{RFB_ERR_CUDA};                                                  \
+        }                                                                              \
+        ++(b)->launches;                                                               \
+    } while (0)
+
+// Work items of every lattice for a z-chunk length; item_begin[i] .. item_begin[i+1]
+// are lattice i's items (contiguous, in x-fastest tile order).
+void build_items(rfb_batch* b, int kchunk) {
+    if (b->items_kchunk == kchunk) return;
+    std::vector<BatchItem> items;
+    b->item_begin.assign(1, 0);
+    for (size_t q = 0; q < b->hs.size(); ++q) {
+        const rfb_soc_handle* h = b->hs[q];
+        const int tx = (h->nx / 4 + VBX - 1) / VBX, ty = (h->ny + VBY - 1) / VBY;
+        for (int kb = 0; kb < h->nz; kb += kchunk)
+            for (int by = 0; by < ty; ++by)
+                for (int bx = 0; bx < tx; ++bx)
+                    items.push_back(BatchItem{(int)q, bx, by, kb, std::min(kb + kchunk, h->nz)});
+        b->item_begin.push_back((int)items.size());
+    }
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_item_begin) cudaFree(b->d_item_begin);
+    if (b->d_partials) cudaFree(b->d_partials);
+    b->d_items = nullptr; b->d_item_begin = nullptr; b->d_partials = nullptr;
+    BCK(b, cudaMalloc((void**)&b->d_items, items.size() * sizeof(BatchItem)));
+    BCK(b, cudaMalloc((void**)&b->d_item_begin, b->item_begin.size() * sizeof(int)));
+    BCK(b, cudaMalloc((void**)&b->d_partials, items.size() * NRED * sizeof(double)));
+    BCK(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
+                      cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_item_begin, b->item_begin.data(), b->item_begin.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+    b->n_items = (int)items.size();
+    b->items_kchunk = kchunk;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+}
+
+void batch_sweeps(rfb_batch* b, int n, bool local) {
+    for (int q = 0; q < n; ++q) {
+        if (local)
+            batch_sweep_kernel<true><<<b->grid_blocks, dim3(VBX, VBY), 0, b->stream>>>(
+                b->d_insts, b->d_items, b->n_items, q & 1);
+        else
+            batch_sweep_kernel<false><<<b->grid_blocks, dim3(VBX, VBY), 0, b->stream>>>(
+                b->d_insts, b->d_items, b->n_items, q & 1);
+        BLAUNCHED(b);
+    }
+}
+
+void batch_check(rfb_batch* b, bool fused, int sweeps_done) {
+    if (fused)
+        batch_check_kernel<true><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
+            b->d_insts, b->d_items, b->n_items, b->d_partials);
+    else
+        batch_check_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
+            b->d_insts, b->d_items, b->n_items, b->d_partials);
+    BLAUNCHED(b);
+    batch_finalize_kernel<<<(int)b->hs.size(), 256, 0, b->stream>>>(
+        b->d_insts, b->d_item_begin, b->d_partials, b->d_ctl, fused ? 1 : 0, sweeps_done);
+    BLAUNCHED(b);
+}
+
+// One correction cycle: delta = 0, `every` sweeps, fused FP64 check, bookkeeping, and
+// the control block copied to the host.
+void batch_cycle(rfb_batch* b, int every, bool local) {
+    batch_zero_kernel<<<152 * 4, 256, 0, b->stream>>>(b->d_insts, (int)b->hs.size());
+    BLAUNCHED(b);
+    batch_sweeps(b, every, local);
+    batch_check(b, true, every);
+    BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->hs.size() * sizeof(BatchCtl),
+                           cudaMemcpyDeviceToHost, b->stream));
+}
+
+// Project-written autotuner: for each candidate z-chunk of the work items, time a few
+// persistent sweeps of the whole batch (CUDA events) and keep the fastest; then set the
+// sweeps per cycle so that the FP64 check costs about 3% of a cycle.
+void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0) {
+    const int cands[] = {8, 16, 32, 64};
+    float best = 1e30f;
+    int best_k = 16;
+    for (int kc : cands) {
+        build_items(b, kc);
+        batch_sweeps(b, 2, local);   // warm-up
+        BCK(b, cudaEventRecord(b->ev[0], b->stream));
+        batch_sweeps(b, 4, local);
+        BCK(b, cudaEventRecord(b->ev[1], b->stream));
+        BCK(b, cudaEventSynchronize(b->ev[1]));
+        float ms = 0;
+        BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+        if (ms < best) { best = ms; best_k = kc; }
+    }
+    build_items(b, best_k);
+    b->tuned_kchunk = best_k;
+    b->tuned_sweep_ms = best / 4.0;
+    BCK(b, cudaEventRecord(b->ev[0], b->stream));
+    batch_check_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
+        b->d_insts, b->d_items, b->n_items, b->d_partials);
+    BLAUNCHED(b);
+    BCK(b, cudaEventRecord(b->ev[1], b->stream));
+    BCK(b, cudaEventSynchronize(b->ev[1]));
+    float cms = 0;
+    BCK(b, cudaEventElapsedTime(&cms, b->ev[0], b->ev[1]));
+    b->tuned_check_ms = cms;
+    int every = (int)std::ceil(cms / (0.03 * std::max(1e-6, b->tuned_sweep_ms)));
+    every = std::max(20, std::min(400, every + (every & 1)));
+    b->tuned_every = every;
+    // the tuning sweeps touched delta only; restore the descriptors (cur / active)
+    BCK(b, cudaMemcpy(b->d_insts, insts0.data(), insts0.size() * sizeof(BatchInst),
+                      cudaMemcpyHostToDevice));
+}
+
+}  // namespace
+
+extern "C" {
+
+rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** out) {
+    if (!out) return RFB_ERR_INVALID_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!hs || n < 1) { g_create_error = "need at least one handle"; return RFB_ERR_INVALID_ARG; }
+    for (int q = 0; q < n; ++q) {
+        if (!hs[q]) { g_create_error = "NULL handle"; return RFB_ERR_INVALID_ARG; }
+        if (hs[q]->device != hs[0]->device) { g_create_error = "handles on different devices"; return RFB_ERR_INVALID_ARG; }
+        if (hs[q]->nx % 4 != 0) { g_create_error = "batched lattices need nx % 4 == 0"; return RFB_ERR_INVALID_ARG; }
+        for (int p = 0; p < q; ++p)
+            if (hs[p] == hs[q]) { g_create_error = "a handle appears twice"; return RFB_ERR_INVALID_ARG; }
+    }
+    rfb_batch* b = new rfb_batch();
+    b->hs.assign(hs, hs + n);
+    b->device = hs[0]->device;
+    try {
+        BCK(b, cudaSetDevice(b->device));
+        // a stream of its own: the cycle is captured into a CUDA graph, which the legacy
+        // default stream does not allow
+        BCK(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        BCK(b, cudaMalloc((void**)&b->d_insts, n * sizeof(BatchInst)));
+        BCK(b, cudaMalloc((void**)&b->d_ctl, n * sizeof(BatchCtl)));
+        BCK(b, cudaMallocHost((void**)&b->h_ctl, n * sizeof(BatchCtl)));
+        BCK(b, cudaEventCreate(&b->ev[0]));
+        BCK(b, cudaEventCreate(&b->ev[1]));
+        int sms = 152, per = 4;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_sweep_kernel<true>, VBX * VBY, 0);
+        b->grid_blocks = sms * std::max(1, per);
+    } catch (Fail f) {
+        g_create_error = b->err;
+        rfb_soc_batch_destroy(b);
+        return f.st;
+    }
+    *out = b;
+    return RFB_OK;
+}
+
+rfb_status rfb_soc_batch_destroy(rfb_batch* b) {
+    if (!b) return RFB_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    void* ptrs[] = {b->d_insts, b->d_ctl, b->d_items, b->d_item_begin, b->d_partials};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return RFB_OK;
+}
+
+const char* rfb_soc_batch_last_error(const rfb_batch* b) {
+    return b ? b->err.c_str() : g_create_error.c_str();
+}
+
+rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* eta,
+                               const double* tol, const rfb_solve_opts* opts,
+                               rfb_solve_result* res, rfb_batch_info* info) {
+    if (!b) return RFB_ERR_INVALID_ARG;
+    b->err.clear();
+    if (!s_in || !eta || !tol) { bset_err(b, "s_in, eta and tol are required"); return RFB_ERR_INVALID_ARG; }
+    const int n = (int)b->hs.size();
+    rfb_solve_opts o;
+    if (!read_opts(b->hs[0], opts, &o)) { b->err = b->hs[0]->err; return RFB_ERR_INVALID_ARG; }
+    if (o.precision != RFB_PREC_MIXED) {
+        bset_err(b, "batched solves run FP32 correction sweeps: precision must be RFB_PREC_MIXED");
+        return RFB_ERR_UNSUPPORTED;
+    }
+    for (int q = 0; q < n; ++q) {
+        if (!(s_in[q] >= 0 && s_in[q] <= 1) || !std::isfinite(eta[q]) || !(tol[q] > 0)) {
+            bset_err(b, "lattice %d: need 0 <= s_in <= 1, finite eta, tol > 0", q);
+            return RFB_ERR_INVALID_ARG;
+        }
+    }
+    const bool local = o.dt_mode == RFB_DT_LOCAL;
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        (void)cudaGetLastError();
+        BCK(b, cudaSetDevice(b->device));
+        std::vector<BatchInst> insts(n);
+        std::vector<BatchCtl> ctl(n);
+        std::vector<OpPoint> ops(n);
+        for (int q = 0; q < n; ++q) {
+            rfb_soc_handle* h = b->hs[q];
+            OpPoint op = make_op(o, s_in[q], eta[q], false);
+            try {
+                prepare(h, op);
+                if (!h->have_state) init_state(h, false, op.s_in);
+                CK(h, cudaStreamSynchronize(h->stream));
+            } catch (Fail f) {
+                bset_err(b, "lattice %d: %s", q, h->err.c_str());
+                throw;
+            }
+            h->op = op;
+            h->s_converged = false;
+            ops[q] = op;
+            BatchInst& I = insts[q];
+            std::memset(&I, 0, sizeof I);
+            I.L = lattice(h);
+            I.C32 = make_coef<float>(h, op, true, false);
+            I.C64 = make_coef<double>(h, op, false, false);
+            I.delta[0] = h->d_delta[0];
+            I.delta[1] = h->d_delta[1];
+            I.r32 = h->d_r32;
+            I.s64[0] = h->d_s[0];
+            I.s64[1] = h->d_s[1];
+            I.cfl = (float)op.cfl;
+            I.active = 1;
+            I.cur = h->s_cur;
+            BatchCtl& k = ctl[q];
+            std::memset(&k, 0, sizeof k);
+            const double h3 = h->h * h->h * h->h;
+            const double Q = op.beta * h->sum_w_in * h->h * h->h;
+            k.tol = tol[q];
+            k.tau = Q > 0 ? (double)h->n_fluid * h3 / Q : std::pow(h->nz * h->h, 2) / h->D;
+            k.n_unknown = (double)h->n_fluid;
+        }
+        BCK(b, cudaMemcpy(b->d_insts, insts.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(BatchCtl), cudaMemcpyHostToDevice));
+        if (!b->tuned_kchunk) autotune(b, local, insts);
+        else build_items(b, b->tuned_kchunk);
+        const int every = o.check_every > 0 ? std::max(2, o.check_every + (o.check_every & 1))
+                                            : b->tuned_every;
+        // residual of the starting states (forcing for the first cycle)
+        batch_check(b, false, 0);
+        BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl), cudaMemcpyDeviceToHost,
+                               b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        // capture one cycle as a CUDA graph (rebuilt when the cycle length changes)
+        if (!b->exec || b->exec_every != every) {
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+            cudaGraph_t g = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t l0 = b->launches;
+            try {
+                batch_cycle(b, every, local);
+            } catch (Fail) {
+                cudaStreamEndCapture(b->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            b->launches = l0;   // counted when replayed
+            BCK(b, cudaStreamEndCapture(b->stream, &g));
+            BCK(b, cudaGraphInstantiate(&b->exec, g, 0));
+            cudaGraphDestroy(g);
+            b->exec_every = every;
+        }
+        int64_t done = 0;
+        rfb_status st = RFB_OK;
+        auto all_done = [&]() {
+            for (int q = 0; q < n; ++q)
+                if (!b->h_ctl[q].converged && !b->h_ctl[q].nonfinite) return false;
+            return true;
+        };
+        while (!all_done()) {
+            if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            BCK(b, cudaGraphLaunch(b->exec, b->stream));
+            b->launches += every + 3;
+            BCK(b, cudaStreamSynchronize(b->stream));
+            done += every;
+        }
+        BCK(b, cudaMemcpy(insts.data(), b->d_insts, n * sizeof(BatchInst), cudaMemcpyDeviceToHost));
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (int q = 0; q < n; ++q) {
+            rfb_soc_handle* h = b->hs[q];
+            h->s_cur = insts[q].cur;
+            h->have_state = true;
+            h->s_converged = b->h_ctl[q].converged != 0;
+            if (b->h_ctl[q].nonfinite) st = RFB_ERR_NONFINITE;
+            if (res) {
+                rfb_solve_result r{};
+                fill_result(h, ops[q], &r, h->n_fluid, b->h_ctl[q].sums);
+                r.residual = b->h_ctl[q].residual;
+                r.sweeps = b->h_ctl[q].sweeps;
+                r.time_ms = ms;
+                res[q] = r;
+            }
+        }
+        if (info) {
+            info->kchunk = b->tuned_kchunk;
+            info->sweeps_per_cycle = every;
+            info->n_items = b->n_items;
+            info->grid_blocks = b->grid_blocks;
+            info->sweep_ms = b->tuned_sweep_ms;
+            info->check_ms = b->tuned_check_ms;
+            info->cycles = done / every;
+            info->time_ms = ms;
+            info->launches = b->launches;
+        }
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+}  // extern "C"

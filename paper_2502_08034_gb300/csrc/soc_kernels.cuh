@@ -194,19 +194,20 @@ template <bool LOCAL_DT>
 __global__ void __launch_bounds__(VBX * VBY)
 sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
                 float* __restrict__ s_out, const float* __restrict__ force, float cfl,
-                int kchunk) {
-    __shared__ float tB[8];
-    {
-        const int t_ = threadIdx.y * VBX + threadIdx.x;
-        if (t_ < 8) tB[t_] = C.rB[t_];
-        __syncthreads();
-    }
-    const int i0 = 4 * (blockIdx.x * VBX + threadIdx.x);
-    const int j = blockIdx.y * VBY + threadIdx.y;
+                int kchunk);
+
+// One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
+// kb .. ke-1. tB: the block's shared copy of the per-n_wall reaction slope.
+template <bool LOCAL_DT>
+__device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float>& C,
+                                              const float* tB, const float* __restrict__ s,
+                                              float* __restrict__ s_out,
+                                              const float* __restrict__ force, float cfl,
+                                              int bx, int by, int kb, int ke) {
+    const int i0 = 4 * (bx * VBX + threadIdx.x);
+    const int j = by * VBY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
-    const int kb = blockIdx.z * kchunk;
-    const int ke = min(kb + kchunk, nz);
     const bool has_xm = i0 > 0, has_xp = i0 + 4 < nx;
     const bool has_ym = j > 0, has_yp = j + 1 < ny;
     const int64_t off_xm = has_xm ? -1 : 0, off_xp = has_xp ? 4 : 3;
@@ -287,6 +288,90 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
     }
 }
 
+template <bool LOCAL_DT>
+__global__ void __launch_bounds__(VBX * VBY)
+sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
+                float* __restrict__ s_out, const float* __restrict__ force, float cfl,
+                int kchunk) {
+    __shared__ float tB[8];
+    {
+        const int t_ = threadIdx.y * VBX + threadIdx.x;
+        if (t_ < 8) tB[t_] = C.rB[t_];
+        __syncthreads();
+    }
+    const int kb = blockIdx.z * kchunk;
+    sweep32v_tile<LOCAL_DT>(L, C, tB, s, s_out, force, cfl, blockIdx.x, blockIdx.y, kb,
+                            min(kb + kchunk, L.nz));
+}
+
+// ---------------------------------------------------------------------------------
+// Batches: many lattices of uneven size advanced by one persistent launch per sweep.
+// Every lattice is cut into work items (a 128 x VBY column tile times a chunk of z
+// planes, the block shape of the single-lattice kernels); a grid of resident blocks walks
+// the item list in a fixed round-robin order. Items of lattices that have converged are
+// skipped (their `active` flag lives in device memory, so a captured CUDA graph keeps
+// working as lattices drop out).
+// ---------------------------------------------------------------------------------
+struct BatchInst {
+    Lattice L;
+    Coef<float> C32;       // correction sweep coefficients (homogeneous operator)
+    Coef<double> C64;      // FP64 check coefficients (full operator)
+    float* delta[2];
+    float* r32;
+    double* s64[2];
+    float cfl;
+    int active;            // 1 while the lattice has not converged
+    int cur;               // which s64 buffer holds the state
+    int pad_;
+};
+
+struct BatchItem {
+    int inst;
+    int bx, by;
+    int kb, ke;
+};
+
+template <bool LOCAL_DT>
+__global__ void __launch_bounds__(VBX * VBY)
+batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
+                   int n_items, int parity) {
+    __shared__ float tB[8];
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const BatchInst* I = insts + it.inst;
+        if (!I->active) continue;   // uniform over the block
+        // copies in registers: read through the descriptor, every field would be reloaded
+        // after each store (the compiler cannot rule out aliasing)
+        const Lattice L = I->L;
+        const Coef<float> C = I->C32;
+        const float* src = I->delta[parity];
+        float* dst = I->delta[parity ^ 1];
+        const float* r32 = I->r32;
+        const float cfl = I->cfl;
+        __syncthreads();
+        if (threadIdx.y * VBX + threadIdx.x < 8) tB[threadIdx.y * VBX + threadIdx.x] =
+            C.rB[threadIdx.y * VBX + threadIdx.x];
+        __syncthreads();
+        sweep32v_tile<LOCAL_DT>(L, C, tB, src, dst, r32, cfl, it.bx, it.by, it.kb, it.ke);
+    }
+}
+
+// delta := 0 on both buffers of every active lattice (start of a correction cycle)
+__global__ void batch_zero_kernel(const BatchInst* __restrict__ insts, int n_inst) {
+    for (int q = 0; q < n_inst; ++q) {
+        const BatchInst& I = insts[q];
+        if (!I.active) continue;
+        const int64_t n = (int64_t)I.L.nxny * I.L.nz;
+        float4* a = reinterpret_cast<float4*>(I.delta[0]);
+        float4* b = reinterpret_cast<float4*>(I.delta[1]);
+        for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n / 4;
+             c += (int64_t)gridDim.x * blockDim.x) {
+            a[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            b[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // Block reduction helpers (fixed order => deterministic)
 // ---------------------------------------------------------------------------------
@@ -330,19 +415,16 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NRED], double* 
 // WRITE_R: RHS is stored as FP32 forcing for the next correction sweeps.
 // ---------------------------------------------------------------------------------
 template <bool FUSE, bool WRITE_R>
-__global__ void __launch_bounds__(BX * BY)
-check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
-             const float* __restrict__ delta, double* __restrict__ s_new,
-             float* __restrict__ r_out, double* __restrict__ partials, int kchunk) {
-    RFB_LOAD_TABLES(double, C)
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    double acc[NRED];
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+__device__ __forceinline__ void check_tile(const Lattice& L, const Coef<double>& C,
+                                           const double* tA, const double* tB,
+                                           const double* __restrict__ s,
+                                           const float* __restrict__ delta,
+                                           double* __restrict__ s_new,
+                                           float* __restrict__ r_out, double (&acc)[NRED],
+                                           int bx, int by, int kb, int ke) {
+    const int i = bx * BX + threadIdx.x;
+    const int j = by * BY + threadIdx.y;
     if (i < L.nx && j < L.ny) {
-        const int kb = blockIdx.z * kchunk;
-        const int ke = min(kb + kchunk, L.nz);
         const int nx = L.nx, nxny = L.nxny;
         auto val = [&](int64_t cc) -> double {
             return FUSE ? s[cc] + (double)delta[cc] : s[cc];
@@ -399,9 +481,116 @@ check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
             wL = wH;
         }
     }
+}
+
+template <bool FUSE, bool WRITE_R>
+__global__ void __launch_bounds__(BX * BY)
+check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
+             const float* __restrict__ delta, double* __restrict__ s_new,
+             float* __restrict__ r_out, double* __restrict__ partials, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    const int kb = blockIdx.z * kchunk;
+    check_tile<FUSE, WRITE_R>(L, C, tA, tB, s, delta, s_new, r_out, acc, blockIdx.x,
+                              blockIdx.y, kb, min(kb + kchunk, L.nz));
     const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
                         ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
     block_reduce_store(acc, partials + bid * NRED);
+}
+
+// Batched FP64 check (FUSE: state = s64[cur] + delta[0] written to s64[cur ^ 1], FP32
+// forcing refreshed), one work item per loop trip; partial sums per item. Items of
+// inactive lattices write zero partials.
+template <bool FUSE>
+__global__ void __launch_bounds__(BX * BY)
+batch_check_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
+                   int n_items, double* __restrict__ partials) {
+    __shared__ double tA[8], tB[8];
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const BatchInst* I = insts + it.inst;
+        double acc[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+        const int active = I->active;
+        const Lattice L = I->L;
+        const Coef<double> C = I->C64;
+        const int cur = I->cur;
+        const double* s = I->s64[cur];
+        double* s_new = I->s64[cur ^ 1];
+        const float* d0 = I->delta[0];
+        float* r32 = I->r32;
+        __syncthreads();
+        const int t = threadIdx.y * BX + threadIdx.x;
+        if (t < 8) { tA[t] = C.rA[t]; tB[t] = C.rB[t]; }
+        __syncthreads();
+        if (active) {
+            // a work item spans VBX * 4 = 4 * BX cells in x
+            for (int q = 0; q < 4; ++q)
+                check_tile<FUSE, true>(L, C, tA, tB, s, d0, s_new, r32, acc, 4 * it.bx + q,
+                                       it.by, it.kb, it.ke);
+        }
+        block_reduce_store(acc, partials + (int64_t)w * NRED);
+    }
+}
+
+// Per-lattice sums of the item partials (one block per lattice, fixed order), then the
+// convergence bookkeeping: residual = tau sqrt(sum r^2 / n_unknown); a lattice whose
+// residual is <= tol (or that produced a non-finite value) becomes inactive. `fused`:
+// the check just wrote s64[cur ^ 1], so active lattices flip cur first.
+struct BatchCtl {
+    double tol;
+    double tau;
+    double n_unknown;
+    double residual;
+    double sums[NRED];
+    int64_t sweeps;
+    int converged;
+    int nonfinite;
+};
+
+__global__ void __launch_bounds__(256)
+batch_finalize_kernel(BatchInst* __restrict__ insts, const int* __restrict__ item_begin,
+                      const double* __restrict__ partials, BatchCtl* __restrict__ ctl,
+                      int fused, int sweeps_done) {
+    __shared__ double sh[256];
+    const int q_inst = blockIdx.x;
+    BatchInst& I = insts[q_inst];
+    const int was_active = I.active;
+    __syncthreads();
+    if (!was_active) return;   // uniform per block
+    const int b0 = item_begin[q_inst], b1 = item_begin[q_inst + 1];
+    for (int q = 0; q < NRED; ++q) {
+        const bool is_max = (q == NRED - 1);
+        double a = 0.0;
+        for (int b = b0 + threadIdx.x; b < b1; b += 256) {
+            const double x = partials[(int64_t)b * NRED + q];
+            a = is_max ? fmax(a, x) : a + x;
+        }
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int sft = 128; sft > 0; sft >>= 1) {
+            if (threadIdx.x < sft)
+                sh[threadIdx.x] = is_max ? fmax(sh[threadIdx.x], sh[threadIdx.x + sft])
+                                         : sh[threadIdx.x] + sh[threadIdx.x + sft];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) ctl[q_inst].sums[q] = sh[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        BatchCtl& k = ctl[q_inst];
+        if (fused) I.cur ^= 1;
+        k.sweeps += sweeps_done;
+        k.residual = k.n_unknown > 0 ? k.tau * sqrt(k.sums[0] / k.n_unknown) : 0.0;
+        k.nonfinite = k.sums[6] > 0;
+        if (k.residual <= k.tol || k.nonfinite) {
+            k.converged = !k.nonfinite;
+            I.active = 0;
+        }
+    }
 }
 
 // Largest diagonal of -L over unknown fluid cells (for dt = cfl / max d), and the

@@ -251,10 +251,12 @@ __global__ void k_faces(G g, const double* x, double* U, double* V, double* W, d
             double v = 0.0;
             bool face = false;
             if (k == 0) {
-                if (fl(g, ij)) { v = dl - 2.0 * x[ij]; face = true; }
+                // phi <= 1 in the exact solution, so inflow is >= 0; a negative value
+                // here is CG rounding in a stagnant pocket
+                if (fl(g, ij)) { v = fmax(dl - 2.0 * x[ij], 0.0); face = true; }
             } else if (k == nz) {
                 const int64_t c = ij + g.nxny * (nz - 1);
-                if (fl(g, c)) { v = dl + 2.0 * x[c]; face = true; }
+                if (fl(g, c)) { v = fmax(dl + 2.0 * x[c], 0.0); face = true; }
             } else {
                 const int64_t c0 = ij + g.nxny * (k - 1);
                 if (fl(g, c0) && fl(g, c0 + g.nxny)) {

@@ -85,6 +85,13 @@ def lib():
         L.rfb_soc_reset_state.argtypes = [H]
         L.rfb_soc_upsample.argtypes = [H, H]
         L.rfb_soc_set_area_mult.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(H)]
+        L.rfb_soc_batch_solve.argtypes = [H, POINTER(c_double), POINTER(c_double),
+                                          POINTER(c_double), POINTER(SolveOpts),
+                                          POINTER(SolveResult), POINTER(BatchInfo)]
+        L.rfb_soc_batch_destroy.argtypes = [H]
+        L.rfb_soc_batch_last_error.argtypes = [H]
+        L.rfb_soc_batch_last_error.restype = c_char_p
         L.rfb_soc_adjoint.argtypes = [H, c_int, c_double, POINTER(SolveOpts), c_void_p,
                                       POINTER(c_double), c_int, POINTER(SolveResult)]
         L.rfb_soc_info.argtypes = [H, POINTER(c_int64), POINTER(c_int64)]
@@ -94,7 +101,8 @@ def lib():
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
                      "rfb_soc_current_noalloc", "rfb_soc_upsample", "rfb_soc_set_area_mult",
-                     "rfb_soc_adjoint"):
+                     "rfb_soc_adjoint", "rfb_soc_batch_create", "rfb_soc_batch_solve",
+                     "rfb_soc_batch_destroy"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -271,6 +279,60 @@ class Solver:
         if getattr(self, "h", None):
             lib().rfb_soc_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("kchunk", c_int32), ("sweeps_per_cycle", c_int32), ("n_items", c_int32),
+                ("grid_blocks", c_int32), ("sweep_ms", c_double), ("check_ms", c_double),
+                ("cycles", c_int64), ("time_ms", c_double), ("launches", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Batch:
+    """rfb_soc_batch_*: several Solvers advanced together (mixed precision)."""
+
+    def __init__(self, solvers):
+        L = lib()
+        self.solvers = list(solvers)
+        arr = (c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        b = c_void_p()
+        st = L.rfb_soc_batch_create(arr, len(self.solvers), byref(b))
+        if st != RFB_OK:
+            raise RfbError(st, L.rfb_soc_batch_last_error(None).decode())
+        self.b = b
+
+    def solve(self, s_in, eta, tol, allow_not_converged=False, **opts):
+        n = len(self.solvers)
+        opts.setdefault("precision", "mixed")
+        D = c_double * n
+        res = (SolveResult * n)()
+        info = BatchInfo()
+        o = make_opts(**opts)
+        st = lib().rfb_soc_batch_solve(self.b, D(*map(float, s_in)), D(*map(float, eta)),
+                                       D(*map(float, tol)), byref(o), res, byref(info))
+        ok = (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,)
+        if st not in ok:
+            raise RfbError(st, lib().rfb_soc_batch_last_error(self.b).decode())
+        return [r.as_dict() for r in res], info.as_dict()
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().rfb_soc_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

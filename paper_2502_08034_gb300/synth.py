@@ -246,6 +246,9 @@ def potential_flow(solid: np.ndarray, h: float, u_mean: float, tol: float = 1e-1
     U[:, :, 1:-1] = -(x[:, :, 1:] - x[:, :, :-1]) * gx / h * sigma
     V[:, 1:-1, :] = -(x[:, 1:, :] - x[:, :-1, :]) * gy / h * sigma
     W = wz * sigma
+    # inflow / outflow through the inlet and outlet planes is >= 0 in the exact solution
+    W[0] = torch.clamp(W[0], min=0.0)
+    W[-1] = torch.clamp(W[-1], min=0.0)
     div = (U[:, :, 1:] - U[:, :, :-1]) + (V[:, 1:, :] - V[:, :-1, :]) + (W[1:] - W[:-1])
     div = div * fd
     info = {"cg_iters": it, "max_div_rel": float(div.abs().max()) / u_mean,
@@ -389,6 +392,45 @@ def adjoint_case(dims=(128, 128, 256), seed=4, **kw) -> Case:
     s_in = 0.5."""
     return build_case("fiber%dx%dx%d_adjoint" % tuple(dims), dims, 0.80, 8.0, seed, 0.01,
                       -0.10, 0.5, 1e-12, **kw)
+
+
+def batch_instance_params(i: int, n_x_choices=tuple(range(64, 193, 16))):
+    """Geometry and operating point of lattice i of the batched workload.
+
+    Lattice 0 is 64^3 and lattice 1 is 192x192x384; others draw (SplitMix64, seed
+    3000 + i, in this order) nx = ny uniform over {64, 80, ..., 192},
+    nz = 16 round(nx U[1, 2] / 16) clipped to [64, 384], porosity U[0.75, 0.90]; then
+    for every lattice the operating point: mean velocity log-uniform in [0.1, 5] cm/s,
+    s_in U[0.1, 0.9], eta U[-0.2, -0.02] V. Fibers (d = 8 cells) use their own stream
+    (generate_fibers with seed 3000 + i)."""
+    rng = SplitMix64(3000 + i)
+    if i == 0:
+        nx, nz = 64, 64
+        por = rng.uniform(0.75, 0.90)
+    elif i == 1:
+        nx, nz = 192, 384
+        por = rng.uniform(0.75, 0.90)
+    else:
+        nx = n_x_choices[min(int(rng.uniform() * len(n_x_choices)), len(n_x_choices) - 1)]
+        nz = int(16 * round(nx * rng.uniform(1.0, 2.0) / 16))
+        nz = max(64, min(384, nz))
+        por = rng.uniform(0.75, 0.90)
+    u = 10 ** rng.uniform(math.log10(0.001), math.log10(0.05))
+    s_in = rng.uniform(0.1, 0.9)
+    eta = rng.uniform(-0.2, -0.02)
+    return dict(dims=(nx, nx, nz), porosity=por, u_mean=u, s_in=s_in, eta=eta, seed=3000 + i)
+
+
+def batch_cases(n: int = 48, flow_device: str = "cpu", tol: float = 1e-8, scale: int = 1):
+    """The batched workload (``scale`` > 1 divides every dimension, for tests)."""
+    out = []
+    for i in range(n):
+        q = batch_instance_params(i)
+        dims = tuple(max(16, d // scale) for d in q["dims"])
+        out.append(build_case("batch%02d_%dx%dx%d" % ((i,) + dims), dims, q["porosity"],
+                              8.0 / scale if scale > 1 else 8.0, q["seed"], q["u_mean"],
+                              q["eta"], q["s_in"], tol, flow_device=flow_device))
+    return out
 
 
 def fiber_channel_case(dims=(48, 48, 96), porosity=0.80, diameter=8.0, seed=1,
