@@ -309,6 +309,11 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
                                const double* tol, const rfb_solve_opts* opts,
                                rfb_solve_result* res, rfb_batch_info* info);
 
+/* Queue the batch's work on this cudaStream_t (a created stream, not the legacy or
+ * per-thread default stream: the cycle is captured into a CUDA graph). By default the
+ * batch creates a non-blocking stream of its own. */
+rfb_status rfb_soc_batch_set_stream(rfb_batch* b, void* cuda_stream);
+
 /* Last error detail of the batch (b = NULL: of the last failed rfb_soc_batch_create). */
 const char* rfb_soc_batch_last_error(const rfb_batch* b);
 

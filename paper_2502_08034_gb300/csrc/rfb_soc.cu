@@ -1105,6 +1105,7 @@ struct rfb_batch {
     std::vector<rfb_soc_handle*> hs;
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;
     BatchInst* d_insts = nullptr;
     BatchCtl* d_ctl = nullptr;
     BatchCtl* h_ctl = nullptr;          // pinned
@@ -1114,7 +1115,9 @@ struct rfb_batch {
     int n_items = 0;
     int items_kchunk = -1;
     std::vector<int> item_begin;
-    int grid_blocks = 0;
+    int grid_blocks = 0;             // blocks of the sweep launch (autotuned)
+    int grid_blocks_resident = 0;    // SMs x resident blocks per SM
+    int tuned_grid = 0;
     // autotuner results
     int tuned_kchunk = 0;
     int tuned_every = 0;
@@ -1229,21 +1232,30 @@ void batch_cycle(rfb_batch* b, int every, bool local) {
 // persistent sweeps of the whole batch (CUDA events) and keep the fastest; then set the
 // sweeps per cycle so that the FP64 check costs about 3% of a cycle.
 void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0) {
+    // candidates: z-chunk of the items x grid size (1x / 2x the resident blocks, walking
+    // the item list persistently, or one block per item)
     const int cands[] = {8, 16, 32, 64};
+    const int resident = b->grid_blocks_resident;
     float best = 1e30f;
-    int best_k = 16;
+    int best_k = 16, best_grid = resident;
     for (int kc : cands) {
         build_items(b, kc);
-        batch_sweeps(b, 2, local);   // warm-up
-        BCK(b, cudaEventRecord(b->ev[0], b->stream));
-        batch_sweeps(b, 4, local);
-        BCK(b, cudaEventRecord(b->ev[1], b->stream));
-        BCK(b, cudaEventSynchronize(b->ev[1]));
-        float ms = 0;
-        BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
-        if (ms < best) { best = ms; best_k = kc; }
+        const int grids[] = {resident, 2 * resident, b->n_items};
+        for (int gsz : grids) {
+            b->grid_blocks = std::max(1, std::min(gsz, b->n_items));
+            batch_sweeps(b, 2, local);   // warm-up
+            BCK(b, cudaEventRecord(b->ev[0], b->stream));
+            batch_sweeps(b, 4, local);
+            BCK(b, cudaEventRecord(b->ev[1], b->stream));
+            BCK(b, cudaEventSynchronize(b->ev[1]));
+            float ms = 0;
+            BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+            if (ms < best) { best = ms; best_k = kc; best_grid = gsz; }
+        }
     }
     build_items(b, best_k);
+    b->grid_blocks = std::max(1, std::min(best_grid, b->n_items));
+    b->tuned_grid = best_grid;
     b->tuned_kchunk = best_k;
     b->tuned_sweep_ms = best / 4.0;
     BCK(b, cudaEventRecord(b->ev[0], b->stream));
@@ -1287,6 +1299,7 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
         // a stream of its own: the cycle is captured into a CUDA graph, which the legacy
         // default stream does not allow
         BCK(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
         BCK(b, cudaMalloc((void**)&b->d_insts, n * sizeof(BatchInst)));
         BCK(b, cudaMalloc((void**)&b->d_ctl, n * sizeof(BatchCtl)));
         BCK(b, cudaMallocHost((void**)&b->h_ctl, n * sizeof(BatchCtl)));
@@ -1296,6 +1309,7 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_sweep_kernel<true>, VBX * VBY, 0);
         b->grid_blocks = sms * std::max(1, per);
+        b->grid_blocks_resident = b->grid_blocks;
     } catch (Fail f) {
         g_create_error = b->err;
         rfb_soc_batch_destroy(b);
@@ -1316,7 +1330,7 @@ rfb_status rfb_soc_batch_destroy(rfb_batch* b) {
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
-    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->stream && b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return RFB_OK;
 }
@@ -1390,7 +1404,10 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         BCK(b, cudaMemcpy(b->d_insts, insts.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice));
         BCK(b, cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(BatchCtl), cudaMemcpyHostToDevice));
         if (!b->tuned_kchunk) autotune(b, local, insts);
-        else build_items(b, b->tuned_kchunk);
+        else {
+            build_items(b, b->tuned_kchunk);
+            b->grid_blocks = std::max(1, std::min(b->tuned_grid, b->n_items));
+        }
         const int every = o.check_every > 0 ? std::max(2, o.check_every + (o.check_every & 1))
                                             : b->tuned_every;
         // residual of the starting states (forcing for the first cycle)
@@ -1466,3 +1483,23 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
 }
 
 }  // extern "C"
+
+extern "C" rfb_status rfb_soc_batch_set_stream(rfb_batch* b, void* stream) {
+    if (!b) return RFB_ERR_INVALID_ARG;
+    b->err.clear();
+    if (stream == nullptr || stream == (void*)cudaStreamLegacy ||
+        stream == (void*)cudaStreamPerThread) {
+        bset_err(b, "a batch needs a created stream (its cycle is captured into a CUDA graph)");
+        return RFB_ERR_INVALID_ARG;
+    }
+    try {
+        BCK(b, cudaSetDevice(b->device));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->own_stream) { cudaStreamDestroy(b->stream); b->own_stream = false; }
+        b->stream = (cudaStream_t)stream;
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
+}

@@ -332,7 +332,7 @@ struct BatchItem {
 };
 
 template <bool LOCAL_DT>
-__global__ void __launch_bounds__(VBX * VBY)
+__global__ void __launch_bounds__(VBX * VBY, 3)
 batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
                    int n_items, int parity) {
     __shared__ float tB[8];
@@ -350,7 +350,7 @@ batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         const float cfl = I->cfl;
         __syncthreads();
         if (threadIdx.y * VBX + threadIdx.x < 8) tB[threadIdx.y * VBX + threadIdx.x] =
-            C.rB[threadIdx.y * VBX + threadIdx.x];
+            I->C32.rB[threadIdx.y * VBX + threadIdx.x];
         __syncthreads();
         sweep32v_tile<LOCAL_DT>(L, C, tB, src, dst, r32, cfl, it.bx, it.by, it.kb, it.ke);
     }
@@ -504,7 +504,7 @@ check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
 // forcing refreshed), one work item per loop trip; partial sums per item. Items of
 // inactive lattices write zero partials.
 template <bool FUSE>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 3)
 batch_check_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
                    int n_items, double* __restrict__ partials) {
     __shared__ double tA[8], tB[8];
@@ -524,7 +524,7 @@ batch_check_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         float* r32 = I->r32;
         __syncthreads();
         const int t = threadIdx.y * BX + threadIdx.x;
-        if (t < 8) { tA[t] = C.rA[t]; tB[t] = C.rB[t]; }
+        if (t < 8) { tA[t] = I->C64.rA[t]; tB[t] = I->C64.rB[t]; }
         __syncthreads();
         if (active) {
             // a work item spans VBX * 4 = 4 * BX cells in x

@@ -90,6 +90,8 @@ def lib():
                                           POINTER(c_double), POINTER(SolveOpts),
                                           POINTER(SolveResult), POINTER(BatchInfo)]
         L.rfb_soc_batch_destroy.argtypes = [H]
+        L.rfb_soc_batch_set_stream.argtypes = [H, c_void_p]
+        L.rfb_soc_batch_set_stream.restype = c_int
         L.rfb_soc_batch_last_error.argtypes = [H]
         L.rfb_soc_batch_last_error.restype = c_char_p
         L.rfb_soc_adjoint.argtypes = [H, c_int, c_double, POINTER(SolveOpts), c_void_p,
@@ -314,6 +316,11 @@ class Batch:
         if st != RFB_OK:
             raise RfbError(st, L.rfb_soc_batch_last_error(None).decode())
         self.b = b
+
+    def set_stream(self, stream):
+        st = lib().rfb_soc_batch_set_stream(self.b, _stream_ptr(stream))
+        if st != RFB_OK:
+            raise RfbError(st, lib().rfb_soc_batch_last_error(self.b).decode())
 
     def solve(self, s_in, eta, tol, allow_not_converged=False, **opts):
         n = len(self.solvers)
