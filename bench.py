@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dims", default="256,256,512")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batch48"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "batch48", "upsample"],
                     help="mixed: the 256x256x512 mixed-precision solve (default); batch48: the "
-                         "48-lattice batched workload")
+                         "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
+                         "512x512x1024 iterative upsampling")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -53,6 +54,17 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_over_ranks(dist, elapsed_ms, units, device="cpu"):
+    """Max of the timed region and sum of the cell updates over ranks (replicas)."""
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def make_case(dims, device):
@@ -265,6 +277,81 @@ def run_batch(args):
         s.close()
 
 
+def upsample_chain(solvers, cases, tol, umt=True):
+    """Solve the coarsest level cold, then prolong and solve each finer level (mixed)."""
+    out = []
+    for q, (sv, c) in enumerate(zip(solvers, cases)):
+        if q == 0:
+            sv.reset_state()
+        else:
+            sv.upsample_from(solvers[q - 1])
+        out.append(sv.solve(c.s_in, c.eta, tol, precision="mixed"))
+    u = solvers[-1].umt(tol, precision="mixed") if umt else None
+    return out, u
+
+
+def run_upsample(args):
+    """The largest single-GPU run: the same analytic fibers at 128x128x256 (h = 5 um),
+    256x256x512 and 512x512x1024 (h = 1.25 um, d = 8, porosity 0.82), 1 cm/s,
+    eta = -0.10 V, s_in = 0.5; each level warm-started from the prolonged coarser one."""
+    import torch
+
+    from paper_2502_08034_gb300 import _build, rfb, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    t0 = time.time()
+    cases = synth.multilevel_cases((512, 512, 1024), 3, 0.82, 8.0, 5, 0.01, -0.10, 0.5,
+                                   args.tol, flow_device="cuda:%d" % local)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    solvers = [rfb.Solver.from_case(c, device_inputs=True, stream=stream) for c in cases]
+    for _ in range(args.warmup):
+        upsample_chain(solvers, cases, args.tol, umt=False)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    runs = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            runs.append(upsample_chain(solvers, cases, args.tol, umt=False))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1)
+    levels, _ = runs[-1]
+    cells = sum(c.n * r["sweeps"] for res, _ in runs for c, r in zip(cases, res))
+    fine = solvers[-1]
+    u_mt, ru = fine.umt(args.tol, precision="mixed")
+    # cold start of the finest level for comparison
+    fine.reset_state()
+    cold = fine.solve(cases[-1].s_in, cases[-1].eta, args.tol, precision="mixed")
+    peak, peak_kind = peak_hbm()
+    N = cases[-1].n
+    fr = levels[-1]
+    achieved = SWEEP_BYTES_PER_CELL * N * fr["sweeps"] / (fr["sweep_ms"] / 1e3) / 1e9
+    out = {"metric": METRIC, "value": cells / (elapsed / 1e3) / 1e9, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "upsample_512x512x1024", "levels": [list(c.dims) for c in cases],
+                      "porosity_finest": round(cases[-1].porosity, 4), "tol": args.tol},
+           "levels": [{"dims": list(c.dims), "sweeps": r["sweeps"], "time_ms": r["time_ms"],
+                       "residual": r["residual"]} for c, r in zip(cases, levels)],
+           "finest": {"I_tot_A": fr["I_tot"], "U": fr["U"],
+                      "mass_balance_rel": fr["mass_balance_rel"], "U_mt": u_mt,
+                      "U_mt_sweeps": ru["sweeps"]},
+           "cold_start_finest": {"sweeps": cold["sweeps"], "time_ms": cold["time_ms"]},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "sweep32v_kernel on the finest level",
+                        "peak_kind": peak_kind},
+           "clocks": clk.summary(), "setup_s": setup_s}
+    print(json.dumps(out), flush=True)
+    for s in solvers:
+        s.close()
+
+
 def main():
     args = parse()
     dims = tuple(int(x) for x in args.dims.split(","))
@@ -273,6 +360,9 @@ def main():
         return
     if args.workload == "batch48":
         run_batch(args)
+        return
+    if args.workload == "upsample":
+        run_upsample(args)
         return
     import numpy as np
     import torch
@@ -322,12 +412,9 @@ def main():
     clocks = clk.summary()
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = sv.kernel_launches - launches0
-    t_local = torch.tensor([elapsed_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_local.item())
     sweeps = sum(r["sweeps"] for r in results)
-    value = world * N * sweeps / (elapsed_ms / 1e3) / 1e9
+    elapsed_ms, units = reduce_over_ranks(dist, elapsed_ms, N * sweeps, device="cuda")
+    value = units / (elapsed_ms / 1e3) / 1e9
     sweep_ms = sum(r["sweep_ms"] for r in results)
     peak, peak_kind = peak_hbm()
     achieved = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9

@@ -85,7 +85,11 @@ typedef struct rfb_solve_opts {
     double cfl;             /* C_CFL in (0, 1] (default 0.4) */
     double velocity_scale;  /* beta >= 0: every face velocity is multiplied by it (1) */
     int64_t max_sweeps;     /* give up after this many sweeps (0 = 50,000,000) */
-    int32_t reserved[8];    /* must be zero */
+    int32_t fp32_kernel;    /* RFB_PREC_MIXED only: 0 = chosen by timing both on the
+                               lattice (once per handle), 1 = one sweep per launch,
+                               2 = two sweeps per pass (TMA-staged, temporally blocked;
+                               needs nx % 16 == 0 and no area multiplier) */
+    int32_t reserved[7];    /* must be zero */
 } rfb_solve_opts;
 
 typedef struct rfb_solve_result {

@@ -3,7 +3,9 @@
 // management. All kernels live in soc_kernels.cuh.
 #include "rfb_soc.h"
 #include "soc_kernels.cuh"
+#include "sweep_tb.cuh"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,6 +83,14 @@ struct rfb_soc_handle {
     int64_t nblocks = 0;
     int vkchunk = 8;          // vectorised FP32 sweep (nx % 4 == 0)
     dim3 vgrid, vblock;
+    // temporally blocked FP32 sweep (nx % 16 == 0, no area multiplier)
+    int tb_mode = -1;         // -1 not chosen yet, 0 one-sweep kernel, 1 two-sweep passes
+    int tb_kchunk = 0;
+    dim3 tb_grid;
+    bool tm_ready = false;
+    CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f;
+    float* tm_delta_ptr[2] = {nullptr, nullptr};
+    double tb_tuned_plain_ms = 0, tb_tuned_tb_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -269,32 +279,164 @@ void sweeps64(rfb_soc_handle* h, const OpPoint& op, bool umt, int64_t n) {
 
 // n FP32 correction sweeps delta <- delta + dt (L delta + r), starting from delta = 0.
 // The result is left in d_delta[0].
-void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n) {
+// ---- temporally blocked FP32 passes (TMA tensor maps, see sweep_tb.cuh)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool tb_eligible(const rfb_soc_handle* h) {
+    // 16-byte TMA rows for the 8-bit mask; the blocked kernel streams no area multiplier
+    return (h->nx % 16) == 0 && h->d_m32 == nullptr && h->nz >= 2;
+}
+
+void tb_encode(rfb_soc_handle* h, CUtensorMap* m, CUtensorMapDataType t, size_t esize, void* ptr,
+               int planes) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        CK(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                               cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) {
+            set_err(h, "cuTensorMapEncodeTiled is not available from the driver");
+            throw Fail{RFB_ERR_CUDA};
+        }
+        fn = (EncodeTiledFn)p;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->nx * esize, (cuuint64_t)h->nxny * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)TB_BW, (cuuint32_t)TB_BH, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, t, 3, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_err(h, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        throw Fail{RFB_ERR_CUDA};
+    }
+}
+
+void tb_prepare(rfb_soc_handle* h) {
+    if (h->tm_ready) return;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[0]) {
+        CK(h, cudaFuncSetAttribute(sweep32tb_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
+        attr_set[0] = true;
+    }
+    if (!attr_set[1]) {
+        CK(h, cudaFuncSetAttribute(sweep32tb_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
+        attr_set[1] = true;
+    }
+    for (int q = 0; q < 2; ++q) {
+        tb_encode(h, &h->tm_delta[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_delta[q], h->nz);
+        h->tm_delta_ptr[q] = h->d_delta[q];
+    }
+    tb_encode(h, &h->tm_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz);
+    tb_encode(h, &h->tm_u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz);
+    tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz);
+    tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1);
+    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_flags, h->nz);
+    // z chunks: at least two waves of one resident CTA per SM
+    const int gx = (h->nx + TB_TXI - 1) / TB_TXI, gy = (h->ny + TB_TYI - 1) / TB_TYI;
+    int kc = h->nz;
+    while (kc > 8 && (int64_t)gx * gy * ((h->nz + kc - 1) / kc) < 152 * 2) kc = (kc + 1) / 2;
+    h->tb_kchunk = kc;
+    h->tb_grid = dim3(gx, gy, (h->nz + kc - 1) / kc);
+    h->tm_ready = true;
+}
+
+unsigned int* tb_err_word(rfb_soc_handle* h) { return reinterpret_cast<unsigned int*>(h->d_err + 3); }
+
+// one two-sweep pass from delta[cur] into delta[cur ^ 1]
+void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur, bool local) {
+    const CUtensorMap& td = (h->d_delta[cur] == h->tm_delta_ptr[0]) ? h->tm_delta[0]
+                                                                     : h->tm_delta[1];
+    TBArgs A{};
+    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz; A.kchunk = h->tb_kchunk;
+    A.d_in = h->d_delta[cur];
+    A.d_out = h->d_delta[cur ^ 1];
+    A.Dh = C.Dh; A.gDh = C.gDh; A.dt = C.dt; A.cfl = (float)op.cfl; A.umt = C.umt;
+    for (int q = 0; q < 8; ++q) A.tB[q] = C.rB[q];
+    A.err = tb_err_word(h);
+    if (local)
+        sweep32tb_kernel<true><<<h->tb_grid, TB_THREADS, TB_SMEM, h->stream>>>(
+            td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_f, A);
+    else
+        sweep32tb_kernel<false><<<h->tb_grid, TB_THREADS, TB_SMEM, h->stream>>>(
+            td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_f, A);
+    LAUNCHED(h);
+}
+
+// one plain sweep from delta[cur] into delta[cur ^ 1]
+void plain_sweep(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur,
+                 bool local) {
+    const bool vec = (h->nx % 4) == 0;
+    Lattice L = lattice(h);
+    if (vec && local)
+        sweep32v_kernel<true><<<h->vgrid, h->vblock, 0, h->stream>>>(
+            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+    else if (vec)
+        sweep32v_kernel<false><<<h->vgrid, h->vblock, 0, h->stream>>>(
+            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+    else
+        sweep_kernel<float, true><<<h->grid, h->block, 0, h->stream>>>(
+            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->kchunk);
+    LAUNCHED(h);
+}
+
+// n FP32 correction sweeps delta <- delta + dt (L delta + r), starting from delta = 0.
+// The result is left in d_delta[0]. use_tb: two-sweep passes (plus one plain sweep when
+// n is odd).
+void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = false) {
     const size_t bytes = (size_t)h->N * sizeof(float);
     CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
     CK(h, cudaMemsetAsync(h->d_delta[1], 0, bytes, h->stream));
     const bool local = op.dt_mode == RFB_DT_LOCAL;
     const bool vec = (h->nx % 4) == 0;
-    // the vectorised kernel computes the local step on the fly; the scalar one reads dtc
+    // the vectorised kernels compute the local step on the fly; the scalar one reads dtc
     Coef<float> C = make_coef<float>(h, op, true, local && !vec);
-    Lattice L = lattice(h);
     int cur = 0;
-    for (int64_t q = 0; q < n; ++q) {
-        if (vec && local)
-            sweep32v_kernel<true><<<h->vgrid, h->vblock, 0, h->stream>>>(
-                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl,
-                h->vkchunk);
-        else if (vec)
-            sweep32v_kernel<false><<<h->vgrid, h->vblock, 0, h->stream>>>(
-                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl,
-                h->vkchunk);
-        else
-            sweep_kernel<float, true><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->kchunk);
-        LAUNCHED(h);
+    int64_t q = 0;
+    if (use_tb) {
+        tb_prepare(h);
+        for (; q + 2 <= n; q += 2) {
+            tb_pass(h, op, C, cur, local);
+            cur ^= 1;
+        }
+    }
+    for (; q < n; ++q) {
+        plain_sweep(h, op, C, cur, local);
         cur ^= 1;
     }
-    if (cur == 1) std::swap(h->d_delta[0], h->d_delta[1]);
+    if (cur == 1) {
+        std::swap(h->d_delta[0], h->d_delta[1]);
+        if (h->tm_ready) {
+            std::swap(h->tm_delta[0], h->tm_delta[1]);
+            std::swap(h->tm_delta_ptr[0], h->tm_delta_ptr[1]);
+        }
+    }
+}
+
+// Project-written autotuner for one lattice: time 8 plain sweeps against 4 two-sweep
+// passes (CUDA events, on the current forcing) and keep the faster.
+void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op) {
+    if (!tb_eligible(h)) { h->tb_mode = 0; return; }
+    float ms[2] = {0.f, 0.f};
+    for (int mode = 0; mode < 2; ++mode) {
+        sweeps32(h, op, 2, mode == 1);   // warm-up (and tensor maps)
+        CK(h, cudaEventRecord(h->ev[0], h->stream));
+        sweeps32(h, op, 8, mode == 1);
+        CK(h, cudaEventRecord(h->ev[1], h->stream));
+        CK(h, cudaEventSynchronize(h->ev[1]));
+        CK(h, cudaEventElapsedTime(&ms[mode], h->ev[0], h->ev[1]));
+    }
+    h->tb_tuned_plain_ms = ms[0] / 8;
+    h->tb_tuned_tb_ms = ms[1] / 8;
+    h->tb_mode = ms[1] < ms[0] ? 1 : 0;
 }
 
 void init_state(rfb_soc_handle* h, bool umt, double s_in) {
@@ -330,8 +472,16 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
         set_err(h, "opts.check_every / max_sweeps must be >= 0");
         return false;
     }
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < 7; ++q)
         if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
+    if (o->fp32_kernel < 0 || o->fp32_kernel > 2) {
+        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep) or 2 (two-sweep passes)");
+        return false;
+    }
+    if (o->fp32_kernel == 2 && !tb_eligible(h)) {
+        set_err(h, "two-sweep passes need nx %% 16 == 0 and no area multiplier");
+        return false;
+    }
     if (o->max_sweeps == 0) o->max_sweeps = 50000000;
     return true;
 }
@@ -374,6 +524,17 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     check(h, op, umt, false, mixed);
     ++r.checks;
     fill_result(h, op, &r, n_unknown);
+    // FP32 kernel: one-sweep or two-sweep passes (forced by opts or autotuned once)
+    bool use_tb = false;
+    if (mixed) {
+        if (o.fp32_kernel == 2) {
+            use_tb = true;
+        } else if (o.fp32_kernel == 0) {
+            if (h->tb_mode < 0) tune_fp32_kernel(h, op);
+            use_tb = h->tb_mode == 1;
+        }
+        if (use_tb) CK(h, cudaMemsetAsync(tb_err_word(h), 0, sizeof(unsigned int), h->stream));
+    }
     while (true) {
         if (r.nonfinite > 0) { st = RFB_ERR_NONFINITE; break; }
         if (fixed_sweeps < 0 && r.residual <= tol) break;
@@ -383,7 +544,7 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         }
         const int64_t n = std::min(every, limit - done);
         CK(h, cudaEventRecord(h->ev[0], h->stream));
-        if (mixed) sweeps32(h, op, n);
+        if (mixed) sweeps32(h, op, n, use_tb);
         else sweeps64(h, op, umt, n);
         CK(h, cudaEventRecord(h->ev[1], h->stream));
         check(h, op, umt, mixed, mixed);
@@ -403,6 +564,16 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     r.check_ms = check_ms;
     r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                     .count();
+    if (use_tb) {
+        unsigned int bad = 0;
+        CK(h, cudaMemcpyAsync(&bad, tb_err_word(h), sizeof bad, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (bad) {
+            set_err(h, "a TMA stage of the two-sweep kernel did not arrive in time");
+            st = RFB_ERR_CUDA;
+        }
+    }
     if (res) *res = r;
     return st;
 }

@@ -196,6 +196,51 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
                 float* __restrict__ s_out, const float* __restrict__ force, float cfl,
                 int kchunk);
 
+// One FP32 correction update of one cell, delta' = delta + dt (L delta + r), with the
+// homogeneous operator (zero inlet value, no intercept). The *_raw neighbour values are
+// taken only where the flags say the neighbour is fluid (else the cell's own value), so
+// out-of-domain or solid neighbours may hold anything finite. Shared by the plain and
+// the temporally blocked sweeps, which therefore do bitwise the same arithmetic.
+template <bool LOCAL_DT>
+__device__ __forceinline__ float cell_update32(
+    unsigned f, float sc, float xm_raw, float xp_raw, float ym_raw, float yp_raw,
+    float zm_raw, float zp_raw, float uL, float uH, float vL, float vH, float wl, float wh,
+    float r, float mult, const float* tB, float Dh, float gDh, float dt_global, float cfl,
+    int umt, bool inlet, bool outlet, int i, int j, int k, int nx, int ny, int nz) {
+    const bool upd = (f & F_FLUID) && !(umt && (f & F_ELEC));
+    const float sxm = (f & F_XM) ? xm_raw : sc;
+    const float sxp = (f & F_XP) ? xp_raw : sc;
+    const float sym = (f & F_YM) ? ym_raw : sc;
+    const float syp = (f & F_YP) ? yp_raw : sc;
+    const float szm = (f & F_ZM) ? zm_raw : sc;
+    const float szp = (f & F_ZP) ? zp_raw : sc;
+    // upwind advection (the inlet carries the correction's zero boundary value)
+    float adv = uL * (uL > 0.f ? sxm : sc);
+    adv -= uH * (uH > 0.f ? sc : sxp);
+    adv += vL * (vL > 0.f ? sym : sc);
+    adv -= vH * (vH > 0.f ? sc : syp);
+    adv += wl * (wl > 0.f ? (inlet ? 0.f : szm) : sc);
+    adv -= wh * ((wh > 0.f || outlet) ? sc : szp);
+    // diffusion between fluid cells; inlet face term with zero boundary value
+    const float zmd = inlet ? sc : szm;
+    const float nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
+    float dif = Dh * nsum - (6.f * Dh) * sc;
+    if (inlet) dif -= gDh * sc;
+    const int nw = n_wall_of(f, i, j, k, nx, ny, nz);
+    const float rb = mult * tB[nw];
+    const float rhs = (adv + dif) - rb * sc + r;
+    float dt;
+    if (LOCAL_DT) {
+        float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
+                  fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
+        d += Dh * (float)__popc(f & F_NBRS) + (inlet ? gDh : 0.f) + rb;
+        dt = d > 0.f ? __fdividef(cfl, d) : 0.f;
+    } else {
+        dt = dt_global;
+    }
+    return upd ? sc + dt * rhs : sc;
+}
+
 // One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
 // kb .. ke-1. tB: the block's shared copy of the per-n_wall reaction slope.
 template <bool LOCAL_DT>
@@ -239,47 +284,12 @@ __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const unsigned f = (f4 >> (8 * e)) & 0xffu;
-            const float sc = el(d_cur, e);
-            const bool upd = (f & F_FLUID) && !(C.umt && (f & F_ELEC));
-            const float xm_raw = e == 0 ? d_xm : el(d_cur, e - 1);
-            const float xp_raw = e == 3 ? d_xp : el(d_cur, e + 1);
-            const float sxm = (f & F_XM) ? xm_raw : sc;
-            const float sxp = (f & F_XP) ? xp_raw : sc;
-            const float sym = (f & F_YM) ? el(d_ym, e) : sc;
-            const float syp = (f & F_YP) ? el(d_yp, e) : sc;
-            const float szm = (f & F_ZM) ? el(d_prev, e) : sc;
-            const float szp = (f & F_ZP) ? el(d_next, e) : sc;
-            const float uL = el(u4, e);
-            const float uH = e == 3 ? u_nx : el(u4, e + 1);
-            const float vL = el(v4, e), vH = el(vH4, e);
-            const float wl = el(wL, e), wh = el(wH, e);
-            // upwind advection (the inlet carries the correction's zero boundary value)
-            float adv = uL * (uL > 0.f ? sxm : sc);
-            adv -= uH * (uH > 0.f ? sc : sxp);
-            adv += vL * (vL > 0.f ? sym : sc);
-            adv -= vH * (vH > 0.f ? sc : syp);
-            adv += wl * (wl > 0.f ? (inlet ? 0.f : szm) : sc);
-            adv -= wh * ((wh > 0.f || outlet) ? sc : szp);
-            // diffusion between fluid cells; inlet face term with zero boundary value
-            const float zmd = inlet ? sc : szm;
-            const float nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
-            float dif = Dh * nsum - (6.f * Dh) * sc;
-            if (inlet) dif -= gDh * sc;
-            const int ii = i0 + e;
-            const int nw = n_wall_of(f, ii, j, k, nx, ny, nz);
-            const float mult = el(m4, e);
-            const float rb = mult * tB[nw];
-            const float rhs = (adv + dif) - rb * sc + el(r4, e);
-            float dt;
-            if (LOCAL_DT) {
-                float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
-                          fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
-                d += Dh * (float)__popc(f & F_NBRS) + (inlet ? gDh : 0.f) + rb;
-                dt = d > 0.f ? __fdividef(cfl, d) : 0.f;
-            } else {
-                dt = C.dt;
-            }
-            out[e] = upd ? sc + dt * rhs : sc;
+            out[e] = cell_update32<LOCAL_DT>(
+                f, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
+                e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e), el(d_prev, e),
+                el(d_next, e), el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
+                el(wL, e), el(wH, e), el(r4, e), el(m4, e), tB, Dh, gDh, C.dt, cfl, C.umt, inlet,
+                outlet, i0 + e, j, k, nx, ny, nz);
         }
         *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
         d_prev = d_cur;

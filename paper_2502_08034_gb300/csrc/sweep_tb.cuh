@@ -1,0 +1,226 @@
+// Temporally blocked FP32 correction sweep for sm_103a: two pseudo-time steps per pass
+// over HBM, z-planes staged into shared memory by TMA (cp.async.bulk.tensor) through a
+// three-stage mbarrier ring.
+//
+// A CTA owns an x-y tile of 128 x 14 cells (plus a halo of 16 columns and 2 rows on each
+// side, so that the 8-bit mask's TMA boxes start on 16-byte boundaries) and marches a
+// chunk of z planes. At step z it
+//   - computes level 1 (one sweep) at plane z from the staged level-0 planes z, z+1 and
+//     its own level-0 value at z-1 kept in registers, for every cell of the tile and a
+//     one-cell ring around it, and stores it in a double-buffered shared plane;
+//   - computes level 2 (the second sweep) at plane z-1 for the 128 x 14 interior from the
+//     level-1 plane z-1 (shared), its own level-1 values at z-2, z, and the coefficients of
+//     plane z-1 kept in registers from the previous step; level 2 is written to HBM.
+// Per pass each cell's delta, forcing, three face velocities and mask byte are read once
+// and delta is written once, for two sweeps. The per-cell arithmetic is cell_update32,
+// the same function as the one-sweep kernel: a pass is bitwise two plain sweeps.
+#pragma once
+
+#include <cuda.h>
+
+#include "soc_kernels.cuh"
+
+namespace rfb {
+
+constexpr int TB_TXI = 128;                    // interior columns of a tile
+constexpr int TB_TYI = 14;                     // interior rows of a tile
+constexpr int TB_BW = TB_TXI + 32;             // staged columns: 16 halo + 128 + 16 halo
+constexpr int TB_BH = TB_TYI + 4;              // staged rows: 2 halo + 14 + 2 halo
+constexpr int TB_GX = (TB_TXI + 16) / 4;       // 36 groups of 4 cells: columns [-8, 136)
+constexpr int TB_GY = TB_TYI + 2;              // 16 rows of threads: rows [-1, 15)
+constexpr int TB_THREADS = TB_GX * TB_GY;      // 576
+constexpr int TB_PLANE = TB_BW * TB_BH;        // 2880 cells per staged plane
+constexpr int TB_F32 = TB_PLANE * 4;           // 11520 bytes (90 x 128)
+constexpr int TB_FLAGS = 2944;                 // 2880 bytes rounded up to 128
+constexpr int TB_STAGE = 5 * TB_F32 + TB_FLAGS;
+constexpr int TB_NSTAGE = 3;
+constexpr int TB_L1 = TB_NSTAGE * TB_STAGE;    // offset of the two level-1 planes
+constexpr int TB_BAR = TB_L1 + 2 * TB_F32;     // offset of the stage barriers
+constexpr int TB_SMEM = TB_BAR + 64 + 128;     // + alignment slack for the base
+constexpr uint32_t TB_TX_BYTES = 5 * TB_F32 + TB_PLANE;
+constexpr unsigned long long TB_SPIN_LIMIT = 1ull << 26;   // bounded mbarrier waits
+
+struct TBArgs {
+    int nx, ny, nz, kchunk;
+    const float* __restrict__ d_in;   // delta read by this pass (prologue plane)
+    float* __restrict__ d_out;
+    float Dh, gDh, dt, cfl;
+    int umt;
+    float tB[8];
+    unsigned int* err;                // set if a stage never arrives
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+template <bool LOCAL_DT>
+__global__ void __launch_bounds__(TB_THREADS, 1)
+sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_r,
+                 const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
+                 const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_f,
+                 TBArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TB_BAR);
+    __shared__ float tB[8];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x;
+    if (tid < 8) tB[tid] = A.tB[tid];
+    if (tid == 0) abort_flag = 0;
+    const int tx = tid % TB_GX, ty = tid / TB_GX;
+    const int bxx = 8 + 4 * tx, byy = 1 + ty;          // this thread's cells in the box
+    const int x0 = TB_TXI * blockIdx.x - 16;           // box origin (16-cell aligned)
+    const int y0 = TB_TYI * blockIdx.y - 2;
+    const int i0 = x0 + bxx, j = y0 + byy;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+    const bool interior = tx >= 2 && tx < 2 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
+    const int kb = blockIdx.z * A.kchunk;
+    const int ke = min(kb + A.kchunk, nz);
+    const int64_t nxny = (int64_t)nx * ny;
+    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
+
+    auto stage = [&](int s) { return smem + s * TB_STAGE; };
+    auto issue = [&](int p, int s) {                   // one thread: plane p -> stage s
+        unsigned char* S = stage(s);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[s], TB_TX_BYTES);
+        tma_load_3d(S, &tm_d, x0, y0, p, &bar[s]);
+        tma_load_3d(S + TB_F32, &tm_r, x0, y0, p, &bar[s]);
+        tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
+        tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
+        tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
+        tma_load_3d(S + 5 * TB_F32, &tm_f, x0, y0, p, &bar[s]);
+    };
+    uint32_t phase = 0;
+    auto wait = [&](int s) -> bool {                   // bounded wait for stage s
+        unsigned long long n = 0;
+        while (!mbar_try_wait(&bar[s], (phase >> s) & 1u)) {
+            if (++n > TB_SPIN_LIMIT) {
+                atomicExch(A.err, 1u);
+                return false;
+            }
+        }
+        phase ^= 1u << s;
+        return true;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < TB_NSTAGE; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < TB_NSTAGE; ++q) issue(kb - 1 + q, q);   // planes kb-1, kb, kb+1
+
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 d0_prev = zero4;                            // own level 0 at z-1
+    if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
+    float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
+    // coefficients of plane z-1 (for level 2), kept from the previous step
+    float4 su = zero4, sv = zero4, svh = zero4, sw = zero4, sr = zero4;
+    float sun = 0.f;
+    uint32_t sf = 0;
+    bool ok = wait(0);
+
+    for (int z = kb - 1; z <= ke && ok; ++z) {
+        const int s0 = (z - (kb - 1)) % TB_NSTAGE;
+        const int s1 = (z + 1 - (kb - 1)) % TB_NSTAGE;
+        if (!wait(s1)) { ok = false; break; }
+        const float* D0 = reinterpret_cast<const float*>(stage(s0));
+        const float* R0 = D0 + TB_PLANE;
+        const float* U0 = R0 + TB_PLANE;
+        const float* V0 = U0 + TB_PLANE;
+        const float* W0 = V0 + TB_PLANE;
+        const unsigned char* F0 = reinterpret_cast<const unsigned char*>(W0 + TB_PLANE);
+        const float* D1 = reinterpret_cast<const float*>(stage(s1));
+        const float* W1 = D1 + 4 * TB_PLANE;
+        // ---- level 1 at plane z
+        const float4 dc = lds4(D0 + o);
+        const float4 dn = lds4(D1 + o);
+        const float4 u4 = lds4(U0 + o);
+        const float un = U0[o + 4];
+        const float4 v4 = lds4(V0 + o);
+        const float4 vh4 = lds4(V0 + o + TB_BW);
+        const float4 wl4 = lds4(W0 + o);
+        const float4 wh4 = lds4(W1 + o);
+        const float4 r4 = lds4(R0 + o);
+        const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
+        float4 l1 = dc;
+        if (in_dom && z >= 0 && z < nz) {
+            const float dxm = D0[o - 1], dxp = D0[o + 4];
+            const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                out[e] = cell_update32<LOCAL_DT>(
+                    (f4 >> (8 * e)) & 0xffu, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
+                    e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e), el(d0_prev, e),
+                    el(dn, e), el(u4, e), e == 3 ? un : el(u4, e + 1), el(v4, e), el(vh4, e),
+                    el(wl4, e), el(wh4, e), el(r4, e), 1.f, tB, A.Dh, A.gDh, A.dt, A.cfl, A.umt,
+                    z == 0, z == nz - 1, i0 + e, j, z, nx, ny, nz);
+            l1 = make_float4(out[0], out[1], out[2], out[3]);
+        }
+        float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
+        *reinterpret_cast<float4*>(L1w + o) = l1;
+        // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
+        const int zz = z - 1;
+        if (zz >= kb && interior && in_dom) {
+            const float* L1r = reinterpret_cast<const float*>(smem + TB_L1) + (zz & 1) * TB_PLANE;
+            const float lxm = L1r[o - 1], lxp = L1r[o + 4];
+            const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                out[e] = cell_update32<LOCAL_DT>(
+                    (sf >> (8 * e)) & 0xffu, el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
+                    e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e), el(l1_m2, e),
+                    el(l1, e), el(su, e), e == 3 ? sun : el(su, e + 1), el(sv, e), el(svh, e),
+                    el(sw, e), el(wl4, e), el(sr, e), 1.f, tB, A.Dh, A.gDh, A.dt, A.cfl, A.umt,
+                    zz == 0, zz == nz - 1, i0 + e, j, zz, nx, ny, nz);
+            *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
+                make_float4(out[0], out[1], out[2], out[3]);
+        }
+        // ---- keep what the next step needs; free stage s0 for plane z + 3
+        su = u4; sun = un; sv = v4; svh = vh4; sw = wl4; sr = r4; sf = f4;
+        d0_prev = dc;
+        l1_m2 = l1_m1;
+        l1_m1 = l1;
+        __syncthreads();
+        if (tid == 0 && z + 3 <= ke + 1) issue(z + 3, s0);
+    }
+    if (!ok) abort_flag = 1;
+}
+
+}  // namespace rfb

@@ -33,7 +33,7 @@ class Kinetics(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("inlet_bc", c_int32), ("dt_mode", c_int32),
                 ("check_every", c_int32), ("cfl", c_double), ("velocity_scale", c_double),
-                ("max_sweeps", c_int64), ("reserved", c_int32 * 8)]
+                ("max_sweeps", c_int64), ("fp32_kernel", c_int32), ("reserved", c_int32 * 7)]
 
 
 class SolveResult(ctypes.Structure):
@@ -116,8 +116,11 @@ class RfbError(RuntimeError):
         self.status = status
 
 
+FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2}
+
+
 def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
-              velocity_scale=1.0, max_sweeps=0) -> SolveOpts:
+              velocity_scale=1.0, max_sweeps=0, fp32_kernel="auto") -> SolveOpts:
     o = SolveOpts()
     lib().rfb_solve_opts_default(byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -127,6 +130,7 @@ def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0,
     o.cfl = float(cfl)
     o.velocity_scale = float(velocity_scale)
     o.max_sweeps = int(max_sweeps)
+    o.fp32_kernel = FP32_KERNEL[fp32_kernel] if isinstance(fp32_kernel, str) else int(fp32_kernel)
     return o
 
 

@@ -1,0 +1,91 @@
+"""The two-sweep (temporally blocked, TMA-staged) FP32 correction pass is bitwise two
+one-sweep launches, on lattices with several tiles, ragged tile edges in y, odd z
+extents and both pseudo-time step modes; and mixed-precision solves with it match the
+oracle."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import soc
+from tests._cases import problem_from_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_08034_gb300 import _build
+    _build.build()
+
+
+@functools.lru_cache(maxsize=None)
+def _case(dims, seed=7, d=4.0):
+    from paper_2502_08034_gb300 import synth
+    return synth.build_case("tb%dx%dx%d" % dims, dims, 0.82, d, seed, 0.01, -0.10, 0.4, 1e-10)
+
+
+@pytest.mark.parametrize("dims", [(48, 48, 96), (64, 40, 37), (144, 30, 21), (256, 32, 16)])
+@pytest.mark.parametrize("dt_mode", ["local", "global"])
+def test_two_sweep_pass_is_bitwise_two_sweeps(dims, dt_mode):
+    from paper_2502_08034_gb300 import rfb
+    case = _case(dims)
+    states = []
+    for kernel in ("plain", "blocked"):
+        with rfb.Solver.from_case(case) as sv:
+            for n in (6, 10, 4):      # several correction cycles
+                sv.step(case.s_in, case.eta, n, precision="mixed", dt_mode=dt_mode,
+                        fp32_kernel=kernel)
+            states.append(sv.get_state())
+    assert np.array_equal(states[0], states[1])
+
+
+def test_two_sweep_pass_odd_count():
+    """An odd sweep count ends with one one-sweep launch."""
+    from paper_2502_08034_gb300 import rfb
+    case = _case((64, 40, 37))
+    out = []
+    for kernel in ("plain", "blocked"):
+        with rfb.Solver.from_case(case) as sv:
+            sv.step(case.s_in, case.eta, 7, precision="mixed", fp32_kernel=kernel)
+            out.append(sv.get_state())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_umt_with_two_sweep_passes_matches_oracle():
+    from paper_2502_08034_gb300 import rfb
+    case = _case((48, 48, 96))
+    ref = soc.umt(problem_from_case(case, soc))
+    with rfb.Solver.from_case(case) as sv:
+        u, _ = sv.umt(1e-11, precision="mixed", fp32_kernel="blocked")
+    assert abs(u - ref) < 1e-7
+
+
+@pytest.mark.parametrize("dims", [(48, 48, 96), (64, 40, 37)])
+def test_mixed_solve_with_two_sweep_passes_matches_oracle(dims):
+    from paper_2502_08034_gb300 import rfb
+    case = _case(dims)
+    ref = soc.steady_state(soc.assemble(problem_from_case(case, soc)))
+    with rfb.Solver.from_case(case) as sv:
+        r = sv.solve(case.s_in, case.eta, 1e-11, precision="mixed", fp32_kernel="blocked")
+        s = sv.get_state()
+    assert r["residual"] <= 1e-11
+    assert np.abs(s - ref).max() < 1e-7
+
+
+def test_two_sweep_passes_need_a_16_multiple_and_no_area_multiplier():
+    from paper_2502_08034_gb300 import rfb, synth
+    case = _case((36, 20, 24))
+    with rfb.Solver.from_case(case) as sv:
+        with pytest.raises(rfb.RfbError) as e:
+            sv.solve(case.s_in, case.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
+        assert e.value.status == rfb.RFB_ERR_INVALID_ARG
+    c2 = _case((48, 48, 96))
+    m = synth.lognormal_area_mult(c2.solid)
+    with rfb.Solver.from_case(c2, area_mult=m) as sv:
+        with pytest.raises(rfb.RfbError):
+            sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
+        sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed")   # auto falls back

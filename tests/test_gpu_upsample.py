@@ -1,6 +1,10 @@
 """Iterative upsampling (Sec. III.A): GPU prolongation against the oracle's, and the
 upsampled solve reaching the same fixed point as a cold start in fewer sweeps."""
 import functools
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 import numpy as np
 import pytest
@@ -86,3 +90,55 @@ def test_upsample_argument_checks():
         with pytest.raises(rfb.RfbError) as e:
             c.upsample_from(f)            # dims are not 2x
         assert e.value.status == rfb.RFB_ERR_INVALID_ARG
+
+
+def _oracle_slab_residual(case, s, k0, k1):
+    """tau * RMS of the oracle's RHS(s) over planes [k0, k1) of a large lattice, from an
+    oracle assembly of planes [k0 - 1, k1 + 1) (the rows of the inner planes are exact;
+    the inlet / outlet planes are exact when the slab reaches them)."""
+    nz, ny, nx = case.solid.shape
+    a, b = max(0, k0 - 1), min(nz, k1 + 1)
+    p = soc.Problem(np.ascontiguousarray(case.solid[a:b]), case.U[a:b], case.V[a:b],
+                    case.W[a:b + 1], case.h, case.D, case.s_in, k0=case.k0, eta=case.eta)
+    op = soc.assemble(p)
+    sl = s.reshape(nz, ny, nx)[a:b].ravel()
+    r = soc.rhs(op, sl).reshape(b - a, ny, nx)[k0 - a:k1 - a]
+    fl = case.solid[k0:k1].ravel() == 0
+    full = soc.assemble(problem_from_case(case, soc)) if case.n < 3_000_000 else None
+    tau = full.tau if full is not None else None
+    if tau is None:
+        Q = case.h ** 2 * float(np.sum(np.where(case.solid[0] == 0, case.W[0], 0.0)))
+        tau = int((case.solid == 0).sum()) * case.h ** 3 / Q
+    return tau * float(np.sqrt(np.mean(r.ravel()[fl] ** 2)))
+
+
+def test_upsampling_workload_512x512x1024_full_size():
+    """The largest single-GPU run at full size: 128x128x256 -> 256x256x512 ->
+    512x512x1024 (268M cells, porosity 0.82, d = 8 at the finest level), mixed precision
+    to residual 1e-8 at each level. Checked by properties that hold at any size: the
+    oracle's residual of the GPU state on inlet, middle and outlet slabs, the mass
+    balance, the maximum principle and U <= U_mt."""
+    from paper_2502_08034_gb300 import rfb, synth
+    sys_path_bench = __import__("bench")
+    cases = synth.multilevel_cases((512, 512, 1024), 3, 0.82, 8.0, 5, 0.01, -0.10, 0.5, 1e-8,
+                                   flow_device="cuda")
+    solvers = [rfb.Solver.from_case(c, device_inputs=True) for c in cases]
+    try:
+        levels, _ = sys_path_bench.upsample_chain(solvers, cases, 1e-8, umt=False)
+        fine, case = solvers[-1], cases[-1]
+        s = fine.get_state()
+        r = levels[-1]
+        u_mt, _ = fine.umt(1e-8, precision="mixed")
+    finally:
+        for sv in solvers:
+            sv.close()
+    assert all(x["residual"] <= 1e-8 for x in levels)
+    assert r["mass_balance_rel"] < 1e-5
+    fl = case.solid.ravel() == 0
+    kin = soc.kinetics(case.eta)
+    assert s[fl].min() >= min(case.s_in, kin.s_eq) - 1e-6
+    assert s[fl].max() <= max(case.s_in, kin.s_eq) + 1e-6
+    assert 0.0 <= r["U"] <= u_mt <= 1.0
+    nz = case.dims[2]
+    for k0, k1 in ((0, 8), (nz // 2 - 4, nz // 2 + 4), (nz - 8, nz)):
+        assert _oracle_slab_residual(case, s, k0, k1) < 1e-6, (k0, k1)
