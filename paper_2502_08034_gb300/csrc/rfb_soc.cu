@@ -47,6 +47,7 @@ struct rfb_soc_handle {
     cudaStream_t stream = nullptr;
 
     uint8_t* d_flags = nullptr;
+    uint8_t* d_mask32 = nullptr;   // mask byte of the FP32 kernels
     double *d_u = nullptr, *d_v = nullptr, *d_w = nullptr;      // m/s, cell aligned
     double *d_us = nullptr, *d_vs = nullptr, *d_ws = nullptr;   // * beta / h
     float *d_u32 = nullptr, *d_v32 = nullptr, *d_w32 = nullptr; // * beta / h, FP32
@@ -141,7 +142,7 @@ int flat_grid(int64_t n) {
 }
 
 Lattice lattice(const rfb_soc_handle* h) {
-    return Lattice{h->nx, h->ny, h->nz, h->nxny, h->d_flags};
+    return Lattice{h->nx, h->ny, h->nz, h->nxny, h->d_flags, h->d_mask32};
 }
 
 void kinetics_AB(const rfb_kinetics& k, double eta, double* A, double* B) {
@@ -339,7 +340,7 @@ void tb_prepare(rfb_soc_handle* h) {
     tb_encode(h, &h->tm_u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz);
     tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz);
     tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1);
-    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_flags, h->nz);
+    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz);
     // z chunks: at least two waves of one resident CTA per SM
     const int gx = (h->nx + TB_TXI - 1) / TB_TXI, gy = (h->ny + TB_TYI - 1) / TB_TYI;
     int kc = h->nz;
@@ -591,7 +592,7 @@ rfb_status guard(rfb_soc_handle* h) {
 }
 
 void free_all(rfb_soc_handle* h) {
-    void* ptrs[] = {h->d_flags, h->d_u,  h->d_v,   h->d_w,     h->d_us,   h->d_vs,
+    void* ptrs[] = {h->d_flags, h->d_mask32, h->d_u,  h->d_v,   h->d_w,     h->d_us,   h->d_vs,
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
@@ -685,6 +686,7 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         const int64_t nU = (int64_t)(nx + 1) * ny * nz, nV = (int64_t)nx * (ny + 1) * nz,
                       nW = nxny * (nz + 1);
         dalloc(h, &h->d_flags, N);
+        dalloc(h, &h->d_mask32, N);
         dalloc(h, &h->d_u, N); dalloc(h, &h->d_v, N); dalloc(h, &h->d_w, N + nxny);
         dalloc(h, &h->d_us, N); dalloc(h, &h->d_vs, N); dalloc(h, &h->d_ws, N + nxny);
         dalloc(h, &h->d_u32, N); dalloc(h, &h->d_v32, N); dalloc(h, &h->d_w32, N + nxny);
@@ -734,7 +736,8 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
             CK(h, cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned long long), h->stream));
             CK(h, cudaMemsetAsync(h->d_u, 0, N * 8, h->stream));
             CK(h, cudaMemsetAsync(h->d_v, 0, N * 8, h->stream));
-            flags_kernel<<<flat_grid(N), 256, 0, h->stream>>>(d_mask, h->d_flags, nx, ny, nz);
+            flags_kernel<<<flat_grid(N), 256, 0, h->stream>>>(d_mask, h->d_flags, h->d_mask32,
+                                                              nx, ny, nz);
             LAUNCHED(h);
             repack_kernel<<<flat_grid(nU), 256, 0, h->stream>>>(dU, d_mask, h->d_u, nx, ny, nz,
                                                                 0, h->d_err);

@@ -38,7 +38,17 @@ constexpr int NRED = 8;   // reduction slots of the FP64 check
 struct Lattice {
     int nx, ny, nz, nxny;
     const uint8_t* __restrict__ flags;
+    const uint8_t* __restrict__ mask32;   // mask byte of the FP32 kernels (below)
 };
+
+// Mask byte of the FP32 correction kernels: bit0 fluid, bit1 electrode, bits 2-4 the
+// number of in-domain fluid neighbours n_f, bits 5-7 the number of fiber neighbours
+// n_wall. These kernels keep the correction at 0 on solid and out-of-domain cells, so
+// neighbour values need no per-face mask test: a solid or missing neighbour enters with
+// value 0 and its face carries zero velocity.
+constexpr unsigned M_FLUID = 1u, M_ELEC = 2u;
+__device__ __forceinline__ int m_nf(unsigned m) { return (m >> 2) & 7u; }
+__device__ __forceinline__ int m_nwall(unsigned m) { return m >> 5; }
 
 template <typename T>
 struct Coef {
@@ -201,44 +211,40 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
 // taken only where the flags say the neighbour is fluid (else the cell's own value), so
 // out-of-domain or solid neighbours may hold anything finite. Shared by the plain and
 // the temporally blocked sweeps, which therefore do bitwise the same arithmetic.
-template <bool LOCAL_DT>
-__device__ __forceinline__ float cell_update32(
-    unsigned f, float sc, float xm_raw, float xp_raw, float ym_raw, float yp_raw,
-    float zm_raw, float zp_raw, float uL, float uH, float vL, float vH, float wl, float wh,
-    float r, float mult, const float* tB, float Dh, float gDh, float dt_global, float cfl,
-    int umt, bool inlet, bool outlet, int i, int j, int k, int nx, int ny, int nz) {
-    const bool upd = (f & F_FLUID) && !(umt && (f & F_ELEC));
-    const float sxm = (f & F_XM) ? xm_raw : sc;
-    const float sxp = (f & F_XP) ? xp_raw : sc;
-    const float sym = (f & F_YM) ? ym_raw : sc;
-    const float syp = (f & F_YP) ? yp_raw : sc;
-    const float szm = (f & F_ZM) ? zm_raw : sc;
-    const float szp = (f & F_ZP) ? zp_raw : sc;
-    // upwind advection (the inlet carries the correction's zero boundary value)
-    float adv = uL * (uL > 0.f ? sxm : sc);
-    adv -= uH * (uH > 0.f ? sc : sxp);
-    adv += vL * (vL > 0.f ? sym : sc);
-    adv -= vH * (vH > 0.f ? sc : syp);
-    adv += wl * (wl > 0.f ? (inlet ? 0.f : szm) : sc);
-    adv -= wh * ((wh > 0.f || outlet) ? sc : szp);
-    // diffusion between fluid cells; inlet face term with zero boundary value
-    const float zmd = inlet ? sc : szm;
-    const float nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
-    float dif = Dh * nsum - (6.f * Dh) * sc;
-    if (inlet) dif -= gDh * sc;
-    const int nw = n_wall_of(f, i, j, k, nx, ny, nz);
-    const float rb = mult * tB[nw];
-    const float rhs = (adv + dif) - rb * sc + r;
-    float dt;
-    if (LOCAL_DT) {
-        float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
-                  fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
-        d += Dh * (float)__popc(f & F_NBRS) + (inlet ? gDh : 0.f) + rb;
-        dt = d > 0.f ? __fdividef(cfl, d) : 0.f;
-    } else {
-        dt = dt_global;
-    }
+//
+// The neighbour values must be 0 for solid and out-of-domain neighbours (the correction
+// is 0 there and its boundary value at the inlet is 0): then every face term is right
+// without testing the mask, since a face to a solid cell or a side wall has zero
+// velocity, and the diffusion sum over all six neighbours equals the sum over fluid
+// neighbours. The outlet face (zero gradient) is an outflow face (W >= 0 there), which
+// the upwind choice already handles. rb = m_c k0 n_wall B / h, the reaction slope.
+__device__ __forceinline__ float cell_update32(unsigned m, int umt, float sc, float xm, float xp,
+                                               float ym, float yp, float zm, float zp, float uL,
+                                               float uH, float vL, float vH, float wl, float wh,
+                                               float r, float rb, float dt, float Dh, float gDh,
+                                               bool inlet) {
+    const bool upd = (m & M_FLUID) && !(umt && (m & M_ELEC));
+    float adv = uL * (uL > 0.f ? xm : sc);
+    adv -= uH * (uH > 0.f ? sc : xp);
+    adv += vL * (vL > 0.f ? ym : sc);
+    adv -= vH * (vH > 0.f ? sc : yp);
+    adv += wl * (wl > 0.f ? zm : sc);
+    adv -= wh * (wh > 0.f ? sc : zp);
+    const float nsum = ((xm + xp) + (ym + yp)) + (zm + zp);
+    const float dself = Dh * (float)m_nf(m) + (inlet ? gDh : 0.f);
+    const float rhs = (adv + (Dh * nsum - dself * sc)) - rb * sc + r;
     return upd ? sc + dt * rhs : sc;
+}
+
+// Local pseudo-time step dt_c = cfl / d_c of one cell, d_c = outflow + D/h^2 n_f
+// (+ inlet face term) + reaction slope; 0 for a cell with d_c = 0.
+__device__ __forceinline__ float local_dt32(unsigned m, float uL, float uH, float vL, float vH,
+                                            float wl, float wh, float rb, float Dh, float gDh,
+                                            bool inlet, float cfl) {
+    float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
+              fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
+    d += Dh * (float)m_nf(m) + (inlet ? gDh : 0.f) + rb;
+    return d > 0.f ? __fdividef(cfl, d) : 0.f;
 }
 
 // One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
@@ -255,41 +261,44 @@ __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
     const bool has_xm = i0 > 0, has_xp = i0 + 4 < nx;
     const bool has_ym = j > 0, has_yp = j + 1 < ny;
-    const int64_t off_xm = has_xm ? -1 : 0, off_xp = has_xp ? 4 : 3;
-    const int64_t off_ym = has_ym ? -nx : 0, off_yp = has_yp ? nx : 0;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     int64_t c = (int64_t)i0 + (int64_t)nx * j + (int64_t)nxny * kb;
-    float4 d_prev = kb > 0 ? ldg4(s + c - nxny) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 d_prev = kb > 0 ? ldg4(s + c - nxny) : zero4;   // plane -1: outside, 0
     float4 d_cur = ldg4(s + c);
     float4 wL = ldg4(C.w + c);
     const float Dh = C.Dh, gDh = C.gDh;
     for (int k = kb; k < ke; ++k, c += nxny) {
         const bool outlet = (k == nz - 1);
         const bool inlet = (k == 0);
-        // ---- all loads of this plane
-        const float4 d_next = outlet ? d_cur : ldg4(s + c + nxny);
+        // ---- all loads of this plane (outside the domain the correction is 0)
+        const float4 d_next = outlet ? zero4 : ldg4(s + c + nxny);
         const float4 wH = ldg4(C.w + c + nxny);
-        const float4 d_ym = ldg4(s + c + off_ym);
-        const float4 d_yp = ldg4(s + c + off_yp);
-        const float d_xm = __ldg(s + c + off_xm);
-        const float d_xp = __ldg(s + c + off_xp);
+        const float4 d_ym = has_ym ? ldg4(s + c - nx) : zero4;
+        const float4 d_yp = has_yp ? ldg4(s + c + nx) : zero4;
+        const float d_xm = has_xm ? __ldg(s + c - 1) : 0.f;
+        const float d_xp = has_xp ? __ldg(s + c + 4) : 0.f;
         const float4 u4 = ldg4(C.u + c);
         const float u_nx = has_xp ? __ldg(C.u + c + 4) : 0.f;
         const float4 v4 = ldg4(C.v + c);
-        const float4 vH4 = has_yp ? ldg4(C.v + c + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 vH4 = has_yp ? ldg4(C.v + c + nx) : zero4;
         const float4 r4 = ldg4(force + c);
-        const uint32_t f4 = __ldg(reinterpret_cast<const unsigned int*>(L.flags + c));
+        const uint32_t m4b = __ldg(reinterpret_cast<const unsigned int*>(L.mask32 + c));
         const float4 m4 = C.m ? ldg4(C.m + c) : make_float4(1.f, 1.f, 1.f, 1.f);
         // ---- arithmetic
         float out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const unsigned f = (f4 >> (8 * e)) & 0xffu;
-            out[e] = cell_update32<LOCAL_DT>(
-                f, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
-                e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e), el(d_prev, e),
-                el(d_next, e), el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
-                el(wL, e), el(wH, e), el(r4, e), el(m4, e), tB, Dh, gDh, C.dt, cfl, C.umt, inlet,
-                outlet, i0 + e, j, k, nx, ny, nz);
+            const unsigned m = (m4b >> (8 * e)) & 0xffu;
+            const float uL = el(u4, e), uH = e == 3 ? u_nx : el(u4, e + 1);
+            const float vL = el(v4, e), vH = el(vH4, e), wl = el(wL, e), wh = el(wH, e);
+            const float rb = el(m4, e) * tB[m_nwall(m)];
+            const float dt = LOCAL_DT ? local_dt32(m, uL, uH, vL, vH, wl, wh, rb, Dh, gDh,
+                                                   inlet, cfl)
+                                      : C.dt;
+            out[e] = cell_update32(m, C.umt, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
+                                   e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
+                                   el(d_prev, e), el(d_next, e), uL, uH, vL, vH, wl, wh,
+                                   el(r4, e), rb, dt, Dh, gDh, inlet);
         }
         *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
         d_prev = d_cur;
@@ -690,9 +699,9 @@ finalize_kernel(const double* __restrict__ partials, int64_t nblocks, double* __
 // Setup kernels
 // ---------------------------------------------------------------------------------
 
-// flags from the solid mask (1 = fiber)
+// flags (and the FP32 kernels' mask byte) from the solid mask (1 = fiber)
 __global__ void flags_kernel(const uint8_t* __restrict__ solid, uint8_t* __restrict__ flags,
-                             int nx, int ny, int nz) {
+                             uint8_t* __restrict__ mask32, int nx, int ny, int nz) {
     const int64_t N = (int64_t)nx * ny * nz;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -700,7 +709,7 @@ __global__ void flags_kernel(const uint8_t* __restrict__ solid, uint8_t* __restr
         const int j = (int)((c / nx) % ny);
         const int k = (int)(c / ((int64_t)nx * ny));
         const int64_t nxny = (int64_t)nx * ny;
-        if (solid[c]) { flags[c] = 0; continue; }
+        if (solid[c]) { flags[c] = 0; mask32[c] = 0; continue; }
         unsigned f = F_FLUID;
         int dom = 0, fl = 0;
         if (i > 0) { ++dom; if (!solid[c - 1]) { f |= F_XM; ++fl; } }
@@ -711,6 +720,8 @@ __global__ void flags_kernel(const uint8_t* __restrict__ solid, uint8_t* __restr
         if (k + 1 < nz) { ++dom; if (!solid[c + nxny]) { f |= F_ZP; ++fl; } }
         if (dom > fl) f |= F_ELEC;
         flags[c] = (uint8_t)f;
+        mask32[c] = (uint8_t)(M_FLUID | (dom > fl ? M_ELEC : 0u) | ((unsigned)fl << 2) |
+                              ((unsigned)(dom - fl) << 5));
     }
 }
 

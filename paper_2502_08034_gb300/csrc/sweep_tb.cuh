@@ -2,13 +2,13 @@
 // over HBM, z-planes staged into shared memory by TMA (cp.async.bulk.tensor) through a
 // three-stage mbarrier ring.
 //
-// A CTA owns an x-y tile of 128 x 14 cells (plus a halo of 16 columns and 2 rows on each
+// A CTA owns an x-y tile of 128 x 12 cells (plus a halo of 16 columns and 2 rows on each
 // side, so that the 8-bit mask's TMA boxes start on 16-byte boundaries) and marches a
 // chunk of z planes. At step z it
 //   - computes level 1 (one sweep) at plane z from the staged level-0 planes z, z+1 and
 //     its own level-0 value at z-1 kept in registers, for every cell of the tile and a
 //     one-cell ring around it, and stores it in a double-buffered shared plane;
-//   - computes level 2 (the second sweep) at plane z-1 for the 128 x 14 interior from the
+//   - computes level 2 (the second sweep) at plane z-1 for the 128 x 12 interior from the
 //     level-1 plane z-1 (shared), its own level-1 values at z-2, z, and the coefficients of
 //     plane z-1 kept in registers from the previous step; level 2 is written to HBM.
 // Per pass each cell's delta, forcing, three face velocities and mask byte are read once
@@ -23,15 +23,16 @@
 namespace rfb {
 
 constexpr int TB_TXI = 128;                    // interior columns of a tile
-constexpr int TB_TYI = 14;                     // interior rows of a tile
+constexpr int TB_TYI = 12;                     // interior rows of a tile
 constexpr int TB_BW = TB_TXI + 32;             // staged columns: 16 halo + 128 + 16 halo
-constexpr int TB_BH = TB_TYI + 4;              // staged rows: 2 halo + 14 + 2 halo
+constexpr int TB_BH = TB_TYI + 4;              // staged rows: 2 halo + 12 + 2 halo
 constexpr int TB_GX = (TB_TXI + 16) / 4;       // 36 groups of 4 cells: columns [-8, 136)
-constexpr int TB_GY = TB_TYI + 2;              // 16 rows of threads: rows [-1, 15)
-constexpr int TB_THREADS = TB_GX * TB_GY;      // 576
-constexpr int TB_PLANE = TB_BW * TB_BH;        // 2880 cells per staged plane
-constexpr int TB_F32 = TB_PLANE * 4;           // 11520 bytes (90 x 128)
-constexpr int TB_FLAGS = 2944;                 // 2880 bytes rounded up to 128
+constexpr int TB_GY = TB_TYI + 2;              // 14 rows of threads: rows [-1, 13)
+// 504 threads = 16 warps, 4 per SM sub-partition, so up to 128 registers a thread fit
+constexpr int TB_THREADS = TB_GX * TB_GY;
+constexpr int TB_PLANE = TB_BW * TB_BH;        // 2560 cells per staged plane
+constexpr int TB_F32 = TB_PLANE * 4;           // 10240 bytes (80 x 128)
+constexpr int TB_FLAGS = (TB_PLANE + 127) / 128 * 128;
 constexpr int TB_STAGE = 5 * TB_F32 + TB_FLAGS;
 constexpr int TB_NSTAGE = 3;
 constexpr int TB_L1 = TB_NSTAGE * TB_STAGE;    // offset of the two level-1 planes
@@ -84,7 +85,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 template <bool LOCAL_DT>
-__global__ void __launch_bounds__(TB_THREADS, 1)
+__global__ void __maxnreg__(128)
 sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_r,
                  const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
                  const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_f,
@@ -149,7 +150,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
     if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
     float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
     // coefficients of plane z-1 (for level 2), kept from the previous step
-    float4 su = zero4, sv = zero4, svh = zero4, sw = zero4, sr = zero4;
+    float4 su = zero4, sv = zero4, svh = zero4, sw = zero4, sr = zero4, srb = zero4, sdt = zero4;
     float sun = 0.f;
     uint32_t sf = 0;
     bool ok = wait(0);
@@ -177,6 +178,17 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         const float4 wh4 = lds4(W1 + o);
         const float4 r4 = lds4(R0 + o);
         const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
+        // the cell's reaction slope and local step, used again by level 2 next step
+        float rb[4], dtc[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned m = (f4 >> (8 * e)) & 0xffu;
+            rb[e] = tB[m_nwall(m)];
+            dtc[e] = LOCAL_DT ? local_dt32(m, el(u4, e), e == 3 ? un : el(u4, e + 1), el(v4, e),
+                                           el(vh4, e), el(wl4, e), el(wh4, e), rb[e], A.Dh,
+                                           A.gDh, z == 0, A.cfl)
+                              : A.dt;
+        }
         float4 l1 = dc;
         if (in_dom && z >= 0 && z < nz) {
             const float dxm = D0[o - 1], dxp = D0[o + 4];
@@ -184,12 +196,13 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = cell_update32<LOCAL_DT>(
-                    (f4 >> (8 * e)) & 0xffu, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
-                    e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e), el(d0_prev, e),
-                    el(dn, e), el(u4, e), e == 3 ? un : el(u4, e + 1), el(v4, e), el(vh4, e),
-                    el(wl4, e), el(wh4, e), el(r4, e), 1.f, tB, A.Dh, A.gDh, A.dt, A.cfl, A.umt,
-                    z == 0, z == nz - 1, i0 + e, j, z, nx, ny, nz);
+                out[e] = cell_update32((f4 >> (8 * e)) & 0xffu, A.umt, el(dc, e),
+                                       e == 0 ? dxm : el(dc, e - 1),
+                                       e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                       el(d0_prev, e), el(dn, e), el(u4, e),
+                                       e == 3 ? un : el(u4, e + 1), el(v4, e), el(vh4, e),
+                                       el(wl4, e), el(wh4, e), el(r4, e), rb[e], dtc[e], A.Dh,
+                                       A.gDh, z == 0);
             l1 = make_float4(out[0], out[1], out[2], out[3]);
         }
         float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
@@ -203,17 +216,20 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = cell_update32<LOCAL_DT>(
-                    (sf >> (8 * e)) & 0xffu, el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
-                    e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e), el(l1_m2, e),
-                    el(l1, e), el(su, e), e == 3 ? sun : el(su, e + 1), el(sv, e), el(svh, e),
-                    el(sw, e), el(wl4, e), el(sr, e), 1.f, tB, A.Dh, A.gDh, A.dt, A.cfl, A.umt,
-                    zz == 0, zz == nz - 1, i0 + e, j, zz, nx, ny, nz);
+                out[e] = cell_update32((sf >> (8 * e)) & 0xffu, A.umt, el(l1_m1, e),
+                                       e == 0 ? lxm : el(l1_m1, e - 1),
+                                       e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
+                                       el(l1_m2, e), el(l1, e), el(su, e),
+                                       e == 3 ? sun : el(su, e + 1), el(sv, e), el(svh, e),
+                                       el(sw, e), el(wl4, e), el(sr, e), el(srb, e), el(sdt, e),
+                                       A.Dh, A.gDh, zz == 0);
             *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
                 make_float4(out[0], out[1], out[2], out[3]);
         }
         // ---- keep what the next step needs; free stage s0 for plane z + 3
         su = u4; sun = un; sv = v4; svh = vh4; sw = wl4; sr = r4; sf = f4;
+        srb = make_float4(rb[0], rb[1], rb[2], rb[3]);
+        sdt = make_float4(dtc[0], dtc[1], dtc[2], dtc[3]);
         d0_prev = dc;
         l1_m2 = l1_m1;
         l1_m1 = l1;
