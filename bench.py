@@ -44,6 +44,9 @@ def parse():
                     help="mixed: the 256x256x512 mixed-precision solve (default); batch48: the "
                          "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
                          "512x512x1024 iterative upsampling")
+    ap.add_argument("--fp32-kernel", default="auto", choices=["auto", "plain", "blocked"],
+                    help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
+                         "per launch, or two-sweep TMA-staged passes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -398,7 +401,8 @@ def main():
 
     def step(precision="mixed", tol=args.tol):
         sv.reset_state()
-        return sv.solve(case.s_in, case.eta, tol, precision=precision)
+        return sv.solve(case.s_in, case.eta, tol, precision=precision,
+                        fp32_kernel=args.fp32_kernel)
 
     for _ in range(args.warmup):
         step()
