@@ -431,7 +431,7 @@ def main():
     # algorithmic bytes per launch: a launch reads each cell's correction, forcing, three
     # face velocities and mask once and writes the correction once, whether it applies
     # one sweep or a two-sweep pass
-    two_sweep = launches < 2.0 * sweeps   # the autotuner chose two-sweep passes
+    two_sweep = launches < sweeps   # two-sweep passes: about one launch per two sweeps
     kernel_launches = (sweeps + 1) // 2 if two_sweep else sweeps
     achieved = SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
     effective = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9

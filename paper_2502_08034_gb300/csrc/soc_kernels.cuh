@@ -218,33 +218,53 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
 // velocity, and the diffusion sum over all six neighbours equals the sum over fluid
 // neighbours. The outlet face (zero gradient) is an outflow face (W >= 0 there), which
 // the upwind choice already handles. rb = m_c k0 n_wall B / h, the reaction slope.
-__device__ __forceinline__ float cell_update32(unsigned m, int umt, float sc, float xm, float xp,
-                                               float ym, float yp, float zm, float zp, float uL,
-                                               float uH, float vL, float vH, float wl, float wh,
-                                               float r, float rb, float dt, float Dh, float gDh,
-                                               bool inlet) {
+//
+// In this form one update is linear in the seven values with coefficients fixed for the
+// whole solve: s' = a_c s + sum_f a_f s_f + dt r, where a_f = dt (inflow through face f
+// + D/h^2) and a_c = 1 - dt d_c with d_c = outflow + D/h^2 n_f (+ the inlet face term)
+// + rb, the diagonal of -L. With the local step dt = cfl / d_c, a_c = 1 - cfl.
+struct Coef32 {
+    float a[6];   // -x, +x, -y, +y, -z, +z
+    float ac;     // own value
+    float dt;     // step (multiplies the forcing)
+};
+
+template <bool LOCAL_DT>
+__device__ __forceinline__ Coef32 cell_coef32(unsigned m, int umt, float uL, float uH, float vL,
+                                              float vH, float wl, float wh, float rb, float Dh,
+                                              float gDh, bool inlet, float cfl,
+                                              float dt_global) {
+    Coef32 k;
     const bool upd = (m & M_FLUID) && !(umt && (m & M_ELEC));
-    float adv = uL * (uL > 0.f ? xm : sc);
-    adv -= uH * (uH > 0.f ? sc : xp);
-    adv += vL * (vL > 0.f ? ym : sc);
-    adv -= vH * (vH > 0.f ? sc : yp);
-    adv += wl * (wl > 0.f ? zm : sc);
-    adv -= wh * (wh > 0.f ? sc : zp);
-    const float nsum = ((xm + xp) + (ym + yp)) + (zm + zp);
-    const float dself = Dh * (float)m_nf(m) + (inlet ? gDh : 0.f);
-    const float rhs = (adv + (Dh * nsum - dself * sc)) - rb * sc + r;
-    return upd ? sc + dt * rhs : sc;
+    const float d = (fmaxf(-uL, 0.f) + fmaxf(uH, 0.f)) + (fmaxf(-vL, 0.f) + fmaxf(vH, 0.f)) +
+                    (fmaxf(-wl, 0.f) + fmaxf(wh, 0.f)) +
+                    (Dh * (float)m_nf(m) + (inlet ? gDh : 0.f) + rb);
+    float dt;
+    if (LOCAL_DT) dt = (upd && d > 0.f) ? __fdividef(cfl, d) : 0.f;
+    else dt = upd ? dt_global : 0.f;
+    k.dt = dt;
+    k.ac = LOCAL_DT ? (dt > 0.f ? 1.f - cfl : 1.f) : 1.f - dt * d;
+    k.a[0] = dt * (fmaxf(uL, 0.f) + Dh);
+    k.a[1] = dt * (fmaxf(-uH, 0.f) + Dh);
+    k.a[2] = dt * (fmaxf(vL, 0.f) + Dh);
+    k.a[3] = dt * (fmaxf(-vH, 0.f) + Dh);
+    k.a[4] = dt * (fmaxf(wl, 0.f) + Dh);
+    k.a[5] = dt * (fmaxf(-wh, 0.f) + Dh);
+    return k;
 }
 
-// Local pseudo-time step dt_c = cfl / d_c of one cell, d_c = outflow + D/h^2 n_f
-// (+ inlet face term) + reaction slope; 0 for a cell with d_c = 0.
-__device__ __forceinline__ float local_dt32(unsigned m, float uL, float uH, float vL, float vH,
-                                            float wl, float wh, float rb, float Dh, float gDh,
-                                            bool inlet, float cfl) {
-    float d = fmaxf(uH, 0.f) + fmaxf(-uL, 0.f) + fmaxf(vH, 0.f) + fmaxf(-vL, 0.f) +
-              fmaxf(wh, 0.f) + fmaxf(-wl, 0.f);
-    d += Dh * (float)m_nf(m) + (inlet ? gDh : 0.f) + rb;
-    return d > 0.f ? __fdividef(cfl, d) : 0.f;
+// one update with the coefficients of cell_coef32 (cells that are not updated have
+// dt = 0, a_f = 0, a_c = 1 and keep their value exactly)
+__device__ __forceinline__ float cell_apply32(const Coef32& k, float sc, float xm, float xp,
+                                              float ym, float yp, float zm, float zp, float r) {
+    float acc = k.dt * r;
+    acc = fmaf(k.a[0], xm, acc);
+    acc = fmaf(k.a[1], xp, acc);
+    acc = fmaf(k.a[2], ym, acc);
+    acc = fmaf(k.a[3], yp, acc);
+    acc = fmaf(k.a[4], zm, acc);
+    acc = fmaf(k.a[5], zp, acc);
+    return fmaf(k.ac, sc, acc);
 }
 
 // One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
@@ -289,16 +309,12 @@ __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const unsigned m = (m4b >> (8 * e)) & 0xffu;
-            const float uL = el(u4, e), uH = e == 3 ? u_nx : el(u4, e + 1);
-            const float vL = el(v4, e), vH = el(vH4, e), wl = el(wL, e), wh = el(wH, e);
-            const float rb = el(m4, e) * tB[m_nwall(m)];
-            const float dt = LOCAL_DT ? local_dt32(m, uL, uH, vL, vH, wl, wh, rb, Dh, gDh,
-                                                   inlet, cfl)
-                                      : C.dt;
-            out[e] = cell_update32(m, C.umt, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
-                                   e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
-                                   el(d_prev, e), el(d_next, e), uL, uH, vL, vH, wl, wh,
-                                   el(r4, e), rb, dt, Dh, gDh, inlet);
+            const Coef32 kc = cell_coef32<LOCAL_DT>(
+                m, C.umt, el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
+                el(wL, e), el(wH, e), el(m4, e) * tB[m_nwall(m)], Dh, gDh, inlet, cfl, C.dt);
+            out[e] = cell_apply32(kc, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
+                                  e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
+                                  el(d_prev, e), el(d_next, e), el(r4, e));
         }
         *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
         d_prev = d_cur;

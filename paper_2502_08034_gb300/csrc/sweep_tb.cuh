@@ -149,10 +149,14 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
     float4 d0_prev = zero4;                            // own level 0 at z-1
     if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
     float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
-    // coefficients of plane z-1 (for level 2), kept from the previous step
-    float4 su = zero4, sv = zero4, svh = zero4, sw = zero4, sr = zero4, srb = zero4, sdt = zero4;
-    float sun = 0.f;
-    uint32_t sf = 0;
+    Coef32 skc[4];       // update coefficients of plane z-1 (level 2), from the previous step
+    float4 sr = zero4;   // forcing of plane z-1
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        for (int q = 0; q < 6; ++q) skc[e].a[q] = 0.f;
+        skc[e].ac = 1.f;
+        skc[e].dt = 0.f;
+    }
     bool ok = wait(0);
 
     for (int z = kb - 1; z <= ke && ok; ++z) {
@@ -178,16 +182,15 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         const float4 wh4 = lds4(W1 + o);
         const float4 r4 = lds4(R0 + o);
         const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
-        // the cell's reaction slope and local step, used again by level 2 next step
-        float rb[4], dtc[4];
+        // the cells' update coefficients for plane z, used by level 1 now and by level 2
+        // at the next step
+        Coef32 kc[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const unsigned m = (f4 >> (8 * e)) & 0xffu;
-            rb[e] = tB[m_nwall(m)];
-            dtc[e] = LOCAL_DT ? local_dt32(m, el(u4, e), e == 3 ? un : el(u4, e + 1), el(v4, e),
-                                           el(vh4, e), el(wl4, e), el(wh4, e), rb[e], A.Dh,
-                                           A.gDh, z == 0, A.cfl)
-                              : A.dt;
+            kc[e] = cell_coef32<LOCAL_DT>(m, A.umt, el(u4, e), e == 3 ? un : el(u4, e + 1),
+                                          el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e),
+                                          tB[m_nwall(m)], A.Dh, A.gDh, z == 0, A.cfl, A.dt);
         }
         float4 l1 = dc;
         if (in_dom && z >= 0 && z < nz) {
@@ -196,13 +199,9 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = cell_update32((f4 >> (8 * e)) & 0xffu, A.umt, el(dc, e),
-                                       e == 0 ? dxm : el(dc, e - 1),
-                                       e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                       el(d0_prev, e), el(dn, e), el(u4, e),
-                                       e == 3 ? un : el(u4, e + 1), el(v4, e), el(vh4, e),
-                                       el(wl4, e), el(wh4, e), el(r4, e), rb[e], dtc[e], A.Dh,
-                                       A.gDh, z == 0);
+                out[e] = cell_apply32(kc[e], el(dc, e), e == 0 ? dxm : el(dc, e - 1),
+                                      e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                      el(d0_prev, e), el(dn, e), el(r4, e));
             l1 = make_float4(out[0], out[1], out[2], out[3]);
         }
         float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
@@ -216,20 +215,16 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = cell_update32((sf >> (8 * e)) & 0xffu, A.umt, el(l1_m1, e),
-                                       e == 0 ? lxm : el(l1_m1, e - 1),
-                                       e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
-                                       el(l1_m2, e), el(l1, e), el(su, e),
-                                       e == 3 ? sun : el(su, e + 1), el(sv, e), el(svh, e),
-                                       el(sw, e), el(wl4, e), el(sr, e), el(srb, e), el(sdt, e),
-                                       A.Dh, A.gDh, zz == 0);
+                out[e] = cell_apply32(skc[e], el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
+                                      e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
+                                      el(l1_m2, e), el(l1, e), el(sr, e));
             *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
                 make_float4(out[0], out[1], out[2], out[3]);
         }
         // ---- keep what the next step needs; free stage s0 for plane z + 3
-        su = u4; sun = un; sv = v4; svh = vh4; sw = wl4; sr = r4; sf = f4;
-        srb = make_float4(rb[0], rb[1], rb[2], rb[3]);
-        sdt = make_float4(dtc[0], dtc[1], dtc[2], dtc[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) skc[e] = kc[e];
+        sr = r4;
         d0_prev = dc;
         l1_m2 = l1_m1;
         l1_m1 = l1;
