@@ -40,10 +40,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dims", default="256,256,512")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "batch48", "upsample"],
+    ap.add_argument("--workload", default="mixed",
+                    choices=["mixed", "batch48", "upsample", "adjoint"],
                     help="mixed: the 256x256x512 mixed-precision solve (default); batch48: the "
                          "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
-                         "512x512x1024 iterative upsampling")
+                         "512x512x1024 iterative upsampling; adjoint: gradients of I_tot, U "
+                         "and U_mt on the 128x128x256 differentiation workload")
     ap.add_argument("--fp32-kernel", default="auto", choices=["auto", "plain", "blocked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
                          "per launch, or two-sweep TMA-staged passes")
@@ -362,6 +364,61 @@ def run_upsample(args):
         s.close()
 
 
+def run_adjoint(args):
+    """Differentiation workload: 128x128x256, porosity 0.8, d = 8, lognormal (sigma 0.3)
+    area multipliers on wall cells; step = FP64 solve to 1e-12 + U_mt solve + the three
+    adjoint solves (I_tot, U, U_mt) with their gradients."""
+    import torch
+
+    from paper_2502_08034_gb300 import _build, rfb, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    t0 = time.time()
+    case = synth.adjoint_case(flow_device="cuda:%d" % local)
+    m = synth.lognormal_area_mult(case.solid, 0.3, 40)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    sv = rfb.Solver.from_case(case, area_mult=m, device_inputs=True, stream=stream)
+    grad = torch.empty(case.n, dtype=torch.float64, device="cuda")
+
+    def step():
+        sv.reset_state()
+        fwd = sv.solve(case.s_in, case.eta, 1e-12, precision="fp64")
+        sv.umt(1e-12, precision="fp64")
+        adj = [sv.adjoint(o, 1e-11, out=grad)[2] for o in ("I_tot", "U", "U_mt")]
+        return fwd, adj
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    outs = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            outs.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1)
+    fwd, adj = outs[-1]
+    sweeps = fwd["sweeps"] + sum(a["sweeps"] for a in adj)
+    out = {"metric": METRIC, "value": case.n * sweeps * args.steps / (elapsed / 1e3) / 1e9,
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "adjoint_128x128x256", "tol_forward": 1e-12,
+                      "tol_adjoint": 1e-11},
+           "forward": {"sweeps": fwd["sweeps"], "time_ms": fwd["time_ms"]},
+           "adjoints": [{"objective": o, "sweeps": a["sweeps"], "time_ms": a["time_ms"],
+                         "relative_residual": a["residual"]}
+                        for o, a in zip(("I_tot", "U", "U_mt"), adj)],
+           "clocks": clk.summary(), "setup_s": setup_s}
+    print(json.dumps(out), flush=True)
+    sv.close()
+
+
 def main():
     args = parse()
     dims = tuple(int(x) for x in args.dims.split(","))
@@ -373,6 +430,9 @@ def main():
         return
     if args.workload == "upsample":
         run_upsample(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
     import numpy as np
     import torch

@@ -71,6 +71,12 @@ struct rfb_soc_handle {
     double* d_lam[2] = {nullptr, nullptr};   // adjoint state (allocated on first use)
     double* d_g = nullptr;
     double* d_grad = nullptr;
+    // assembled FP64 operator (6 neighbour coefficients, diagonal, source) and its key
+    double* d_L64 = nullptr;
+    L64 K{};
+    bool L64_valid = false;
+    double L64_key[8] = {};
+    int64_t area_version = 0;
     double scaled_beta = NAN;
 
     int64_t n_fluid = 0, n_elec = 0;
@@ -235,44 +241,65 @@ void fill_result(const rfb_soc_handle* h, const OpPoint& op, rfb_solve_result* r
     r->nonfinite = (int64_t)v[6];
 }
 
+// The assembled FP64 operator of the operating point op (U_mt or state of charge),
+// rebuilt only when the operating point or the area multipliers changed.
+void ensure_L64(rfb_soc_handle* h, const OpPoint& op) {
+    if (!h->d_L64) dalloc(h, &h->d_L64, (size_t)8 * h->N);
+    const double key[8] = {(double)op.umt, op.s_in,           op.A,
+                           op.B,           op.beta,           (double)op.inlet_bc,
+                           (double)h->area_version, 1.0};
+    if (h->L64_valid && std::memcmp(key, h->L64_key, sizeof key) == 0) return;
+    for (int q = 0; q < 6; ++q) h->K.f[q] = h->d_L64 + (size_t)q * h->N;
+    h->K.diag = h->d_L64 + (size_t)6 * h->N;
+    h->K.b = h->d_L64 + (size_t)7 * h->N;
+    Coef<double> C = make_coef<double>(h, op, false, false);
+    assemble64_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(lattice(h), C, h->K);
+    LAUNCHED(h);
+    std::memcpy(h->L64_key, key, sizeof key);
+    h->L64_valid = true;
+}
+
 // FP64 check on buffer set (s/t). fuse: add delta and write the other buffer.
 void check(rfb_soc_handle* h, const OpPoint& op, bool umt, bool fuse, bool write_r) {
     double** buf = umt ? h->d_t : h->d_s;
     int& cur = umt ? h->t_cur : h->s_cur;
+    ensure_L64(h, op);
     Coef<double> C = make_coef<double>(h, op, false, false);
     Lattice L = lattice(h);
+    const L64 K = h->K;
     if (fuse) {
         if (write_r)
-            check_kernel<true, true><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, buf[cur], h->d_delta[0], buf[cur ^ 1], h->d_r32, h->d_partials,
+            check64c_kernel<true, true><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, K, buf[cur], h->d_delta[0], buf[cur ^ 1], h->d_r32, h->d_partials,
                 h->kchunk);
         else
-            check_kernel<true, false><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, buf[cur], h->d_delta[0], buf[cur ^ 1], nullptr, h->d_partials,
+            check64c_kernel<true, false><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, K, buf[cur], h->d_delta[0], buf[cur ^ 1], nullptr, h->d_partials,
                 h->kchunk);
         LAUNCHED(h);
         cur ^= 1;
     } else {
         if (write_r)
-            check_kernel<false, true><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, buf[cur], nullptr, nullptr, h->d_r32, h->d_partials, h->kchunk);
+            check64c_kernel<false, true><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, K, buf[cur], nullptr, nullptr, h->d_r32, h->d_partials, h->kchunk);
         else
-            check_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, buf[cur], nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
+            check64c_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
+                L, C, K, buf[cur], nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
         LAUNCHED(h);
     }
     reduce_readback(h, 0);
 }
 
-// n FP64 sweeps on s (or t for U_mt), ping-pong
+// n FP64 sweeps on s (or t for U_mt), ping-pong, with the assembled operator
 void sweeps64(rfb_soc_handle* h, const OpPoint& op, bool umt, int64_t n) {
     double** buf = umt ? h->d_t : h->d_s;
     int& cur = umt ? h->t_cur : h->s_cur;
-    Coef<double> C = make_coef<double>(h, op, false, op.dt_mode == RFB_DT_LOCAL);
+    ensure_L64(h, op);
+    const float* dtc = op.dt_mode == RFB_DT_LOCAL ? h->d_dtc : nullptr;
     Lattice L = lattice(h);
     for (int64_t q = 0; q < n; ++q) {
-        sweep_kernel<double, false><<<h->grid, h->block, 0, h->stream>>>(
-            L, C, buf[cur], buf[cur ^ 1], nullptr, h->kchunk);
+        sweep64c_kernel<<<h->grid, h->block, 0, h->stream>>>(L, h->K, dtc, op.dt, buf[cur],
+                                                             buf[cur ^ 1], op.umt, h->kchunk);
         LAUNCHED(h);
         cur ^= 1;
     }
@@ -600,7 +627,7 @@ void free_all(rfb_soc_handle* h) {
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
-                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad};
+                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -1046,6 +1073,7 @@ rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kin
         CK(h, cudaStreamSynchronize(h->stream));
         cudaFree(tmp);
         h->s_converged = false;   // the operator changed; the state stays as a warm start
+        ++h->area_version;
     } catch (Fail f) {
         return f.st;
     }
@@ -1111,6 +1139,7 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         const double w_out_sum = op.beta / h->h * h->sum_w_out;
         Coef<double> C = make_coef<double>(h, op, false, op.dt_mode == RFB_DT_LOCAL);
         const double kB1 = h->kin.k0 / h->h * op.B;
+        ensure_L64(h, op);   // L^T is gathered from the assembled rows
         adjoint_source_kernel<<<flat_grid(N), 256, 0, h->stream>>>(lattice(h), C, umt ? 2 : 0,
                                                                    w_out_sum, kB1, h->d_g);
         LAUNCHED(h);
@@ -1123,8 +1152,9 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         double rel = INFINITY;
         int64_t done = 0;
         while (true) {
-            adjoint_kernel<1><<<h->grid, h->block, 0, h->stream>>>(
-                lattice(h), C, h->d_lam[cur], nullptr, h->d_g, h->d_partials, h->kchunk);
+            adjoint64c_kernel<1><<<h->grid, h->block, 0, h->stream>>>(
+                lattice(h), h->K, C.dtc, op.dt, h->d_lam[cur], nullptr, h->d_g, h->d_partials,
+                op.umt, h->kchunk);
             LAUNCHED(h);
             reduce_readback(h, 0);
             ++r.checks;
@@ -1134,8 +1164,9 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
             if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
             const int64_t n = std::min(every, o.max_sweeps - done);
             for (int64_t q = 0; q < n; ++q) {
-                adjoint_kernel<0><<<h->grid, h->block, 0, h->stream>>>(
-                    lattice(h), C, h->d_lam[cur], h->d_lam[cur ^ 1], h->d_g, nullptr, h->kchunk);
+                adjoint64c_kernel<0><<<h->grid, h->block, 0, h->stream>>>(
+                    lattice(h), h->K, C.dtc, op.dt, h->d_lam[cur], h->d_lam[cur ^ 1], h->d_g,
+                    nullptr, op.umt, h->kchunk);
                 LAUNCHED(h);
                 cur ^= 1;
             }

@@ -408,6 +408,166 @@ __global__ void batch_zero_kernel(const BatchInst* __restrict__ insts, int n_ins
 }
 
 // ---------------------------------------------------------------------------------
+// FP64 operator in coefficient form. For one operating point, RHS(s)_c =
+//   b_c + L_cc s_c + sum_f L_f(c) s_f
+// with L_f(c) = inflow through face f + D/h^2 (fluid neighbours only), L_cc = -(outflow +
+// D/h^2 n_f + inlet face term + m k0 n_wall B / h) and b_c = inlet inflow and face terms
+// times s_in + m k0 n_wall A / h. Assembled once per solve (FP64, 8 doubles a cell), it
+// turns the FP64 sweep, check and adjoint into about 8 DFMAs a cell, which matters on
+// GB300 whose FP64 rate is a small fraction of its FP32 rate. Rows of solid and pinned
+// (U_mt) cells are all zero.
+// ---------------------------------------------------------------------------------
+struct L64 {
+    double* __restrict__ f[6];   // neighbour coefficients: -x, +x, -y, +y, -z, +z
+    double* __restrict__ diag;   // L_cc
+    double* __restrict__ b;      // source
+};
+
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NRED], double* out);
+
+__global__ void assemble64_kernel(Lattice L, Coef<double> C, L64 K) {
+    __shared__ double tA[8], tB[8];
+    if (threadIdx.x < 8) { tA[threadIdx.x] = C.rA[threadIdx.x]; tB[threadIdx.x] = C.rB[threadIdx.x]; }
+    __syncthreads();
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int64_t nxny = L.nxny, N = nxny * nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = L.flags[c];
+        double a[6] = {0, 0, 0, 0, 0, 0}, dg = 0.0, bb = 0.0;
+        if ((f & F_FLUID) && !(C.umt && (f & F_ELEC))) {
+            const int i = (int)(c % nx);
+            const int j = (int)((c / nx) % ny);
+            const int k = (int)(c / nxny);
+            const double uL = C.u[c], uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
+            const double vL = C.v[c], vH = (j + 1 < ny) ? C.v[c + nx] : 0.0;
+            const double wL = C.w[c], wH = C.w[c + nxny];
+            const double Dh = C.Dh;
+            // inflow coefficients (upwind) and diffusion to fluid neighbours
+            a[0] = fmax(uL, 0.0) + ((f & F_XM) ? Dh : 0.0);
+            a[1] = fmax(-uH, 0.0) + ((f & F_XP) ? Dh : 0.0);
+            a[2] = fmax(vL, 0.0) + ((f & F_YM) ? Dh : 0.0);
+            a[3] = fmax(-vH, 0.0) + ((f & F_YP) ? Dh : 0.0);
+            a[4] = (k > 0) ? fmax(wL, 0.0) + ((f & F_ZM) ? Dh : 0.0) : 0.0;
+            a[5] = fmax(-wH, 0.0) + ((f & F_ZP) ? Dh : 0.0);
+            const double outflow = (fmax(-uL, 0.0) + fmax(uH, 0.0)) +
+                                   (fmax(-vL, 0.0) + fmax(vH, 0.0)) +
+                                   (fmax(-wL, 0.0) + fmax(wH, 0.0));
+            const int nw = n_wall_of(f, i, j, k, nx, ny, nz);
+            const double mult = C.m ? C.m[c] : 1.0;
+            dg = -(outflow + Dh * (double)__popc(f & F_NBRS) + (k == 0 ? C.gDh : 0.0) +
+                   mult * tB[nw]);
+            bb = mult * tA[nw];
+            if (k == 0) bb += (fmax(wL, 0.0) + C.gDh) * C.s_in;
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) K.f[q][c] = a[q];
+        K.diag[c] = dg;
+        K.b[c] = bb;
+    }
+}
+
+// RHS at one cell from the assembled coefficients; neighbour values of missing
+// neighbours may be anything finite (their coefficient is 0).
+__device__ __forceinline__ double rhs64(const L64& K, int64_t c, double sc, double sxm, double sxp,
+                                        double sym, double syp, double szm, double szp) {
+    double r = fma(K.diag[c], sc, K.b[c]);
+    r = fma(K.f[0][c], sxm, r);
+    r = fma(K.f[1][c], sxp, r);
+    r = fma(K.f[2][c], sym, r);
+    r = fma(K.f[3][c], syp, r);
+    r = fma(K.f[4][c], szm, r);
+    r = fma(K.f[5][c], szp, r);
+    return r;
+}
+
+// FP64 sweep s_out = s + dt RHS(s) with the assembled operator (2.5D z marching).
+__global__ void __launch_bounds__(BX * BY)
+sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_global,
+                const double* __restrict__ s, double* __restrict__ s_out, int umt, int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= L.nx || j >= L.ny) return;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, L.nz);
+    const int nx = L.nx, nxny = L.nxny;
+    const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+    const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+    int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+    double s_prev = kb > 0 ? s[c - nxny] : 0.0;
+    double s_cur = s[c];
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const double s_next = (k + 1 < L.nz) ? s[c + nxny] : 0.0;
+        const unsigned f = L.flags[c];
+        if ((f & F_FLUID) && !(umt && (f & F_ELEC))) {
+            const double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym], s[c + oyp],
+                                   s_prev, s_next);
+            const double dt = dtc ? (double)dtc[c] : dt_global;
+            s_out[c] = fma(dt, r, s_cur);
+        }
+        s_prev = s_cur;
+        s_cur = s_next;
+    }
+}
+
+// Transposed step with the assembled operator: (L^T lam)_c gathers, from each neighbour
+// row, the coefficient that points back to c (e.g. from the +x neighbour its -x
+// coefficient). MODE 0: lam_out = lam + dt (L^T lam + g); MODE 1: reductions of
+// r = L^T lam + g over unknown cells (0 sum r^2, 1 sum g^2, 6 non-finite, 7 max |r|).
+template <int MODE>
+__global__ void __launch_bounds__(BX * BY)
+adjoint64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_global,
+                  const double* __restrict__ lam, double* __restrict__ lam_out,
+                  const double* __restrict__ g, double* __restrict__ partials, int umt,
+                  int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double l_prev = kb > 0 ? lam[c - nxny] : 0.0;
+        double l_cur = lam[c];
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const double l_next = (k + 1 < nz) ? lam[c + nxny] : 0.0;
+            const unsigned f = L.flags[c];
+            if ((f & F_FLUID) && !(umt && (f & F_ELEC))) {
+                double r = fma(K.diag[c], l_cur, g[c]);
+                if (i > 0) r = fma(K.f[1][c - 1], lam[c - 1], r);
+                if (i + 1 < nx) r = fma(K.f[0][c + 1], lam[c + 1], r);
+                if (j > 0) r = fma(K.f[3][c - nx], lam[c - nx], r);
+                if (j + 1 < ny) r = fma(K.f[2][c + nx], lam[c + nx], r);
+                if (k > 0) r = fma(K.f[5][c - nxny], l_prev, r);
+                if (k + 1 < nz) r = fma(K.f[4][c + nxny], l_next, r);
+                if (MODE == 0) {
+                    const double dt = dtc ? (double)dtc[c] : dt_global;
+                    lam_out[c] = fma(dt, r, l_cur);
+                } else {
+                    if (isfinite(r)) {
+                        acc[0] += r * r;
+                        acc[7] = fmax(acc[7], fabs(r));
+                    } else {
+                        acc[6] += 1.0;
+                    }
+                    acc[1] += g[c] * g[c];
+                }
+            }
+            l_prev = l_cur;
+            l_cur = l_next;
+        }
+    }
+    if (MODE == 1) {
+        const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                            ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+        block_reduce_store(acc, partials + bid * NRED);
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Block reduction helpers (fixed order => deterministic)
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double x) {
@@ -530,6 +690,73 @@ check_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
     const int kb = blockIdx.z * kchunk;
     check_tile<FUSE, WRITE_R>(L, C, tA, tB, s, delta, s_new, r_out, acc, blockIdx.x,
                               blockIdx.y, kb, min(kb + kchunk, L.nz));
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+}
+
+// FP64 check with the assembled operator (same reductions and fusion as check_kernel);
+// velocities are read only on the inlet and outlet planes, for the currents.
+template <bool FUSE, bool WRITE_R>
+__global__ void __launch_bounds__(BX * BY)
+check64c_kernel(Lattice L, Coef<double> C, L64 K, const double* __restrict__ s,
+                const float* __restrict__ delta, double* __restrict__ s_new,
+                float* __restrict__ r_out, double* __restrict__ partials, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+        const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+        auto val = [&](int64_t cc) -> double {
+            return FUSE ? s[cc] + (double)delta[cc] : s[cc];
+        };
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double s_prev = kb > 0 ? val(c - nxny) : 0.0;
+        double s_cur = val(c);
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const bool outlet = (k == L.nz - 1);
+            const double s_next = outlet ? 0.0 : val(c + nxny);
+            const unsigned f = L.flags[c];
+            if (FUSE) s_new[c] = s_cur;
+            if (f & F_FLUID) {
+                const bool pinned = C.umt && (f & F_ELEC);
+                if (!pinned) {
+                    const double r = rhs64(K, c, s_cur, val(c + oxm), val(c + oxp), val(c + oym),
+                                           val(c + oyp), s_prev, s_next);
+                    if (isfinite(r)) {
+                        acc[0] += r * r;
+                        acc[7] = fmax(acc[7], fabs(r));
+                    } else {
+                        acc[6] += 1.0;
+                    }
+                    if (WRITE_R) r_out[c] = (float)r;
+                } else if (WRITE_R) {
+                    r_out[c] = 0.0f;
+                }
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                const double mult = C.m ? C.m[c] : 1.0;
+                acc[1] += mult * (tA[nw] - tB[nw] * s_cur);
+                if (k == 0) {
+                    acc[2] += C.gDh * (C.s_in - s_cur);
+                    acc[3] += C.w[c] * C.s_in;
+                }
+                if (outlet) {
+                    const double wH = C.w[c + nxny];
+                    acc[4] += wH * s_cur;
+                    acc[5] += wH;
+                }
+            }
+            s_prev = s_cur;
+            s_cur = s_next;
+        }
+    }
     const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
                         ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
     block_reduce_store(acc, partials + bid * NRED);
