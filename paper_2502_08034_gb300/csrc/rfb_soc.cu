@@ -1378,11 +1378,12 @@ void build_items(rfb_batch* b, int kchunk) {
     b->item_begin.assign(1, 0);
     for (size_t q = 0; q < b->hs.size(); ++q) {
         const rfb_soc_handle* h = b->hs[q];
-        const int tx = (h->nx / 4 + VBX - 1) / VBX, ty = (h->ny + VBY - 1) / VBY;
+        // runs of 1024 consecutive cells of the flattened x-y plane (no x-tile waste on
+        // lattices whose width is not a multiple of 128)
+        const int groups = h->nxny / 4;
         for (int kb = 0; kb < h->nz; kb += kchunk)
-            for (int by = 0; by < ty; ++by)
-                for (int bx = 0; bx < tx; ++bx)
-                    items.push_back(BatchItem{(int)q, bx, by, kb, std::min(kb + kchunk, h->nz)});
+            for (int g0 = 0; g0 < groups; g0 += VBX * VBY)
+                items.push_back(BatchItem{(int)q, g0, 0, kb, std::min(kb + kchunk, h->nz)});
         b->item_begin.push_back((int)items.size());
     }
     if (b->d_items) cudaFree(b->d_items);

@@ -270,6 +270,13 @@ __device__ __forceinline__ float cell_apply32(const Coef32& k, float sc, float x
 // One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
 // kb .. ke-1. tB: the block's shared copy of the per-n_wall reaction slope.
 template <bool LOCAL_DT>
+__device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
+                                               const float* tB, const float* __restrict__ s,
+                                               float* __restrict__ s_out,
+                                               const float* __restrict__ force, float cfl,
+                                               int i0, int j, int kb, int ke);
+
+template <bool LOCAL_DT>
 __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float>& C,
                                               const float* tB, const float* __restrict__ s,
                                               float* __restrict__ s_out,
@@ -278,6 +285,16 @@ __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float
     const int i0 = 4 * (bx * VBX + threadIdx.x);
     const int j = by * VBY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
+    sweep32v_cells<LOCAL_DT>(L, C, tB, s, s_out, force, cfl, i0, j, kb, ke);
+}
+
+// The 4 cells (i0 .. i0+3, j) of every plane kb .. ke-1 (i0 % 4 == 0, nx % 4 == 0).
+template <bool LOCAL_DT>
+__device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
+                                               const float* tB, const float* __restrict__ s,
+                                               float* __restrict__ s_out,
+                                               const float* __restrict__ force, float cfl,
+                                               int i0, int j, int kb, int ke) {
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
     const bool has_xm = i0 > 0, has_xp = i0 + 4 < nx;
     const bool has_ym = j > 0, has_yp = j + 1 < ny;
@@ -341,9 +358,10 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
 
 // ---------------------------------------------------------------------------------
 // Batches: many lattices of uneven size advanced by one persistent launch per sweep.
-// Every lattice is cut into work items (a 128 x VBY column tile times a chunk of z
-// planes, the block shape of the single-lattice kernels); a grid of resident blocks walks
-// the item list in a fixed round-robin order. Items of lattices that have converged are
+// Every lattice is cut into work items (1024 consecutive cells of the flattened x-y plane,
+// 4 a thread, times a chunk of z planes); a grid of blocks walks the item list in a fixed
+// round-robin order (the autotuner picks the grid size, from the resident blocks up to one
+// block per item). Items of lattices that have converged are
 // skipped (their `active` flag lives in device memory, so a captured CUDA graph keeps
 // working as lattices drop out).
 // ---------------------------------------------------------------------------------
@@ -362,8 +380,9 @@ struct BatchInst {
 
 struct BatchItem {
     int inst;
-    int bx, by;
-    int kb, ke;
+    int bx;        // first 4-cell group of the item in the flattened x-y plane (256 groups)
+    int by;        // unused (0)
+    int kb, ke;    // planes kb .. ke-1
 };
 
 template <bool LOCAL_DT>
@@ -384,10 +403,15 @@ batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         const float* r32 = I->r32;
         const float cfl = I->cfl;
         __syncthreads();
-        if (threadIdx.y * VBX + threadIdx.x < 8) tB[threadIdx.y * VBX + threadIdx.x] =
-            I->C32.rB[threadIdx.y * VBX + threadIdx.x];
+        const int t = threadIdx.y * VBX + threadIdx.x;
+        if (t < 8) tB[t] = I->C32.rB[t];
         __syncthreads();
-        sweep32v_tile<LOCAL_DT>(L, C, tB, src, dst, r32, cfl, it.bx, it.by, it.kb, it.ke);
+        // the item covers 4-cell groups it.bx .. it.bx + 255 of the flattened x-y plane
+        // (a group never crosses a row because nx % 4 == 0)
+        const int64_t cell = 4 * ((int64_t)it.bx + t);
+        if (cell < (int64_t)L.nxny)
+            sweep32v_cells<LOCAL_DT>(L, C, tB, src, dst, r32, cfl, (int)(cell % L.nx),
+                                     (int)(cell / L.nx), it.kb, it.ke);
     }
 }
 
@@ -610,6 +634,15 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NRED], double* 
 // WRITE_R: RHS is stored as FP32 forcing for the next correction sweeps.
 // ---------------------------------------------------------------------------------
 template <bool FUSE, bool WRITE_R>
+__device__ __forceinline__ void check_column(const Lattice& L, const Coef<double>& C,
+                                             const double* tA, const double* tB,
+                                             const double* __restrict__ s,
+                                             const float* __restrict__ delta,
+                                             double* __restrict__ s_new,
+                                             float* __restrict__ r_out, double (&acc)[NRED],
+                                             int i, int j, int kb, int ke);
+
+template <bool FUSE, bool WRITE_R>
 __device__ __forceinline__ void check_tile(const Lattice& L, const Coef<double>& C,
                                            const double* tA, const double* tB,
                                            const double* __restrict__ s,
@@ -617,8 +650,19 @@ __device__ __forceinline__ void check_tile(const Lattice& L, const Coef<double>&
                                            double* __restrict__ s_new,
                                            float* __restrict__ r_out, double (&acc)[NRED],
                                            int bx, int by, int kb, int ke) {
-    const int i = bx * BX + threadIdx.x;
-    const int j = by * BY + threadIdx.y;
+    check_column<FUSE, WRITE_R>(L, C, tA, tB, s, delta, s_new, r_out, acc,
+                                bx * BX + threadIdx.x, by * BY + threadIdx.y, kb, ke);
+}
+
+// FP64 RHS and reductions down the column (i, j), planes kb .. ke-1.
+template <bool FUSE, bool WRITE_R>
+__device__ __forceinline__ void check_column(const Lattice& L, const Coef<double>& C,
+                                             const double* tA, const double* tB,
+                                             const double* __restrict__ s,
+                                             const float* __restrict__ delta,
+                                             double* __restrict__ s_new,
+                                             float* __restrict__ r_out, double (&acc)[NRED],
+                                             int i, int j, int kb, int ke) {
     if (i < L.nx && j < L.ny) {
         const int nx = L.nx, nxny = L.nxny;
         auto val = [&](int64_t cc) -> double {
@@ -789,10 +833,15 @@ batch_check_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         if (t < 8) { tA[t] = I->C64.rA[t]; tB[t] = I->C64.rB[t]; }
         __syncthreads();
         if (active) {
-            // a work item spans VBX * 4 = 4 * BX cells in x
-            for (int q = 0; q < 4; ++q)
-                check_tile<FUSE, true>(L, C, tA, tB, s, d0, s_new, r32, acc, 4 * it.bx + q,
-                                       it.by, it.kb, it.ke);
+            // the item's 1024 cells of the flattened plane, 4 consecutive cells a thread
+            const int64_t cell0 = 4 * ((int64_t)it.bx + t);
+            for (int q = 0; q < 4; ++q) {
+                const int64_t cell = cell0 + q;
+                if (cell < (int64_t)L.nxny)
+                    check_column<FUSE, true>(L, C, tA, tB, s, d0, s_new, r32, acc,
+                                             (int)(cell % L.nx), (int)(cell / L.nx), it.kb,
+                                             it.ke);
+            }
         }
         block_reduce_store(acc, partials + (int64_t)w * NRED);
     }
