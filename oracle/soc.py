@@ -18,6 +18,10 @@ What it computes, in FP64, following the paper (arXiv 2502.08034):
   and fiber faces, and the Butler-Volmer source k0 a_c R~(s_c) with a_c = m_c n_wall/h
   (n_wall = number of fiber 6-neighbours; the paper's a = A/V of a cut cell).
   RHS(s) = L s + b.
+* Kinetics mode 1 (the literal uniform activation overpotential): the source is the
+  Butler-Volmer rate at a fixed eta~ = -n_e eta / V_T (Eqs. etat-def,
+  source-term-bv-gen), k0 a_c s^alpha (1-s)^(1-alpha) (e^{alpha eta~} - e^{(alpha-1) eta~}),
+  nonlinear in s; its steady state is found by Newton's method with the exact Jacobian.
 * The steady state is the solution of RHS(s) = 0 (a sparse direct solve; the affine rate
   law makes the problem linear). ``explicit_iterate`` runs the paper's pseudo-time loop
   s <- s + dt RHS(s) (Algorithm 7's two-buffer loop with F = I + dt(A + D + R)).
@@ -62,6 +66,8 @@ class Kinetics:
     s_eq: float       # sigma(Vt)
     A: float          # intercept of R~(s): e^{alpha Vt}
     B: float          # -slope of R~(s): e^{alpha Vt} (1 + e^{-Vt})
+    alpha: float = 0.5
+    K1: float = 0.0   # e^{alpha eta~} - e^{(alpha-1) eta~} at eta~ = Vt (kinetics mode 1)
 
 
 def kinetics(eta: float, alpha: float = 0.5, n_e: int = 2, T: float = 298.0) -> Kinetics:
@@ -71,7 +77,8 @@ def kinetics(eta: float, alpha: float = 0.5, n_e: int = 2, T: float = 298.0) -> 
     A = math.exp(alpha * Vt)
     B = A * (1.0 + math.exp(-Vt))
     s_eq = 1.0 / (1.0 + math.exp(-Vt))
-    return Kinetics(V_T, V_ar, Vt, s_eq, A, B)
+    K1 = math.exp(alpha * Vt) - math.exp((alpha - 1.0) * Vt)
+    return Kinetics(V_T, V_ar, Vt, s_eq, A, B, alpha, K1)
 
 
 def rate_affine(s, kin: Kinetics):
@@ -86,6 +93,24 @@ def rate_bv(s, Vt: float, alpha: float = 0.5):
     etat = Vt - np.log(s / (1.0 - s))
     return s ** alpha * (1.0 - s) ** (1.0 - alpha) * (np.exp(alpha * etat) -
                                                      np.exp((alpha - 1.0) * etat))
+
+
+def rate_uniform(s, etat: float, alpha: float = 0.5):
+    """R~(s) = S / (a k0 C_T) at a fixed dimensionless overpotential eta~ (Eq. etat-def):
+    s^alpha (1 - s)^(1 - alpha) (e^{alpha eta~} - e^{(alpha - 1) eta~})
+    (Eq. source-term-bv-gen; Eq. source-term-bv at alpha = 1/2). Kinetics mode 1, the
+    literal uniform activation overpotential."""
+    s = np.asarray(s, dtype=np.float64)
+    return s ** alpha * (1.0 - s) ** (1.0 - alpha) * (math.exp(alpha * etat) -
+                                                     math.exp((alpha - 1.0) * etat))
+
+
+def rate_uniform_slope(s, etat: float, alpha: float = 0.5):
+    """d R~/ds of ``rate_uniform`` for 0 < s < 1:
+    (e^{alpha eta~} - e^{(alpha-1) eta~}) s^(alpha-1) (1-s)^(-alpha) (alpha - s)."""
+    s = np.asarray(s, dtype=np.float64)
+    return (math.exp(alpha * etat) - math.exp((alpha - 1.0) * etat)) * \
+        s ** (alpha - 1.0) * (1.0 - s) ** (-alpha) * (alpha - s)
 
 
 # --------------------------------------------------------------------------------------
@@ -111,6 +136,7 @@ class Problem:
     beta: float = 1.0
     area_mult: Optional[np.ndarray] = None
     inlet_bc: str = "face"
+    kinetics_mode: int = 0    # 0 affine (Eq. rate-from-soc-gen), 1 uniform eta_act
 
     @property
     def dims(self):
@@ -129,6 +155,9 @@ class Operator:
     Q: float                  # volumetric flow rate through the inlet
     tau: float                # V_f / Q
     n_fluid: int
+    nonlinear: bool = False   # kinetics mode 1: L, b hold transport only and the source
+                              # kappa_c R~(s_c) is rate_uniform at eta~ = kin.Vt
+    s_in: float = 0.0         # inlet value the operator was assembled with
 
 
 def n_wall(solid: np.ndarray) -> np.ndarray:
@@ -147,7 +176,11 @@ def n_wall(solid: np.ndarray) -> np.ndarray:
 def assemble(p: Problem, mode: str = "sbv") -> Operator:
     """Build RHS(s) = L s + b for every fluid cell.
 
-    mode 'sbv': Eq. nernst-planck-soc with the affine source (Eq. rate-from-soc-gen).
+    mode 'sbv': Eq. nernst-planck-soc with the affine source (Eq. rate-from-soc-gen); with
+    ``p.kinetics_mode == 1`` the source is the Butler-Volmer rate at a uniform activation
+    overpotential (Eq. source-term-bv-gen, eta~ = -n_e eta / V_T by Eq. etat-def), which is
+    nonlinear in s: L and b then hold advection and diffusion only and ``rhs`` adds
+    kappa_c R~(s_c).
     mode 'umt': Eqs. np-fast-interior/np-fast-boundary with s_in = 0 and the cells that
     touch a fiber held at 1 (Eq. umt-def)."""
     solid = p.solid.astype(bool)
@@ -199,11 +232,13 @@ def assemble(p: Problem, mode: str = "sbv") -> Operator:
     kin = kinetics(p.eta, p.alpha, p.n_e, p.T)
     kappa = np.zeros(N)
     nw = n_wall(solid)
+    nonlinear = mode == "sbv" and p.kinetics_mode == 1
     if mode == "sbv":
         m = np.ones(N) if p.area_mult is None else np.asarray(p.area_mult, np.float64).ravel()
         kappa = np.where(fluid.ravel(), p.k0 * m * nw.ravel() / h, 0.0)
-        add(idx.ravel(), idx.ravel(), -kappa * kin.B)
-        b += kappa * kin.A
+        if not nonlinear:
+            add(idx.ravel(), idx.ravel(), -kappa * kin.B)
+            b += kappa * kin.A
 
     L = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(N, N)).tocsr()
@@ -225,16 +260,46 @@ def assemble(p: Problem, mode: str = "sbv") -> Operator:
     nf = int(fl.sum())
     Vf = nf * h ** 3
     tau = Vf / Q if Q > 0 else (nz * h) ** 2 / D
-    return Operator(L, b, unknown, fixed, kappa, kin, Q, tau, nf)
+    return Operator(L, b, unknown, fixed, kappa, kin, Q, tau, nf, nonlinear, s_in)
 
 
 # --------------------------------------------------------------------------------------
 # Steady state, iteration, outputs
 # --------------------------------------------------------------------------------------
 
+def source(op: Operator, s: np.ndarray) -> np.ndarray:
+    """k0 a_c R~(s_c) per cell (s^-1), for either kinetics mode."""
+    if op.nonlinear:
+        return op.kappa * rate_uniform(np.clip(s, 0.0, 1.0), op.kin.Vt, op.kin.alpha)
+    return op.kappa * rate_affine(s, op.kin)
+
+
 def rhs(op: Operator, s: np.ndarray) -> np.ndarray:
-    """RHS(s) = L s + b on all cells (zero on solid cells)."""
-    return op.L @ s + op.b
+    """RHS(s) = L s + b (+ the nonlinear source in kinetics mode 1), zero on solid cells."""
+    r = op.L @ s + op.b
+    if op.nonlinear:
+        r = r + source(op, s)
+    return r
+
+
+def jacobian(op: Operator, s: np.ndarray) -> sp.csr_matrix:
+    """d RHS / ds at s: L itself for the affine law; L + diag(kappa R~'(s)) in mode 1."""
+    if not op.nonlinear:
+        return op.L
+    d = np.zeros(s.size)
+    k = op.kappa != 0
+    d[k] = op.kappa[k] * rate_uniform_slope(s[k], op.kin.Vt, op.kin.alpha)
+    return (op.L + sp.diags(d)).tocsr()
+
+
+def step_diagonal(op: Operator) -> np.ndarray:
+    """d_c of the pseudo-time step: the diagonal of -L plus, in kinetics mode 1, the
+    affine law's reaction slope k0 a_c (e^{alpha V~} + e^{(alpha-1) V~}) at the same
+    dimensionless voltage (the step does not depend on the state)."""
+    d = -op.L.diagonal()
+    if op.nonlinear:
+        d = d + op.kappa * op.kin.B
+    return d
 
 
 def residual(op: Operator, s: np.ndarray) -> float:
@@ -249,27 +314,60 @@ def steady_state(op: Operator, direct_max: int = 40000, rtol: float = 1e-14) -> 
     Up to ``direct_max`` unknowns: sparse LU (SuperLU). Larger systems: GMRES on the
     row-scaled system D^{-1} L (D = diag L) with an incomplete-LU preconditioner, to a
     relative residual of ``rtol``; both are library linear solvers of the same system."""
+    if op.nonlinear:
+        return newton_steady_state(op, direct_max=direct_max, rtol=rtol)
     u = op.unknown
     s = op.fixed.copy()
     Luu = op.L[u][:, u].tocsc()
     rhs_u = -(op.b[u] + op.L[u] @ op.fixed)
-    if Luu.shape[0] <= direct_max:
-        s[u] = spla.spsolve(Luu, rhs_u)
-        return s
-    dinv = sp.diags(1.0 / Luu.diagonal())
-    As = (dinv @ Luu).tocsc()
-    rs = dinv @ rhs_u
+    s[u] = _linear_solve(Luu, rhs_u, direct_max, rtol)
+    return s
+
+
+def _linear_solve(A: sp.spmatrix, r: np.ndarray, direct_max: int, rtol: float) -> np.ndarray:
+    if A.shape[0] <= direct_max:
+        return spla.spsolve(A.tocsc(), r)
+    dinv = sp.diags(1.0 / A.diagonal())
+    As = (dinv @ A).tocsc()
+    rs = dinv @ r
     ilu = spla.spilu(As, drop_tol=1e-5, fill_factor=10)
     M = spla.LinearOperator(As.shape, ilu.solve)
     x, info = spla.gmres(As, rs, M=M, rtol=rtol, atol=0.0, restart=200, maxiter=20)
     if info != 0:
         raise RuntimeError("oracle GMRES did not reach rtol=%g (info=%d)" % (rtol, info))
-    s[u] = x
-    return s
+    return x
+
+
+def newton_steady_state(op: Operator, s0: Optional[np.ndarray] = None, direct_max: int = 40000,
+                        rtol: float = 1e-14, max_iter: int = 60) -> np.ndarray:
+    """RHS(s) = 0 for kinetics mode 1 by Newton's method on the unknown cells:
+    J(s) ds = -RHS(s) with J = L + diag(kappa R~'(s)), steps halved while they would
+    leave (0, 1); from s = s_in (clamped into (0, 1)) unless s0 is given. Stops when the
+    step is below rtol max|s|."""
+    u = op.unknown
+    if s0 is None:
+        s = initial_state(op, op.s_in)
+    else:
+        s = np.array(s0, dtype=np.float64)
+    s[u] = np.clip(s[u], 1e-12, 1.0 - 1e-12)
+    for _ in range(max_iter):
+        r = rhs(op, s)[u]
+        J = jacobian(op, s)[u][:, u]
+        ds = _linear_solve(J, -r, direct_max, rtol)
+        lam = 1.0
+        while True:
+            t_ = s[u] + lam * ds
+            if np.all(t_ > 0.0) and np.all(t_ < 1.0):
+                break
+            lam *= 0.5
+        s[u] = t_
+        if lam == 1.0 and np.max(np.abs(ds)) <= rtol * max(1.0, float(np.max(np.abs(s)))):
+            return s
+    raise RuntimeError("oracle Newton iteration did not converge")
 
 
 def dt_global(op: Operator, cfl: float) -> float:
-    d = -op.L.diagonal()[op.unknown]
+    d = step_diagonal(op)[op.unknown]
     return cfl / float(d.max())
 
 
@@ -277,9 +375,11 @@ def explicit_iterate(op: Operator, cfl: float, tol: float, s0: Optional[np.ndarr
                      max_steps: int = 10_000_000, check_every: int = 1, local_dt: bool = False):
     """Explicit pseudo-time stepping to tau*RMS(RHS) < tol, two buffers as in Algorithm 7.
 
+    In kinetics mode 1 the update is clipped into [0, 1] (a guard of Sec. III.B; at a
+    converged state it does not bind, since there RHS = 0 with s inside the interval).
     Returns (s, steps)."""
     u = op.unknown
-    d = -op.L.diagonal()
+    d = step_diagonal(op)
     if local_dt:
         dt = np.where(u, cfl / np.where(d > 0, d, 1.0), 0.0)
     else:
@@ -290,7 +390,9 @@ def explicit_iterate(op: Operator, cfl: float, tol: float, s0: Optional[np.ndarr
     n = 0
     while n < max_steps:
         i, j = n % 2, (n + 1) % 2
-        s[j] = s[i] + dt * (op.L @ s[i] + op.b)
+        s[j] = s[i] + dt * rhs(op, s[i])
+        if op.nonlinear:
+            s[j] = np.clip(s[j], 0.0, 1.0)
         s[j][~u] = op.fixed[~u]
         n += 1
         if n % check_every == 0 and residual(op, s[j]) < tol:
@@ -324,7 +426,7 @@ def outputs(p: Problem, op: Operator, s: np.ndarray) -> Outputs:
     nz, ny, nx = solid.shape
     h = p.h
     scale = p.n_e * FARADAY * p.c0
-    I_tot = scale * h ** 3 * float(np.sum(op.kappa * rate_affine(s, op.kin)))
+    I_tot = scale * h ** 3 * float(np.sum(source(op, s)))
     s3 = s.reshape(nz, ny, nx)
     fin = ~solid[0]
     fout = ~solid[-1]
@@ -365,6 +467,8 @@ def umt(p: Problem, s: Optional[np.ndarray] = None) -> float:
 # The steady state solves RHS(s; m, beta) = L(m, beta) s + b(m, beta) = 0 (linear in s,
 # Eq. rate-from-soc-gen). For an objective J(s, m, beta):
 #   L^T lam = -dJ/ds,   dJ/dp = dJ/dp|explicit + lam . dRHS/dp
+# In kinetics mode 1 (nonlinear source) L is the Jacobian dRHS/ds at the steady state,
+# L + diag(kappa R~'(s)), and R~ below is the mode-1 rate.
 # with dRHS_c/dm_c = k0 n_wall(c)/h R~(s_c) (only row c) and dRHS/dbeta = the advective
 # part of RHS divided by beta (every face velocity carries beta). Objectives:
 #   'I_tot' : J = n_e F c0 h^3 sum_c k0 m_c n_wall/h R~(s_c)              (Eq. I-tot-def)
@@ -392,8 +496,16 @@ def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
     fl = p.solid.ravel() == 0
     kap0 = np.where(fl, p.k0 * nw / h, 0.0)             # dkappa/dm
     g = np.zeros(N)
+    if op.nonlinear:
+        slope = np.zeros(N)
+        k = kap0 != 0
+        slope[k] = rate_uniform_slope(s[k], op.kin.Vt, op.kin.alpha)
+        R = rate_uniform(s, op.kin.Vt, op.kin.alpha)
+    else:
+        slope = np.full(N, -op.kin.B)
+        R = rate_affine(s, op.kin)
     if objective in ("I_tot", "U"):
-        g = -scale * kap0 * m * op.kin.B                # dI_tot/ds
+        g = scale * kap0 * m * slope                    # dI_tot/ds
         denom = p.n_e * FARADAY * p.c0 * op.Q * (1.0 - p.s_in)
         if objective == "U":
             g = g / denom
@@ -405,11 +517,10 @@ def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
         g = np.where(u, w_out / w_out.sum(), 0.0)
     else:
         raise ValueError(objective)
-    Luu = op.L[u][:, u]
+    Luu = jacobian(op, s)[u][:, u]
     lam = np.zeros(N)
     lam[u] = spla.spsolve(Luu.T.tocsc(), -g[u])
     # gradients
-    R = rate_affine(s, op.kin)
     dm = np.zeros(N)
     if objective == "I_tot":
         dm = (scale + lam) * kap0 * R

@@ -339,12 +339,14 @@ def _fd_objective(p, objective):
     return o.I_tot if objective == "I_tot" else o.U
 
 
-@pytest.mark.parametrize("objective", ["I_tot", "U", "U_mt"])
-def test_oracle_adjoint_matches_central_differences(objective):
+@pytest.mark.parametrize("objective,kmode", [("I_tot", 0), ("U", 0), ("U_mt", 0),
+                                            ("I_tot", 1), ("U", 1)])
+def test_oracle_adjoint_matches_central_differences(objective, kmode):
     """The adjoint gradients equal central finite differences of the steady-state solve
-    with respect to the per-voxel area multiplier and the velocity scale."""
+    with respect to the per-voxel area multiplier and the velocity scale (kinetics mode 1:
+    of Newton solves of the nonlinear problem, adjoint of the Jacobian at the solution)."""
     import dataclasses
-    base = _p3((8, 8, 12))
+    base = _p3((8, 8, 12), kinetics_mode=kmode)
     rng = np.random.default_rng(40)
     nw = soc.n_wall(base.solid.astype(bool)).ravel()
     fl = base.solid.ravel() == 0
@@ -370,3 +372,124 @@ def test_oracle_adjoint_matches_central_differences(objective):
     jm = _fd_objective(dataclasses.replace(p, beta=1 - eps), objective)
     fd = (jp - jm) / (2 * eps)
     assert abs(fd - adj["d_beta"]) <= 1e-6 * abs(fd), (fd, adj["d_beta"])
+
+
+# ------------------------------------ kinetics mode 1: uniform activation overpotential
+
+def test_uniform_eta_rate_is_the_butler_volmer_source():
+    """Eq. source-term-bv (alpha = 1/2): R~ = 2 sqrt(s(1-s)) sinh(eta~/2); for any alpha,
+    substituting eta~ = V~ - logit(s) (Eq. etat-from-s) gives the affine law
+    (Eq. rate-from-soc-gen); R~ vanishes at s = 0 and s = 1 and is positive between them
+    for a reducing eta~ > 0."""
+    s = np.linspace(0.0, 1.0, 41)
+    for etat in (0.3, 3.9, 7.79):
+        ref = 2.0 * np.sqrt(s * (1.0 - s)) * math.sinh(etat / 2.0)
+        assert np.allclose(soc.rate_uniform(s, etat, 0.5), ref, rtol=1e-13, atol=1e-13)
+        r = soc.rate_uniform(s, etat, 0.5)
+        assert r[0] == 0.0 and r[-1] == 0.0 and np.all(r[1:-1] > 0.0)
+    si = np.linspace(0.01, 0.99, 33)
+    for alpha in (0.3, 0.5, 0.7):
+        for eta in (-0.1, -0.03, 0.02):
+            kin = soc.kinetics(eta, alpha)
+            etat = kin.Vt - np.log(si / (1.0 - si))
+            got = np.array([soc.rate_uniform(x, e, alpha) for x, e in zip(si, etat)])
+            assert np.allclose(got, soc.rate_affine(si, kin), rtol=1e-11, atol=1e-12)
+
+
+def test_uniform_eta_slope_matches_central_differences():
+    s = np.linspace(0.02, 0.98, 25)
+    for alpha in (0.3, 0.5, 0.7):
+        for etat in (0.5, 7.79):
+            e = 1e-6
+            fd = (soc.rate_uniform(s + e, etat, alpha) - soc.rate_uniform(s - e, etat, alpha)) / (2 * e)
+            assert np.allclose(soc.rate_uniform_slope(s, etat, alpha), fd, rtol=1e-7, atol=1e-7)
+
+
+def _bisect(f, lo, hi):
+    flo = f(lo)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        fm = f(mid)
+        if (fm > 0) == (flo > 0):
+            lo, flo = mid, fm
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.3])
+def test_uniform_eta_channel_without_diffusion_is_solved_cell_by_cell(alpha):
+    """With D = 0 the 1D channel's rows decouple downstream: cell k solves
+    (w/h)(s_{k-1} - s_k) + kappa R~(s_k) = 0 (s_{-1} = s_in), a concave scalar equation
+    with one root in [s_{k-1}, 1]; bisection cell by cell gives the exact discrete state
+    that the oracle's Newton solve of the assembled system must reproduce."""
+    n, w, h, k0, m, eta, s_in = 30, 0.004, 1.25e-6, 5e-6, 0.8, -0.06, 0.2
+    solid, U, V, W, _ = channel_1d(n, w, h)
+    p = soc.Problem(solid, U, V, W, h, 0.0, s_in, k0=k0, eta=eta, alpha=alpha,
+                    area_mult=np.full(solid.shape, m), kinetics_mode=1)
+    op = soc.assemble(p)
+    s = soc.steady_state(op).reshape(solid.shape)[:, 1, 1]
+    etat = soc.kinetics(eta, alpha).Vt
+    kappa = k0 * m * 4 / h
+    prev, ref = s_in, []
+    for _ in range(n):
+        f = lambda x, pr=prev: (w / h) * (pr - x) + kappa * float(soc.rate_uniform(x, etat, alpha))
+        prev = _bisect(f, prev, 1.0)
+        ref.append(prev)
+    assert np.max(np.abs(s - np.array(ref))) < 1e-13
+    assert ref[-1] > s_in + 0.05       # the reaction matters
+
+
+def test_uniform_eta_plug_flow_closed_form_first_order():
+    """alpha = 1/2, D = 0: ds/dz = (k0 a/w) 2 sqrt(s(1-s)) sinh(eta~/2) integrates with
+    s = sin^2(theta) to s(z) = sin^2(asin(sqrt(s_in)) + (k0 a/w) sinh(eta~/2) z); the
+    upwind solution approaches it at first order in h."""
+    L, w, eta, s_in, k0, h0 = 50e-6, 0.01, -0.05, 0.1, 1e-5, 1.25e-6
+    etat = soc.kinetics(eta).Vt
+    c = k0 * 4 / h0 * math.sinh(etat / 2) / w
+    assert math.asin(math.sqrt(s_in)) + c * L < math.pi / 2
+    errs = []
+    for n in (20, 40, 80, 160):
+        h = L / n
+        solid, U, V, W, _ = channel_1d(n, w, h)
+        p = soc.Problem(solid, U, V, W, h, 0.0, s_in, k0=k0, eta=eta,
+                        area_mult=np.full(solid.shape, h / h0), kinetics_mode=1)
+        s = soc.steady_state(soc.assemble(p)).reshape(solid.shape)[:, 1, 1]
+        z = (np.arange(n) + 1.0) * h
+        exact = np.sin(math.asin(math.sqrt(s_in)) + c * z) ** 2
+        errs.append(np.max(np.abs(s - exact)))
+    assert errs[0] > 1e-3
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in ratios), ratios
+
+
+@pytest.mark.parametrize("local_dt", [True, False])
+def test_uniform_eta_3d_newton_explicit_and_balance(local_dt):
+    """On a fiber lattice: the Newton state has RHS = 0, the explicit pseudo-time loop
+    (clip guard never active at the end) reaches it, I_tot = F_out - F_in holds, and
+    s_in <= s <= 1 (the source is >= 0 for a reducing overpotential)."""
+    p = _p3((12, 12, 24), kinetics_mode=1, k0=2e-6)
+    op = soc.assemble(p)
+    assert op.nonlinear
+    s = soc.steady_state(op)
+    assert soc.residual(op, s) < 1e-12
+    o = soc.outputs(p, op, s)
+    assert o.mass_balance_rel < 1e-10
+    fl = p.solid.ravel() == 0
+    assert np.all(s[fl] >= p.s_in - 1e-14) and np.all(s[fl] < 1.0)
+    se, n = soc.explicit_iterate(op, 0.4, 1e-12, s0=soc.initial_state(op, p.s_in),
+                                 check_every=50, local_dt=local_dt)
+    assert np.max(np.abs(se - s)) < 1e-10
+    # mode 1 is a different problem from mode 0 at the same overpotential
+    s0 = soc.steady_state(soc.assemble(_p3((12, 12, 24), k0=2e-6)))
+    assert np.max(np.abs(s0 - s)) > 1e-4
+
+
+def test_uniform_eta_zero_overpotential_is_inert():
+    """eta = 0 gives eta~ = 0 and R~ = 0: with divergence-free faces s = s_in is steady."""
+    p = _p3((12, 12, 24), kinetics_mode=1, k0=2e-6, eta=0.0)
+    op = soc.assemble(p)
+    s = soc.initial_state(op, p.s_in)
+    assert np.max(np.abs(soc.rhs(op, s))) < 1e-9 * np.max(np.abs(op.L.diagonal()))
