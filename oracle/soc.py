@@ -339,21 +339,29 @@ def _linear_solve(A: sp.spmatrix, r: np.ndarray, direct_max: int, rtol: float) -
 
 
 def newton_steady_state(op: Operator, s0: Optional[np.ndarray] = None, direct_max: int = 40000,
-                        rtol: float = 1e-14, max_iter: int = 60) -> np.ndarray:
-    """RHS(s) = 0 for kinetics mode 1 by Newton's method on the unknown cells:
-    J(s) ds = -RHS(s) with J = L + diag(kappa R~'(s)), steps halved while they would
-    leave (0, 1); from s = s_in (clamped into (0, 1)) unless s0 is given. Stops when the
-    step is below rtol max|s|."""
+                        rtol: float = 1e-14, max_iter: int = 400) -> np.ndarray:
+    """RHS(s) = 0 for kinetics mode 1 by Newton's method globalised with pseudo-transient
+    continuation (Kelley and Keyes, SIAM J. Numer. Anal. 35, 1998): on the unknown cells
+    (D/delta - J(s)) ds = RHS(s), with J = L + diag(kappa R~'(s)) the exact Jacobian and D
+    the pseudo-time step diagonal (``step_diagonal``); delta starts at 0.4 (one implicit
+    step of the explicit loop's size) and grows by switched evolution relaxation,
+    delta <- delta ||RHS_prev|| / ||RHS||, so the iteration turns into Newton's method near
+    the solution. Steps are halved while they would leave (0, 1). Starts from s = s_in
+    (clamped into (0, 1)) unless s0 is given; stops once delta is large (a Newton step)
+    and the step is below rtol max|s|, or below 1e-9 max|s| and no smaller than half the
+    previous one (the rounding floor of the linear solves)."""
     u = op.unknown
-    if s0 is None:
-        s = initial_state(op, op.s_in)
-    else:
-        s = np.array(s0, dtype=np.float64)
+    s = initial_state(op, op.s_in) if s0 is None else np.array(s0, dtype=np.float64)
     s[u] = np.clip(s[u], 1e-12, 1.0 - 1e-12)
+    d = step_diagonal(op)[u]
+    delta = 0.4
+    r = rhs(op, s)[u]
+    rn = float(np.linalg.norm(r))
+    prev = math.inf
     for _ in range(max_iter):
-        r = rhs(op, s)[u]
         J = jacobian(op, s)[u][:, u]
-        ds = _linear_solve(J, -r, direct_max, rtol)
+        A = (sp.diags(d / delta) - J).tocsr() if delta < 1e15 else -J
+        ds = _linear_solve(A, r, direct_max, rtol)
         lam = 1.0
         while True:
             t_ = s[u] + lam * ds
@@ -361,9 +369,34 @@ def newton_steady_state(op: Operator, s0: Optional[np.ndarray] = None, direct_ma
                 break
             lam *= 0.5
         s[u] = t_
-        if lam == 1.0 and np.max(np.abs(ds)) <= rtol * max(1.0, float(np.max(np.abs(s)))):
+        r = rhs(op, s)[u]
+        rn_new = float(np.linalg.norm(r))
+        step = float(np.max(np.abs(ds))) if ds.size else 0.0
+        scale = max(1.0, float(np.max(np.abs(s))))
+        newton = delta >= 1e12
+        if newton and lam == 1.0 and (step <= rtol * scale or
+                                      (step <= 1e-9 * scale and step >= 0.5 * prev)):
             return s
-    raise RuntimeError("oracle Newton iteration did not converge")
+        prev = step if (newton and lam == 1.0) else math.inf
+        if rn_new == 0.0:
+            return s
+        delta = min(delta * rn / rn_new, 1e16) if lam == 1.0 else max(delta * 0.5, 1e-3)
+        rn = rn_new
+    raise RuntimeError("oracle pseudo-transient Newton iteration did not converge")
+
+
+def nonlinear_step_cap(op: Operator, s: np.ndarray, cfl: float) -> np.ndarray:
+    """Kinetics mode 1: cfl / (d_T,c + kappa_c max(0, -R~'(s_c))) per cell, d_T the
+    transport diagonal of -L. Near s = 1 the rate's slope grows like (1-s)^(-alpha), and
+    the explicit update stays stable only with a step below the inverse of that local
+    stiffness; the slope is taken at min(s, 1 - 2^-40) so the cap never reaches 0."""
+    d = -op.L.diagonal()
+    sh = np.minimum(s, 1.0 - 2.0 ** -40)
+    sl = np.zeros(s.size)
+    k = (op.kappa != 0) & (sh > op.kin.alpha)
+    sl[k] = -rate_uniform_slope(sh[k], op.kin.Vt, op.kin.alpha)
+    den = d + op.kappa * sl
+    return np.where(den > 0, cfl / np.where(den > 0, den, 1.0), np.inf)
 
 
 def dt_global(op: Operator, cfl: float) -> float:
@@ -375,8 +408,10 @@ def explicit_iterate(op: Operator, cfl: float, tol: float, s0: Optional[np.ndarr
                      max_steps: int = 10_000_000, check_every: int = 1, local_dt: bool = False):
     """Explicit pseudo-time stepping to tau*RMS(RHS) < tol, two buffers as in Algorithm 7.
 
-    In kinetics mode 1 the update is clipped into [0, 1] (a guard of Sec. III.B; at a
-    converged state it does not bind, since there RHS = 0 with s inside the interval).
+    In kinetics mode 1 each cell's step is also capped by ``nonlinear_step_cap`` (the
+    fixed point does not depend on the step) and the update is clipped into [0, 1] (a
+    guard of Sec. III.B; at a converged state it does not bind, since there RHS = 0 with
+    s inside the interval).
     Returns (s, steps)."""
     u = op.unknown
     d = step_diagonal(op)
@@ -390,9 +425,11 @@ def explicit_iterate(op: Operator, cfl: float, tol: float, s0: Optional[np.ndarr
     n = 0
     while n < max_steps:
         i, j = n % 2, (n + 1) % 2
-        s[j] = s[i] + dt * rhs(op, s[i])
         if op.nonlinear:
-            s[j] = np.clip(s[j], 0.0, 1.0)
+            dtn = np.minimum(dt, nonlinear_step_cap(op, s[i], cfl))
+            s[j] = np.clip(s[i] + dtn * rhs(op, s[i]), 0.0, 1.0)
+        else:
+            s[j] = s[i] + dt * rhs(op, s[i])
         s[j][~u] = op.fixed[~u]
         n += 1
         if n % check_every == 0 and residual(op, s[j]) < tol:

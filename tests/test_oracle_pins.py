@@ -465,12 +465,14 @@ def test_uniform_eta_plug_flow_closed_form_first_order():
     assert all(1.8 < r < 2.2 for r in ratios), ratios
 
 
-@pytest.mark.parametrize("local_dt", [True, False])
-def test_uniform_eta_3d_newton_explicit_and_balance(local_dt):
+@pytest.mark.parametrize("local_dt,k0", [(True, 2e-6), (False, 2e-6), (True, 6e-6),
+                                         (False, 6e-6)])
+def test_uniform_eta_3d_newton_explicit_and_balance(local_dt, k0):
     """On a fiber lattice: the Newton state has RHS = 0, the explicit pseudo-time loop
     (clip guard never active at the end) reaches it, I_tot = F_out - F_in holds, and
-    s_in <= s <= 1 (the source is >= 0 for a reducing overpotential)."""
-    p = _p3((12, 12, 24), kinetics_mode=1, k0=2e-6)
+    s_in <= s <= 1 (the source is >= 0 for a reducing overpotential). k0 = 6e-6 drives
+    wall cells to s > 0.9999, where the rate's slope is steep and the step cap acts."""
+    p = _p3((12, 12, 24), kinetics_mode=1, k0=k0)
     op = soc.assemble(p)
     assert op.nonlinear
     s = soc.steady_state(op)
@@ -479,11 +481,15 @@ def test_uniform_eta_3d_newton_explicit_and_balance(local_dt):
     assert o.mass_balance_rel < 1e-10
     fl = p.solid.ravel() == 0
     assert np.all(s[fl] >= p.s_in - 1e-14) and np.all(s[fl] < 1.0)
+    if k0 > 5e-6:
+        assert s[fl].max() > 0.9999
+        cap = soc.nonlinear_step_cap(op, s, 0.4)
+        assert np.any(cap[op.unknown] < soc.dt_global(op, 0.4))
     se, n = soc.explicit_iterate(op, 0.4, 1e-12, s0=soc.initial_state(op, p.s_in),
                                  check_every=50, local_dt=local_dt)
     assert np.max(np.abs(se - s)) < 1e-10
     # mode 1 is a different problem from mode 0 at the same overpotential
-    s0 = soc.steady_state(soc.assemble(_p3((12, 12, 24), k0=2e-6)))
+    s0 = soc.steady_state(soc.assemble(_p3((12, 12, 24), k0=k0)))
     assert np.max(np.abs(s0 - s)) > 1e-4
 
 
