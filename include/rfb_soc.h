@@ -67,12 +67,33 @@ typedef enum rfb_dt_mode {
     RFB_DT_LOCAL = 1     /* dt_c = cfl / d_c per cell (same fixed point, fewer sweeps) */
 } rfb_dt_mode;
 
+/* How the overpotential argument of a solve enters the source term. With
+ * eta~ = -n_e eta / V_T (Eq. etat-def; the same number as V~ = n_e V_ar / V_T with
+ * V_ar = -eta):
+ *   RFB_KIN_AFFINE       eta is the activation overpotential at s = 1/2 (phi_L = 0), so the
+ *                        applied voltage is uniform and the rate is the affine law
+ *                        R~(s) = e^{alpha V~} (1 - (1 + e^{-V~}) s) (Eq. rate-from-soc-gen);
+ *                        the steady problem is linear. Default.
+ *   RFB_KIN_UNIFORM_ETA  eta is the activation overpotential itself, uniform over the
+ *                        electrode: R~(s) = s^alpha (1-s)^(1-alpha) (e^{alpha eta~} -
+ *                        e^{(alpha-1) eta~}) (Eq. source-term-bv-gen), nonlinear in s.
+ *                        FP64 precision only (solve / step return RFB_ERR_INVALID_ARG for
+ *                        RFB_PREC_MIXED; batches refuse such handles). The explicit update
+ *                        is clipped into [0, 1] (a guard; it does not bind at a steady
+ *                        state), and the pseudo-time step is the affine law's at the same
+ *                        eta. With s_in = 0 the rate vanishes everywhere at the start and
+ *                        s = 0 is the (trivial) steady state. */
+typedef enum rfb_kinetics_mode {
+    RFB_KIN_AFFINE = 0,
+    RFB_KIN_UNIFORM_ETA = 1
+} rfb_kinetics_mode;
+
 /* Butler-Volmer kinetics (Sec. II.B, parameter table). */
 typedef struct rfb_kinetics {
     double k0;      /* rate constant [m/s] */
     double alpha;   /* charge-transfer coefficient, 0 < alpha < 1 */
     int32_t n_e;    /* electrons per reaction (2 for AQDS) */
-    int32_t pad_;
+    int32_t mode;   /* rfb_kinetics_mode (0 = RFB_KIN_AFFINE) */
     double T;       /* temperature [K] */
     double c0;      /* total concentration of redox species C_T [mol/m^3] */
 } rfb_kinetics;
@@ -251,6 +272,8 @@ typedef enum rfb_objective {
  * I_TOT and U need a converged rfb_soc_solve at the current operating point (and area
  * multipliers); U_MT needs a converged rfb_soc_umt. dU_mt/dm is identically zero (the
  * U_mt problem has no kinetics) and is returned as zeros. velocity_scale must be > 0.
+ * RFB_KIN_UNIFORM_ETA: the source is nonlinear; L above is the Jacobian dRHS/ds at the
+ * converged state (transport plus k0 a_c dR~/ds on the diagonal) and R~ the mode's rate.
  *   opts             nullable; dt_mode / cfl / check_every / max_sweeps are used
  *   d_area_mult      nullable; N doubles (host or device per kind) receiving dJ/dm_c
  *                    (zero on solid cells and cells without fiber neighbours)

@@ -32,6 +32,7 @@ struct OpPoint {
     double s_in = 0, eta = 0, beta = 1, cfl = 0.4;
     int inlet_bc = 0, dt_mode = 1, umt = 0;
     double A = 0, B = 0;      // affine rate law intercept / -slope
+    double K1 = 0;            // e^{alpha eta~} - e^{(alpha-1) eta~} (kinetics mode 1)
     double dt = 0;            // global step
     double dmin = 0;          // smallest diagonal (local-dt bookkeeping)
 };
@@ -151,11 +152,12 @@ Lattice lattice(const rfb_soc_handle* h) {
     return Lattice{h->nx, h->ny, h->nz, h->nxny, h->d_flags, h->d_mask32};
 }
 
-void kinetics_AB(const rfb_kinetics& k, double eta, double* A, double* B) {
+void kinetics_AB(const rfb_kinetics& k, double eta, double* A, double* B, double* K1) {
     const double VT = R_GAS * k.T / FARADAY;
-    const double Vt = k.n_e * (-eta) / VT;
+    const double Vt = k.n_e * (-eta) / VT;   // V~ (mode 0) = eta~ (mode 1), Eq. etat-def
     *A = std::exp(k.alpha * Vt);
     *B = *A * (1.0 + std::exp(-Vt));
+    *K1 = *A - std::exp((k.alpha - 1.0) * Vt);
 }
 
 template <typename T>
@@ -171,12 +173,15 @@ Coef<T> make_coef(const rfb_soc_handle* h, const OpPoint& op, bool correction, b
     C.Dh = T(h->D / (h->h * h->h));
     C.gDh = T((op.inlet_bc == RFB_INLET_GHOST ? 1.0 : 2.0) * h->D / (h->h * h->h));
     C.dt = T(op.dt);
+    const bool nl = h->kin.mode == RFB_KIN_UNIFORM_ETA && !op.umt && !correction;
     for (int n = 0; n < 8; ++n) {
         const double kap = op.umt ? 0.0 : h->kin.k0 * n / h->h;
-        C.rA[n] = (correction || op.umt) ? T(0) : T(kap * op.A);
+        C.rA[n] = (correction || op.umt) ? T(0) : T(kap * (nl ? op.K1 : op.A));
         C.rB[n] = T(kap * op.B);
     }
     C.umt = op.umt;
+    C.nl = nl ? 1 : 0;
+    C.alpha = T(h->kin.alpha);
     return C;
 }
 
@@ -202,7 +207,7 @@ void prepare(rfb_soc_handle* h, OpPoint& op) {
         LAUNCHED(h);
         h->scaled_beta = op.beta;
     }
-    kinetics_AB(h->kin, op.eta, &op.A, &op.B);
+    kinetics_AB(h->kin, op.eta, &op.A, &op.B, &op.K1);
     Coef<double> C = make_coef<double>(h, op, false, false);
     const bool local = op.dt_mode == RFB_DT_LOCAL;
     diag_kernel<<<h->grid, h->block, 0, h->stream>>>(lattice(h), C, op.cfl,
@@ -245,14 +250,18 @@ void fill_result(const rfb_soc_handle* h, const OpPoint& op, rfb_solve_result* r
 // rebuilt only when the operating point or the area multipliers changed.
 void ensure_L64(rfb_soc_handle* h, const OpPoint& op) {
     if (!h->d_L64) dalloc(h, &h->d_L64, (size_t)8 * h->N);
+    Coef<double> C = make_coef<double>(h, op, false, false);
     const double key[8] = {(double)op.umt, op.s_in,           op.A,
                            op.B,           op.beta,           (double)op.inlet_bc,
-                           (double)h->area_version, 1.0};
+                           (double)h->area_version, C.nl ? 2.0 : 1.0};
     if (h->L64_valid && std::memcmp(key, h->L64_key, sizeof key) == 0) return;
     for (int q = 0; q < 6; ++q) h->K.f[q] = h->d_L64 + (size_t)q * h->N;
     h->K.diag = h->d_L64 + (size_t)6 * h->N;
     h->K.b = h->d_L64 + (size_t)7 * h->N;
-    Coef<double> C = make_coef<double>(h, op, false, false);
+    if (C.nl) {   // mode 1: transport only; the kernels add the nonlinear source
+        for (int n = 0; n < 8; ++n) C.rA[n] = C.rB[n] = 0.0;
+        C.nl = 0;
+    }
     assemble64_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(lattice(h), C, h->K);
     LAUNCHED(h);
     std::memcpy(h->L64_key, key, sizeof key);
@@ -297,9 +306,14 @@ void sweeps64(rfb_soc_handle* h, const OpPoint& op, bool umt, int64_t n) {
     ensure_L64(h, op);
     const float* dtc = op.dt_mode == RFB_DT_LOCAL ? h->d_dtc : nullptr;
     Lattice L = lattice(h);
+    const Coef<double> C = make_coef<double>(h, op, false, false);
     for (int64_t q = 0; q < n; ++q) {
-        sweep64c_kernel<<<h->grid, h->block, 0, h->stream>>>(L, h->K, dtc, op.dt, buf[cur],
-                                                             buf[cur ^ 1], op.umt, h->kchunk);
+        if (C.nl)
+            sweep64c_kernel<true><<<h->grid, h->block, 0, h->stream>>>(
+                L, h->K, dtc, op.dt, buf[cur], buf[cur ^ 1], op.umt, h->kchunk, C, op.cfl);
+        else
+            sweep64c_kernel<false><<<h->grid, h->block, 0, h->stream>>>(
+                L, h->K, dtc, op.dt, buf[cur], buf[cur ^ 1], op.umt, h->kchunk, C, op.cfl);
         LAUNCHED(h);
         cur ^= 1;
     }
@@ -542,6 +556,10 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     bool& have = umt ? h->have_umt_state : h->have_state;
     if (!have) init_state(h, umt, op.s_in);
     const bool mixed = o.precision == RFB_PREC_MIXED;
+    if (mixed && !umt && h->kin.mode != RFB_KIN_AFFINE) {
+        set_err(h, "kinetics mode 1 (nonlinear source) runs in RFB_PREC_FP64 only");
+        throw Fail{RFB_ERR_INVALID_ARG};
+    }
     const int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, o.precision);
     rfb_solve_result r{};
     rfb_status st = RFB_OK;
@@ -705,6 +723,10 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         kin->n_e < 1 || !(kin->T > 0 && std::isfinite(kin->T)) ||
         !(kin->c0 > 0 && std::isfinite(kin->c0))) {
         set_err(nullptr, "kinetics out of range (k0 >= 0, 0 < alpha < 1, n_e >= 1, T > 0, c0 > 0)");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (kin->mode != RFB_KIN_AFFINE && kin->mode != RFB_KIN_UNIFORM_ETA) {
+        set_err(nullptr, "kinetics mode must be RFB_KIN_AFFINE (0) or RFB_KIN_UNIFORM_ETA (1)");
         return RFB_ERR_INVALID_ARG;
     }
     rfb_soc_handle* h = new rfb_soc_handle();
@@ -1117,14 +1139,8 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         const double* s = umt ? h->d_t[h->t_cur] : h->d_s[h->s_cur];
         // objective value (for the explicit beta term of U) and the scales
         rfb_solve_result fwd{};
-        {
-            Coef<double> C = make_coef<double>(h, op, false, false);
-            check_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
-                lattice(h), C, s, nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
-            LAUNCHED(h);
-            reduce_readback(h, 0);
-            fill_result(h, op, &fwd, umt ? h->n_fluid - h->n_elec : h->n_fluid);
-        }
+        check(h, op, umt, false, false);
+        fill_result(h, op, &fwd, umt ? h->n_fluid - h->n_elec : h->n_fluid);
         const double h3 = h->h * h->h * h->h;
         const double scale = h->kin.n_e * FARADAY * h->kin.c0 * h3;
         const double Q = op.beta * h->sum_w_in * h->h * h->h;
@@ -1138,10 +1154,18 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         // outlet flux sum (beta-scaled velocities / h) for U_mt's dJ/ds
         const double w_out_sum = op.beta / h->h * h->sum_w_out;
         Coef<double> C = make_coef<double>(h, op, false, op.dt_mode == RFB_DT_LOCAL);
-        const double kB1 = h->kin.k0 / h->h * op.B;
+        // dR~/ds per fiber face: -k0 B / h (affine law) or k0 K1 / h times g'(s) (mode 1)
+        const double kR = C.nl ? h->kin.k0 / h->h * op.K1 : -(h->kin.k0 / h->h * op.B);
         ensure_L64(h, op);   // L^T is gathered from the assembled rows
+        if (C.nl) {
+            // mode 1: the Jacobian at the steady state (transport + source derivative);
+            // the operator is re-assembled by the next call that needs it
+            linearise64_kernel<<<flat_grid(N), 256, 0, h->stream>>>(lattice(h), C, h->K, s);
+            LAUNCHED(h);
+            h->L64_valid = false;
+        }
         adjoint_source_kernel<<<flat_grid(N), 256, 0, h->stream>>>(lattice(h), C, umt ? 2 : 0,
-                                                                   w_out_sum, kB1, h->d_g);
+                                                                   w_out_sum, kR, s, h->d_g);
         LAUNCHED(h);
         CK(h, cudaMemsetAsync(h->d_lam[0], 0, N * 8, h->stream));
         CK(h, cudaMemsetAsync(h->d_lam[1], 0, N * 8, h->stream));
@@ -1173,7 +1197,7 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
             done += n;
         }
         // gradients
-        const double kap0A = umt ? 0.0 : h->kin.k0 / h->h * op.A;
+        const double kap0A = umt ? 0.0 : h->kin.k0 / h->h * (C.nl ? op.K1 : op.A);
         const double kap0B = umt ? 0.0 : h->kin.k0 / h->h * op.B;
         gradient_kernel<<<h->grid, h->block, 0, h->stream>>>(
             lattice(h), C, s, h->d_lam[cur], kap0A, kap0B, jscale, 1.0,
@@ -1498,6 +1522,7 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
         if (!hs[q]) { g_create_error = "NULL handle"; return RFB_ERR_INVALID_ARG; }
         if (hs[q]->device != hs[0]->device) { g_create_error = "handles on different devices"; return RFB_ERR_INVALID_ARG; }
         if (hs[q]->nx % 4 != 0) { g_create_error = "batched lattices need nx % 4 == 0"; return RFB_ERR_INVALID_ARG; }
+        if (hs[q]->kin.mode != RFB_KIN_AFFINE) { g_create_error = "batched solves need kinetics mode 0 (FP32 correction sweeps)"; return RFB_ERR_INVALID_ARG; }
         for (int p = 0; p < q; ++p)
             if (hs[p] == hs[q]) { g_create_error = "a handle appears twice"; return RFB_ERR_INVALID_ARG; }
     }

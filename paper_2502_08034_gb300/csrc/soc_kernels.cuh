@@ -61,10 +61,40 @@ struct Coef {
     T Dh;      // D / h^2
     T gDh;     // inlet diffusion coefficient: 2 D/h^2 (face) or D/h^2 (ghost)
     T dt;      // global pseudo-time step
-    T rA[8];   // k0 n_wall / h * A     by n_wall (zero in correction sweeps / U_mt)
-    T rB[8];   // k0 n_wall / h * B     by n_wall (zero in U_mt)
+    T rA[8];   // k0 n_wall / h * A     by n_wall (zero in correction sweeps / U_mt);
+               // kinetics mode 1: k0 n_wall / h * (e^{alpha eta~} - e^{(alpha-1) eta~})
+    T rB[8];   // k0 n_wall / h * B     by n_wall (zero in U_mt); in mode 1 it only
+               // bounds the pseudo-time step
     int umt;   // electrode cells are Dirichlet (value untouched), no reaction
+    int nl;    // kinetics mode 1 (FP64 kernels only): source rA * g(s), see g_uniform
+    T alpha;   // charge-transfer coefficient (mode 1)
 };
+
+// Kinetics mode 1, the Butler-Volmer rate at a uniform activation overpotential
+// (Eq. source-term-bv-gen): R~(s) = K1 g(s) with g(s) = s^alpha (1-s)^(1-alpha) and
+// K1 = e^{alpha eta~} - e^{(alpha-1) eta~}; g is evaluated on s clamped into [0, 1].
+__device__ __forceinline__ double g_uniform(double s, double alpha) {
+    s = fmin(fmax(s, 0.0), 1.0);
+    if (alpha == 0.5) return sqrt(s * (1.0 - s));
+    return pow(s, alpha) * pow(1.0 - s, 1.0 - alpha);
+}
+
+// g'(s) = s^(alpha-1) (1-s)^(-alpha) (alpha - s) = g(s) (alpha - s) / (s (1 - s)),
+// for 0 < s < 1 (the adjoint's linearisation at a steady state).
+__device__ __forceinline__ double g_uniform_slope(double s, double alpha) {
+    return g_uniform(s, alpha) * (alpha - s) / (s * (1.0 - s));
+}
+
+// Source k0 a_c R~(s_c) of one cell from the per-n_wall tables: affine (A - B s), or
+// mode 1 (FP64 only) K1 g(s).
+template <typename T>
+__device__ __forceinline__ T reaction(const Coef<T>& C, const T* tA, const T* tB, int nw,
+                                      T mult, T sc) {
+    if constexpr (sizeof(T) == 8) {
+        if (C.nl) return mult * tA[nw] * g_uniform(sc, C.alpha);
+    }
+    return mult * (tA[nw] - tB[nw] * sc);
+}
 
 // q > 0 for an FP64 q, decided on the integer pipe (the FP64 pipe of GB300 is narrow);
 // identical to the floating-point comparison for every non-NaN q, including -0.0.
@@ -101,8 +131,8 @@ __device__ __forceinline__ T cell_rhs(const Coef<T>& C, const T* tA, const T* tB
     T nsum = ((sxm + sxp) + (sym + syp)) + (zmd + szp);
     T dif = C.Dh * nsum - (T(6) * C.Dh) * sc;
     if (inlet) dif += C.gDh * (C.s_in - sc);
-    // Butler-Volmer source k0 a_c (A - B s)
-    T rea = mult * (tA[nw] - tB[nw] * sc);
+    // Butler-Volmer source k0 a_c R~(s)
+    T rea = reaction<T>(C, tA, tB, nw, mult, sc);
     return (adv + dif) + rea;
 }
 
@@ -506,9 +536,23 @@ __device__ __forceinline__ double rhs64(const L64& K, int64_t c, double sc, doub
 }
 
 // FP64 sweep s_out = s + dt RHS(s) with the assembled operator (2.5D z marching).
+// NL (kinetics mode 1): the operator holds transport only; the source
+// k_c g(s_c), k_c = m_c rA[n_wall], is added per cell; the step is capped by the source's
+// local stiffness, dt <= cfl / (d_T + k_c max(0, -g'(s))) with d_T = -diag the transport
+// diagonal and the slope taken at min(s, 1 - 2^-40) (near s = 1 it grows like
+// (1-s)^(-alpha)); the update is clipped into [0, 1] (a guard that does not bind at a
+// steady state). C and cfl are read only for NL.
+template <bool NL>
 __global__ void __launch_bounds__(BX * BY)
 sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_global,
-                const double* __restrict__ s, double* __restrict__ s_out, int umt, int kchunk) {
+                const double* __restrict__ s, double* __restrict__ s_out, int umt, int kchunk,
+                Coef<double> C, double cfl) {
+    __shared__ double tK[8];
+    if (NL) {
+        const int t = threadIdx.y * BX + threadIdx.x;
+        if (t < 8) tK[t] = C.rA[t];
+        __syncthreads();
+    }
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     if (i >= L.nx || j >= L.ny) return;
@@ -524,13 +568,47 @@ sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_globa
         const double s_next = (k + 1 < L.nz) ? s[c + nxny] : 0.0;
         const unsigned f = L.flags[c];
         if ((f & F_FLUID) && !(umt && (f & F_ELEC))) {
-            const double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym], s[c + oyp],
-                                   s_prev, s_next);
+            double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym], s[c + oyp],
+                             s_prev, s_next);
             const double dt = dtc ? (double)dtc[c] : dt_global;
-            s_out[c] = fma(dt, r, s_cur);
+            if (NL) {
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                const double kc = (C.m ? C.m[c] : 1.0) * tK[nw];
+                r += kc * g_uniform(s_cur, C.alpha);
+                const double sh = fmin(s_cur, 1.0 - 0x1p-40);
+                const double sl = (kc != 0.0 && sh > C.alpha) ? -g_uniform_slope(sh, C.alpha)
+                                                              : 0.0;
+                const double cap = cfl / (kc * sl - K.diag[c]);
+                s_out[c] = fmin(fmax(fma(fmin(dt, cap), r, s_cur), 0.0), 1.0);
+            } else {
+                s_out[c] = fma(dt, r, s_cur);
+            }
         }
         s_prev = s_cur;
         s_cur = s_next;
+    }
+}
+
+// Kinetics mode 1: adds the source's derivative m_c rA[n_wall] g'(s_c) to the assembled
+// diagonal, so that the operator becomes the Jacobian dRHS/ds at the state s (the
+// adjoint of the nonlinear steady state).
+__global__ void linearise64_kernel(Lattice L, Coef<double> C, L64 K,
+                                   const double* __restrict__ s) {
+    __shared__ double tK[8];
+    if (threadIdx.x < 8) tK[threadIdx.x] = C.rA[threadIdx.x];
+    __syncthreads();
+    const int64_t N = (int64_t)L.nxny * L.nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = L.flags[c];
+        if (!(f & F_FLUID) || (C.umt && (f & F_ELEC))) continue;
+        const int i = (int)(c % L.nx);
+        const int j = (int)((c / L.nx) % L.ny);
+        const int k = (int)(c / L.nxny);
+        const int nw = n_wall_of(f, i, j, k, L.nx, L.ny, L.nz);
+        if (nw == 0) continue;
+        const double mult = C.m ? C.m[c] : 1.0;
+        K.diag[c] += mult * tK[nw] * g_uniform_slope(s[c], C.alpha);
     }
 }
 
@@ -705,7 +783,7 @@ __device__ __forceinline__ void check_column(const Lattice& L, const Coef<double
                 } else if (WRITE_R) {
                     r_out[c] = 0.0f;
                 }
-                acc[1] += mult * (tA[nw] - tB[nw] * s_cur);
+                acc[1] += reaction<double>(C, tA, tB, nw, mult, s_cur);
                 if (k == 0) {
                     acc[2] += C.gDh * (C.s_in - s_cur);
                     acc[3] += wL * C.s_in;
@@ -771,9 +849,13 @@ check64c_kernel(Lattice L, Coef<double> C, L64 K, const double* __restrict__ s,
             if (FUSE) s_new[c] = s_cur;
             if (f & F_FLUID) {
                 const bool pinned = C.umt && (f & F_ELEC);
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                const double mult = C.m ? C.m[c] : 1.0;
+                const double src = reaction<double>(C, tA, tB, nw, mult, s_cur);
                 if (!pinned) {
-                    const double r = rhs64(K, c, s_cur, val(c + oxm), val(c + oxp), val(c + oym),
-                                           val(c + oyp), s_prev, s_next);
+                    double r = rhs64(K, c, s_cur, val(c + oxm), val(c + oxp), val(c + oym),
+                                     val(c + oyp), s_prev, s_next);
+                    if (C.nl) r += src;   // mode 1: the operator holds transport only
                     if (isfinite(r)) {
                         acc[0] += r * r;
                         acc[7] = fmax(acc[7], fabs(r));
@@ -784,9 +866,7 @@ check64c_kernel(Lattice L, Coef<double> C, L64 K, const double* __restrict__ s,
                 } else if (WRITE_R) {
                     r_out[c] = 0.0f;
                 }
-                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
-                const double mult = C.m ? C.m[c] : 1.0;
-                acc[1] += mult * (tA[nw] - tB[nw] * s_cur);
+                acc[1] += src;
                 if (k == 0) {
                     acc[2] += C.gDh * (C.s_in - s_cur);
                     acc[3] += C.w[c] * C.s_in;
@@ -1196,9 +1276,12 @@ adjoint_kernel(Lattice L, Coef<double> C, const double* __restrict__ lam,
 }
 
 // g~ = dJ/ds / jscale on unknown fluid cells (0 elsewhere):
-//   OBJ 0 (I_tot, U): -m_c kappa0(n_wall) B;   OBJ 2 (U_mt): [outlet] w_c / w_out_sum
+//   OBJ 0 (I_tot, U): m_c n_wall kR R~'(s_c)/K with kR = -k0 B / h (affine law, R~' = -B)
+//                     or k0 K1 / h (mode 1, times g'(s_c));
+//   OBJ 2 (U_mt):     [outlet] w_c / w_out_sum
 __global__ void adjoint_source_kernel(Lattice L, Coef<double> C, int obj, double w_out_sum,
-                                      double kB1, double* __restrict__ g) {
+                                      double kR, const double* __restrict__ s,
+                                      double* __restrict__ g) {
     const int64_t N = (int64_t)L.nxny * L.nz;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -1212,7 +1295,8 @@ __global__ void adjoint_source_kernel(Lattice L, Coef<double> C, int obj, double
                 if (k == L.nz - 1) x = C.w[c + L.nxny] / w_out_sum;
             } else {
                 const int nw = n_wall_of(f, i, j, k, L.nx, L.ny, L.nz);
-                x = -(C.m ? C.m[c] : 1.0) * kB1 * nw;   // kB1 = k0 B / h per fiber face
+                x = (C.m ? C.m[c] : 1.0) * kR * nw;
+                if (C.nl && nw > 0) x *= g_uniform_slope(s[c], C.alpha);
             }
         }
         g[c] = x;
@@ -1220,7 +1304,8 @@ __global__ void adjoint_source_kernel(Lattice L, Coef<double> C, int obj, double
 }
 
 // Gradients at the steady state s with adjoint lam~ = lam / jscale:
-//   dm[c] = jscale (mscale + lam~_c) kappa0(n_wall) R~(s_c)   (fluid cells, OBJ 0)
+//   dm[c] = jscale (mscale + lam~_c) kappa0(n_wall) R~(s_c)   (fluid cells, OBJ 0;
+//           kappa0 R~ = n_wall (kap0A - kap0B s), or n_wall kap0A g(s) in mode 1)
 //   slot 0 of the reduction: sum over unknown cells of lam~_c adv_c(s) (beta-scaled
 //   velocities, so d/dbeta of RHS is adv/beta).
 __global__ void __launch_bounds__(BX * BY)
@@ -1256,7 +1341,8 @@ gradient_kernel(Lattice L, Coef<double> C, const double* __restrict__ s,
             double dmv = 0.0;
             if (f & F_FLUID) {
                 const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
-                dmv = jscale * (mscale + lam[c]) * nw * (kap0A - kap0B * s_cur);
+                dmv = jscale * (mscale + lam[c]) * nw *
+                      (C.nl ? kap0A * g_uniform(s_cur, C.alpha) : kap0A - kap0B * s_cur);
                 if (!(C.umt && (f & F_ELEC))) {
                     double sxm = (f & F_XM) ? s[c - 1] : s_cur;
                     double sxp = (f & F_XP) ? s[c + 1] : s_cur;

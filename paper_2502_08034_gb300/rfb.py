@@ -20,13 +20,14 @@ RFB_OK, RFB_ERR_INVALID_ARG, RFB_ERR_CUDA, RFB_ERR_OOM = 0, 1, 2, 3
 RFB_ERR_NOT_CONVERGED, RFB_ERR_NONFINITE, RFB_ERR_STATE, RFB_ERR_UNSUPPORTED = 4, 5, 6, 7
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC = {"fp64": 0, "mixed": 1}
+KIN_AFFINE, KIN_UNIFORM_ETA = 0, 1
 INLET = {"face": 0, "ghost": 1}
 DT = {"global": 0, "local": 1}
 OBJECTIVES = {"I_tot": 0, "U": 1, "U_mt": 2}
 
 
 class Kinetics(ctypes.Structure):
-    _fields_ = [("k0", c_double), ("alpha", c_double), ("n_e", c_int32), ("pad_", c_int32),
+    _fields_ = [("k0", c_double), ("alpha", c_double), ("n_e", c_int32), ("mode", c_int32),
                 ("T", c_double), ("c0", c_double)]
 
 
@@ -159,11 +160,12 @@ class Solver:
     """One lattice + flow field on the GPU (a ``rfb_soc_handle``)."""
 
     def __init__(self, dims, dx, solid, U, V, W, D, k0, alpha=0.5, n_e=2, T=298.0, c0=20.0,
-                 area_mult=None, stream=None):
+                 area_mult=None, stream=None, kinetics_mode=KIN_AFFINE):
         L = lib()
         self.dims = tuple(int(d) for d in dims)
         d = (c_int32 * 3)(*self.dims)
-        kin = Kinetics(float(k0), float(alpha), int(n_e), 0, float(T), float(c0))
+        kin = Kinetics(float(k0), float(alpha), int(n_e), int(kinetics_mode), float(T),
+                       float(c0))
         ptrs = [_ptr(solid, np.uint8), _ptr(U, np.float64), _ptr(V, np.float64),
                 _ptr(W, np.float64), _ptr(area_mult, np.float64)]
         kinds = {p[2] for p in ptrs if p[2] is not None}
@@ -184,7 +186,8 @@ class Solver:
         self.n_cells, self.n_fluid = n.value, nf.value
 
     @classmethod
-    def from_case(cls, case, area_mult=None, stream=None, device_inputs=False):
+    def from_case(cls, case, area_mult=None, stream=None, device_inputs=False,
+                  kinetics_mode=0):
         arrays = [case.solid, case.U, case.V, case.W]
         if device_inputs:
             import torch
@@ -192,7 +195,7 @@ class Solver:
             if area_mult is not None:
                 area_mult = torch.from_numpy(np.ascontiguousarray(area_mult)).cuda()
         return cls(case.dims, case.h, *arrays, case.D, case.k0, case.alpha, case.n_e, case.T,
-                   case.c0, area_mult=area_mult, stream=stream)
+                   case.c0, area_mult=area_mult, stream=stream, kinetics_mode=kinetics_mode)
 
     def _check(self, st, ok=(RFB_OK,)):
         if st not in ok:
