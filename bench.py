@@ -568,6 +568,9 @@ def main():
                                        "frac": effective / peak,
                                        "note": "24.125 B per cell per sweep x sweeps/s"},
                "sweep_kernel_ms_per_sweep": sweep_ms / sweeps,
+               "check_ms_per_check": (sum(r["check_ms"] for r in results) /
+                                      max(1, sum(r["checks"] - 1 for r in results))),
+               "fluid_GCell_updates_per_s": value * sv.n_fluid / N,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "gpu_launches": launches,
                "setup_s": {"case": setup_case_s, "create": create_s}}

@@ -110,7 +110,10 @@ typedef struct rfb_solve_opts {
                                lattice (once per handle), 1 = one sweep per launch,
                                2 = two sweeps per pass (TMA-staged, temporally blocked;
                                needs nx % 16 == 0 and no area multiplier) */
-    int32_t reserved[7];    /* must be zero */
+    int32_t timeout_ms;     /* > 0: stop after the first FP64 check at or past this much
+                               wall time since the call began and return
+                               RFB_ERR_NOT_CONVERGED (the state is valid); 0 = none */
+    int32_t reserved[6];    /* must be zero */
 } rfb_solve_opts;
 
 typedef struct rfb_solve_result {

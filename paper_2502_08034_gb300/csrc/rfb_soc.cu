@@ -93,7 +93,8 @@ struct rfb_soc_handle {
     dim3 vgrid, vblock;
     // temporally blocked FP32 sweep (nx % 16 == 0, no area multiplier)
     int tb_mode = -1;         // -1 not chosen yet, 0 one-sweep kernel, 1 two-sweep passes
-    int tb_kchunk = 0;
+    int64_t tb_total = 0;     // tiles x planes of the two-sweep pass
+    int64_t tb_per = 0;       // planes per CTA of its persistent launch
     dim3 tb_grid;
     bool tm_ready = false;
     CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f;
@@ -382,12 +383,15 @@ void tb_prepare(rfb_soc_handle* h) {
     tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz);
     tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1);
     tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz);
-    // z chunks: at least two waves of one resident CTA per SM
-    const int gx = (h->nx + TB_TXI - 1) / TB_TXI, gy = (h->ny + TB_TYI - 1) / TB_TYI;
-    int kc = h->nz;
-    while (kc > 8 && (int64_t)gx * gy * ((h->nz + kc - 1) / kc) < 152 * 2) kc = (kc + 1) / 2;
-    h->tb_kchunk = kc;
-    h->tb_grid = dim3(gx, gy, (h->nz + kc - 1) / kc);
+    // one CTA per SM (182 KB of shared memory each); the (tile, plane) space is split in
+    // equal shares, so no partial last wave; shares of at least 16 planes, since every z
+    // segment pays a two-plane prologue
+    const int64_t gx = (h->nx + TB_TXI - 1) / TB_TXI, gy = (h->ny + TB_TYI - 1) / TB_TYI;
+    int sms = 152;
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->tb_total = gx * gy * h->nz;
+    h->tb_per = std::max<int64_t>((h->tb_total + sms - 1) / sms, 16);
+    h->tb_grid = dim3((unsigned)((h->tb_total + h->tb_per - 1) / h->tb_per));
     h->tm_ready = true;
 }
 
@@ -398,7 +402,8 @@ void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur
     const CUtensorMap& td = (h->d_delta[cur] == h->tm_delta_ptr[0]) ? h->tm_delta[0]
                                                                      : h->tm_delta[1];
     TBArgs A{};
-    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz; A.kchunk = h->tb_kchunk;
+    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
+    A.total = h->tb_total; A.per = h->tb_per;
     A.d_in = h->d_delta[cur];
     A.d_out = h->d_delta[cur ^ 1];
     A.Dh = C.Dh; A.gDh = C.gDh; A.dt = C.dt; A.cfl = (float)op.cfl; A.umt = C.umt;
@@ -514,8 +519,9 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
         set_err(h, "opts.check_every / max_sweeps must be >= 0");
         return false;
     }
-    for (int q = 0; q < 7; ++q)
+    for (int q = 0; q < 6; ++q)
         if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
+    if (o->timeout_ms < 0) { set_err(h, "opts.timeout_ms must be >= 0"); return false; }
     if (o->fp32_kernel < 0 || o->fp32_kernel > 2) {
         set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep) or 2 (two-sweep passes)");
         return false;
@@ -590,6 +596,13 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         if (fixed_sweeps < 0 && r.residual <= tol) break;
         if (done >= limit) {
             st = fixed_sweeps >= 0 ? RFB_OK : RFB_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (o.timeout_ms > 0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                    .count() >= o.timeout_ms) {
+            set_err(h, "opts.timeout_ms reached after %lld sweeps", (long long)done);
+            st = RFB_ERR_NOT_CONVERGED;
             break;
         }
         const int64_t n = std::min(every, limit - done);
@@ -1186,6 +1199,13 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
             if (h->h_red[6] > 0) { st = RFB_ERR_NONFINITE; break; }
             if (rel <= tol) break;
             if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            if (o.timeout_ms > 0 &&
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                        .count() >= o.timeout_ms) {
+                set_err(h, "opts.timeout_ms reached after %lld adjoint sweeps", (long long)done);
+                st = RFB_ERR_NOT_CONVERGED;
+                break;
+            }
             const int64_t n = std::min(every, o.max_sweeps - done);
             for (int64_t q = 0; q < n; ++q) {
                 adjoint64c_kernel<0><<<h->grid, h->block, 0, h->stream>>>(
@@ -1678,6 +1698,12 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         };
         while (!all_done()) {
             if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
+                                        std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
+                bset_err(b, "opts.timeout_ms reached after %lld sweeps", (long long)done);
+                st = RFB_ERR_NOT_CONVERGED;
+                break;
+            }
             BCK(b, cudaGraphLaunch(b->exec, b->stream));
             b->launches += every + 3;
             BCK(b, cudaStreamSynchronize(b->stream));

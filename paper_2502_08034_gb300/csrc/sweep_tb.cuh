@@ -42,7 +42,9 @@ constexpr uint32_t TB_TX_BYTES = 5 * TB_F32 + TB_PLANE;
 constexpr unsigned long long TB_SPIN_LIMIT = 1ull << 26;   // bounded mbarrier waits
 
 struct TBArgs {
-    int nx, ny, nz, kchunk;
+    int nx, ny, nz;
+    int64_t total;                    // tiles x nz planes
+    int64_t per;                      // planes of the (tile, plane) space per CTA
     const float* __restrict__ d_in;   // delta read by this pass (prologue plane)
     float* __restrict__ d_out;
     float Dh, gDh, dt, cfl;
@@ -95,36 +97,19 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TB_BAR);
     __shared__ float tB[8];
-    __shared__ int abort_flag;
     const int tid = threadIdx.x;
     if (tid < 8) tB[tid] = A.tB[tid];
-    if (tid == 0) abort_flag = 0;
     const int tx = tid % TB_GX, ty = tid / TB_GX;
     const int bxx = 8 + 4 * tx, byy = 1 + ty;          // this thread's cells in the box
-    const int x0 = TB_TXI * blockIdx.x - 16;           // box origin (16-cell aligned)
-    const int y0 = TB_TYI * blockIdx.y - 2;
-    const int i0 = x0 + bxx, j = y0 + byy;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
     const bool interior = tx >= 2 && tx < 2 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
-    const int kb = blockIdx.z * A.kchunk;
-    const int ke = min(kb + A.kchunk, nz);
     const int64_t nxny = (int64_t)nx * ny;
     const int o = byy * TB_BW + bxx;                   // offset in a staged plane
+    const int gx = (nx + TB_TXI - 1) / TB_TXI;
 
     auto stage = [&](int s) { return smem + s * TB_STAGE; };
-    auto issue = [&](int p, int s) {                   // one thread: plane p -> stage s
-        unsigned char* S = stage(s);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar[s], TB_TX_BYTES);
-        tma_load_3d(S, &tm_d, x0, y0, p, &bar[s]);
-        tma_load_3d(S + TB_F32, &tm_r, x0, y0, p, &bar[s]);
-        tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
-        tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
-        tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
-        tma_load_3d(S + 5 * TB_F32, &tm_f, x0, y0, p, &bar[s]);
-    };
-    uint32_t phase = 0;
+    uint32_t phase = 0;   // parity of each stage's next completion
+    uint32_t pend = 0;    // stages with a load in flight (every thread tracks the same set)
     auto wait = [&](int s) -> bool {                   // bounded wait for stage s
         unsigned long long n = 0;
         while (!mbar_try_wait(&bar[s], (phase >> s) & 1u)) {
@@ -134,6 +119,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             }
         }
         phase ^= 1u << s;
+        pend &= ~(1u << s);
         return true;
     };
 
@@ -142,96 +128,133 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0)
-        for (int q = 0; q < TB_NSTAGE; ++q) issue(kb - 1 + q, q);   // planes kb-1, kb, kb+1
 
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 d0_prev = zero4;                            // own level 0 at z-1
-    if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
-    float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
-    Coef32 skc[4];       // update coefficients of plane z-1 (level 2), from the previous step
-    float4 sr = zero4;   // forcing of plane z-1
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        for (int q = 0; q < 6; ++q) skc[e].a[q] = 0.f;
-        skc[e].ac = 1.f;
-        skc[e].dt = 0.f;
-    }
-    bool ok = wait(0);
+    // This CTA's share of the (tile, plane) space, tile-major: planes q0 .. q1-1 of the
+    // linear index tile * nz + z, walked as one z segment per tile it touches. Every
+    // segment waits for each stage it issues, so the ring is empty between segments.
+    const int64_t q1 = min((int64_t)(blockIdx.x + 1) * A.per, A.total);
+    bool ok = true;
+    for (int64_t q = (int64_t)blockIdx.x * A.per; q < q1 && ok;) {
+        const int tile = (int)(q / nz);
+        const int kb = (int)(q % nz);
+        const int ke = (int)min((int64_t)nz, kb + (q1 - q));
+        q += ke - kb;
+        const int x0 = TB_TXI * (tile % gx) - 16;      // box origin (16-cell aligned)
+        const int y0 = TB_TYI * (tile / gx) - 2;
+        const int i0 = x0 + bxx, j = y0 + byy;
+        const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+        auto issue = [&](int p, int s) {               // plane p -> stage s
+            pend |= 1u << s;
+            if (tid != 0) return;                      // one thread issues the copies
+            unsigned char* S = stage(s);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[s], TB_TX_BYTES);
+            tma_load_3d(S, &tm_d, x0, y0, p, &bar[s]);
+            tma_load_3d(S + TB_F32, &tm_r, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 5 * TB_F32, &tm_f, x0, y0, p, &bar[s]);
+        };
+        __syncthreads();   // the previous segment's readers are done with every stage
+        for (int s = 0; s < TB_NSTAGE; ++s) issue(kb - 1 + s, s);       // kb-1, kb, kb+1
 
-    for (int z = kb - 1; z <= ke && ok; ++z) {
-        const int s0 = (z - (kb - 1)) % TB_NSTAGE;
-        const int s1 = (z + 1 - (kb - 1)) % TB_NSTAGE;
-        if (!wait(s1)) { ok = false; break; }
-        const float* D0 = reinterpret_cast<const float*>(stage(s0));
-        const float* R0 = D0 + TB_PLANE;
-        const float* U0 = R0 + TB_PLANE;
-        const float* V0 = U0 + TB_PLANE;
-        const float* W0 = V0 + TB_PLANE;
-        const unsigned char* F0 = reinterpret_cast<const unsigned char*>(W0 + TB_PLANE);
-        const float* D1 = reinterpret_cast<const float*>(stage(s1));
-        const float* W1 = D1 + 4 * TB_PLANE;
-        // ---- level 1 at plane z
-        const float4 dc = lds4(D0 + o);
-        const float4 dn = lds4(D1 + o);
-        const float4 u4 = lds4(U0 + o);
-        const float un = U0[o + 4];
-        const float4 v4 = lds4(V0 + o);
-        const float4 vh4 = lds4(V0 + o + TB_BW);
-        const float4 wl4 = lds4(W0 + o);
-        const float4 wh4 = lds4(W1 + o);
-        const float4 r4 = lds4(R0 + o);
-        const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
-        // the cells' update coefficients for plane z, used by level 1 now and by level 2
-        // at the next step
-        Coef32 kc[4];
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 d0_prev = zero4;                        // own level 0 at z-1
+        if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
+        float4 l1_m2 = zero4, l1_m1 = zero4;           // own level 1 at z-2, z-1
+        Coef32 skc[4];   // update coefficients of plane z-1 (level 2), from the previous step
+        float4 sr = zero4;                             // forcing of plane z-1
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const unsigned m = (f4 >> (8 * e)) & 0xffu;
-            kc[e] = cell_coef32<LOCAL_DT>(m, A.umt, el(u4, e), e == 3 ? un : el(u4, e + 1),
-                                          el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e),
-                                          tB[m_nwall(m)], A.Dh, A.gDh, z == 0, A.cfl, A.dt);
+            for (int s = 0; s < 6; ++s) skc[e].a[s] = 0.f;
+            skc[e].ac = 1.f;
+            skc[e].dt = 0.f;
         }
-        float4 l1 = dc;
-        if (in_dom && z >= 0 && z < nz) {
-            const float dxm = D0[o - 1], dxp = D0[o + 4];
-            const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
-            float out[4];
+        // A wait that gives up leaves this thread's `good` false; the CTA decides together
+        // at the step's barrier (so no thread is left at a barrier the others skipped).
+        bool good = wait(0);
+
+        for (int z = kb - 1; z <= ke; ++z) {
+            const int s0 = (z - (kb - 1)) % TB_NSTAGE;
+            const int s1 = (z + 1 - (kb - 1)) % TB_NSTAGE;
+            if (good) good = wait(s1);
+            const float* D0 = reinterpret_cast<const float*>(stage(s0));
+            const float* R0 = D0 + TB_PLANE;
+            const float* U0 = R0 + TB_PLANE;
+            const float* V0 = U0 + TB_PLANE;
+            const float* W0 = V0 + TB_PLANE;
+            const unsigned char* F0 = reinterpret_cast<const unsigned char*>(W0 + TB_PLANE);
+            const float* D1 = reinterpret_cast<const float*>(stage(s1));
+            const float* W1 = D1 + 4 * TB_PLANE;
+            // ---- level 1 at plane z
+            const float4 dc = lds4(D0 + o);
+            const float4 dn = lds4(D1 + o);
+            const float4 u4 = lds4(U0 + o);
+            const float un = U0[o + 4];
+            const float4 v4 = lds4(V0 + o);
+            const float4 vh4 = lds4(V0 + o + TB_BW);
+            const float4 wl4 = lds4(W0 + o);
+            const float4 wh4 = lds4(W1 + o);
+            const float4 r4 = lds4(R0 + o);
+            const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
+            // the cells' update coefficients for plane z, used by level 1 now and by
+            // level 2 at the next step
+            Coef32 kc[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                out[e] = cell_apply32(kc[e], el(dc, e), e == 0 ? dxm : el(dc, e - 1),
-                                      e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                      el(d0_prev, e), el(dn, e), el(r4, e));
-            l1 = make_float4(out[0], out[1], out[2], out[3]);
+            for (int e = 0; e < 4; ++e) {
+                const unsigned m = (f4 >> (8 * e)) & 0xffu;
+                kc[e] = cell_coef32<LOCAL_DT>(m, A.umt, el(u4, e), e == 3 ? un : el(u4, e + 1),
+                                              el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e),
+                                              tB[m_nwall(m)], A.Dh, A.gDh, z == 0, A.cfl, A.dt);
+            }
+            float4 l1 = dc;
+            if (in_dom && z >= 0 && z < nz) {
+                const float dxm = D0[o - 1], dxp = D0[o + 4];
+                const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+                float out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    out[e] = cell_apply32(kc[e], el(dc, e), e == 0 ? dxm : el(dc, e - 1),
+                                          e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                          el(d0_prev, e), el(dn, e), el(r4, e));
+                l1 = make_float4(out[0], out[1], out[2], out[3]);
+            }
+            float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
+            *reinterpret_cast<float4*>(L1w + o) = l1;
+            // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
+            const int zz = z - 1;
+            if (zz >= kb && interior && in_dom) {
+                const float* L1r =
+                    reinterpret_cast<const float*>(smem + TB_L1) + (zz & 1) * TB_PLANE;
+                const float lxm = L1r[o - 1], lxp = L1r[o + 4];
+                const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
+                float out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    out[e] = cell_apply32(skc[e], el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
+                                          e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e),
+                                          el(lyp, e), el(l1_m2, e), el(l1, e), el(sr, e));
+                *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
+                    make_float4(out[0], out[1], out[2], out[3]);
+            }
+            // ---- keep what the next step needs; free stage s0 for plane z + 3
+#pragma unroll
+            for (int e = 0; e < 4; ++e) skc[e] = kc[e];
+            sr = r4;
+            d0_prev = dc;
+            l1_m2 = l1_m1;
+            l1_m1 = l1;
+            if (!__syncthreads_and(good)) { ok = false; break; }
+            if (z + 3 <= ke + 1) issue(z + 3, s0);
         }
-        float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
-        *reinterpret_cast<float4*>(L1w + o) = l1;
-        // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
-        const int zz = z - 1;
-        if (zz >= kb && interior && in_dom) {
-            const float* L1r = reinterpret_cast<const float*>(smem + TB_L1) + (zz & 1) * TB_PLANE;
-            const float lxm = L1r[o - 1], lxp = L1r[o + 4];
-            const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
-            float out[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                out[e] = cell_apply32(skc[e], el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
-                                      e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
-                                      el(l1_m2, e), el(l1, e), el(sr, e));
-            *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
-                make_float4(out[0], out[1], out[2], out[3]);
-        }
-        // ---- keep what the next step needs; free stage s0 for plane z + 3
-#pragma unroll
-        for (int e = 0; e < 4; ++e) skc[e] = kc[e];
-        sr = r4;
-        d0_prev = dc;
-        l1_m2 = l1_m1;
-        l1_m1 = l1;
-        __syncthreads();
-        if (tid == 0 && z + 3 <= ke + 1) issue(z + 3, s0);
     }
-    if (!ok) abort_flag = 1;
+    if (!ok) {
+        // error path (a stage never arrived): wait, again with the limit, for the copies
+        // still in flight into this CTA's shared memory before returning
+        for (int s = 0; s < TB_NSTAGE; ++s)
+            if (pend & (1u << s)) (void)wait(s);
+    }
 }
 
 }  // namespace rfb

@@ -34,7 +34,8 @@ class Kinetics(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("inlet_bc", c_int32), ("dt_mode", c_int32),
                 ("check_every", c_int32), ("cfl", c_double), ("velocity_scale", c_double),
-                ("max_sweeps", c_int64), ("fp32_kernel", c_int32), ("reserved", c_int32 * 7)]
+                ("max_sweeps", c_int64), ("fp32_kernel", c_int32), ("timeout_ms", c_int32),
+                ("reserved", c_int32 * 6)]
 
 
 class SolveResult(ctypes.Structure):
@@ -121,7 +122,7 @@ FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2}
 
 
 def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
-              velocity_scale=1.0, max_sweeps=0, fp32_kernel="auto") -> SolveOpts:
+              velocity_scale=1.0, max_sweeps=0, fp32_kernel="auto", timeout_ms=0) -> SolveOpts:
     o = SolveOpts()
     lib().rfb_solve_opts_default(byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -132,6 +133,7 @@ def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0,
     o.velocity_scale = float(velocity_scale)
     o.max_sweeps = int(max_sweeps)
     o.fp32_kernel = FP32_KERNEL[fp32_kernel] if isinstance(fp32_kernel, str) else int(fp32_kernel)
+    o.timeout_ms = int(timeout_ms)
     return o
 
 
