@@ -46,9 +46,11 @@ def parse():
                          "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
                          "512x512x1024 iterative upsampling; adjoint: gradients of I_tot, U "
                          "and U_mt on the 128x128x256 differentiation workload")
-    ap.add_argument("--fp32-kernel", default="auto", choices=["auto", "plain", "blocked"],
+    ap.add_argument("--fp32-kernel", default="auto",
+                    choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
-                         "per launch, or two-sweep TMA-staged passes")
+                         "per launch, or two-sweep TMA-staged passes (launch shape autotuned, "
+                         "persistent, or one (tile, z chunk) item per CTA)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -491,11 +493,14 @@ def main():
     # algorithmic bytes per launch: a launch reads each cell's correction, forcing, three
     # face velocities and mask once and writes the correction once, whether it applies
     # one sweep or a two-sweep pass
-    two_sweep = launches < sweeps   # two-sweep passes: about one launch per two sweeps
+    kname, tuned_plain_ms, tuned_blocked_ms = sv.tuned_fp32_kernel()
+    if args.fp32_kernel not in ("auto", "blocked"):
+        kname = args.fp32_kernel
+    two_sweep = kname.startswith("blocked")   # about one launch per two sweeps
     kernel_launches = (sweeps + 1) // 2 if two_sweep else sweeps
     achieved = SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
     effective = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
-    traffic = kernel_traffic(N, "blocked" if two_sweep else "plain")
+    traffic = kernel_traffic(N, kname)
     last = results[-1]
 
     extras = {}
@@ -560,8 +565,11 @@ def main():
                "mass_balance_rel": last["mass_balance_rel"],
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                            "kernel": ("sweep32tb_kernel (two-sweep TMA-staged pass)"
-                                       if two_sweep else "sweep32v_kernel (one sweep)"),
+                            "kernel": ("sweep32tb_kernel (two-sweep TMA-staged pass, %s "
+                                       "launch)" % kname.split("_")[1] if two_sweep
+                                       else "sweep32v_kernel (one sweep)"),
+                            "autotuner_ms_per_sweep": {"plain": tuned_plain_ms,
+                                                       "blocked": tuned_blocked_ms},
                             "bytes_per_cell_per_launch": SWEEP_BYTES_PER_CELL,
                             "peak_kind": peak_kind},
                "effective_bandwidth": {"value": effective, "unit": "GB/s",

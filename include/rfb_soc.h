@@ -106,10 +106,13 @@ typedef struct rfb_solve_opts {
     double cfl;             /* C_CFL in (0, 1] (default 0.4) */
     double velocity_scale;  /* beta >= 0: every face velocity is multiplied by it (1) */
     int64_t max_sweeps;     /* give up after this many sweeps (0 = 50,000,000) */
-    int32_t fp32_kernel;    /* RFB_PREC_MIXED only: 0 = chosen by timing both on the
-                               lattice (once per handle), 1 = one sweep per launch,
+    int32_t fp32_kernel;    /* RFB_PREC_MIXED only: 0 = chosen by timing the kernels on
+                               the lattice (once per handle), 1 = one sweep per launch,
                                2 = two sweeps per pass (TMA-staged, temporally blocked;
-                               needs nx % 16 == 0 and no area multiplier) */
+                               needs nx % 16 == 0 and no area multiplier), launch shape
+                               chosen by timing; 3 = two-sweep passes in a persistent
+                               launch (one CTA per SM, equal shares); 4 = two-sweep passes,
+                               one (tile, z chunk) item per CTA */
     int32_t timeout_ms;     /* > 0: stop after the first FP64 check at or past this much
                                wall time since the call began and return
                                RFB_ERR_NOT_CONVERGED (the state is valid); 0 = none */
@@ -356,6 +359,15 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
 /* Number of CUDA kernels this handle has launched since creation (graph replays count
  * every kernel inside the graph). */
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h);
+
+/* The FP32 correction kernel the handle's autotuner chose for RFB_PREC_MIXED solves with
+ * fp32_kernel = 0 or 2, as an opts.fp32_kernel value: 0 = not chosen yet, 1 = one sweep
+ * per launch, 3 / 4 = two-sweep passes in the persistent / chunked launch shape; and the
+ * timed device milliseconds per sweep of the one-sweep kernel and of the faster two-sweep
+ * shape (0 if not timed). Any output pointer may be NULL. */
+rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
+                                     double* plain_ms_per_sweep,
+                                     double* blocked_ms_per_sweep);
 
 #ifdef __cplusplus
 }

@@ -93,9 +93,16 @@ struct rfb_soc_handle {
     dim3 vgrid, vblock;
     // temporally blocked FP32 sweep (nx % 16 == 0, no area multiplier)
     int tb_mode = -1;         // -1 not chosen yet, 0 one-sweep kernel, 1 two-sweep passes
-    int64_t tb_total = 0;     // tiles x planes of the two-sweep pass
-    int64_t tb_per = 0;       // planes per CTA of its persistent launch
-    dim3 tb_grid;
+    // two launch shapes of the two-sweep pass (sweep_tb.cuh): 0 persistent (one CTA per
+    // SM, equal shares of the tile-major plane space), 1 one (tile, z chunk) item per CTA
+    // with the chunk count that wastes least of the last wave; the autotuner picks one
+    struct TBLaunch {
+        int lc = 0;           // planes per z chunk
+        int64_t total = 0;    // tiles x chunks x lc
+        int64_t per = 0;      // positions per CTA
+        dim3 grid;
+    } tb_launch[2];
+    int tb_variant = -1;      // -1 not chosen yet
     bool tm_ready = false;
     CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f;
     float* tm_delta_ptr[2] = {nullptr, nullptr};
@@ -335,7 +342,7 @@ bool tb_eligible(const rfb_soc_handle* h) {
 }
 
 void tb_encode(rfb_soc_handle* h, CUtensorMap* m, CUtensorMapDataType t, size_t esize, void* ptr,
-               int planes) {
+               int planes, int box_w) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -350,10 +357,12 @@ void tb_encode(rfb_soc_handle* h, CUtensorMap* m, CUtensorMapDataType t, size_t 
     }
     const cuuint64_t dims[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)h->nx * esize, (cuuint64_t)h->nxny * esize};
-    const cuuint32_t box[3] = {(cuuint32_t)TB_BW, (cuuint32_t)TB_BH, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)TB_BH, 1};
+    // no L2 promotion: a box row is fetched at sector granularity (a 256-byte promotion
+    // would pull whole 256-byte chunks for the halo columns at both ends of every row)
     const cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, t, 3, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_err(h, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -375,23 +384,42 @@ void tb_prepare(rfb_soc_handle* h) {
         attr_set[1] = true;
     }
     for (int q = 0; q < 2; ++q) {
-        tb_encode(h, &h->tm_delta[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_delta[q], h->nz);
+        tb_encode(h, &h->tm_delta[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_delta[q], h->nz,
+                  TB_BW);
         h->tm_delta_ptr[q] = h->d_delta[q];
     }
-    tb_encode(h, &h->tm_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz);
-    tb_encode(h, &h->tm_u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz);
-    tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz);
-    tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1);
-    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz);
-    // one CTA per SM (182 KB of shared memory each); the (tile, plane) space is split in
-    // equal shares, so no partial last wave; shares of at least 16 planes, since every z
-    // segment pays a two-plane prologue
-    const int64_t gx = (h->nx + TB_TXI - 1) / TB_TXI, gy = (h->ny + TB_TYI - 1) / TB_TYI;
+    tb_encode(h, &h->tm_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz, TB_BW);
+    tb_encode(h, &h->tm_u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz, TB_BW);
+    tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz, TB_BW);
+    tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1, TB_BW);
+    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz, TB_BWM);
+    // One CTA per SM fits (152 KB of shared memory each).
+    // Shape 0, persistent: the tile-major (tile, plane) space in equal shares of at least
+    // 16 planes (every z segment pays a two-plane prologue): no partial last wave, but
+    // CTAs on neighbouring tiles run at different planes and do not share halo rows in L2.
+    // Shape 1, chunked: one (tile, z chunk) item per CTA in chunk-major order, so that
+    // neighbouring tiles run together; the chunk count minimises waves x (chunk + 2).
+    const int64_t tiles = (int64_t)((h->nx + TB_TXI - 1) / TB_TXI) *
+                          ((h->ny + TB_TYI - 1) / TB_TYI);
     int sms = 152;
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    h->tb_total = gx * gy * h->nz;
-    h->tb_per = std::max<int64_t>((h->tb_total + sms - 1) / sms, 16);
-    h->tb_grid = dim3((unsigned)((h->tb_total + h->tb_per - 1) / h->tb_per));
+    auto& P = h->tb_launch[0];
+    P.lc = h->nz;
+    P.total = tiles * h->nz;
+    P.per = std::max<int64_t>((P.total + sms - 1) / sms, 16);
+    P.grid = dim3((unsigned)((P.total + P.per - 1) / P.per));
+    int best_c = 1;
+    double best = INFINITY;
+    for (int c = 1; c <= std::max(1, h->nz / 8); ++c) {
+        const int lc = (h->nz + c - 1) / c, cc = (h->nz + lc - 1) / lc;
+        const double cost = std::ceil((double)(tiles * cc) / sms) * (lc + 2);
+        if (cost < best) { best = cost; best_c = cc; }
+    }
+    auto& Q = h->tb_launch[1];
+    Q.lc = (h->nz + best_c - 1) / best_c;
+    Q.total = tiles * best_c * Q.lc;
+    Q.per = Q.lc;
+    Q.grid = dim3((unsigned)(tiles * best_c));
     h->tm_ready = true;
 }
 
@@ -403,17 +431,18 @@ void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur
                                                                      : h->tm_delta[1];
     TBArgs A{};
     A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
-    A.total = h->tb_total; A.per = h->tb_per;
+    const auto& S = h->tb_launch[h->tb_variant > 0 ? 1 : 0];
+    A.lc = S.lc; A.total = S.total; A.per = S.per;
     A.d_in = h->d_delta[cur];
     A.d_out = h->d_delta[cur ^ 1];
     A.Dh = C.Dh; A.gDh = C.gDh; A.dt = C.dt; A.cfl = (float)op.cfl; A.umt = C.umt;
     for (int q = 0; q < 8; ++q) A.tB[q] = C.rB[q];
     A.err = tb_err_word(h);
     if (local)
-        sweep32tb_kernel<true><<<h->tb_grid, TB_THREADS, TB_SMEM, h->stream>>>(
+        sweep32tb_kernel<true><<<S.grid, TB_THREADS, TB_SMEM, h->stream>>>(
             td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_f, A);
     else
-        sweep32tb_kernel<false><<<h->tb_grid, TB_THREADS, TB_SMEM, h->stream>>>(
+        sweep32tb_kernel<false><<<S.grid, TB_THREADS, TB_SMEM, h->stream>>>(
             td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_f, A);
     LAUNCHED(h);
 }
@@ -468,22 +497,26 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = fal
     }
 }
 
-// Project-written autotuner for one lattice: time 8 plain sweeps against 4 two-sweep
-// passes (CUDA events, on the current forcing) and keep the faster.
-void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op) {
+// Project-written autotuner for one lattice: time 8 plain sweeps and 8 sweeps of each
+// launch shape of the two-sweep pass (CUDA events, on the current forcing) and keep the
+// fastest (tb_only: choose between the two-sweep shapes only).
+void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false) {
     if (!tb_eligible(h)) { h->tb_mode = 0; return; }
-    float ms[2] = {0.f, 0.f};
-    for (int mode = 0; mode < 2; ++mode) {
-        sweeps32(h, op, 2, mode == 1);   // warm-up (and tensor maps)
+    float ms[3] = {INFINITY, INFINITY, INFINITY};   // plain, shape 0, shape 1
+    for (int cand = tb_only ? 1 : 0; cand < 3; ++cand) {
+        if (cand > 0) h->tb_variant = cand - 1;
+        sweeps32(h, op, 2, cand > 0);   // warm-up (and tensor maps)
         CK(h, cudaEventRecord(h->ev[0], h->stream));
-        sweeps32(h, op, 8, mode == 1);
+        sweeps32(h, op, 8, cand > 0);
         CK(h, cudaEventRecord(h->ev[1], h->stream));
         CK(h, cudaEventSynchronize(h->ev[1]));
-        CK(h, cudaEventElapsedTime(&ms[mode], h->ev[0], h->ev[1]));
+        CK(h, cudaEventElapsedTime(&ms[cand], h->ev[0], h->ev[1]));
     }
+    h->tb_variant = ms[2] < ms[1] ? 1 : 0;
+    const float tb = std::min(ms[1], ms[2]);
     h->tb_tuned_plain_ms = ms[0] / 8;
-    h->tb_tuned_tb_ms = ms[1] / 8;
-    h->tb_mode = ms[1] < ms[0] ? 1 : 0;
+    h->tb_tuned_tb_ms = tb / 8;
+    if (!tb_only) h->tb_mode = tb < ms[0] ? 1 : 0;
 }
 
 void init_state(rfb_soc_handle* h, bool umt, double s_in) {
@@ -522,11 +555,12 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
     for (int q = 0; q < 6; ++q)
         if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
     if (o->timeout_ms < 0) { set_err(h, "opts.timeout_ms must be >= 0"); return false; }
-    if (o->fp32_kernel < 0 || o->fp32_kernel > 2) {
-        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep) or 2 (two-sweep passes)");
+    if (o->fp32_kernel < 0 || o->fp32_kernel > 4) {
+        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep), 2 (two-sweep passes) "
+                   "or 3 / 4 (two-sweep passes, persistent / chunked launch)");
         return false;
     }
-    if (o->fp32_kernel == 2 && !tb_eligible(h)) {
+    if (o->fp32_kernel >= 2 && !tb_eligible(h)) {
         set_err(h, "two-sweep passes need nx %% 16 == 0 and no area multiplier");
         return false;
     }
@@ -580,6 +614,10 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     bool use_tb = false;
     if (mixed) {
         if (o.fp32_kernel == 2) {
+            if (h->tb_variant < 0) tune_fp32_kernel(h, op, true);
+            use_tb = true;
+        } else if (o.fp32_kernel >= 3) {
+            h->tb_variant = o.fp32_kernel - 3;   // a forced shape (kept for later calls)
             use_tb = true;
         } else if (o.fp32_kernel == 0) {
             if (h->tb_mode < 0) tune_fp32_kernel(h, op);
@@ -1258,6 +1296,19 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
 }
 
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h) { return h ? h->launches : 0; }
+
+rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
+                                     double* plain_ms_per_sweep,
+                                     double* blocked_ms_per_sweep) {
+    if (!h) return RFB_ERR_INVALID_ARG;
+    int32_t k = 0;
+    if (h->tb_mode == 0) k = 1;
+    else if (h->tb_mode == 1 || h->tb_variant >= 0) k = 3 + std::max(h->tb_variant, 0);
+    if (kernel) *kernel = k;
+    if (plain_ms_per_sweep) *plain_ms_per_sweep = h->tb_tuned_plain_ms;
+    if (blocked_ms_per_sweep) *blocked_ms_per_sweep = h->tb_tuned_tb_ms;
+    return RFB_OK;
+}
 
 }  // extern "C"
 

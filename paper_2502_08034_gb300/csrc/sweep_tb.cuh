@@ -2,9 +2,10 @@
 // over HBM, z-planes staged into shared memory by TMA (cp.async.bulk.tensor) through a
 // three-stage mbarrier ring.
 //
-// A CTA owns an x-y tile of 128 x 12 cells (plus a halo of 16 columns and 2 rows on each
-// side, so that the 8-bit mask's TMA boxes start on 16-byte boundaries) and marches a
-// chunk of z planes. At step z it
+// A CTA owns an x-y tile of 128 x 12 cells and marches z. The FP32 fields are staged as
+// 136 x 16 boxes (4 halo columns and 2 halo rows on each side; a 32-bit TMA box starts on
+// a multiple of 4 cells), the 8-bit mask as a 160 x 16 box (16 halo columns: an 8-bit box
+// starts on a multiple of 16 cells). At step z the CTA
 //   - computes level 1 (one sweep) at plane z from the staged level-0 planes z, z+1 and
 //     its own level-0 value at z-1 kept in registers, for every cell of the tile and a
 //     one-cell ring around it, and stores it in a double-buffered shared plane;
@@ -24,27 +25,30 @@ namespace rfb {
 
 constexpr int TB_TXI = 128;                    // interior columns of a tile
 constexpr int TB_TYI = 12;                     // interior rows of a tile
-constexpr int TB_BW = TB_TXI + 32;             // staged columns: 16 halo + 128 + 16 halo
+constexpr int TB_BW = TB_TXI + 8;              // staged FP32 columns: 4 halo + 128 + 4 halo
+constexpr int TB_BWM = TB_TXI + 32;            // staged mask columns: 16 + 128 + 16
 constexpr int TB_BH = TB_TYI + 4;              // staged rows: 2 halo + 12 + 2 halo
-constexpr int TB_GX = (TB_TXI + 16) / 4;       // 36 groups of 4 cells: columns [-8, 136)
+constexpr int TB_GX = TB_BW / 4;               // 34 groups of 4 cells: columns [-4, 132)
 constexpr int TB_GY = TB_TYI + 2;              // 14 rows of threads: rows [-1, 13)
-// 504 threads = 16 warps, 4 per SM sub-partition, so up to 128 registers a thread fit
+// 476 threads (15 warps): 128 registers a thread fit in the register file
 constexpr int TB_THREADS = TB_GX * TB_GY;
-constexpr int TB_PLANE = TB_BW * TB_BH;        // 2560 cells per staged plane
-constexpr int TB_F32 = TB_PLANE * 4;           // 10240 bytes (80 x 128)
-constexpr int TB_FLAGS = (TB_PLANE + 127) / 128 * 128;
-constexpr int TB_STAGE = 5 * TB_F32 + TB_FLAGS;
+constexpr int TB_PLANE = TB_BW * TB_BH;        // 2176 cells per staged FP32 plane
+constexpr int TB_F32 = TB_PLANE * 4;           // 8704 bytes (68 x 128)
+constexpr int TB_MPLANE = TB_BWM * TB_BH;      // 2560 mask bytes (20 x 128)
+constexpr int TB_STAGE = 5 * TB_F32 + TB_MPLANE;
 constexpr int TB_NSTAGE = 3;
 constexpr int TB_L1 = TB_NSTAGE * TB_STAGE;    // offset of the two level-1 planes
 constexpr int TB_BAR = TB_L1 + 2 * TB_F32;     // offset of the stage barriers
 constexpr int TB_SMEM = TB_BAR + 64 + 128;     // + alignment slack for the base
-constexpr uint32_t TB_TX_BYTES = 5 * TB_F32 + TB_PLANE;
+constexpr uint32_t TB_TX_BYTES = 5 * TB_F32 + TB_MPLANE;
+static_assert(TB_F32 % 128 == 0 && TB_MPLANE % 128 == 0, "stage buffers stay 128-B aligned");
 constexpr unsigned long long TB_SPIN_LIMIT = 1ull << 26;   // bounded mbarrier waits
 
 struct TBArgs {
     int nx, ny, nz;
-    int64_t total;                    // tiles x nz planes
-    int64_t per;                      // planes of the (tile, plane) space per CTA
+    int lc;                           // planes per z chunk (nz: one chunk)
+    int64_t total;                    // tiles x chunks x lc (chunk-major, tile fastest)
+    int64_t per;                      // planes of that space per CTA
     const float* __restrict__ d_in;   // delta read by this pass (prologue plane)
     float* __restrict__ d_out;
     float Dh, gDh, dt, cfl;
@@ -100,11 +104,12 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
     const int tid = threadIdx.x;
     if (tid < 8) tB[tid] = A.tB[tid];
     const int tx = tid % TB_GX, ty = tid / TB_GX;
-    const int bxx = 8 + 4 * tx, byy = 1 + ty;          // this thread's cells in the box
+    const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
     const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const bool interior = tx >= 2 && tx < 2 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
+    const bool interior = tx >= 1 && tx < 1 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
     const int64_t nxny = (int64_t)nx * ny;
-    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
+    const int o = byy * TB_BW + bxx;                   // offset in a staged FP32 plane
+    const int om = byy * TB_BWM + 12 + bxx;            // offset in the staged mask plane
     const int gx = (nx + TB_TXI - 1) / TB_TXI;
 
     auto stage = [&](int s) { return smem + s * TB_STAGE; };
@@ -129,17 +134,25 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
     }
     __syncthreads();
 
-    // This CTA's share of the (tile, plane) space, tile-major: planes q0 .. q1-1 of the
-    // linear index tile * nz + z, walked as one z segment per tile it touches. Every
-    // segment waits for each stage it issues, so the ring is empty between segments.
+    // This CTA's share of the work: positions q0 .. q1-1 of the linear index
+    // ((chunk * tiles + tile) * lc + plane in chunk), walked as one z segment per
+    // (chunk, tile) item it touches; positions past nz in the last chunk are skipped.
+    // With one chunk and per = tiles * nz / CTAs this is a persistent launch with equal
+    // shares; with per = lc every CTA takes one item and neighbouring tiles run together.
+    // Every segment waits for each stage it issues, so the ring is empty between segments.
+    const int tiles = gx * ((ny + TB_TYI - 1) / TB_TYI);
     const int64_t q1 = min((int64_t)(blockIdx.x + 1) * A.per, A.total);
     bool ok = true;
     for (int64_t q = (int64_t)blockIdx.x * A.per; q < q1 && ok;) {
-        const int tile = (int)(q / nz);
-        const int kb = (int)(q % nz);
-        const int ke = (int)min((int64_t)nz, kb + (q1 - q));
-        q += ke - kb;
-        const int x0 = TB_TXI * (tile % gx) - 16;      // box origin (16-cell aligned)
+        const int64_t item = q / A.lc;
+        const int zl = (int)(q % A.lc);
+        const int tile = (int)(item % tiles);
+        const int kb = (int)(item / tiles) * A.lc + zl;
+        const int64_t item_end = (item + 1) * A.lc;
+        if (kb >= nz) { q = item_end; continue; }     // padding of a short last chunk
+        const int ke = (int)min((int64_t)nz, kb + (min(q1, item_end) - q));
+        q = min(q1, item_end);   // the rest of an item past nz is padding
+        const int x0 = TB_TXI * (tile % gx) - 4;       // FP32 box origin (4-cell aligned)
         const int y0 = TB_TYI * (tile / gx) - 2;
         const int i0 = x0 + bxx, j = y0 + byy;
         const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
@@ -154,7 +167,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
             tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
             tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
-            tma_load_3d(S + 5 * TB_F32, &tm_f, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 5 * TB_F32, &tm_f, x0 - 12, y0, p, &bar[s]);   // 16-aligned
         };
         __syncthreads();   // the previous segment's readers are done with every stage
         for (int s = 0; s < TB_NSTAGE; ++s) issue(kb - 1 + s, s);       // kb-1, kb, kb+1
@@ -197,7 +210,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             const float4 wl4 = lds4(W0 + o);
             const float4 wh4 = lds4(W1 + o);
             const float4 r4 = lds4(R0 + o);
-            const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + o);
+            const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + om);
             // the cells' update coefficients for plane z, used by level 1 now and by
             // level 2 at the next step
             Coef32 kc[4];

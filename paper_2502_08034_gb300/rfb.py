@@ -101,12 +101,14 @@ def lib():
         L.rfb_soc_info.argtypes = [H, POINTER(c_int64), POINTER(c_int64)]
         L.rfb_soc_kernel_launches.argtypes = [H]
         L.rfb_soc_kernel_launches.restype = c_int64
+        L.rfb_soc_tuned_fp32_kernel.argtypes = [H, POINTER(c_int32), POINTER(c_double),
+                                                POINTER(c_double)]
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
                      "rfb_soc_current_noalloc", "rfb_soc_upsample", "rfb_soc_set_area_mult",
                      "rfb_soc_adjoint", "rfb_soc_batch_create", "rfb_soc_batch_solve",
-                     "rfb_soc_batch_destroy"):
+                     "rfb_soc_batch_destroy", "rfb_soc_tuned_fp32_kernel"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -118,7 +120,8 @@ class RfbError(RuntimeError):
         self.status = status
 
 
-FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2}
+FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2, "blocked_persistent": 3,
+               "blocked_chunked": 4}
 
 
 def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
@@ -285,6 +288,13 @@ class Solver:
     @property
     def kernel_launches(self) -> int:
         return int(lib().rfb_soc_kernel_launches(self.h))
+
+    def tuned_fp32_kernel(self):
+        """(name, plain ms/sweep, blocked ms/sweep) chosen by the autotuner."""
+        k, a, b = c_int32(), c_double(), c_double()
+        self._check(lib().rfb_soc_tuned_fp32_kernel(self.h, byref(k), byref(a), byref(b)))
+        names = {0: None, 1: "plain", 3: "blocked_persistent", 4: "blocked_chunked"}
+        return names[k.value], a.value, b.value
 
     def close(self):
         if getattr(self, "h", None):
