@@ -78,6 +78,12 @@ struct rfb_soc_handle {
     bool L64_valid = false;
     double L64_key[8] = {};
     int64_t area_version = 0;
+    // double-float copies for the mixed-precision checks: the operator (same layout as
+    // d_L64) and the state being corrected (ping-pong); allocated on the first mixed solve
+    float2* d_L2F = nullptr;
+    bool L2F_valid = false;
+    float2* d_sdf[2] = {nullptr, nullptr};
+    int df_cur = 0;
     double scaled_beta = NAN;
 
     int64_t n_fluid = 0, n_elec = 0;
@@ -263,6 +269,7 @@ void ensure_L64(rfb_soc_handle* h, const OpPoint& op) {
                            op.B,           op.beta,           (double)op.inlet_bc,
                            (double)h->area_version, C.nl ? 2.0 : 1.0};
     if (h->L64_valid && std::memcmp(key, h->L64_key, sizeof key) == 0) return;
+    h->L2F_valid = false;
     for (int q = 0; q < 6; ++q) h->K.f[q] = h->d_L64 + (size_t)q * h->N;
     h->K.diag = h->d_L64 + (size_t)6 * h->N;
     h->K.b = h->d_L64 + (size_t)7 * h->N;
@@ -276,34 +283,71 @@ void ensure_L64(rfb_soc_handle* h, const OpPoint& op) {
     h->L64_valid = true;
 }
 
-// FP64 check on buffer set (s/t). fuse: add delta and write the other buffer.
-void check(rfb_soc_handle* h, const OpPoint& op, bool umt, bool fuse, bool write_r) {
+// FP64 check of the state (s, or t for U_mt): defect, reductions and outputs.
+void check(rfb_soc_handle* h, const OpPoint& op, bool umt) {
     double** buf = umt ? h->d_t : h->d_s;
-    int& cur = umt ? h->t_cur : h->s_cur;
+    const int cur = umt ? h->t_cur : h->s_cur;
     ensure_L64(h, op);
-    Coef<double> C = make_coef<double>(h, op, false, false);
-    Lattice L = lattice(h);
-    const L64 K = h->K;
-    if (fuse) {
-        if (write_r)
-            check64c_kernel<true, true><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, K, buf[cur], h->d_delta[0], buf[cur ^ 1], h->d_r32, h->d_partials,
-                h->kchunk);
-        else
-            check64c_kernel<true, false><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, K, buf[cur], h->d_delta[0], buf[cur ^ 1], nullptr, h->d_partials,
-                h->kchunk);
-        LAUNCHED(h);
-        cur ^= 1;
-    } else {
-        if (write_r)
-            check64c_kernel<false, true><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, K, buf[cur], nullptr, nullptr, h->d_r32, h->d_partials, h->kchunk);
-        else
-            check64c_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
-                L, C, K, buf[cur], nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
-        LAUNCHED(h);
+    const Coef<double> C = make_coef<double>(h, op, false, false);
+    check64c_kernel<false, false><<<h->grid, h->block, 0, h->stream>>>(
+        lattice(h), C, h->K, buf[cur], nullptr, nullptr, nullptr, h->d_partials, h->kchunk);
+    LAUNCHED(h);
+    reduce_readback(h, 0);
+}
+
+// ---- mixed-precision checks in double-float (check_df_kernel)
+
+void ensure_L2F(rfb_soc_handle* h, const OpPoint& op) {
+    ensure_L64(h, op);
+    if (h->L2F_valid) return;
+    if (!h->d_L2F) dalloc(h, &h->d_L2F, (size_t)8 * h->N);
+    split64_kernel<<<flat_grid(8 * h->N), 256, 0, h->stream>>>(h->d_L64, h->d_L2F, 8 * h->N);
+    LAUNCHED(h);
+    h->L2F_valid = true;
+}
+
+// state (s, or t for U_mt) -> its double-float copy
+void df_begin(rfb_soc_handle* h, bool umt) {
+    if (!h->d_sdf[0]) {
+        dalloc(h, &h->d_sdf[0], h->N);
+        dalloc(h, &h->d_sdf[1], h->N);
     }
+    double** buf = umt ? h->d_t : h->d_s;
+    const int cur = umt ? h->t_cur : h->s_cur;
+    split64_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(buf[cur], h->d_sdf[0], h->N);
+    LAUNCHED(h);
+    h->df_cur = 0;
+}
+
+// double-float copy -> the FP64 state
+void df_end(rfb_soc_handle* h, bool umt) {
+    double** buf = umt ? h->d_t : h->d_s;
+    const int cur = umt ? h->t_cur : h->s_cur;
+    join64_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(h->d_sdf[h->df_cur], buf[cur], h->N);
+    LAUNCHED(h);
+}
+
+// defect of the double-float state (fuse: of state + delta, which becomes the state);
+// refreshes the FP32 forcing; reductions 0, 6, 7 only
+void check_df(rfb_soc_handle* h, const OpPoint& op, bool umt, bool fuse) {
+    ensure_L2F(h, op);
+    const size_t N = h->N;
+    L2F K;
+    for (int q = 0; q < 6; ++q) K.f[q] = h->d_L2F + q * N;
+    K.diag = h->d_L2F + 6 * N;
+    K.b = h->d_L2F + 7 * N;
+    const int cur = h->df_cur;
+    if (fuse) {
+        check_df_kernel<true><<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), K, h->d_sdf[cur], h->d_delta[0], h->d_sdf[cur ^ 1], h->d_r32,
+            h->d_partials, op.umt, h->kchunk);
+        h->df_cur ^= 1;
+    } else {
+        check_df_kernel<false><<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), K, h->d_sdf[cur], nullptr, nullptr, h->d_r32, h->d_partials, op.umt,
+            h->kchunk);
+    }
+    LAUNCHED(h);
     reduce_readback(h, 0);
 }
 
@@ -606,10 +650,31 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     int64_t done = 0;
     double sweep_ms = 0.0, check_ms = 0.0;
     const int64_t limit = fixed_sweeps >= 0 ? fixed_sweeps : o.max_sweeps;
-    // first check: residual of the starting state (mixed: also the FP32 forcing)
-    check(h, op, umt, false, mixed);
+    // first check: residual of the starting state (mixed: of its double-float copy, and
+    // the FP32 forcing)
+    if (mixed) {
+        df_begin(h, umt);
+        check_df(h, op, umt, false);
+    } else {
+        check(h, op, umt);
+    }
     ++r.checks;
     fill_result(h, op, &r, n_unknown);
+    // mixed: the FP64 state equals the double-float one and r holds its FP64 check
+    bool joined = !mixed;
+    auto join_and_check = [&]() {
+        CK(h, cudaEventRecord(h->ev[1], h->stream));
+        df_end(h, umt);
+        check(h, op, umt);
+        CK(h, cudaEventRecord(h->ev[2], h->stream));
+        CK(h, cudaEventSynchronize(h->ev[2]));
+        float ms_c = 0.f;
+        CK(h, cudaEventElapsedTime(&ms_c, h->ev[1], h->ev[2]));
+        check_ms += ms_c;
+        ++r.checks;
+        fill_result(h, op, &r, n_unknown);
+        joined = true;
+    };
     // FP32 kernel: one-sweep or two-sweep passes (forced by opts or autotuned once)
     bool use_tb = false;
     if (mixed) {
@@ -631,7 +696,11 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     // pessimistic; one FP64 check costs about 16 FP32 sweeps.
     while (true) {
         if (r.nonfinite > 0) { st = RFB_ERR_NONFINITE; break; }
-        if (fixed_sweeps < 0 && r.residual <= tol) break;
+        if (fixed_sweeps < 0 && r.residual <= tol) {
+            if (joined) break;
+            join_and_check();   // the double-float defect met tol: confirm it in FP64
+            continue;
+        }
         if (done >= limit) {
             st = fixed_sweeps >= 0 ? RFB_OK : RFB_ERR_NOT_CONVERGED;
             break;
@@ -648,7 +717,12 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         if (mixed) sweeps32(h, op, n, use_tb);
         else sweeps64(h, op, umt, n);
         CK(h, cudaEventRecord(h->ev[1], h->stream));
-        check(h, op, umt, mixed, mixed);
+        if (mixed) {
+            check_df(h, op, umt, true);
+            joined = false;
+        } else {
+            check(h, op, umt);
+        }
         CK(h, cudaEventRecord(h->ev[2], h->stream));   // check() synchronised the stream
         CK(h, cudaEventSynchronize(h->ev[2]));
         float ms_s = 0.f, ms_c = 0.f;
@@ -659,6 +733,11 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         done += n;
         ++r.checks;
         fill_result(h, op, &r, n_unknown);
+    }
+    if (!joined) {
+        const rfb_status keep = st;
+        join_and_check();   // the state and the outputs of the call in FP64
+        if (keep == RFB_OK && r.nonfinite > 0) st = RFB_ERR_NONFINITE;
     }
     r.sweeps = done;
     r.sweep_ms = sweep_ms;
@@ -696,7 +775,8 @@ void free_all(rfb_soc_handle* h) {
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
-                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64};
+                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F,
+                    h->d_sdf[0], h->d_sdf[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -977,7 +1057,7 @@ rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res) {
     }
     try {
         OpPoint op = h->op;
-        check(h, op, false, false, false);
+        check(h, op, false);
         rfb_solve_result r{};
         r.checks = 1;
         fill_result(h, op, &r, h->n_fluid);
@@ -1190,7 +1270,7 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         const double* s = umt ? h->d_t[h->t_cur] : h->d_s[h->s_cur];
         // objective value (for the explicit beta term of U) and the scales
         rfb_solve_result fwd{};
-        check(h, op, umt, false, false);
+        check(h, op, umt);
         fill_result(h, op, &fwd, umt ? h->n_fluid - h->n_elec : h->n_fluid);
         const double h3 = h->h * h->h * h->h;
         const double scale = h->kin.n_e * FARADAY * h->kin.c0 * h3;

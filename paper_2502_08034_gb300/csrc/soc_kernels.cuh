@@ -274,12 +274,13 @@ __device__ __forceinline__ Coef32 cell_coef32(unsigned m, int umt, float uL, flo
     else dt = upd ? dt_global : 0.f;
     k.dt = dt;
     k.ac = LOCAL_DT ? (dt > 0.f ? 1.f - cfl : 1.f) : 1.f - dt * d;
-    k.a[0] = dt * (fmaxf(uL, 0.f) + Dh);
-    k.a[1] = dt * (fmaxf(-uH, 0.f) + Dh);
-    k.a[2] = dt * (fmaxf(vL, 0.f) + Dh);
-    k.a[3] = dt * (fmaxf(-vH, 0.f) + Dh);
-    k.a[4] = dt * (fmaxf(wl, 0.f) + Dh);
-    k.a[5] = dt * (fmaxf(-wh, 0.f) + Dh);
+    const float dtD = dt * Dh;
+    k.a[0] = fmaf(dt, fmaxf(uL, 0.f), dtD);
+    k.a[1] = fmaf(dt, fmaxf(-uH, 0.f), dtD);
+    k.a[2] = fmaf(dt, fmaxf(vL, 0.f), dtD);
+    k.a[3] = fmaf(dt, fmaxf(-vH, 0.f), dtD);
+    k.a[4] = fmaf(dt, fmaxf(wl, 0.f), dtD);
+    k.a[5] = fmaf(dt, fmaxf(-wh, 0.f), dtD);
     return k;
 }
 
@@ -881,6 +882,124 @@ check64c_kernel(Lattice L, Coef<double> C, L64 K, const double* __restrict__ s,
             s_cur = s_next;
         }
     }
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+}
+
+// ---------------------------------------------------------------------------------
+// Mixed-precision defect check in double-float arithmetic. GB300 issues FP64 at a small
+// fraction of its FP32 rate, and the FP64 check (about 25 FP64 operations a cell) runs
+// several times longer than its HBM traffic takes. Here the assembled operator and the
+// state are unevaluated sums hi + lo of two FP32 numbers (about 48 significant bits), and
+// the defect is formed with error-free transformations on the FP32 pipes: Knuth's
+// TwoSum, Dekker's FastTwoSum and the exact product through an FMA. The absolute error of
+// a defect is about 2^-47 of its largest term, far below the tolerances of a solve; the
+// last check of every mixed solve is the FP64 one.
+// ---------------------------------------------------------------------------------
+struct L2F {
+    const float2* __restrict__ f[6];   // neighbour coefficients as (hi, lo)
+    const float2* __restrict__ diag;
+    const float2* __restrict__ b;
+};
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {      // a + b = s + e exactly
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) { // needs |a| >= |b|
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+// acc + a x for pairs: exact product of the high parts, the cross terms through FMAs
+__device__ __forceinline__ float2 df_fma(float2 a, float2 x, float2 acc) {
+    const float ph = a.x * x.x;
+    float pl = fmaf(a.x, x.x, -ph);
+    pl = fmaf(a.x, x.y, pl);
+    pl = fmaf(a.y, x.x, pl);
+    const float2 s = two_sum(acc.x, ph);
+    return fast_two_sum(s.x, s.y + (acc.y + pl));
+}
+// pair + FP32 number
+__device__ __forceinline__ float2 df_add_f(float2 a, float b) {
+    const float2 s = two_sum(a.x, b);
+    return fast_two_sum(s.x, s.y + a.y);
+}
+
+// pairs (hi, lo) of FP64 numbers: hi = rn(x), lo = rn(x - hi)
+__global__ void split64_kernel(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double x = in[q];
+        const float hi = __double2float_rn(x);
+        out[q] = make_float2(hi, __double2float_rn(x - (double)hi));
+    }
+}
+__global__ void join64_kernel(const float2* __restrict__ in, double* __restrict__ out, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = in[q];
+        out[q] = (double)v.x + (double)v.y;
+    }
+}
+
+// The defect RHS(s [+ delta]) = b + L (s [+ delta]) at every unknown cell, written as the
+// FP32 forcing (its high part), with the reductions the iteration needs: 0 sum RHS^2,
+// 6 count of non-finite values, 7 max |RHS| (slots 1-5 stay 0). FUSE: the state is
+// s + delta, written to s_new (every cell).
+template <bool FUSE>
+__global__ void __launch_bounds__(BX * BY)
+check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __restrict__ delta,
+                float2* __restrict__ s_new, float* __restrict__ r_out,
+                double* __restrict__ partials, int umt, int kchunk) {
+    float sum2 = 0.f, vmax = 0.f;
+    int bad = 0;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+        const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+        auto val = [&](int64_t cc) -> float2 {
+            return FUSE ? df_add_f(s[cc], delta[cc]) : s[cc];
+        };
+        const float2 zero = make_float2(0.f, 0.f);
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        float2 s_prev = kb > 0 ? val(c - nxny) : zero;
+        float2 s_cur = val(c);
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const float2 s_next = (k + 1 < L.nz) ? val(c + nxny) : zero;
+            const unsigned f = L.flags[c];
+            if (FUSE) s_new[c] = s_cur;
+            if (f & F_FLUID) {
+                if (!(umt && (f & F_ELEC))) {
+                    float2 r = df_fma(K.diag[c], s_cur, K.b[c]);
+                    r = df_fma(K.f[0][c], val(c + oxm), r);
+                    r = df_fma(K.f[1][c], val(c + oxp), r);
+                    r = df_fma(K.f[2][c], val(c + oym), r);
+                    r = df_fma(K.f[3][c], val(c + oyp), r);
+                    r = df_fma(K.f[4][c], s_prev, r);
+                    r = df_fma(K.f[5][c], s_next, r);
+                    r_out[c] = r.x;
+                    const float q = r.x * r.x;
+                    if (isfinite(q)) {
+                        sum2 += q;
+                        vmax = fmaxf(vmax, fabsf(r.x));
+                    } else {
+                        ++bad;
+                    }
+                } else {
+                    r_out[c] = 0.f;
+                }
+            }
+            s_prev = s_cur;
+            s_cur = s_next;
+        }
+    }
+    double acc[NRED] = {(double)sum2, 0.0, 0.0, 0.0, 0.0, 0.0, (double)bad, (double)vmax};
     const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
                         ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
     block_reduce_store(acc, partials + bid * NRED);

@@ -173,24 +173,27 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         for (int s = 0; s < TB_NSTAGE; ++s) issue(kb - 1 + s, s);       // kb-1, kb, kb+1
 
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 d0_prev = zero4;                        // own level 0 at z-1
-        if (in_dom && kb >= 2) d0_prev = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
         float4 l1_m2 = zero4, l1_m1 = zero4;           // own level 1 at z-2, z-1
-        Coef32 skc[4];   // update coefficients of plane z-1 (level 2), from the previous step
-        float4 sr = zero4;                             // forcing of plane z-1
+        // Two register sets that swap roles every step (the loop below is unrolled by two,
+        // so nothing is copied): update coefficients, forcing and own level-0 value of the
+        // step's plane (written) and of the plane before it (read).
+        Coef32 kcA[4], kcB[4];
+        float4 rA = zero4, rB = zero4, dA = zero4, dB = zero4;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            for (int s = 0; s < 6; ++s) skc[e].a[s] = 0.f;
-            skc[e].ac = 1.f;
-            skc[e].dt = 0.f;
+            for (int s = 0; s < 6; ++s) kcB[e].a[s] = 0.f;
+            kcB[e].ac = 1.f;
+            kcB[e].dt = 0.f;
         }
+        if (in_dom && kb >= 2) dB = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
         // A wait that gives up leaves this thread's `good` false; the CTA decides together
         // at the step's barrier (so no thread is left at a barrier the others skipped).
         bool good = wait(0);
+        int s0 = 0;                                    // stage holding plane z
 
-        for (int z = kb - 1; z <= ke; ++z) {
-            const int s0 = (z - (kb - 1)) % TB_NSTAGE;
-            const int s1 = (z + 1 - (kb - 1)) % TB_NSTAGE;
+        auto step = [&](int z, Coef32 (&kc)[4], float4& rr, float4& dc,
+                        const Coef32 (&pkc)[4], const float4& prr, const float4& pdc) -> bool {
+            const int s1 = s0 == TB_NSTAGE - 1 ? 0 : s0 + 1;
             if (good) good = wait(s1);
             const float* D0 = reinterpret_cast<const float*>(stage(s0));
             const float* R0 = D0 + TB_PLANE;
@@ -201,7 +204,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             const float* D1 = reinterpret_cast<const float*>(stage(s1));
             const float* W1 = D1 + 4 * TB_PLANE;
             // ---- level 1 at plane z
-            const float4 dc = lds4(D0 + o);
+            dc = lds4(D0 + o);
             const float4 dn = lds4(D1 + o);
             const float4 u4 = lds4(U0 + o);
             const float un = U0[o + 4];
@@ -209,11 +212,10 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
             const float4 vh4 = lds4(V0 + o + TB_BW);
             const float4 wl4 = lds4(W0 + o);
             const float4 wh4 = lds4(W1 + o);
-            const float4 r4 = lds4(R0 + o);
+            rr = lds4(R0 + o);
             const uint32_t f4 = *reinterpret_cast<const uint32_t*>(F0 + om);
             // the cells' update coefficients for plane z, used by level 1 now and by
             // level 2 at the next step
-            Coef32 kc[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const unsigned m = (f4 >> (8 * e)) & 0xffu;
@@ -230,7 +232,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
                 for (int e = 0; e < 4; ++e)
                     out[e] = cell_apply32(kc[e], el(dc, e), e == 0 ? dxm : el(dc, e - 1),
                                           e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                          el(d0_prev, e), el(dn, e), el(r4, e));
+                                          el(pdc, e), el(dn, e), el(rr, e));
                 l1 = make_float4(out[0], out[1], out[2], out[3]);
             }
             float* L1w = reinterpret_cast<float*>(smem + TB_L1) + (z & 1) * TB_PLANE;
@@ -245,21 +247,25 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
                 float out[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    out[e] = cell_apply32(skc[e], el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
+                    out[e] = cell_apply32(pkc[e], el(l1_m1, e), e == 0 ? lxm : el(l1_m1, e - 1),
                                           e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e),
-                                          el(lyp, e), el(l1_m2, e), el(l1, e), el(sr, e));
+                                          el(lyp, e), el(l1_m2, e), el(l1, e), el(prr, e));
                 *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
                     make_float4(out[0], out[1], out[2], out[3]);
             }
-            // ---- keep what the next step needs; free stage s0 for plane z + 3
-#pragma unroll
-            for (int e = 0; e < 4; ++e) skc[e] = kc[e];
-            sr = r4;
-            d0_prev = dc;
             l1_m2 = l1_m1;
             l1_m1 = l1;
-            if (!__syncthreads_and(good)) { ok = false; break; }
+            // ---- all threads are done with stage s0: refill it with plane z + 3
+            if (!__syncthreads_and(good)) return false;
             if (z + 3 <= ke + 1) issue(z + 3, s0);
+            s0 = s1;
+            return true;
+        };
+
+        for (int z = kb - 1; z <= ke; z += 2) {
+            if (!step(z, kcA, rA, dA, kcB, rB, dB)) { ok = false; break; }
+            if (z + 1 > ke) break;
+            if (!step(z + 1, kcB, rB, dB, kcA, rA, dA)) { ok = false; break; }
         }
     }
     if (!ok) {
