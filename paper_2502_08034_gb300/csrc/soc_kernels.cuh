@@ -259,21 +259,43 @@ struct Coef32 {
     float dt;     // step (multiplies the forcing)
 };
 
+// The part of a cell's diagonal that depends only on its mask byte and on whether it
+// lies on the inlet plane: D/h^2 n_f (+ the inlet face term) + rb, the reaction slope
+// k0 m n_wall B / h; +inf for a cell that is not updated (solid, or a pinned electrode
+// cell in U_mt mode).
+__device__ __forceinline__ float dfix_of(unsigned m, bool inlet, int umt, float Dh, float gDh,
+                                         float rb) {
+    const bool upd = (m & M_FLUID) && !(umt && (m & M_ELEC));
+    return upd ? fmaf(Dh, (float)m_nf(m), inlet ? gDh : 0.f) + rb : INFINITY;
+}
+
+// Per-block table of dfix_of for every mask byte (entries 0-255) and on the inlet plane
+// (256-511), for lattices without area multipliers; tB: the block's copy of the
+// per-n_wall reaction slopes. Callers synchronise the block before reading it.
+constexpr int DFIX_TABLE = 512;
+__device__ __forceinline__ void build_dfix_table(float* tdf, const float* tB, int umt, float Dh,
+                                                 float gDh, int tid, int nthreads) {
+    for (int q = tid; q < DFIX_TABLE; q += nthreads) {
+        const unsigned m = (unsigned)q & 255u;
+        tdf[q] = dfix_of(m, q >= 256, umt, Dh, gDh, tB[m_nwall(m)]);
+    }
+}
+
+// Update coefficients of one cell: d = outflow + dfix is the diagonal of -L, the step is
+// cfl / d (local) or the global one, a_f = dt (inflow_f + D/h^2) and a_c = 1 - dt d.
 template <bool LOCAL_DT>
-__device__ __forceinline__ Coef32 cell_coef32(unsigned m, int umt, float uL, float uH, float vL,
-                                              float vH, float wl, float wh, float rb, float Dh,
-                                              float gDh, bool inlet, float cfl,
+__device__ __forceinline__ Coef32 cell_coef32(float dfix, float uL, float uH, float vL, float vH,
+                                              float wl, float wh, float Dh, float cfl,
                                               float dt_global) {
     Coef32 k;
-    const bool upd = (m & M_FLUID) && !(umt && (m & M_ELEC));
     const float d = (fmaxf(-uL, 0.f) + fmaxf(uH, 0.f)) + (fmaxf(-vL, 0.f) + fmaxf(vH, 0.f)) +
-                    (fmaxf(-wl, 0.f) + fmaxf(wh, 0.f)) +
-                    (Dh * (float)m_nf(m) + (inlet ? gDh : 0.f) + rb);
+                    (fmaxf(-wl, 0.f) + fmaxf(wh, 0.f)) + dfix;
+    const bool upd = dfix < INFINITY;
     float dt;
     if (LOCAL_DT) dt = (upd && d > 0.f) ? __fdividef(cfl, d) : 0.f;
     else dt = upd ? dt_global : 0.f;
     k.dt = dt;
-    k.ac = LOCAL_DT ? (dt > 0.f ? 1.f - cfl : 1.f) : 1.f - dt * d;
+    k.ac = dt > 0.f ? (LOCAL_DT ? 1.f - cfl : 1.f - dt * d) : 1.f;
     const float dtD = dt * Dh;
     k.a[0] = fmaf(dt, fmaxf(uL, 0.f), dtD);
     k.a[1] = fmaf(dt, fmaxf(-uH, 0.f), dtD);
@@ -302,27 +324,31 @@ __device__ __forceinline__ float cell_apply32(const Coef32& k, float sc, float x
 // kb .. ke-1. tB: the block's shared copy of the per-n_wall reaction slope.
 template <bool LOCAL_DT>
 __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
-                                               const float* tB, const float* __restrict__ s,
+                                               const float* tB, const float* tdf,
+                                               const float* __restrict__ s,
                                                float* __restrict__ s_out,
                                                const float* __restrict__ force, float cfl,
                                                int i0, int j, int kb, int ke);
 
 template <bool LOCAL_DT>
 __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float>& C,
-                                              const float* tB, const float* __restrict__ s,
+                                              const float* tB, const float* tdf,
+                                              const float* __restrict__ s,
                                               float* __restrict__ s_out,
                                               const float* __restrict__ force, float cfl,
                                               int bx, int by, int kb, int ke) {
     const int i0 = 4 * (bx * VBX + threadIdx.x);
     const int j = by * VBY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
-    sweep32v_cells<LOCAL_DT>(L, C, tB, s, s_out, force, cfl, i0, j, kb, ke);
+    sweep32v_cells<LOCAL_DT>(L, C, tB, tdf, s, s_out, force, cfl, i0, j, kb, ke);
 }
 
 // The 4 cells (i0 .. i0+3, j) of every plane kb .. ke-1 (i0 % 4 == 0, nx % 4 == 0).
+// tdf: the block's table of dfix_of (used when the lattice has no area multipliers).
 template <bool LOCAL_DT>
 __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
-                                               const float* tB, const float* __restrict__ s,
+                                               const float* tB, const float* tdf,
+                                               const float* __restrict__ s,
                                                float* __restrict__ s_out,
                                                const float* __restrict__ force, float cfl,
                                                int i0, int j, int kb, int ke) {
@@ -357,9 +383,11 @@ __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<floa
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const unsigned m = (m4b >> (8 * e)) & 0xffu;
+            const float dfix = C.m ? dfix_of(m, inlet, C.umt, Dh, gDh, el(m4, e) * tB[m_nwall(m)])
+                                   : tdf[(inlet ? 256 : 0) + m];
             const Coef32 kc = cell_coef32<LOCAL_DT>(
-                m, C.umt, el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
-                el(wL, e), el(wH, e), el(m4, e) * tB[m_nwall(m)], Dh, gDh, inlet, cfl, C.dt);
+                dfix, el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
+                el(wL, e), el(wH, e), Dh, cfl, C.dt);
             out[e] = cell_apply32(kc, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
                                   e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
                                   el(d_prev, e), el(d_next, e), el(r4, e));
@@ -377,13 +405,16 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
                 float* __restrict__ s_out, const float* __restrict__ force, float cfl,
                 int kchunk) {
     __shared__ float tB[8];
+    __shared__ float tdf[DFIX_TABLE];
     {
         const int t_ = threadIdx.y * VBX + threadIdx.x;
         if (t_ < 8) tB[t_] = C.rB[t_];
         __syncthreads();
+        build_dfix_table(tdf, tB, C.umt, C.Dh, C.gDh, t_, VBX * VBY);
+        __syncthreads();
     }
     const int kb = blockIdx.z * kchunk;
-    sweep32v_tile<LOCAL_DT>(L, C, tB, s, s_out, force, cfl, blockIdx.x, blockIdx.y, kb,
+    sweep32v_tile<LOCAL_DT>(L, C, tB, tdf, s, s_out, force, cfl, blockIdx.x, blockIdx.y, kb,
                             min(kb + kchunk, L.nz));
 }
 
@@ -421,6 +452,7 @@ __global__ void __launch_bounds__(VBX * VBY, 3)
 batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
                    int n_items, int parity) {
     __shared__ float tB[8];
+    __shared__ float tdf[DFIX_TABLE];
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
         const BatchItem it = items[w];
         const BatchInst* I = insts + it.inst;
@@ -437,11 +469,15 @@ batch_sweep_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         const int t = threadIdx.y * VBX + threadIdx.x;
         if (t < 8) tB[t] = I->C32.rB[t];
         __syncthreads();
+        if (!C.m) {
+            build_dfix_table(tdf, tB, C.umt, C.Dh, C.gDh, t, VBX * VBY);
+            __syncthreads();
+        }
         // the item covers 4-cell groups it.bx .. it.bx + 255 of the flattened x-y plane
         // (a group never crosses a row because nx % 4 == 0)
         const int64_t cell = 4 * ((int64_t)it.bx + t);
         if (cell < (int64_t)L.nxny)
-            sweep32v_cells<LOCAL_DT>(L, C, tB, src, dst, r32, cfl, (int)(cell % L.nx),
+            sweep32v_cells<LOCAL_DT>(L, C, tB, tdf, src, dst, r32, cfl, (int)(cell % L.nx),
                                      (int)(cell / L.nx), it.kb, it.ke);
     }
 }

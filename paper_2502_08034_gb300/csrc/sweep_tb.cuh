@@ -101,8 +101,12 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TB_BAR);
     __shared__ float tB[8];
+    __shared__ float tdf[DFIX_TABLE];
     const int tid = threadIdx.x;
     if (tid < 8) tB[tid] = A.tB[tid];
+    __syncthreads();
+    build_dfix_table(tdf, tB, A.umt, A.Dh, A.gDh, tid, TB_THREADS);   // read after the
+                                                                     // barrier below
     const int tx = tid % TB_GX, ty = tid / TB_GX;
     const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
     const int nx = A.nx, ny = A.ny, nz = A.nz;
@@ -219,9 +223,10 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const unsigned m = (f4 >> (8 * e)) & 0xffu;
-                kc[e] = cell_coef32<LOCAL_DT>(m, A.umt, el(u4, e), e == 3 ? un : el(u4, e + 1),
-                                              el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e),
-                                              tB[m_nwall(m)], A.Dh, A.gDh, z == 0, A.cfl, A.dt);
+                kc[e] = cell_coef32<LOCAL_DT>(tdf[(z == 0 ? 256 : 0) + m], el(u4, e),
+                                              e == 3 ? un : el(u4, e + 1), el(v4, e),
+                                              el(vh4, e), el(wl4, e), el(wh4, e), A.Dh, A.cfl,
+                                              A.dt);
             }
             float4 l1 = dc;
             if (in_dom && z >= 0 && z < nz) {
