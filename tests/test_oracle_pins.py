@@ -499,3 +499,38 @@ def test_uniform_eta_zero_overpotential_is_inert():
     op = soc.assemble(p)
     s = soc.initial_state(op, p.s_in)
     assert np.max(np.abs(soc.rhs(op, s))) < 1e-9 * np.max(np.abs(op.L.diagonal()))
+
+
+# ------------------------------------------------------------------ grid convergence
+
+def _restrict_fluid_mean(s_f, fluid_f):
+    """2x coarsening: the mean of a coarse cell's fluid children (Sec. IV compares levels
+    by averaging the fine solution onto the coarse cells)."""
+    nz, ny, nx = s_f.shape
+    a = (s_f * fluid_f).reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).sum(axis=(1, 3, 5))
+    n = fluid_f.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).sum(axis=(1, 3, 5))
+    return np.where(n > 0, a / np.maximum(n, 1), 0.0), n > 0
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_grid_convergence_same_fibers_three_levels(seed):
+    """The same analytic fibers rasterised at h, h/2, h/4 (8x8x16 to 32x32x64, each level
+    with its own flood fill and flow): the RMS difference between a level and the next
+    finer one (restricted by fluid-cell averaging) falls, and so does the change in U."""
+    from paper_2502_08034_gb300 import synth
+    cases = synth.multilevel_cases((32, 32, 64), 3, 0.8, 8.0, seed, 0.01, -0.10, 0.5, 1e-10)
+    sols = []
+    for c in cases:
+        p = problem_from_case(c, soc)
+        op = soc.assemble(p)
+        s = soc.steady_state(op)
+        sols.append((s.reshape(c.solid.shape), c.solid == 0, soc.outputs(p, op, s).U))
+    errs = []
+    for lev in range(2):
+        sc, fc, _ = sols[lev]
+        r, has = _restrict_fluid_mean(*sols[lev + 1][:2])
+        m = fc & has
+        errs.append(float(np.sqrt(np.mean((r[m] - sc[m]) ** 2))))
+    assert errs[1] < errs[0], errs
+    dU = [abs(sols[1][2] - sols[0][2]), abs(sols[2][2] - sols[1][2])]
+    assert dU[1] < dU[0], dU
