@@ -360,6 +360,14 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
  * every kernel inside the graph). */
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h);
 
+/* Self-test of the bounded waits of the two-sweep pass (no counterpart in the paper):
+ * launches one block on the current device that waits, through the same bounded
+ * mbarrier wait as the pass, on a barrier nothing completes, polling at most spin_limit
+ * times (1 .. 2^26). *gave_up = 1 when every thread gave up, recorded the error and the
+ * kernel ran to its end (the context stays usable). RFB_ERR_INVALID_ARG for a bad
+ * argument, RFB_ERR_CUDA if a CUDA call failed (detail in rfb_soc_last_error(NULL)). */
+rfb_status rfb_selftest_bounded_wait(int64_t spin_limit, int32_t* gave_up);
+
 /* The FP32 correction kernel the handle's autotuner chose for RFB_PREC_MIXED solves with
  * fp32_kernel = 0 or 2, as an opts.fp32_kernel value: 0 = not chosen yet, 1 = one sweep
  * per launch, 3 / 4 = two-sweep passes in the persistent / chunked launch shape; and the

@@ -1377,6 +1377,30 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
 
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h) { return h ? h->launches : 0; }
 
+rfb_status rfb_selftest_bounded_wait(int64_t spin_limit, int32_t* gave_up) {
+    if (!gave_up || spin_limit < 1 || spin_limit > ((int64_t)1 << 26)) {
+        g_create_error = "spin_limit must be in [1, 2^26] and gave_up non-NULL";
+        return RFB_ERR_INVALID_ARG;
+    }
+    (void)cudaGetLastError();
+    unsigned int* d = nullptr;
+    unsigned int hv[2] = {0, 0};
+    cudaError_t e = cudaMalloc((void**)&d, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        mbar_timeout_probe_kernel<<<1, 64>>>((unsigned long long)spin_limit, d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hv, d, sizeof hv, cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("bounded-wait self-test: ") + cudaGetErrorString(e);
+        return RFB_ERR_CUDA;
+    }
+    *gave_up = (hv[0] == 1u && hv[1] == 1u) ? 1 : 0;
+    return RFB_OK;
+}
+
 rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
                                      double* plain_ms_per_sweep,
                                      double* blocked_ms_per_sweep) {

@@ -80,6 +80,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Wait for the phase of `bar` with the given parity, polling at most `limit` times; on
+// giving up, set *err and return false (a wait never blocks a kernel indefinitely).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit, unsigned int* err) {
+    for (unsigned long long n = 0; !mbar_try_wait(bar, parity);) {
+        if (++n > limit) {
+            atomicExch(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Self-test of the bounded wait: one CTA waits on a barrier that no thread or copy ever
+// completes; every thread must give up after `limit` polls and set *err; *done is set
+// after the block's barrier, showing that the kernel ran to its end.
+__global__ void mbar_timeout_probe_kernel(unsigned long long limit, unsigned int* err,
+                                          unsigned int* done) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(&bar, 0u, limit, err);
+    __syncthreads();
+    if (threadIdx.x == 0 && !arrived) atomicExch(done, 1u);
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
                                             uint64_t* bar) {
     asm volatile(
@@ -120,13 +149,7 @@ sweep32tb_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant
     uint32_t phase = 0;   // parity of each stage's next completion
     uint32_t pend = 0;    // stages with a load in flight (every thread tracks the same set)
     auto wait = [&](int s) -> bool {                   // bounded wait for stage s
-        unsigned long long n = 0;
-        while (!mbar_try_wait(&bar[s], (phase >> s) & 1u)) {
-            if (++n > TB_SPIN_LIMIT) {
-                atomicExch(A.err, 1u);
-                return false;
-            }
-        }
+        if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, TB_SPIN_LIMIT, A.err)) return false;
         phase ^= 1u << s;
         pend &= ~(1u << s);
         return true;

@@ -103,12 +103,14 @@ def lib():
         L.rfb_soc_kernel_launches.restype = c_int64
         L.rfb_soc_tuned_fp32_kernel.argtypes = [H, POINTER(c_int32), POINTER(c_double),
                                                 POINTER(c_double)]
+        L.rfb_selftest_bounded_wait.argtypes = [c_int64, POINTER(c_int32)]
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
                      "rfb_soc_current_noalloc", "rfb_soc_upsample", "rfb_soc_set_area_mult",
                      "rfb_soc_adjoint", "rfb_soc_batch_create", "rfb_soc_batch_solve",
-                     "rfb_soc_batch_destroy", "rfb_soc_tuned_fp32_kernel"):
+                     "rfb_soc_batch_destroy", "rfb_soc_tuned_fp32_kernel",
+                     "rfb_selftest_bounded_wait"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -379,3 +381,14 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return c_void_p(stream)
     return c_void_p(int(stream.cuda_stream))
+
+
+def selftest_bounded_wait(spin_limit=1 << 12) -> bool:
+    """rfb_selftest_bounded_wait: True if a wait on a barrier that never completes gave up
+    after spin_limit polls, set the error word and let its kernel finish."""
+    g = c_int32()
+    st = lib().rfb_selftest_bounded_wait(int(spin_limit), byref(g))
+    if st != RFB_OK:
+        raise RfbError(st, lib().rfb_soc_last_error(None).decode())
+    return bool(g.value)
+
