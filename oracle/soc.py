@@ -603,3 +603,66 @@ def prolong(s_coarse: np.ndarray, solid_coarse: np.ndarray, solid_fine: np.ndarr
     fine = parent.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
     fine = np.where(solid_fine.astype(bool), 0.0, fine)
     return fine.ravel()
+
+
+# --------------------------------------------------------------------------------------
+# Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def, nernst-model-eta-update,
+# nernst-model-s-update; explicit form Algorithm 8)
+# --------------------------------------------------------------------------------------
+
+def nernst_iterate(p: Problem, omega: float, tol: float, cfl: float = 0.4,
+                   local_dt: bool = True, max_steps: int = 2_000_000, check_every: int = 10):
+    """The explicit Nernst model for the affine-kinetics problem p (alpha = 1/2).
+
+    Electrode cells (fluid cells with k0 a_c > 0) are Dirichlet cells holding
+    s = sigma(V~ - eta~) (Eq. nernst-model-s-update); every step applies the transport
+    operator (advection + diffusion, the SBV operator without its source) to the current
+    state, the electrode cells' transport rate T_c = (L_T s + b_T)_c plays the part of
+    Delta s_elec / Delta t in Eq. nernst-eta-inst-def,
+        eta~_I = 2 asinh( -T_c / (2 k0 a_c sqrt(s_c (1 - s_c))) ),
+    eta~ <- (1 - w_c) eta~ + w_c eta~_I (Eq. nernst-model-eta-update), and the other fluid
+    cells take the explicit step s <- s + dt T. The paper leaves the relaxation open; the
+    update is a fixed-point map of eta~ whose slope at a cell is
+        G_c = (-d_c sqrt(s(1-s)) / (k0 a_c) + (1 - 2s) sinh(eta~/2)) / cosh(eta~/2)
+    (d_c the transport diagonal), so one global weight must stay below 2 / (1 + |G_c|) at
+    every electrode cell, about 1e-3 for slow kinetics. Each cell therefore uses
+    w_c = omega / (1 + |G_c|) at the current state: stable for omega in (0, 1], the
+    local Newton step at omega = 1. Start: s = s_in, eta~ = 0, electrode
+    cells at sigma(V~). Stops when the SBV residual tau RMS(RHS_SBV(s)) < tol, the steady
+    state of both models (Sec. III.C: they converge to the same solution).
+    Returns (s, eta_t, steps); eta_t is 0 off the electrode cells."""
+    if abs(p.alpha - 0.5) > 1e-15:
+        raise ValueError("the Nernst model is derived for alpha = 1/2 (Eq. source-term-bv)")
+    sbv = assemble(p)                                   # residual of the SBV problem
+    tr = assemble(dataclasses.replace(p, k0=0.0))       # transport only
+    kin = sbv.kin
+    kappa = sbv.kappa                                   # k0 a_c
+    elec = sbv.unknown & (kappa > 0)
+    inner = sbv.unknown & ~elec
+    d = step_diagonal(sbv)
+    d_t = -tr.L.diagonal()                              # transport diagonal
+    if local_dt:
+        dt = np.where(inner, cfl / np.where(d > 0, d, 1.0), 0.0)
+    else:
+        dt = np.where(inner, dt_global(sbv, cfl), 0.0)
+    s = initial_state(sbv, p.s_in)
+    eta_t = np.zeros(s.size)
+    s[elec] = 1.0 / (1.0 + np.exp(-(kin.Vt - eta_t[elec])))
+    n = 0
+    while n < max_steps:
+        T = tr.L @ s + tr.b
+        se = s[elec]
+        root = np.sqrt(se * (1.0 - se))
+        eta_i = 2.0 * np.arcsinh(-T[elec] / (2.0 * kappa[elec] * root))
+        e = eta_t[elec]
+        G = (-d_t[elec] * root / kappa[elec] + (1.0 - 2.0 * se) * np.sinh(e / 2.0)) / \
+            np.cosh(e / 2.0)
+        w = omega / (1.0 + np.abs(G))
+        eta_t[elec] = (1.0 - w) * e + w * eta_i
+        s_new = s + dt * T
+        s_new[elec] = 1.0 / (1.0 + np.exp(-(kin.Vt - eta_t[elec])))
+        s = s_new
+        n += 1
+        if n % check_every == 0 and residual(sbv, s) < tol:
+            break
+    return s, eta_t, n

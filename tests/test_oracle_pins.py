@@ -5,6 +5,7 @@ prints, closed forms, exact discrete identities, symmetries, bounds, limits and 
 force, chosen so that a dropped term, a wrong sign or index, or a transposed operand in
 the oracle fails at least one of them.
 """
+import dataclasses
 import math
 import os
 
@@ -534,3 +535,51 @@ def test_grid_convergence_same_fibers_three_levels(seed):
     assert errs[1] < errs[0], errs
     dU = [abs(sols[1][2] - sols[0][2]), abs(sols[2][2] - sols[1][2])]
     assert dU[1] < dU[0], dU
+
+
+# ------------------------------------------------------------------ Nernst model
+
+def _nernst_problem(k0=7.2e-5, **over):
+    return _p3((12, 12, 24), k0=k0, **over)
+
+
+@pytest.mark.parametrize("local_dt", [True, False])
+def test_nernst_model_reaches_the_sbv_steady_state(local_dt):
+    """The Nernst model's fixed point is the SBV steady state (Sec. III.C: both models
+    converge to the same solution), and there eta~ = V~ - logit(s) on electrode cells
+    (Eq. s-from-etat) with the Butler-Volmer source of Eq. source-term-bv balancing
+    transport (Eq. nernst-model-elec)."""
+    p = _nernst_problem()
+    ref = soc.steady_state(soc.assemble(p))
+    s, eta_t, n = soc.nernst_iterate(p, 1.0 if local_dt else 0.5, 1e-12, local_dt=local_dt)
+    assert np.max(np.abs(s - ref)) < 1e-10 * np.max(np.abs(ref))
+    op = soc.assemble(p)
+    elec = op.unknown & (op.kappa > 0)
+    kin = op.kin
+    assert np.max(np.abs(eta_t[elec] - (kin.Vt - np.log(s[elec] / (1 - s[elec]))))) < 1e-8
+    tr = soc.assemble(dataclasses.replace(p, k0=0.0))
+    T = (tr.L @ s + tr.b)[elec]
+    src = op.kappa[elec] * 2 * np.sqrt(s[elec] * (1 - s[elec])) * np.sinh(eta_t[elec] / 2)
+    assert np.max(np.abs(T + src)) < 1e-6 * np.max(np.abs(src))
+    assert np.all(eta_t[~elec] == 0.0)
+
+
+def test_nernst_model_fast_kinetics_limit():
+    """k0 -> infinity: the electrode cells approach the Dirichlet value s_eq = sigma(V~) of
+    Eq. np-fast-boundary at first order in 1/k0 (a 100x faster rate constant brings them
+    about 100x closer), and eta~ falls towards 0."""
+    errs, etas = [], []
+    for k0 in (1e-2, 1.0):
+        p = _nernst_problem(k0=k0)
+        op = soc.assemble(p)
+        elec = op.unknown & (op.kappa > 0)
+        s, eta_t, _ = soc.nernst_iterate(p, 1.0, 1e-8)
+        errs.append(np.max(np.abs(s[elec] - op.kin.s_eq)))
+        etas.append(np.max(np.abs(eta_t[elec])))
+    assert 80 < errs[0] / errs[1] < 120, errs
+    assert etas[1] < etas[0] / 5, etas
+
+
+def test_nernst_model_needs_alpha_one_half():
+    with pytest.raises(ValueError):
+        soc.nernst_iterate(_nernst_problem(alpha=0.3), 0.5, 1e-8)
