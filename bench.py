@@ -41,11 +41,12 @@ def parse():
     ap.add_argument("--dims", default="256,256,512")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--workload", default="mixed",
-                    choices=["mixed", "batch48", "upsample", "adjoint"],
+                    choices=["mixed", "batch48", "upsample", "adjoint", "nernst"],
                     help="mixed: the 256x256x512 mixed-precision solve (default); batch48: the "
                          "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
                          "512x512x1024 iterative upsampling; adjoint: gradients of I_tot, U "
-                         "and U_mt on the 128x128x256 differentiation workload")
+                         "and U_mt on the 128x128x256 differentiation workload; nernst: the "
+                         "Nernst model against the SBV FP64 solve on 48x48x96 and 128x128x256")
     ap.add_argument("--fp32-kernel", default="auto",
                     choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
@@ -376,6 +377,70 @@ def run_upsample(args):
         s.close()
 
 
+def run_nernst(args):
+    """Nernst model (FP64) against the SBV FP64 solve of the same problem: the 48x48x96 plain
+    workload (d = 8, porosity 0.8, 1 cm/s, eta = -0.10 V, s_in = 0.5) and a 128x128x256
+    lattice of the same recipe, each at the workload's k0 = 1e-7 m/s and at the paper's
+    7.2e-5 m/s, to residual 1e-10; omega = 1. value: cell-updates/s of the Nernst solves."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_2502_08034_gb300 import _build, rfb, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    tol = 1e-10
+    stream = torch.cuda.current_stream()
+    rows, cells, nernst_ms, sweep_ms, sweeps_n = [], 0.0, 0.0, 0.0, 0
+    with Clocks(local) as clk:
+        for dims in ((48, 48, 96), (128, 128, 256)):
+            base = synth.fiber_channel_case(dims=dims, flow_device="cuda:%d" % local)
+            for k0 in (base.k0, 7.2e-5):
+                case = dataclasses.replace(base, k0=k0)
+                with rfb.Solver.from_case(case, stream=stream) as sv:
+                    for _ in range(max(1, args.warmup)):
+                        sv.reset_state()
+                        sv.solve(case.s_in, case.eta, tol, precision="fp64")
+                        sv.reset_state()
+                        sv.solve_nernst(case.s_in, case.eta, tol)
+                    sv.reset_state()
+                    r_sbv = sv.solve(case.s_in, case.eta, tol, precision="fp64")
+                    s_sbv = sv.get_state()
+                    res = []
+                    for _ in range(args.steps):
+                        sv.reset_state()
+                        res.append(sv.solve_nernst(case.s_in, case.eta, tol))
+                    s_n = sv.get_state()
+                r_n = res[-1]
+                n = case.n
+                cells += n * sum(r["sweeps"] for r in res)
+                nernst_ms += sum(r["time_ms"] for r in res)
+                sweep_ms += sum(r["sweep_ms"] for r in res)
+                sweeps_n += n * sum(r["sweeps"] for r in res)
+                rows.append({"dims": list(dims), "k0": k0,
+                             "sbv": {"sweeps": r_sbv["sweeps"], "time_ms": r_sbv["time_ms"]},
+                             "nernst": {"sweeps": r_n["sweeps"], "time_ms": r_n["time_ms"],
+                                        "residual": r_n["residual"]},
+                             "maxabs_state_difference": float(np.abs(s_n - s_sbv).max()),
+                             "I_tot_A": r_n["I_tot"]})
+    # FP64-ALU roofline of the Nernst step: ~16 FP64 flops a cell (7 FMAs of the operator,
+    # the update) against the nominal 1.25 TFLOP/s FP64 rate of GB300
+    achieved = 16.0 * sweeps_n / (sweep_ms / 1e3) / 1e12
+    out = {"metric": METRIC, "value": cells / (nernst_ms / 1e3) / 1e9, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": nernst_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "nernst_48x48x96_128x128x256", "tol": tol, "omega": 1.0},
+           "cases": rows,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                        "frac": achieved / 1.25, "traffic": None,
+                        "kernel": "nernst64_kernel (FP64)", "peak_kind": "nominal FP64"},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Differentiation workload: 128x128x256, porosity 0.8, d = 8, lognormal (sigma 0.3)
     area multipliers on wall cells; step = FP64 solve to 1e-12 + U_mt solve + the three
@@ -445,6 +510,9 @@ def main():
         return
     if args.workload == "adjoint":
         run_adjoint(args)
+        return
+    if args.workload == "nernst":
+        run_nernst(args)
         return
     import numpy as np
     import torch

@@ -360,6 +360,32 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
  * every kernel inside the graph). */
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h);
 
+/*
+ * Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def,
+ * nernst-model-eta-update, nernst-model-s-update; explicit form Algorithm 8): the steady
+ * state of the SBV problem (the same as rfb_soc_solve's) reached by treating electrode
+ * cells (fluid cells with k0 m n_wall / dx > 0) as Dirichlet cells s = sigma(V~ - eta~)
+ * with an overpotential field eta~ updated from the transport rate of each step:
+ *   eta~_I = 2 asinh(-T / (2 k0 a sqrt(s (1 - s)))),  eta~ <- (1 - w) eta~ + w eta~_I,
+ * w = omega / (1 + |G|) per cell, G the slope of this fixed-point map at the cell (a single
+ * weight must stay below 2 / (1 + |G|) at every electrode cell; the scaling makes every
+ * omega in (0, 1] stable, omega = 1 being the cell's Newton step). Other fluid cells take
+ * the explicit pseudo-time step. Convergence is judged by the FP64 residual of the SBV
+ * problem, so res holds the same quantities as rfb_soc_solve's. Cold start (no state):
+ * s = s_in, eta~ = 0, electrode cells at sigma(V~); warm start: the current state with
+ * eta~ = V~ - logit(s). Requirements: kinetics mode 0 with alpha = 1/2 (the sinh form of
+ * Eq. source-term-bv), k0 > 0, opts precision RFB_PREC_FP64, 0 < omega <= 1; otherwise
+ * RFB_ERR_INVALID_ARG. A converged result allows rfb_soc_adjoint at this operating point.
+ */
+rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double overpotential,
+                                double tol, double omega, const rfb_solve_opts* opts,
+                                rfb_solve_result* res);
+
+/* eta~ of the last rfb_soc_solve_nernst on the current state: N doubles (host or device
+ * per kind), 0 off the electrode cells. RFB_ERR_STATE if there is none (reset_state and
+ * set_state drop it). */
+rfb_status rfb_soc_get_overpotential(rfb_soc_handle* h, double* eta_t, rfb_mem_kind kind);
+
 /* Self-test of the bounded waits of the two-sweep pass (no counterpart in the paper):
  * launches one block on the current device that waits, through the same bounded
  * mbarrier wait as the pass, on a barrier nothing completes, polling at most spin_limit

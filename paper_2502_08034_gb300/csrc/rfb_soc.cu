@@ -69,6 +69,8 @@ struct rfb_soc_handle {
     bool s_converged = false;     // state is a converged solve at op (adjoint precondition)
     bool t_converged = false;     // U_mt state converged at umt_op
     OpPoint umt_op;
+    double* d_eta = nullptr;      // Nernst model: eta~ on electrode cells (first use)
+    bool have_eta = false;
     double* d_lam[2] = {nullptr, nullptr};   // adjoint state (allocated on first use)
     double* d_g = nullptr;
     double* d_grad = nullptr;
@@ -775,7 +777,7 @@ void free_all(rfb_soc_handle* h) {
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
-                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F,
+                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F, h->d_eta,
                     h->d_sdf[0], h->d_sdf[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1090,9 +1092,121 @@ rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts
     }
 }
 
+rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double eta, double tol,
+                                double omega, const rfb_solve_opts* opts,
+                                rfb_solve_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    if (!(s_in >= 0 && s_in <= 1)) { set_err(h, "s_in must be in [0, 1]"); return RFB_ERR_INVALID_ARG; }
+    if (!std::isfinite(eta)) { set_err(h, "eta must be finite"); return RFB_ERR_INVALID_ARG; }
+    if (!(tol > 0)) { set_err(h, "tol must be > 0"); return RFB_ERR_INVALID_ARG; }
+    if (!(omega > 0 && omega <= 1)) { set_err(h, "omega must be in (0, 1]"); return RFB_ERR_INVALID_ARG; }
+    if (o.precision != RFB_PREC_FP64 || h->kin.mode != RFB_KIN_AFFINE || h->kin.alpha != 0.5 ||
+        !(h->kin.k0 > 0)) {
+        set_err(h, "the Nernst model needs RFB_PREC_FP64, kinetics mode 0, alpha = 1/2, k0 > 0");
+        return RFB_ERR_INVALID_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        OpPoint op = make_op(o, s_in, eta, false);
+        prepare(h, op);
+        const int64_t N = h->N;
+        if (!h->d_eta) dalloc(h, &h->d_eta, N);
+        const bool warm = h->have_state;
+        if (!warm) init_state(h, false, op.s_in);
+        const Coef<double> C = make_coef<double>(h, op, false, false);
+        const double kap0 = h->kin.k0 / h->h;
+        const double Vt = h->kin.n_e * (-eta) / (R_GAS * h->kin.T / FARADAY);
+        nernst_init_kernel<<<flat_grid(N), 256, 0, h->stream>>>(
+            lattice(h), C, h->d_s[h->s_cur], h->d_s[h->s_cur ^ 1], h->d_eta, kap0, Vt,
+            warm ? 1 : 0);
+        LAUNCHED(h);
+        h->have_eta = true;
+        ensure_L64(h, op);
+        const float* dtc = op.dt_mode == RFB_DT_LOCAL ? h->d_dtc : nullptr;
+        const int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, RFB_PREC_FP64);
+        rfb_solve_result r{};
+        rfb_status st = RFB_OK;
+        int64_t done = 0;
+        double sweep_ms = 0.0, check_ms = 0.0;
+        check(h, op, false);
+        ++r.checks;
+        fill_result(h, op, &r, h->n_fluid);
+        while (true) {
+            if (r.nonfinite > 0) { st = RFB_ERR_NONFINITE; break; }
+            if (r.residual <= tol) break;
+            if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
+                                        std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
+                set_err(h, "opts.timeout_ms reached after %lld steps", (long long)done);
+                st = RFB_ERR_NOT_CONVERGED;
+                break;
+            }
+            const int64_t n = std::min(every, o.max_sweeps - done);
+            CK(h, cudaEventRecord(h->ev[0], h->stream));
+            for (int64_t q = 0; q < n; ++q) {
+                nernst64_kernel<<<h->grid, h->block, 0, h->stream>>>(
+                    lattice(h), h->K, C, dtc, op.dt, h->d_s[h->s_cur], h->d_s[h->s_cur ^ 1],
+                    h->d_eta, kap0, Vt, omega, h->kchunk);
+                LAUNCHED(h);
+                h->s_cur ^= 1;
+            }
+            CK(h, cudaEventRecord(h->ev[1], h->stream));
+            check(h, op, false);
+            CK(h, cudaEventRecord(h->ev[2], h->stream));
+            CK(h, cudaEventSynchronize(h->ev[2]));
+            float ms_s = 0.f, ms_c = 0.f;
+            CK(h, cudaEventElapsedTime(&ms_s, h->ev[0], h->ev[1]));
+            CK(h, cudaEventElapsedTime(&ms_c, h->ev[1], h->ev[2]));
+            sweep_ms += ms_s;
+            check_ms += ms_c;
+            done += n;
+            ++r.checks;
+            fill_result(h, op, &r, h->n_fluid);
+        }
+        r.sweeps = done;
+        r.sweep_ms = sweep_ms;
+        r.check_ms = check_ms;
+        r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                        .count();
+        h->op = op;
+        h->s_converged = (st == RFB_OK);
+        if (res) *res = r;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_get_overpotential(rfb_soc_handle* h, double* eta_t, rfb_mem_kind kind) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (!eta_t || (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE)) {
+        set_err(h, "eta_t must be non-NULL and kind HOST or DEVICE");
+        return RFB_ERR_INVALID_ARG;
+    }
+    if (!h->have_eta) {
+        set_err(h, "no Nernst-model solve on the current state");
+        return RFB_ERR_STATE;
+    }
+    try {
+        CK(h, cudaMemcpyAsync(eta_t, h->d_eta, h->N * sizeof(double),
+                              kind == RFB_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                   : cudaMemcpyDeviceToDevice,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return RFB_OK;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
 rfb_status rfb_soc_reset_state(rfb_soc_handle* h) {
     rfb_status g = guard(h);
     if (g) return g;
+    h->have_eta = false;
     h->have_state = false;
     h->s_converged = false;
     h->op.valid = false;
@@ -1121,6 +1235,7 @@ rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind ki
     if (g) return g;
     if (!s) { set_err(h, "s is NULL"); return RFB_ERR_INVALID_ARG; }
     if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
+    h->have_eta = false;
     try {
         const double* src = s;
         double* tmp = nullptr;

@@ -626,6 +626,98 @@ sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_globa
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def,
+// nernst-model-eta-update, nernst-model-s-update; Algorithm 8), FP64 on the assembled
+// operator of the affine (SBV) problem. Electrode cells (k_c = m_c k0 n_wall / h > 0)
+// hold s = sigma(V~ - eta~); their transport rate is T = RHS_SBV(s) - k_c (A - B s) (the
+// operator without the cell's source), the instantaneous overpotential
+//   eta~_I = 2 asinh(-T / (2 k_c sqrt(s (1 - s)))),
+// and eta~ <- (1 - w) eta~ + w eta~_I with w = omega / (1 + |G|), G the slope of that map:
+//   G = (-d_T sqrt(s(1-s)) / k_c + (1 - 2 s) sinh(eta~/2)) / cosh(eta~/2),
+// d_T = the transport diagonal (one weight for all cells would have to stay below
+// 2 / (1 + |G|) everywhere). Other unknown cells take the explicit step s + dt RHS.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double sigmoid64(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+__global__ void __launch_bounds__(BX * BY)
+nernst64_kernel(Lattice L, L64 K, Coef<double> C, const float* __restrict__ dtc,
+                double dt_global, const double* __restrict__ s, double* __restrict__ s_out,
+                double* __restrict__ eta_t, double kap0, double Vt, double omega, int kchunk) {
+    RFB_LOAD_TABLES(double, C)
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, nxny = L.nxny;
+        const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+        const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        double s_prev = kb > 0 ? s[c - nxny] : 0.0;
+        double s_cur = s[c];
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const double s_next = (k + 1 < L.nz) ? s[c + nxny] : 0.0;
+            const unsigned f = L.flags[c];
+            if (f & F_FLUID) {
+                const double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym],
+                                       s[c + oyp], s_prev, s_next);
+                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
+                const double mult = C.m ? C.m[c] : 1.0;
+                const double kc = mult * kap0 * nw;
+                if (kc > 0.0) {
+                    const double T = r - mult * (tA[nw] - tB[nw] * s_cur);
+                    const double dT = -K.diag[c] - mult * tB[nw];
+                    const double sc = fmin(fmax(s_cur, 1e-300), 1.0 - 0x1p-53);
+                    const double root = sqrt(sc * (1.0 - sc));
+                    const double e = eta_t[c];
+                    const double ei = 2.0 * asinh(-T / (2.0 * kc * root));
+                    const double G = (-dT * root / kc + (1.0 - 2.0 * sc) * sinh(0.5 * e)) /
+                                     cosh(0.5 * e);
+                    const double w = omega / (1.0 + fabs(G));
+                    const double en = fma(w, ei - e, e);
+                    eta_t[c] = en;
+                    s_out[c] = sigmoid64(Vt - en);
+                } else {
+                    const double dt = dtc ? (double)dtc[c] : dt_global;
+                    s_out[c] = fma(dt, r, s_cur);
+                }
+            }
+            s_prev = s_cur;
+            s_cur = s_next;
+        }
+    }
+}
+
+// Start of a Nernst solve: eta~ = 0 and s = sigma(V~) on electrode cells (cold), or
+// eta~ = V~ - logit(s) from the current state (warm); 0 off the electrode cells.
+__global__ void nernst_init_kernel(Lattice L, Coef<double> C, double* __restrict__ sa,
+                                   double* __restrict__ sb, double* __restrict__ eta_t,
+                                   double kap0, double Vt, int warm) {
+    const int64_t N = (int64_t)L.nxny * L.nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = L.flags[c];
+        double e = 0.0;
+        if (f & F_FLUID) {
+            const int i = (int)(c % L.nx);
+            const int j = (int)((c / L.nx) % L.ny);
+            const int k = (int)(c / L.nxny);
+            const int nw = n_wall_of(f, i, j, k, L.nx, L.ny, L.nz);
+            const double kc = (C.m ? C.m[c] : 1.0) * kap0 * nw;
+            if (kc > 0.0) {
+                if (warm) {
+                    const double s = fmin(fmax(sa[c], 1e-300), 1.0 - 0x1p-53);
+                    e = Vt - log(s / (1.0 - s));
+                } else {
+                    sa[c] = sb[c] = sigmoid64(Vt);
+                }
+            }
+        }
+        eta_t[c] = e;
+    }
+}
+
 // Kinetics mode 1: adds the source's derivative m_c rA[n_wall] g'(s_c) to the assembled
 // diagonal, so that the operator becomes the Jacobian dRHS/ds at the state s (the
 // adjoint of the nonlinear steady state).

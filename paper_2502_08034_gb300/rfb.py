@@ -104,13 +104,17 @@ def lib():
         L.rfb_soc_tuned_fp32_kernel.argtypes = [H, POINTER(c_int32), POINTER(c_double),
                                                 POINTER(c_double)]
         L.rfb_selftest_bounded_wait.argtypes = [c_int64, POINTER(c_int32)]
+        L.rfb_soc_solve_nernst.argtypes = [H, c_double, c_double, c_double, c_double,
+                                           POINTER(SolveOpts), POINTER(SolveResult)]
+        L.rfb_soc_get_overpotential.argtypes = [H, c_void_p, c_int]
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
                      "rfb_soc_current_noalloc", "rfb_soc_upsample", "rfb_soc_set_area_mult",
                      "rfb_soc_adjoint", "rfb_soc_batch_create", "rfb_soc_batch_solve",
                      "rfb_soc_batch_destroy", "rfb_soc_tuned_fp32_kernel",
-                     "rfb_selftest_bounded_wait"):
+                     "rfb_selftest_bounded_wait", "rfb_soc_solve_nernst",
+                     "rfb_soc_get_overpotential"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -223,6 +227,27 @@ class Solver:
         o = make_opts(**opts)
         self._check(lib().rfb_soc_step(self.h, float(s_in), float(eta), int(n), byref(o), byref(r)))
         return r.as_dict()
+
+    def solve_nernst(self, s_in, eta, tol, omega=1.0, allow_not_converged=False, **opts) -> dict:
+        """rfb_soc_solve_nernst: the SBV steady state by the Nernst model (FP64)."""
+        r = SolveResult()
+        o = make_opts(**opts)
+        st = lib().rfb_soc_solve_nernst(self.h, float(s_in), float(eta), float(tol),
+                                        float(omega), byref(o), byref(r))
+        self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
+        out = r.as_dict()
+        out["status"] = st
+        return out
+
+    def get_overpotential(self, out=None):
+        """eta~ of the last Nernst-model solve (N values, 0 off the electrode cells)."""
+        if out is None:
+            out = np.empty(self.n_cells, dtype=np.float64)
+        p, keep, kind = _ptr(out, np.float64)
+        if kind == MEM_HOST and keep is not out:
+            raise ValueError("out must be a contiguous float64 array")
+        self._check(lib().rfb_soc_get_overpotential(self.h, p, kind))
+        return out
 
     def current(self) -> dict:
         r = SolveResult()
