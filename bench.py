@@ -436,7 +436,8 @@ def run_nernst(args):
            "cases": rows,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                         "frac": achieved / 1.25, "traffic": None,
-                        "kernel": "nernst64_kernel (FP64)", "peak_kind": "nominal FP64"},
+                        "kernel": "nernst_interior_kernel + nernst_elec_kernel (FP64)",
+                        "peak_kind": "nominal FP64"},
            "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 

@@ -70,6 +70,7 @@ struct rfb_soc_handle {
     bool t_converged = false;     // U_mt state converged at umt_op
     OpPoint umt_op;
     double* d_eta = nullptr;      // Nernst model: eta~ on electrode cells (first use)
+    int* d_elec = nullptr;        // Nernst model: electrode-cell list (+ count at [N])
     bool have_eta = false;
     double* d_lam[2] = {nullptr, nullptr};   // adjoint state (allocated on first use)
     double* d_g = nullptr;
@@ -777,7 +778,7 @@ void free_all(rfb_soc_handle* h) {
                     h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
-                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F, h->d_eta,
+                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F, h->d_eta, h->d_elec,
                     h->d_sdf[0], h->d_sdf[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1124,6 +1125,16 @@ rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double eta, doub
             warm ? 1 : 0);
         LAUNCHED(h);
         h->have_eta = true;
+        // the electrode cells as a list: their update runs in full warps of its own
+        if (!h->d_elec) dalloc(h, &h->d_elec, N + 1);
+        CK(h, cudaMemsetAsync(h->d_elec + N, 0, sizeof(int), h->stream));
+        nernst_list_kernel<<<flat_grid(N), 256, 0, h->stream>>>(lattice(h), C, kap0, h->d_elec,
+                                                                h->d_elec + N);
+        LAUNCHED(h);
+        int n_elec = 0;
+        CK(h, cudaMemcpyAsync(&n_elec, h->d_elec + N, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
         ensure_L64(h, op);
         const float* dtc = op.dt_mode == RFB_DT_LOCAL ? h->d_dtc : nullptr;
         const int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, RFB_PREC_FP64);
@@ -1147,10 +1158,16 @@ rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double eta, doub
             const int64_t n = std::min(every, o.max_sweeps - done);
             CK(h, cudaEventRecord(h->ev[0], h->stream));
             for (int64_t q = 0; q < n; ++q) {
-                nernst64_kernel<<<h->grid, h->block, 0, h->stream>>>(
+                nernst_interior_kernel<<<h->grid, h->block, 0, h->stream>>>(
                     lattice(h), h->K, C, dtc, op.dt, h->d_s[h->s_cur], h->d_s[h->s_cur ^ 1],
-                    h->d_eta, kap0, Vt, omega, h->kchunk);
+                    kap0, h->kchunk);
                 LAUNCHED(h);
+                if (n_elec > 0) {
+                    nernst_elec_kernel<<<flat_grid(n_elec), 256, 0, h->stream>>>(
+                        lattice(h), h->K, C, h->d_elec, n_elec, h->d_s[h->s_cur],
+                        h->d_s[h->s_cur ^ 1], h->d_eta, kap0, Vt, omega);
+                    LAUNCHED(h);
+                }
                 h->s_cur ^= 1;
             }
             CK(h, cudaEventRecord(h->ev[1], h->stream));

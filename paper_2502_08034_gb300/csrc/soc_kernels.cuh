@@ -636,56 +636,114 @@ sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_globa
 // and eta~ <- (1 - w) eta~ + w eta~_I with w = omega / (1 + |G|), G the slope of that map:
 //   G = (-d_T sqrt(s(1-s)) / k_c + (1 - 2 s) sinh(eta~/2)) / cosh(eta~/2),
 // d_T = the transport diagonal (one weight for all cells would have to stay below
-// 2 / (1 + |G|) everywhere). Other unknown cells take the explicit step s + dt RHS.
+// 2 / (1 + |G|) everywhere); G is evaluated in FP32 (GB300's FP64 transcendentals are
+// slow). Other unknown cells take the explicit step s + dt RHS.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double sigmoid64(double x) { return 1.0 / (1.0 + exp(-x)); }
 
+// k0 a_c of fluid cell c (0 on cells without fiber neighbours or with multiplier 0)
+__device__ __forceinline__ double nernst_kc(const Lattice& L, const Coef<double>& C, int64_t c,
+                                            unsigned f, double kap0) {
+    const int i = (int)(c % L.nx);
+    const int j = (int)((c / L.nx) % L.ny);
+    const int k = (int)(c / L.nxny);
+    return (C.m ? C.m[c] : 1.0) * kap0 * n_wall_of(f, i, j, k, L.nx, L.ny, L.nz);
+}
+
+// The electrode cells as a list (warp-aggregated appends: each warp's cells stay
+// together and in order; which warp comes first does not matter, every cell's update is
+// independent of the others within a step).
+__global__ void nernst_list_kernel(Lattice L, Coef<double> C, double kap0,
+                                   int* __restrict__ list, int* __restrict__ count) {
+    const int64_t N = (int64_t)L.nxny * L.nz;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < N;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = base + threadIdx.x;
+        bool e = false;
+        if (c < N) {
+            const unsigned f = L.flags[c];
+            e = (f & F_FLUID) && nernst_kc(L, C, c, f, kap0) > 0.0;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, e);
+        int first = 0;
+        if (lane == 0 && mask) first = atomicAdd(count, __popc(mask));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (e) list[first + __popc(mask & ((1u << lane) - 1u))] = (int)c;
+    }
+}
+
+// Interior step: s_out = s + dt RHS(s) on unknown cells that are not electrode cells.
 __global__ void __launch_bounds__(BX * BY)
-nernst64_kernel(Lattice L, L64 K, Coef<double> C, const float* __restrict__ dtc,
-                double dt_global, const double* __restrict__ s, double* __restrict__ s_out,
-                double* __restrict__ eta_t, double kap0, double Vt, double omega, int kchunk) {
-    RFB_LOAD_TABLES(double, C)
+nernst_interior_kernel(Lattice L, L64 K, Coef<double> C, const float* __restrict__ dtc,
+                       double dt_global, const double* __restrict__ s,
+                       double* __restrict__ s_out, double kap0, int kchunk) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
-    if (i < L.nx && j < L.ny) {
-        const int kb = blockIdx.z * kchunk;
-        const int ke = min(kb + kchunk, L.nz);
-        const int nx = L.nx, nxny = L.nxny;
-        const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
-        const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
-        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
-        double s_prev = kb > 0 ? s[c - nxny] : 0.0;
-        double s_cur = s[c];
-        for (int k = kb; k < ke; ++k, c += nxny) {
-            const double s_next = (k + 1 < L.nz) ? s[c + nxny] : 0.0;
-            const unsigned f = L.flags[c];
-            if (f & F_FLUID) {
-                const double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym],
-                                       s[c + oyp], s_prev, s_next);
-                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
-                const double mult = C.m ? C.m[c] : 1.0;
-                const double kc = mult * kap0 * nw;
-                if (kc > 0.0) {
-                    const double T = r - mult * (tA[nw] - tB[nw] * s_cur);
-                    const double dT = -K.diag[c] - mult * tB[nw];
-                    const double sc = fmin(fmax(s_cur, 1e-300), 1.0 - 0x1p-53);
-                    const double root = sqrt(sc * (1.0 - sc));
-                    const double e = eta_t[c];
-                    const double ei = 2.0 * asinh(-T / (2.0 * kc * root));
-                    const double G = (-dT * root / kc + (1.0 - 2.0 * sc) * sinh(0.5 * e)) /
-                                     cosh(0.5 * e);
-                    const double w = omega / (1.0 + fabs(G));
-                    const double en = fma(w, ei - e, e);
-                    eta_t[c] = en;
-                    s_out[c] = sigmoid64(Vt - en);
-                } else {
-                    const double dt = dtc ? (double)dtc[c] : dt_global;
-                    s_out[c] = fma(dt, r, s_cur);
-                }
-            }
-            s_prev = s_cur;
-            s_cur = s_next;
+    if (i >= L.nx || j >= L.ny) return;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, L.nz);
+    const int nx = L.nx, nxny = L.nxny;
+    const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+    const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+    int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+    double s_prev = kb > 0 ? s[c - nxny] : 0.0;
+    double s_cur = s[c];
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const double s_next = (k + 1 < L.nz) ? s[c + nxny] : 0.0;
+        const unsigned f = L.flags[c];
+        const bool elec = (f & F_ELEC) && (!C.m || C.m[c] > 0.0) && kap0 > 0.0;
+        if ((f & F_FLUID) && !elec) {
+            const double r = rhs64(K, c, s_cur, s[c + oxm], s[c + oxp], s[c + oym], s[c + oyp],
+                                   s_prev, s_next);
+            const double dt = dtc ? (double)dtc[c] : dt_global;
+            s_out[c] = fma(dt, r, s_cur);
         }
+        s_prev = s_cur;
+        s_cur = s_next;
+    }
+}
+
+// Electrode step over the list: T = RHS_SBV(s) - k_c (A - B s), eta~_I, the relaxed
+// eta~ update and s_out = sigma(V~ - eta~).
+__global__ void nernst_elec_kernel(Lattice L, L64 K, Coef<double> C,
+                                   const int* __restrict__ list, int n,
+                                   const double* __restrict__ s, double* __restrict__ s_out,
+                                   double* __restrict__ eta_t, double kap0, double Vt,
+                                   double omega) {
+    __shared__ double tA[8], tB[8];
+    if (threadIdx.x < 8) { tA[threadIdx.x] = C.rA[threadIdx.x]; tB[threadIdx.x] = C.rB[threadIdx.x]; }
+    __syncthreads();
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int64_t nxny = L.nxny;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int64_t c = list[q];
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / nxny);
+        const double sc0 = s[c];
+        const double r = rhs64(K, c, sc0, s[c - (i > 0)], s[c + (i + 1 < nx)],
+                               s[c - (j > 0 ? nx : 0)], s[c + (j + 1 < ny ? nx : 0)],
+                               s[c - (k > 0 ? nxny : 0)], s[c + (k + 1 < nz ? nxny : 0)]);
+        const unsigned f = L.flags[c];
+        const int nw = n_wall_of(f, i, j, k, nx, ny, nz);
+        const double mult = C.m ? C.m[c] : 1.0;
+        const double kc = mult * kap0 * nw;
+        const double T = r - mult * (tA[nw] - tB[nw] * sc0);
+        const double dT = -K.diag[c] - mult * tB[nw];
+        const double sc = fmin(fmax(sc0, 1e-300), 1.0 - 0x1p-53);
+        const double root = sqrt(sc * (1.0 - sc));
+        const double e = eta_t[c];
+        const double ei = 2.0 * asinh(-T / (2.0 * kc * root));
+        // the relaxation weight only sets the step (the fixed point does not depend on
+        // it): FP32, one exponential for sinh and cosh
+        const float ex = __expf(0.5f * (float)e), exi = 1.0f / ex;
+        const float G = (-(float)(dT / kc) * (float)root +
+                         (float)(1.0 - 2.0 * sc) * 0.5f * (ex - exi)) / (0.5f * (ex + exi));
+        const double w = omega / (1.0 + (double)fabsf(G));
+        const double en = fma(w, ei - e, e);
+        eta_t[c] = en;
+        s_out[c] = sigmoid64(Vt - en);
     }
 }
 
