@@ -482,6 +482,17 @@ def run_adjoint(args):
     elapsed = ev0.elapsed_time(ev1)
     fwd, adj = outs[-1]
     sweeps = fwd["sweeps"] + sum(a["sweeps"] for a in adj)
+    # the same adjoints in mixed precision (FP32 transposed correction sweeps, double-float
+    # defects, FP64 confirmation): time and gradient difference from the FP64 ones
+    mixed = []
+    for o in ("I_tot", "U", "U_mt"):
+        g64, b64, _ = sv.adjoint(o, 1e-11)
+        gmx, bmx, rm = sv.adjoint(o, 1e-11, precision="mixed")
+        scale = float(abs(g64).max()) or 1.0
+        mixed.append({"objective": o, "sweeps": rm["sweeps"], "time_ms": rm["time_ms"],
+                      "relative_residual": rm["residual"],
+                      "max_rel_diff_d_area_mult": float(abs(gmx - g64).max()) / scale,
+                      "rel_diff_d_beta": abs(bmx - b64) / abs(b64)})
     out = {"metric": METRIC, "value": case.n * sweeps * args.steps / (elapsed / 1e3) / 1e9,
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -492,6 +503,7 @@ def run_adjoint(args):
            "adjoints": [{"objective": o, "sweeps": a["sweeps"], "time_ms": a["time_ms"],
                          "relative_residual": a["residual"]}
                         for o, a in zip(("I_tot", "U", "U_mt"), adj)],
+           "adjoints_mixed": mixed,
            "clocks": clk.summary(), "setup_s": setup_s}
     print(json.dumps(out), flush=True)
     sv.close()

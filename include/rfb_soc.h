@@ -280,7 +280,12 @@ typedef enum rfb_objective {
  * U_mt problem has no kinetics) and is returned as zeros. velocity_scale must be > 0.
  * RFB_KIN_UNIFORM_ETA: the source is nonlinear; L above is the Jacobian dRHS/ds at the
  * converged state (transport plus k0 a_c dR~/ds on the diagonal) and R~ the mode's rate.
- *   opts             nullable; dt_mode / cfl / check_every / max_sweeps are used
+ *   opts             nullable; dt_mode / cfl / check_every / max_sweeps / timeout_ms are
+ *                    used, and precision: RFB_PREC_FP64 (FP64 transposed sweeps) or
+ *                    RFB_PREC_MIXED (FP32 sweeps of the transposed operator correcting lam,
+ *                    defects g + L^T lam in double-float arithmetic, the last one confirmed
+ *                    in FP64; kinetics mode 0 or U_MT, nx % 4 == 0, else
+ *                    RFB_ERR_INVALID_ARG)
  *   d_area_mult      nullable; N doubles (host or device per kind) receiving dJ/dm_c
  *                    (zero on solid cells and cells without fiber neighbours)
  *   d_velocity_scale nullable; host double receiving dJ/dbeta

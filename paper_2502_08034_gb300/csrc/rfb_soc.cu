@@ -87,6 +87,7 @@ struct rfb_soc_handle {
     bool L2F_valid = false;
     float2* d_sdf[2] = {nullptr, nullptr};
     int df_cur = 0;
+    float2* d_gdf = nullptr;      // adjoint source as pairs (mixed-precision adjoints)
     double scaled_beta = NAN;
 
     int64_t n_fluid = 0, n_elec = 0;
@@ -544,6 +545,35 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = fal
     }
 }
 
+// n FP32 correction sweeps of the transposed operator (adjoint), delta <- delta +
+// dt (L^T delta + r), from delta = 0; the result is left in d_delta[0]. One-sweep kernel
+// only (nx % 4 == 0).
+void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int64_t n) {
+    const size_t bytes = (size_t)h->N * sizeof(float);
+    CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->d_delta[1], 0, bytes, h->stream));
+    const bool local = op.dt_mode == RFB_DT_LOCAL;
+    Lattice L = lattice(h);
+    int cur = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        if (local)
+            sweep32v_kernel<true, true><<<h->vgrid, h->vblock, 0, h->stream>>>(
+                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+        else
+            sweep32v_kernel<false, true><<<h->vgrid, h->vblock, 0, h->stream>>>(
+                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+        LAUNCHED(h);
+        cur ^= 1;
+    }
+    if (cur == 1) {
+        std::swap(h->d_delta[0], h->d_delta[1]);
+        if (h->tm_ready) {
+            std::swap(h->tm_delta[0], h->tm_delta[1]);
+            std::swap(h->tm_delta_ptr[0], h->tm_delta_ptr[1]);
+        }
+    }
+}
+
 // Project-written autotuner for one lattice: time 8 plain sweeps and 8 sweeps of each
 // launch shape of the two-sweep pass (CUDA events, on the current forcing) and keep the
 // fastest (tb_only: choose between the two-sweep shapes only).
@@ -779,7 +809,7 @@ void free_all(rfb_soc_handle* h) {
                     h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
                     h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
                     h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F, h->d_eta, h->d_elec,
-                    h->d_sdf[0], h->d_sdf[1]};
+                    h->d_sdf[0], h->d_sdf[1], h->d_gdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -1387,6 +1417,11 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
     if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
     OpPoint op = umt ? h->umt_op : h->op;
     if (!(op.beta > 0)) { set_err(h, "the adjoint needs velocity_scale > 0"); return RFB_ERR_INVALID_ARG; }
+    const bool mixed = o.precision == RFB_PREC_MIXED;
+    if (mixed && ((!umt && h->kin.mode != RFB_KIN_AFFINE) || h->nx % 4 != 0)) {
+        set_err(h, "a mixed-precision adjoint needs kinetics mode 0 (or U_MT) and nx %% 4 == 0");
+        return RFB_ERR_INVALID_ARG;
+    }
     op.dt_mode = o.dt_mode;
     op.cfl = o.cfl;
     auto t0 = std::chrono::steady_clock::now();
@@ -1433,12 +1468,96 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
         CK(h, cudaMemsetAsync(h->d_lam[0], 0, N * 8, h->stream));
         CK(h, cudaMemsetAsync(h->d_lam[1], 0, N * 8, h->stream));
         int cur = 0;
-        const int64_t every = o.check_every > 0 ? o.check_every : 100;
+        const int64_t every = o.check_every > 0 ? o.check_every : (mixed ? 200 : 100);
         rfb_solve_result r{};
         rfb_status st = RFB_OK;
         double rel = INFINITY;
         int64_t done = 0;
-        while (true) {
+        // FP64 adjoint residual of d_lam[cur] (relative to ||g||)
+        auto check64 = [&]() {
+            adjoint64c_kernel<1><<<h->grid, h->block, 0, h->stream>>>(
+                lattice(h), h->K, C.dtc, op.dt, h->d_lam[cur], nullptr, h->d_g, h->d_partials,
+                op.umt, h->kchunk);
+            LAUNCHED(h);
+            reduce_readback(h, 0);
+            ++r.checks;
+            rel = h->h_red[1] > 0 ? std::sqrt(h->h_red[0] / h->h_red[1]) : 0.0;
+        };
+        auto time_up = [&]() {
+            return o.timeout_ms > 0 &&
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                           .count() >= o.timeout_ms;
+        };
+        if (mixed) {
+            // FP32 transposed correction sweeps on delta, double-float defects
+            // r = g + L^T lam, FP64 confirmation of the cycle that meets tol
+            ensure_L2F(h, op);
+            if (!h->d_gdf) dalloc(h, &h->d_gdf, N);
+            if (!h->d_sdf[0]) {
+                dalloc(h, &h->d_sdf[0], N);
+                dalloc(h, &h->d_sdf[1], N);
+            }
+            split64_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_g, h->d_gdf, N);
+            LAUNCHED(h);
+            CK(h, cudaMemsetAsync(h->d_sdf[0], 0, N * sizeof(float2), h->stream));
+            h->df_cur = 0;
+            L2F K2;
+            for (int q = 0; q < 6; ++q) K2.f[q] = h->d_L2F + q * (size_t)N;
+            K2.diag = h->d_L2F + 6 * (size_t)N;
+            K2.b = h->d_L2F + 7 * (size_t)N;
+            const Coef<float> C32 = make_coef<float>(h, op, true, false);
+            auto df_check = [&](bool fuse) {
+                const int dc = h->df_cur;
+                if (fuse) {
+                    check_df_adjoint_kernel<true><<<h->grid, h->block, 0, h->stream>>>(
+                        lattice(h), K2, h->d_sdf[dc], h->d_delta[0], h->d_sdf[dc ^ 1], h->d_gdf,
+                        h->d_r32, h->d_partials, op.umt, h->kchunk);
+                    h->df_cur ^= 1;
+                } else {
+                    check_df_adjoint_kernel<false><<<h->grid, h->block, 0, h->stream>>>(
+                        lattice(h), K2, h->d_sdf[dc], nullptr, nullptr, h->d_gdf, h->d_r32,
+                        h->d_partials, op.umt, h->kchunk);
+                }
+                LAUNCHED(h);
+                reduce_readback(h, 0);
+                ++r.checks;
+                rel = h->h_red[1] > 0 ? std::sqrt(h->h_red[0] / h->h_red[1]) : 0.0;
+            };
+            auto join_and_check = [&]() {
+                join64_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_sdf[h->df_cur],
+                                                                   h->d_lam[cur], N);
+                LAUNCHED(h);
+                check64();
+            };
+            df_check(false);
+            bool joined = false;
+            while (true) {
+                if (h->h_red[6] > 0) { st = RFB_ERR_NONFINITE; break; }
+                if (rel <= tol) {
+                    if (joined) break;
+                    join_and_check();
+                    joined = true;
+                    continue;
+                }
+                if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+                if (time_up()) {
+                    set_err(h, "opts.timeout_ms reached after %lld adjoint sweeps", (long long)done);
+                    st = RFB_ERR_NOT_CONVERGED;
+                    break;
+                }
+                const int64_t n = std::min(every, o.max_sweeps - done);
+                sweeps32_adjoint(h, op, C32, n);
+                df_check(true);
+                joined = false;
+                done += n;
+            }
+            if (!joined) {
+                const bool bad = st == RFB_ERR_NONFINITE;
+                join_and_check();
+                if (!bad && h->h_red[6] > 0) st = RFB_ERR_NONFINITE;
+            }
+        }
+        while (!mixed) {
             adjoint64c_kernel<1><<<h->grid, h->block, 0, h->stream>>>(
                 lattice(h), h->K, C.dtc, op.dt, h->d_lam[cur], nullptr, h->d_g, h->d_partials,
                 op.umt, h->kchunk);

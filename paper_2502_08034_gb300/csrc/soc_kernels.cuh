@@ -230,7 +230,7 @@ __device__ __forceinline__ float el(const float4& v, int e) {
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
-template <bool LOCAL_DT>
+template <bool LOCAL_DT, bool TR = false>
 __global__ void __launch_bounds__(VBX * VBY)
 sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
                 float* __restrict__ s_out, const float* __restrict__ force, float cfl,
@@ -283,7 +283,10 @@ __device__ __forceinline__ void build_dfix_table(float* tdf, const float* tB, in
 
 // Update coefficients of one cell: d = outflow + dfix is the diagonal of -L, the step is
 // cfl / d (local) or the global one, a_f = dt (inflow_f + D/h^2) and a_c = 1 - dt d.
-template <bool LOCAL_DT>
+// TR: the same for the transposed operator L^T (adjoint), whose coefficient towards the
+// neighbour across face f is that neighbour's inflow from this cell, i.e. this cell's
+// outflow through f: a_f = dt (outflow_f + D/h^2); the diagonal is the same.
+template <bool LOCAL_DT, bool TR = false>
 __device__ __forceinline__ Coef32 cell_coef32(float dfix, float uL, float uH, float vL, float vH,
                                               float wl, float wh, float Dh, float cfl,
                                               float dt_global) {
@@ -297,12 +300,13 @@ __device__ __forceinline__ Coef32 cell_coef32(float dfix, float uL, float uH, fl
     k.dt = dt;
     k.ac = dt > 0.f ? (LOCAL_DT ? 1.f - cfl : 1.f - dt * d) : 1.f;
     const float dtD = dt * Dh;
-    k.a[0] = fmaf(dt, fmaxf(uL, 0.f), dtD);
-    k.a[1] = fmaf(dt, fmaxf(-uH, 0.f), dtD);
-    k.a[2] = fmaf(dt, fmaxf(vL, 0.f), dtD);
-    k.a[3] = fmaf(dt, fmaxf(-vH, 0.f), dtD);
-    k.a[4] = fmaf(dt, fmaxf(wl, 0.f), dtD);
-    k.a[5] = fmaf(dt, fmaxf(-wh, 0.f), dtD);
+    const float sg = TR ? -1.f : 1.f;
+    k.a[0] = fmaf(dt, fmaxf(sg * uL, 0.f), dtD);
+    k.a[1] = fmaf(dt, fmaxf(-sg * uH, 0.f), dtD);
+    k.a[2] = fmaf(dt, fmaxf(sg * vL, 0.f), dtD);
+    k.a[3] = fmaf(dt, fmaxf(-sg * vH, 0.f), dtD);
+    k.a[4] = fmaf(dt, fmaxf(sg * wl, 0.f), dtD);
+    k.a[5] = fmaf(dt, fmaxf(-sg * wh, 0.f), dtD);
     return k;
 }
 
@@ -322,7 +326,7 @@ __device__ __forceinline__ float cell_apply32(const Coef32& k, float sc, float x
 
 // One tile of the vectorised sweep: columns (4 (bx VBX + tx) .. +3, by VBY + ty), planes
 // kb .. ke-1. tB: the block's shared copy of the per-n_wall reaction slope.
-template <bool LOCAL_DT>
+template <bool LOCAL_DT, bool TR = false>
 __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
                                                const float* tB, const float* tdf,
                                                const float* __restrict__ s,
@@ -330,7 +334,7 @@ __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<floa
                                                const float* __restrict__ force, float cfl,
                                                int i0, int j, int kb, int ke);
 
-template <bool LOCAL_DT>
+template <bool LOCAL_DT, bool TR = false>
 __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float>& C,
                                               const float* tB, const float* tdf,
                                               const float* __restrict__ s,
@@ -340,12 +344,13 @@ __device__ __forceinline__ void sweep32v_tile(const Lattice& L, const Coef<float
     const int i0 = 4 * (bx * VBX + threadIdx.x);
     const int j = by * VBY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
-    sweep32v_cells<LOCAL_DT>(L, C, tB, tdf, s, s_out, force, cfl, i0, j, kb, ke);
+    sweep32v_cells<LOCAL_DT, TR>(L, C, tB, tdf, s, s_out, force, cfl, i0, j, kb, ke);
 }
 
 // The 4 cells (i0 .. i0+3, j) of every plane kb .. ke-1 (i0 % 4 == 0, nx % 4 == 0).
 // tdf: the block's table of dfix_of (used when the lattice has no area multipliers).
-template <bool LOCAL_DT>
+// TR: a sweep of the transposed operator (adjoint correction).
+template <bool LOCAL_DT, bool TR>
 __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<float>& C,
                                                const float* tB, const float* tdf,
                                                const float* __restrict__ s,
@@ -385,7 +390,7 @@ __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<floa
             const unsigned m = (m4b >> (8 * e)) & 0xffu;
             const float dfix = C.m ? dfix_of(m, inlet, C.umt, Dh, gDh, el(m4, e) * tB[m_nwall(m)])
                                    : tdf[(inlet ? 256 : 0) + m];
-            const Coef32 kc = cell_coef32<LOCAL_DT>(
+            const Coef32 kc = cell_coef32<LOCAL_DT, TR>(
                 dfix, el(u4, e), e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
                 el(wL, e), el(wH, e), Dh, cfl, C.dt);
             out[e] = cell_apply32(kc, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
@@ -399,7 +404,7 @@ __device__ __forceinline__ void sweep32v_cells(const Lattice& L, const Coef<floa
     }
 }
 
-template <bool LOCAL_DT>
+template <bool LOCAL_DT, bool TR>
 __global__ void __launch_bounds__(VBX * VBY)
 sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
                 float* __restrict__ s_out, const float* __restrict__ force, float cfl,
@@ -414,8 +419,8 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
         __syncthreads();
     }
     const int kb = blockIdx.z * kchunk;
-    sweep32v_tile<LOCAL_DT>(L, C, tB, tdf, s, s_out, force, cfl, blockIdx.x, blockIdx.y, kb,
-                            min(kb + kchunk, L.nz));
+    sweep32v_tile<LOCAL_DT, TR>(L, C, tB, tdf, s, s_out, force, cfl, blockIdx.x, blockIdx.y,
+                                kb, min(kb + kchunk, L.nz));
 }
 
 // ---------------------------------------------------------------------------------
@@ -1186,6 +1191,69 @@ check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __r
         }
     }
     double acc[NRED] = {(double)sum2, 0.0, 0.0, 0.0, 0.0, 0.0, (double)bad, (double)vmax};
+    const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
+                        ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_reduce_store(acc, partials + bid * NRED);
+}
+
+// Adjoint defect r = g + L^T lam in double-float (lam [+ delta] as pairs): (L^T lam)_c
+// gathers from each neighbour row the coefficient that points back to c. Written as the
+// FP32 forcing; reductions 0 sum r^2, 1 sum g^2, 6 non-finite count, 7 max |r| over unknown
+// cells. FUSE: lam + delta is the state, written to lam_new (every cell).
+template <bool FUSE>
+__global__ void __launch_bounds__(BX * BY)
+check_df_adjoint_kernel(Lattice L, L2F K, const float2* __restrict__ lam,
+                        const float* __restrict__ delta, float2* __restrict__ lam_new,
+                        const float2* __restrict__ g, float* __restrict__ r_out,
+                        double* __restrict__ partials, int umt, int kchunk) {
+    float sum2 = 0.f, sumg = 0.f, vmax = 0.f;
+    int bad = 0;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i < L.nx && j < L.ny) {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, L.nz);
+        const int nx = L.nx, ny = L.ny, nz = L.nz, nxny = L.nxny;
+        auto val = [&](int64_t cc) -> float2 {
+            return FUSE ? df_add_f(lam[cc], delta[cc]) : lam[cc];
+        };
+        const float2 zero = make_float2(0.f, 0.f);
+        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+        float2 l_prev = kb > 0 ? val(c - nxny) : zero;
+        float2 l_cur = val(c);
+        for (int k = kb; k < ke; ++k, c += nxny) {
+            const float2 l_next = (k + 1 < nz) ? val(c + nxny) : zero;
+            const unsigned f = L.flags[c];
+            if (FUSE) lam_new[c] = l_cur;
+            if (f & F_FLUID) {
+                if (!(umt && (f & F_ELEC))) {
+                    const float2 gc = g[c];
+                    float2 r = df_fma(K.diag[c], l_cur, gc);
+                    if (i > 0) r = df_fma(K.f[1][c - 1], val(c - 1), r);
+                    if (i + 1 < nx) r = df_fma(K.f[0][c + 1], val(c + 1), r);
+                    if (j > 0) r = df_fma(K.f[3][c - nx], val(c - nx), r);
+                    if (j + 1 < ny) r = df_fma(K.f[2][c + nx], val(c + nx), r);
+                    if (k > 0) r = df_fma(K.f[5][c - nxny], l_prev, r);
+                    if (k + 1 < nz) r = df_fma(K.f[4][c + nxny], l_next, r);
+                    r_out[c] = r.x;
+                    const float q = r.x * r.x;
+                    if (isfinite(q)) {
+                        sum2 += q;
+                        vmax = fmaxf(vmax, fabsf(r.x));
+                    } else {
+                        ++bad;
+                    }
+                    sumg += gc.x * gc.x;
+                } else {
+                    r_out[c] = 0.f;
+                }
+            }
+            l_prev = l_cur;
+            l_cur = l_next;
+        }
+    }
+    double acc[NRED] = {(double)sum2, (double)sumg, 0.0, 0.0, 0.0, 0.0, (double)bad,
+                        (double)vmax};
     const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
                         ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
     block_reduce_store(acc, partials + bid * NRED);
