@@ -1135,12 +1135,14 @@ __global__ void join64_kernel(const float2* __restrict__ in, double* __restrict_
     }
 }
 
+// (Latency bound: four blocks per SM and the z-march unrolled by two keep more loads in
+// flight.)
 // The defect RHS(s [+ delta]) = b + L (s [+ delta]) at every unknown cell, written as the
 // FP32 forcing (its high part), with the reductions the iteration needs: 0 sum RHS^2,
 // 6 count of non-finite values, 7 max |RHS| (slots 1-5 stay 0). FUSE: the state is
 // s + delta, written to s_new (every cell).
 template <bool FUSE>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 4)
 check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __restrict__ delta,
                 float2* __restrict__ s_new, float* __restrict__ r_out,
                 double* __restrict__ partials, int umt, int kchunk) {
@@ -1161,6 +1163,7 @@ check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __r
         int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
         float2 s_prev = kb > 0 ? val(c - nxny) : zero;
         float2 s_cur = val(c);
+#pragma unroll 2
         for (int k = kb; k < ke; ++k, c += nxny) {
             const float2 s_next = (k + 1 < L.nz) ? val(c + nxny) : zero;
             const unsigned f = L.flags[c];
@@ -1201,7 +1204,7 @@ check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __r
 // FP32 forcing; reductions 0 sum r^2, 1 sum g^2, 6 non-finite count, 7 max |r| over unknown
 // cells. FUSE: lam + delta is the state, written to lam_new (every cell).
 template <bool FUSE>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 4)
 check_df_adjoint_kernel(Lattice L, L2F K, const float2* __restrict__ lam,
                         const float* __restrict__ delta, float2* __restrict__ lam_new,
                         const float2* __restrict__ g, float* __restrict__ r_out,
@@ -1221,6 +1224,7 @@ check_df_adjoint_kernel(Lattice L, L2F K, const float2* __restrict__ lam,
         int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
         float2 l_prev = kb > 0 ? val(c - nxny) : zero;
         float2 l_cur = val(c);
+#pragma unroll 2
         for (int k = kb; k < ke; ++k, c += nxny) {
             const float2 l_next = (k + 1 < nz) ? val(c + nxny) : zero;
             const unsigned f = L.flags[c];
