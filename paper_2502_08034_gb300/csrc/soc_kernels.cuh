@@ -1565,92 +1565,9 @@ __global__ void set_state_kernel(const uint8_t* __restrict__ flags, const double
 // lam <- lam + dt_c (L^T lam + g) uses the same dt_c as the forward one (L and L^T
 // share their diagonal). Pinned U_mt cells are not unknowns: lam = 0 there.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ double adjoint_rhs(const Coef<double>& C, const double* tB, double lc,
-                                              double lxm, double lxp, double lym, double lyp,
-                                              double lzm, double lzp, double uL, double uH,
-                                              double vL, double vH, double wL, double wH,
-                                              bool inlet, bool outlet, int nw, double mult) {
-    double a = 0.0;
-    if (positive(uH)) a += uH * (lxp - lc);
-    if (positive(-uL)) a -= uL * (lxm - lc);
-    if (positive(vH)) a += vH * (lyp - lc);
-    if (positive(-vL)) a -= vL * (lym - lc);
-    if (positive(wH)) a += wH * ((outlet ? 0.0 : lzp) - lc);
-    if (positive(-wL)) a -= wL * (lzm - lc);
-    const double zmd = inlet ? lc : lzm;
-    const double nsum = ((lxm + lxp) + (lym + lyp)) + (zmd + lzp);
-    double d = C.Dh * nsum - (6.0 * C.Dh) * lc;
-    if (inlet) d -= C.gDh * lc;
-    return (a + d) - mult * tB[nw] * lc;
-}
-
-// MODE 0: sweep  lam_out = lam + dt (L^T lam + g)
-// MODE 1: check  reductions of r = L^T lam + g over unknown cells:
-//                0 sum r^2, 1 sum g^2, 6 non-finite count, 7 max |r|
-template <int MODE>
-__global__ void __launch_bounds__(BX * BY)
-adjoint_kernel(Lattice L, Coef<double> C, const double* __restrict__ lam,
-               double* __restrict__ lam_out, const double* __restrict__ g,
-               double* __restrict__ partials, int kchunk) {
-    RFB_LOAD_TABLES(double, C)
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    double acc[NRED];
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
-    if (i < L.nx && j < L.ny) {
-        const int kb = blockIdx.z * kchunk;
-        const int ke = min(kb + kchunk, L.nz);
-        const int nx = L.nx, nxny = L.nxny;
-        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
-        double l_prev = kb > 0 ? lam[c - nxny] : 0.0;
-        double l_cur = lam[c];
-        double wL = C.w[c];
-        for (int k = kb; k < ke; ++k, c += nxny) {
-            const bool outlet = (k == L.nz - 1);
-            double l_next = outlet ? 0.0 : lam[c + nxny];
-            double wH = C.w[c + nxny];
-            const unsigned f = L.flags[c];
-            if ((f & F_FLUID) && !(C.umt && (f & F_ELEC))) {
-                double lxm = (f & F_XM) ? lam[c - 1] : l_cur;
-                double lxp = (f & F_XP) ? lam[c + 1] : l_cur;
-                double lym = (f & F_YM) ? lam[c - nx] : l_cur;
-                double lyp = (f & F_YP) ? lam[c + nx] : l_cur;
-                double lzm = (f & F_ZM) ? l_prev : l_cur;
-                double lzp = (f & F_ZP) ? l_next : l_cur;
-                double uL = C.u[c];
-                double uH = (i + 1 < nx) ? C.u[c + 1] : 0.0;
-                double vL = C.v[c];
-                double vH = (j + 1 < L.ny) ? C.v[c + nx] : 0.0;
-                const int nw = n_wall_of(f, i, j, k, nx, L.ny, L.nz);
-                const double mult = C.m ? C.m[c] : 1.0;
-                const double r = adjoint_rhs(C, tB, l_cur, lxm, lxp, lym, lyp, lzm, lzp, uL,
-                                             uH, vL, vH, wL, wH, k == 0, outlet, nw, mult) +
-                                 g[c];
-                if (MODE == 0) {
-                    const double dt = C.dtc ? (double)C.dtc[c] : C.dt;
-                    lam_out[c] = l_cur + dt * r;
-                } else {
-                    if (isfinite(r)) {
-                        acc[0] += r * r;
-                        acc[7] = fmax(acc[7], fabs(r));
-                    } else {
-                        acc[6] += 1.0;
-                    }
-                    acc[1] += g[c] * g[c];
-                }
-            }
-            l_prev = l_cur;
-            l_cur = l_next;
-            wL = wH;
-        }
-    }
-    if (MODE == 1) {
-        const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
-                            ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-        block_reduce_store(acc, partials + bid * NRED);
-    }
-}
+// The FP64 adjoint sweeps and checks are adjoint64c_kernel (the transpose gathered from
+// the assembled operator); the mixed-precision ones sweep32v_kernel<*, true> and
+// check_df_adjoint_kernel.
 
 // g~ = dJ/ds / jscale on unknown fluid cells (0 elsewhere):
 //   OBJ 0 (I_tot, U): m_c n_wall kR R~'(s_c)/K with kR = -k0 B / h (affine law, R~' = -B)
