@@ -299,6 +299,27 @@ void check(rfb_soc_handle* h, const OpPoint& op, bool umt) {
     reduce_readback(h, 0);
 }
 
+// FP64 check that also writes the FP32 forcing (mixed precision near the double-float
+// floor); fuse: the state is s + delta, written to the other buffer.
+void check_forcing64(rfb_soc_handle* h, const OpPoint& op, bool umt, bool fuse) {
+    double** buf = umt ? h->d_t : h->d_s;
+    int& cur = umt ? h->t_cur : h->s_cur;
+    ensure_L64(h, op);
+    const Coef<double> C = make_coef<double>(h, op, false, false);
+    if (fuse) {
+        check64c_kernel<true, true><<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), C, h->K, buf[cur], h->d_delta[0], buf[cur ^ 1], h->d_r32, h->d_partials,
+            h->kchunk);
+        LAUNCHED(h);
+        cur ^= 1;
+    } else {
+        check64c_kernel<false, true><<<h->grid, h->block, 0, h->stream>>>(
+            lattice(h), C, h->K, buf[cur], nullptr, nullptr, h->d_r32, h->d_partials, h->kchunk);
+        LAUNCHED(h);
+    }
+    reduce_readback(h, 0);
+}
+
 // ---- mixed-precision checks in double-float (check_df_kernel)
 
 void ensure_L2F(rfb_soc_handle* h, const OpPoint& op) {
@@ -695,6 +716,10 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
     fill_result(h, op, &r, n_unknown);
     // mixed: the FP64 state equals the double-float one and r holds its FP64 check
     bool joined = !mixed;
+    // mixed: defects in double-float until the residual nears that arithmetic's floor,
+    // about tau 2^-47 (8 terms of size <= max d_c, s <= 1); FP64 defects after that
+    bool df = mixed;
+    const double df_floor = mixed ? r.tau * std::ldexp(1.0, -44) * (op.cfl / op.dt) : 0.0;
     auto join_and_check = [&]() {
         CK(h, cudaEventRecord(h->ev[1], h->stream));
         df_end(h, umt);
@@ -734,6 +759,22 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
             join_and_check();   // the double-float defect met tol: confirm it in FP64
             continue;
         }
+        if (df && fixed_sweeps < 0 && r.residual <= 10.0 * df_floor) {
+            // tol lies below what double-float defects resolve: continue with FP64 ones
+            df_end(h, umt);
+            CK(h, cudaEventRecord(h->ev[1], h->stream));
+            check_forcing64(h, op, umt, false);
+            CK(h, cudaEventRecord(h->ev[2], h->stream));
+            CK(h, cudaEventSynchronize(h->ev[2]));
+            float ms_c = 0.f;
+            CK(h, cudaEventElapsedTime(&ms_c, h->ev[1], h->ev[2]));
+            check_ms += ms_c;
+            ++r.checks;
+            fill_result(h, op, &r, n_unknown);
+            df = false;
+            joined = true;
+            continue;
+        }
         if (done >= limit) {
             st = fixed_sweeps >= 0 ? RFB_OK : RFB_ERR_NOT_CONVERGED;
             break;
@@ -750,9 +791,11 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         if (mixed) sweeps32(h, op, n, use_tb);
         else sweeps64(h, op, umt, n);
         CK(h, cudaEventRecord(h->ev[1], h->stream));
-        if (mixed) {
+        if (df) {
             check_df(h, op, umt, true);
             joined = false;
+        } else if (mixed) {
+            check_forcing64(h, op, umt, true);   // FP64 defects (below the df floor)
         } else {
             check(h, op, umt);
         }

@@ -59,4 +59,15 @@ def test_create_rejects_bad_dims_before_touching_a_device(lib):
     st = lib.rfb_soc_create(dims, 1e-6, p, p, p, p, 4e-10, ctypes.byref(kin), None, 0, None,
                             ctypes.byref(h))
     assert st == rfb.RFB_ERR_INVALID_ARG
+    # largest lattice: N + nx*ny must stay below 2^31 (32-bit cell indices in the kernels)
+    kin = rfb.Kinetics(1e-7, 0.5, 2, 0, 298.0, 20.0)
+    dims = (ctypes.c_int32 * 3)(1024, 1024, 2048)
+    st = lib.rfb_soc_create(dims, 1e-6, p, p, p, p, 4e-10, ctypes.byref(kin), None, 0, None,
+                            ctypes.byref(h))
+    assert st == rfb.RFB_ERR_INVALID_ARG and b"too large" in lib.rfb_soc_last_error(None)
+    kin = rfb.Kinetics(1e-7, 0.5, 2, 7, 298.0, 20.0)     # unknown kinetics mode
+    dims = (ctypes.c_int32 * 3)(4, 4, 4)
+    st = lib.rfb_soc_create(dims, 1e-6, p, p, p, p, 4e-10, ctypes.byref(kin), None, 0, None,
+                            ctypes.byref(h))
+    assert st == rfb.RFB_ERR_INVALID_ARG
     assert lib.rfb_soc_destroy(None) == 0
