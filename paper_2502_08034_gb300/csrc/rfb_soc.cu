@@ -1014,44 +1014,32 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
                 scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(dm, h->d_m, h->d_m32, 1.0, N);
                 LAUNCHED(h);
             }
+            // counts and inlet / outlet sums on the device (fixed-order reduction)
+            const int sblocks = (int)std::min<int64_t>(h->nblocks, 2048);
+            stats_kernel<<<sblocks, 256, 0, h->stream>>>(h->d_flags, h->d_w, h->d_m, N, nxny,
+                                                         h->d_partials);
+            LAUNCHED(h);
+            finalize_kernel<<<1, 256, 0, h->stream>>>(h->d_partials, sblocks, h->d_red, 0);
+            LAUNCHED(h);
             unsigned long long herr[4];
             CK(h, cudaMemcpyAsync(herr, h->d_err, sizeof herr, cudaMemcpyDeviceToHost,
                                   h->stream));
-            std::vector<uint8_t> flags(N);
-            CK(h, cudaMemcpyAsync(flags.data(), h->d_flags, N, cudaMemcpyDeviceToHost,
-                                  h->stream));
-            std::vector<double> w_in(nxny), w_out(nxny);
-            CK(h, cudaMemcpyAsync(w_in.data(), h->d_w, nxny * 8, cudaMemcpyDeviceToHost,
-                                  h->stream));
-            CK(h, cudaMemcpyAsync(w_out.data(), h->d_w + N, nxny * 8, cudaMemcpyDeviceToHost,
-                                  h->stream));
-            std::vector<double> mh;
-            if (area_mult) {
-                mh.resize(N);
-                CK(h, cudaMemcpyAsync(mh.data(), h->d_m, N * 8, cudaMemcpyDeviceToHost,
-                                      h->stream));
-            }
+            CK(h, cudaMemcpyAsync(h->h_red, h->d_red, NRED * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
             for (void* p : tmp) cudaFree(p);
             tmp.clear();
             if (herr[0]) { set_err(nullptr, "%llu non-finite face velocities", herr[0]); throw Fail{RFB_ERR_INVALID_ARG}; }
             if (herr[1]) { set_err(nullptr, "%llu nonzero velocities on side-wall or fiber faces", herr[1]); throw Fail{RFB_ERR_INVALID_ARG}; }
             if (herr[2]) { set_err(nullptr, "%llu negative inlet/outlet velocities", herr[2]); throw Fail{RFB_ERR_INVALID_ARG}; }
-            for (int64_t c = 0; c < N; ++c) {
-                if (flags[c] & F_FLUID) {
-                    ++h->n_fluid;
-                    if (flags[c] & F_ELEC) ++h->n_elec;
-                }
+            h->n_fluid = (int64_t)h->h_red[0];
+            h->n_elec = (int64_t)h->h_red[1];
+            h->sum_w_in = h->h_red[2];
+            h->sum_w_out = h->h_red[3];
+            if (h->h_red[4] > 0) {
+                set_err(nullptr, "area_mult must be finite and > 0 (%.0f cells are not)", h->h_red[4]);
+                throw Fail{RFB_ERR_INVALID_ARG};
             }
-            for (int64_t q = 0; q < nxny; ++q) {
-                if (flags[q] & F_FLUID) h->sum_w_in += w_in[q];
-                if (flags[N - nxny + q] & F_FLUID) h->sum_w_out += w_out[q];
-            }
-            for (size_t c = 0; c < mh.size(); ++c)
-                if (!(mh[c] > 0 && std::isfinite(mh[c]))) {
-                    set_err(nullptr, "area_mult must be finite and > 0 (cell %zu)", c);
-                    throw Fail{RFB_ERR_INVALID_ARG};
-                }
             if (h->n_fluid == 0) { set_err(nullptr, "no fluid cells"); throw Fail{RFB_ERR_INVALID_ARG}; }
         } catch (...) {
             for (void* p : tmp) cudaFree(p);
@@ -1397,34 +1385,39 @@ rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kin
     if (g) return g;
     if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
     try {
-        if (!h->d_m) {
+        // validate on the device (count of entries that are not finite and > 0) before
+        // anything is replaced; NULL restores 1 everywhere
+        const double* src = nullptr;
+        double* tmp = nullptr;
+        if (m && kind == RFB_MEM_HOST) {
+            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
+            CK(h, cudaMemcpyAsync(tmp, m, h->N * 8, cudaMemcpyHostToDevice, h->stream));
+            src = tmp;
+        } else if (m) {
+            src = m;
+        } else {
+            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
+            fill_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(tmp, 1.0, h->N);
+            LAUNCHED(h);
+            src = tmp;
+        }
+        const int sblocks = (int)std::min<int64_t>(h->nblocks, 2048);
+        stats_kernel<<<sblocks, 256, 0, h->stream>>>(h->d_flags, h->d_w, src, h->N, h->nxny,
+                                                     h->d_partials);
+        LAUNCHED(h);
+        finalize_kernel<<<1, 256, 0, h->stream>>>(h->d_partials, sblocks, h->d_red, 0);
+        LAUNCHED(h);
+        CK(h, cudaMemcpyAsync(h->h_red, h->d_red, NRED * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (h->h_red[4] > 0) {
+            if (tmp) cudaFree(tmp);
+            set_err(h, "area_mult must be finite and > 0 (%.0f cells are not)", h->h_red[4]);
+            return RFB_ERR_INVALID_ARG;
+        }
+        if (!h->d_m) {   // allocated only once the values are known to be valid
             dalloc(h, &h->d_m, h->N);
             dalloc(h, &h->d_m32, h->N);
-        }
-        double* src = nullptr;
-        double* tmp = nullptr;
-        std::vector<double> host;
-        if (m) {
-            if (kind == RFB_MEM_HOST) {
-                host.assign(m, m + h->N);
-            } else {
-                host.resize(h->N);
-                CK(h, cudaMemcpyAsync(host.data(), m, h->N * 8, cudaMemcpyDeviceToHost, h->stream));
-                CK(h, cudaStreamSynchronize(h->stream));
-            }
-            for (int64_t c = 0; c < h->N; ++c)
-                if (!(host[c] > 0 && std::isfinite(host[c]))) {
-                    set_err(h, "area_mult must be finite and > 0 (cell %lld)", (long long)c);
-                    return RFB_ERR_INVALID_ARG;
-                }
-            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
-            CK(h, cudaMemcpyAsync(tmp, host.data(), h->N * 8, cudaMemcpyHostToDevice, h->stream));
-            src = tmp;
-        } else {
-            host.assign(h->N, 1.0);
-            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
-            CK(h, cudaMemcpyAsync(tmp, host.data(), h->N * 8, cudaMemcpyHostToDevice, h->stream));
-            src = tmp;
         }
         scale_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(src, h->d_m, h->d_m32, 1.0, h->N);
         LAUNCHED(h);

@@ -1414,6 +1414,40 @@ diag_kernel(Lattice L, Coef<double> C, double cfl, float* __restrict__ dtc,
     if (tid == 0) partials[bid * NRED + 0] = bmin;
 }
 
+__global__ void fill_kernel(double* __restrict__ a, double v, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        a[q] = v;
+}
+
+// Lattice statistics at creation, as per-block partials (fixed order with
+// finalize_kernel): 0 fluid cells, 1 electrode cells, 2 sum of W over fluid inlet faces,
+// 3 sum of W over fluid outlet faces, 4 count of area multipliers that are not finite
+// and > 0 (m nullable). w: cell-aligned low-face W, N + nx*ny entries.
+__global__ void __launch_bounds__(256)
+stats_kernel(const uint8_t* __restrict__ flags, const double* __restrict__ w,
+             const double* __restrict__ m, int64_t N, int64_t nxny,
+             double* __restrict__ partials) {
+    double acc[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) acc[q] = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned f = flags[c];
+        if (f & F_FLUID) {
+            acc[0] += 1.0;
+            if (f & F_ELEC) acc[1] += 1.0;
+            if (c < nxny) acc[2] += w[c];
+            if (c >= N - nxny) acc[3] += w[c + nxny];
+        }
+        if (m) {
+            const double x = m[c];
+            if (!(x > 0.0 && isfinite(x))) acc[4] += 1.0;
+        }
+    }
+    block_reduce_store(acc, partials + (int64_t)blockIdx.x * NRED);
+}
+
 // Sum (slots 0..6) / max (slot 7) of the per-block partials, in a fixed order.
 // min_slot0: slot 0 is reduced with min instead of a sum (diag_kernel).
 __global__ void __launch_bounds__(256)
