@@ -107,7 +107,8 @@ typedef struct rfb_solve_opts {
     double velocity_scale;  /* beta >= 0: every face velocity is multiplied by it (1) */
     int64_t max_sweeps;     /* give up after this many sweeps (0 = 50,000,000) */
     int32_t fp32_kernel;    /* RFB_PREC_MIXED only: 0 = chosen by timing the kernels on
-                               the lattice (once per handle), 1 = one sweep per launch,
+                               the lattice (once per lattice shape, dt mode
+                               and device in a process), 1 = one sweep per launch,
                                2 = two sweeps per pass (TMA-staged, temporally blocked;
                                needs nx % 16 == 0 and no area multiplier), launch shape
                                chosen by timing; 3 = two-sweep passes in a persistent

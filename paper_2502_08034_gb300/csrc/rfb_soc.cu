@@ -14,8 +14,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 using namespace rfb;
@@ -595,11 +597,40 @@ void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C
     }
 }
 
+// Choices of the FP32-kernel autotuner, kept for the process by lattice shape (dims,
+// area multipliers or not, dt mode, device): a new handle on the same shape reuses them.
+struct TuneKey {
+    int nx, ny, nz, mult, local, device;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nx, ny, nz, mult, local, device) <
+               std::tie(o.nx, o.ny, o.nz, o.mult, o.local, o.device);
+    }
+};
+struct TuneVal {
+    int tb_mode, tb_variant;
+    double plain_ms, tb_ms;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
+std::mutex g_tune_mu;
+
 // Project-written autotuner for one lattice: time 8 plain sweeps and 8 sweeps of each
 // launch shape of the two-sweep pass (CUDA events, on the current forcing) and keep the
 // fastest (tb_only: choose between the two-sweep shapes only).
 void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false) {
     if (!tb_eligible(h)) { h->tb_mode = 0; return; }
+    const TuneKey key{h->nx, h->ny, h->nz, h->d_m32 != nullptr,
+                      op.dt_mode == RFB_DT_LOCAL, h->device};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && (tb_only || it->second.tb_mode >= 0)) {
+            h->tb_variant = it->second.tb_variant;
+            if (!tb_only) h->tb_mode = it->second.tb_mode;
+            h->tb_tuned_plain_ms = it->second.plain_ms;
+            h->tb_tuned_tb_ms = it->second.tb_ms;
+            return;
+        }
+    }
     float ms[3] = {INFINITY, INFINITY, INFINITY};   // plain, shape 0, shape 1
     for (int cand = tb_only ? 1 : 0; cand < 3; ++cand) {
         if (cand > 0) h->tb_variant = cand - 1;
@@ -615,6 +646,9 @@ void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false
     h->tb_tuned_plain_ms = ms[0] / 8;
     h->tb_tuned_tb_ms = tb / 8;
     if (!tb_only) h->tb_mode = tb < ms[0] ? 1 : 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = TuneVal{tb_only ? -1 : h->tb_mode, h->tb_variant, h->tb_tuned_plain_ms,
+                                h->tb_tuned_tb_ms};
 }
 
 void init_state(rfb_soc_handle* h, bool umt, double s_in) {
