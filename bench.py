@@ -592,6 +592,9 @@ def main():
     achieved = SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
     effective = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
     traffic = kernel_traffic(N, kname)
+    # measured DRAM bytes per launch over the launch time: the kernel's % of HBM peak
+    launch_s = (sweep_ms / 1e3) / max(1, kernel_launches)
+    dram_frac = traffic / launch_s / 1e9 / peak if traffic else None
     last = results[-1]
 
     extras = {}
@@ -677,6 +680,7 @@ def main():
                             "autotuner_ms_per_sweep": {"plain": tuned_plain_ms,
                                                        "blocked": tuned_blocked_ms},
                             "bytes_per_cell_per_launch": SWEEP_BYTES_PER_CELL,
+                            "dram_frac": dram_frac, "nominal_peak_gbs": 7900.0,
                             "peak_kind": peak_kind},
                "effective_bandwidth": {"value": effective, "unit": "GB/s",
                                        "frac": effective / peak,
