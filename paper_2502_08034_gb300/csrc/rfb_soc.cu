@@ -49,6 +49,8 @@ struct rfb_soc_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
 
+    unsigned char* d_arena = nullptr;   // one allocation holding the buffers below up to
+                                        // d_partials (see rfb_soc_create)
     uint8_t* d_flags = nullptr;
     uint8_t* d_mask32 = nullptr;   // mask byte of the FP32 kernels
     double *d_u = nullptr, *d_v = nullptr, *d_w = nullptr;      // m/s, cell aligned
@@ -881,12 +883,10 @@ rfb_status guard(rfb_soc_handle* h) {
 }
 
 void free_all(rfb_soc_handle* h) {
-    void* ptrs[] = {h->d_flags, h->d_mask32, h->d_u,  h->d_v,   h->d_w,     h->d_us,   h->d_vs,
-                    h->d_ws,    h->d_u32, h->d_v32, h->d_w32,  h->d_m,    h->d_m32,
-                    h->d_s[0],  h->d_s[1], h->d_t[0], h->d_t[1], h->d_delta[0],
-                    h->d_delta[1], h->d_r32, h->d_dtc, h->d_partials, h->d_red, h->d_err,
-                    h->d_lam[0], h->d_lam[1], h->d_g, h->d_grad, h->d_L64, h->d_L2F, h->d_eta, h->d_elec,
-                    h->d_sdf[0], h->d_sdf[1], h->d_gdf};
+    // the arena holds flags .. partials; the rest are allocated on first use
+    void* ptrs[] = {h->d_arena, h->d_m,    h->d_m32,  h->d_lam[0], h->d_lam[1], h->d_g,
+                    h->d_grad,  h->d_L64,  h->d_L2F,  h->d_eta,    h->d_elec,   h->d_sdf[0],
+                    h->d_sdf[1], h->d_gdf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -979,18 +979,6 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         const int64_t nxny = h->nxny;
         const int64_t nU = (int64_t)(nx + 1) * ny * nz, nV = (int64_t)nx * (ny + 1) * nz,
                       nW = nxny * (nz + 1);
-        dalloc(h, &h->d_flags, N);
-        dalloc(h, &h->d_mask32, N);
-        dalloc(h, &h->d_u, N); dalloc(h, &h->d_v, N); dalloc(h, &h->d_w, N + nxny);
-        dalloc(h, &h->d_us, N); dalloc(h, &h->d_vs, N); dalloc(h, &h->d_ws, N + nxny);
-        dalloc(h, &h->d_u32, N); dalloc(h, &h->d_v32, N); dalloc(h, &h->d_w32, N + nxny);
-        for (int q = 0; q < 2; ++q) {
-            dalloc(h, &h->d_s[q], N); dalloc(h, &h->d_t[q], N); dalloc(h, &h->d_delta[q], N);
-        }
-        dalloc(h, &h->d_r32, N); dalloc(h, &h->d_dtc, N);
-        dalloc(h, &h->d_err, 4);
-        CK(h, cudaMallocHost((void**)&h->h_red, NRED * sizeof(double)));
-        dalloc(h, &h->d_red, NRED);
         // launch geometry: 32 x 8 column tiles, z chunks so that there are >= ~8 blocks
         // per SM
         h->block = dim3(BX, BY, 1);
@@ -1008,7 +996,35 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
             h->vkchunk = vk;
             h->vgrid = dim3(vx, vy, (nz + vk - 1) / vk);
         }
-        dalloc(h, &h->d_partials, (size_t)h->nblocks * NRED);
+        // every buffer a handle always needs, carved from one device allocation (one
+        // cudaMalloc / cudaFree per handle instead of ~25); sub-buffers 256-byte aligned
+        {
+            struct Part { void** p; size_t bytes; };
+            const size_t n8 = (size_t)N * 8, n4 = (size_t)N * 4, nw8 = (size_t)(N + nxny) * 8,
+                         nw4 = (size_t)(N + nxny) * 4;
+            const Part parts[] = {
+                {(void**)&h->d_flags, (size_t)N}, {(void**)&h->d_mask32, (size_t)N},
+                {(void**)&h->d_u, n8}, {(void**)&h->d_v, n8}, {(void**)&h->d_w, nw8},
+                {(void**)&h->d_us, n8}, {(void**)&h->d_vs, n8}, {(void**)&h->d_ws, nw8},
+                {(void**)&h->d_u32, n4}, {(void**)&h->d_v32, n4}, {(void**)&h->d_w32, nw4},
+                {(void**)&h->d_s[0], n8}, {(void**)&h->d_s[1], n8},
+                {(void**)&h->d_t[0], n8}, {(void**)&h->d_t[1], n8},
+                {(void**)&h->d_delta[0], n4}, {(void**)&h->d_delta[1], n4},
+                {(void**)&h->d_r32, n4}, {(void**)&h->d_dtc, n4},
+                {(void**)&h->d_err, 4 * sizeof(unsigned long long)},
+                {(void**)&h->d_red, NRED * sizeof(double)},
+                {(void**)&h->d_partials, (size_t)h->nblocks * NRED * sizeof(double)}};
+            auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+            size_t total = 0;
+            for (const Part& q : parts) total += up(q.bytes);
+            CK(h, cudaMalloc((void**)&h->d_arena, total));
+            size_t off = 0;
+            for (const Part& q : parts) {
+                *q.p = h->d_arena + off;
+                off += up(q.bytes);
+            }
+        }
+        CK(h, cudaMallocHost((void**)&h->h_red, NRED * sizeof(double)));
         for (cudaEvent_t& e : h->ev) CK(h, cudaEventCreate(&e));
 
         // staging: the inputs on the device (copied when they are host arrays)
