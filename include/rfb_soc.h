@@ -57,7 +57,10 @@ typedef enum rfb_mem_kind { RFB_MEM_HOST = 0, RFB_MEM_DEVICE = 1 } rfb_mem_kind;
 
 typedef enum rfb_precision {
     RFB_PREC_FP64 = 0,   /* FP64 sweeps and reductions */
-    RFB_PREC_MIXED = 1   /* FP32 correction sweeps, FP64 defect / reductions / state */
+    RFB_PREC_MIXED = 1   /* FP32 correction sweeps; defects in double-float arithmetic
+                            (FP32 pairs, ~48 bits) with FP64 reductions, switching to FP64
+                            defects near that arithmetic's floor; FP64 state and a final
+                            FP64 check that gives the returned residual and outputs */
 } rfb_precision;
 
 typedef enum rfb_inlet_bc { RFB_INLET_FACE = 0, RFB_INLET_GHOST = 1 } rfb_inlet_bc;
@@ -193,6 +196,10 @@ rfb_status rfb_soc_set_stream(rfb_soc_handle* h, void* cuda_stream);
  *   res    nullable; filled on return (also on NOT_CONVERGED / NONFINITE)
  * Starts from the current state if one is set (previous solve, rfb_soc_set_state or
  * rfb_soc_upsample), otherwise from s = s_in on every fluid cell.
+ * RFB_PREC_MIXED: cycles of opts.check_every (default 200) FP32 correction sweeps
+ * delta <- delta + dt (L delta + r) followed by a defect check that adds delta to the
+ * state and refreshes r; res->residual and the outputs come from an FP64 check of the
+ * returned state. Kinetics mode 1 requires RFB_PREC_FP64.
  * Returns RFB_OK, RFB_ERR_NOT_CONVERGED (state valid) or RFB_ERR_NONFINITE.
  */
 rfb_status rfb_soc_solve(rfb_soc_handle* h, double s_in, double eta, double tol,
