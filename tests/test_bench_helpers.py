@@ -1,0 +1,44 @@
+"""Host-side helpers of bench.py (no GPU): the nvidia-smi clock summary that decides which
+throttle reasons a bench line reports."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _clocks_from(lines):
+    c = bench.Clocks(0)
+    import tempfile
+    fd, c.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    return c.summary()
+
+
+def test_clock_summary_median_max_and_reasons():
+    rows = [
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = _clocks_from(rows)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_flags_thermal_and_hw_slowdown():
+    rows = [
+        "0, 1500, 2070, 1300.0, 0x0000000000000048, Active, Not Active, Active, Not Active",
+        "0, [N/A], 2070, 1300.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = _clocks_from(rows)
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert s["sm_mhz"] == 1500.0 and s["samples"] == 2
+
+
+def test_clock_summary_without_nvidia_smi_output():
+    s = _clocks_from([])
+    assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
