@@ -90,9 +90,15 @@ def peak_hbm():
 
 
 def kernel_source_digest():
+    """Digest of the kernel sources' code (comments and whitespace removed, so that a
+    comment edit does not void the traffic figures taken on the same code)."""
+    import re
     h = hashlib.sha256()
     for name in ("soc_kernels.cuh", "sweep_tb.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

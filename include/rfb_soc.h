@@ -250,7 +250,7 @@ rfb_status rfb_soc_umt(rfb_soc_handle* h, double tol, const rfb_solve_opts* opts
                        double* umt, rfb_solve_result* res);
 
 /*
- * Iterative upsampling (Sec. III.A, "iterative upsampling"; the paper solves coarse to
+ * Iterative upsampling (Sec. III.A; the paper solves coarse to
  * steady state and initialises the refined problem from it by coarse-to-fine
  * interpolation). Sets fine's state to the 2x prolongation of coarse's state:
  * injection s_f(i,j,k) = s_c(i/2, j/2, k/2) for fine fluid cells with a fluid parent
@@ -374,7 +374,7 @@ rfb_status rfb_soc_info(const rfb_soc_handle* h, int64_t* n_cells, int64_t* n_fl
 int64_t rfb_soc_kernel_launches(const rfb_soc_handle* h);
 
 /*
- * Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def,
+ * Nernst model (Sec. II.D, Eqs. nernst-eta-inst-def,
  * nernst-model-eta-update, nernst-model-s-update; explicit form Algorithm 8): the steady
  * state of the SBV problem (the same as rfb_soc_solve's) reached by treating electrode
  * cells (fluid cells with k0 m n_wall / dx > 0) as Dirichlet cells s = sigma(V~ - eta~)

@@ -11,9 +11,9 @@ What it computes, in FP64, following the paper (arXiv 2502.08034):
   (Eq. Vart-def); s_eq = sigma(V~) (Eq. seq-from-Var); affine rate law
   R~(s) = e^{alpha V~} (1 - (1 + e^{-V~}) s) (Eq. rate-from-soc-gen).
 * The steady form of Eq. nernst-planck-soc on a voxel lattice, assembled face by face
-  as explicit sparse matrices, the way the paper's explicit proof of concept builds its
-  advection and diffusion operators (Sec. III.C, "explicit sparse matrix
-  representations"): first-order upwind advection by the given face velocities,
+  as explicit sparse matrices, the way the paper's explicit proof of concept holds its
+  advection and diffusion operators as assembled sparse matrices (Sec. III.C):
+  first-order upwind advection by the given face velocities,
   7-point diffusion, a Dirichlet inlet, zero-gradient outlet, no flux through side walls
   and fiber faces, and the Butler-Volmer source k0 a_c R~(s_c) with a_c = m_c n_wall/h
   (n_wall = number of fiber 6-neighbours; the paper's a = A/V of a cut cell).
@@ -574,7 +574,7 @@ def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
 
 
 # --------------------------------------------------------------------------------------
-# Iterative upsampling (Sec. III.A, "iterative upsampling")
+# Iterative upsampling (Sec. III.A)
 # --------------------------------------------------------------------------------------
 
 def prolong(s_coarse: np.ndarray, solid_coarse: np.ndarray, solid_fine: np.ndarray,
@@ -606,7 +606,7 @@ def prolong(s_coarse: np.ndarray, solid_coarse: np.ndarray, solid_fine: np.ndarr
 
 
 # --------------------------------------------------------------------------------------
-# Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def, nernst-model-eta-update,
+# Nernst model (Sec. II.D, Eqs. nernst-eta-inst-def, nernst-model-eta-update,
 # nernst-model-s-update; explicit form Algorithm 8)
 # --------------------------------------------------------------------------------------
 

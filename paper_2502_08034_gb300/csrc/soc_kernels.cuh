@@ -632,7 +632,7 @@ sweep64c_kernel(Lattice L, L64 K, const float* __restrict__ dtc, double dt_globa
 }
 
 // ---------------------------------------------------------------------------------
-// Nernst model (Sec. II.D "Nernst model", Eqs. nernst-eta-inst-def,
+// Nernst model (Sec. II.D, Eqs. nernst-eta-inst-def,
 // nernst-model-eta-update, nernst-model-s-update; Algorithm 8), FP64 on the assembled
 // operator of the affine (SBV) problem. Electrode cells (k_c = m_c k0 n_wall / h > 0)
 // hold s = sigma(V~ - eta~); their transport rate is T = RHS_SBV(s) - k_c (A - B s) (the
