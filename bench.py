@@ -174,6 +174,26 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def host_cpu():
+    """The host the oracle baseline ran on: logical CPUs and the CPU model (from
+    /proc/cpuinfo: "model name" on x86, implementer / part codes on Arm)."""
+    info = {"nproc": os.cpu_count(), "machine": os.uname().machine, "model": None}
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+        if fields.get("model name"):
+            info["model"] = fields["model name"]
+        elif fields.get("CPU part"):
+            info["model"] = "implementer %s part %s" % (fields.get("CPU implementer"),
+                                                       fields["CPU part"])
+    except OSError:
+        pass
+    return info
+
+
 def oracle_sample(case, n_planes=16, sweeps=40, repeats=1):
     """Time the CPU oracle's explicit FP64 sweeps (Algorithm 7 style, scipy CSR matvec,
     one core) on the first ``n_planes`` z-planes of the workload."""
@@ -222,7 +242,7 @@ def run_reference(args, dims):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "fiber%dx%dx%d_mixed" % dims, "sample": "16 z-planes"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
            "setup_s": setup_s}
@@ -659,7 +679,7 @@ def main():
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "explicit FP64 CSR sweeps (scipy, 1 thread) on the first 16 "
                              "z-planes (%d cells) of the workload, %d sweeps, %.1f s" %
-                             (n_s, sw, sec)}
+                             (n_s, sw, sec), "host": host_cpu()}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

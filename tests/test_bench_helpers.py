@@ -42,3 +42,10 @@ def test_clock_summary_flags_thermal_and_hw_slowdown():
 def test_clock_summary_without_nvidia_smi_output():
     s = _clocks_from([])
     assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_host_cpu_reports_core_count_and_model():
+    h = bench.host_cpu()
+    assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
+    assert isinstance(h["machine"], str) and h["machine"]
+    assert h["model"] is None or isinstance(h["model"], str)
