@@ -100,9 +100,10 @@ def _closed_form_1d(n, a, d, K, g, E_in):
 @pytest.mark.parametrize("D", [4e-10, 0.0, 4e-9])
 @pytest.mark.parametrize("inlet_bc", ["face", "ghost"])
 @pytest.mark.parametrize("k0,m", [(1e-7, 1.0), (1e-6, 0.7), (0.0, 1.0)])
-def test_1d_channel_exact_discrete_closed_form(D, inlet_bc, k0, m):
+@pytest.mark.parametrize("h", [1.25e-6, 5e-6])
+def test_1d_channel_exact_discrete_closed_form(D, inlet_bc, k0, m, h):
     n, w = 40, 0.01
-    solid, U, V, W, h = channel_1d(n, w)
+    solid, U, V, W, _ = channel_1d(n, w, h)
     eta, s_in = -0.08, 0.2
     area = np.full(solid.shape, m)
     p = soc.Problem(solid, U, V, W, h, D, s_in, k0=k0, eta=eta, area_mult=area,
@@ -117,6 +118,46 @@ def test_1d_channel_exact_discrete_closed_form(D, inlet_bc, k0, m):
     assert np.allclose(s - s_star, e, rtol=0, atol=1e-12 * max(abs(s_in - s_star), 0.1))
     if k0 == 0.0:
         assert np.allclose(s, s_in, atol=1e-13)
+
+
+def test_residual_is_tau_times_rms_with_tau_the_residence_time():
+    """Eq. convergence-bv-change on the 1D channel at s = s_in in every fluid cell: the
+    advective and diffusive fluxes cancel (a uniform state, the inlet face at s_in), so
+    RHS_c = k0 a R~(s_in) in each of the n cells, with a = 4/h (four fiber faces); and
+    tau = V_f / Q = n h^3 / (w h^2) = n h / w, the time the flow takes to cross the
+    channel. The residual is then tau k0 (4/h) |R~(s_in)|, up to the rounding of the
+    transport terms that cancel (a few ulps of (w/h + 6 D/h^2) s_in per cell)."""
+    n, w, h, D = 40, 0.01, 1.25e-6, 4e-10
+    solid, U, V, W, _ = channel_1d(n, w, h)
+    for s_in, eta, k0 in ((0.2, -0.08, 1e-6), (0.9, -0.02, 3e-7)):
+        p = soc.Problem(solid, U, V, W, h, D, s_in, k0=k0, eta=eta)
+        op = soc.assemble(p)
+        assert abs(op.tau - n * h / w) <= 1e-15 * n * h / w
+        s = soc.initial_state(op, s_in)
+        r = soc.rhs(op, s)[op.unknown]
+        want = k0 * 4.0 / h * float(soc.rate_bv(s_in, op.kin.Vt))
+        ulp = 8 * np.finfo(np.float64).eps * (w / h + 6 * D / h ** 2) * s_in
+        assert r.size == n and np.max(np.abs(r - want)) <= ulp
+        assert abs(soc.residual(op, s) - n * h / w * abs(want)) <= n * h / w * ulp
+
+
+def test_n_wall_brute_force():
+    """n_wall(c) = number of solid cells among the six face neighbours inside the lattice,
+    counted cell by cell with explicit neighbour offsets on a random mask."""
+    rng = np.random.default_rng(9)
+    solid = (rng.uniform(size=(5, 4, 3)) < 0.45).astype(np.uint8)
+    got = soc.n_wall(solid.astype(bool))
+    nz, ny, nx = solid.shape
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                cnt = 0
+                for dk, dj, di in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                   (0, 0, 1), (0, 0, -1)):
+                    kk, jj, ii = k + dk, j + dj, i + di
+                    if 0 <= kk < nz and 0 <= jj < ny and 0 <= ii < nx and solid[kk, jj, ii]:
+                        cnt += 1
+                assert got[k, j, i] == cnt, (k, j, i)
 
 
 def test_plug_flow_continuum_limit_first_order():
@@ -316,15 +357,27 @@ def test_umt_independent_of_kinetics_and_inlet():
 # ------------------------------------------------------------------ prolongation
 
 def test_prolongation_injection():
+    """Every fine cell of a non-cubic lattice against its parent, cell by cell: fine fluid
+    cells under a fluid parent take the parent's value, a fine fluid cell under a solid
+    parent the mean of the parent's fluid 6-neighbours, fine solid cells 0."""
     rng = np.random.default_rng(3)
-    solid_c = np.zeros((4, 3, 3), dtype=np.uint8)
+    solid_c = np.zeros((4, 3, 5), dtype=np.uint8)
     solid_c[1, 1, 1] = 1
+    solid_c[2, 0, 3] = 1
     sc = rng.uniform(size=solid_c.size) * (solid_c.ravel() == 0)
     solid_f = solid_c.repeat(2, 0).repeat(2, 1).repeat(2, 2).copy()
-    solid_f[2, 2, 2] = 0   # fine fluid cell under the solid coarse parent
+    solid_f[2, 2, 2] = 0   # fine fluid cell under the solid coarse parent (1, 1, 1)
     sf = soc.prolong(sc, solid_c, solid_f, 0.5).reshape(solid_f.shape)
     scr = sc.reshape(solid_c.shape)
-    assert sf[0, 0, 0] == scr[0, 0, 0] and sf[7, 5, 5] == scr[3, 2, 2]
+    nz, ny, nx = solid_f.shape
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                parent = (k // 2, j // 2, i // 2)
+                if solid_f[k, j, i]:
+                    assert sf[k, j, i] == 0.0
+                elif not solid_c[parent]:
+                    assert sf[k, j, i] == scr[parent], (k, j, i)
     nb = [scr[0, 1, 1], scr[2, 1, 1], scr[1, 0, 1], scr[1, 2, 1], scr[1, 1, 0], scr[1, 1, 2]]
     assert abs(sf[2, 2, 2] - np.mean(nb)) < 1e-15
     assert sf[3, 3, 3] == 0.0
