@@ -240,7 +240,10 @@ def run_reference(args, dims):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "fiber%dx%dx%d_mixed" % dims, "sample": "16 z-planes"},
+           "config": {"workload": "fiber%dx%dx%d_mixed" % dims, "dims": list(dims),
+                      "porosity": round(case.porosity, 4), "fiber_d": "U[6,10] cells",
+                      "u_mean_m_s": case.u_mean, "eta_V": case.eta, "s_in": case.s_in,
+                      "tol": args.tol, "sample": "16 z-planes"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample, "host": host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

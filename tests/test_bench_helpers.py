@@ -49,3 +49,22 @@ def test_host_cpu_reports_core_count_and_model():
     assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
     assert isinstance(h["machine"], str) and h["machine"]
     assert h["model"] is None or isinstance(h["model"], str)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle timed on the host) on a small lattice of the
+    same recipe: one JSON line with the keys the benchmark contract names."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--dims", "16,16,32", "--steps", "1", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 1
+    assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["higher_is_better"] is True and line["config"]["workload"] == "fiber16x16x32_mixed"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
