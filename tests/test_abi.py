@@ -71,3 +71,51 @@ def test_create_rejects_bad_dims_before_touching_a_device(lib):
                             ctypes.byref(h))
     assert st == rfb.RFB_ERR_INVALID_ARG
     assert lib.rfb_soc_destroy(None) == 0
+
+
+def _create(lib, dims=(4, 4, 4), dx=1e-6, D=4e-10, kin=None, kind=0, null=(), out=True):
+    import numpy as np
+    a = np.zeros(256)
+    p = a.ctypes.data_as(ctypes.c_void_p)
+    ptrs = [None if i in null else p for i in range(4)]          # mask, U, V, W
+    d = None if "dims" in null else (ctypes.c_int32 * 3)(*dims)
+    k = None if "kin" in null else ctypes.byref(kin or rfb.Kinetics(1e-7, 0.5, 2, 0, 298.0, 20.0))
+    h = ctypes.c_void_p()
+    st = lib.rfb_soc_create(d, dx, *ptrs, D, k, None, kind, None,
+                            ctypes.byref(h) if out else None)
+    return st, lib.rfb_soc_last_error(None)
+
+
+NAN = float("nan")
+
+
+@pytest.mark.parametrize("case,kw,msg", [
+    ("out NULL", dict(out=False), b"out is NULL"),
+    ("dims NULL", dict(null=("dims",)), b"NULL input"),
+    ("mask NULL", dict(null=(0,)), b"NULL input"),
+    ("W NULL", dict(null=(3,)), b"NULL input"),
+    ("kinetics NULL", dict(null=("kin",)), b"NULL input"),
+    ("memory kind", dict(kind=5), b"kind"),
+    ("nx = 0", dict(dims=(0, 4, 4)), b"dims"),
+    ("nz = 1", dict(dims=(4, 4, 1)), b"dims"),
+    ("N + nx ny >= 2^31", dict(dims=(2048, 1024, 1024)), b"too large"),
+    ("dx = 0", dict(dx=0.0), b"dx and D"),
+    ("dx NaN", dict(dx=NAN), b"dx and D"),
+    ("D < 0", dict(D=-1.0), b"dx and D"),
+    ("D inf", dict(D=float("inf")), b"dx and D"),
+    ("k0 < 0", dict(kin=rfb.Kinetics(-1e-7, 0.5, 2, 0, 298.0, 20.0)), b"kinetics out of range"),
+    ("k0 NaN", dict(kin=rfb.Kinetics(NAN, 0.5, 2, 0, 298.0, 20.0)), b"kinetics out of range"),
+    ("alpha = 0", dict(kin=rfb.Kinetics(1e-7, 0.0, 2, 0, 298.0, 20.0)), b"kinetics out of range"),
+    ("alpha = 1", dict(kin=rfb.Kinetics(1e-7, 1.0, 2, 0, 298.0, 20.0)), b"kinetics out of range"),
+    ("n_e = 0", dict(kin=rfb.Kinetics(1e-7, 0.5, 0, 0, 298.0, 20.0)), b"kinetics out of range"),
+    ("T = 0", dict(kin=rfb.Kinetics(1e-7, 0.5, 2, 0, 0.0, 20.0)), b"kinetics out of range"),
+    ("c0 < 0", dict(kin=rfb.Kinetics(1e-7, 0.5, 2, 0, 298.0, -20.0)), b"kinetics out of range"),
+    ("mode 2", dict(kin=rfb.Kinetics(1e-7, 0.5, 2, 2, 298.0, 20.0)), b"kinetics mode"),
+    ("mode -1", dict(kin=rfb.Kinetics(1e-7, 0.5, 2, -1, 298.0, 20.0)), b"kinetics mode"),
+])
+def test_create_validates_arguments_on_the_host(lib, case, kw, msg):
+    """Every argument check of rfb_soc_create that precedes device work, one at a time:
+    RFB_ERR_INVALID_ARG and a message naming the argument."""
+    st, err = _create(lib, **kw)
+    assert st == rfb.RFB_ERR_INVALID_ARG, case
+    assert msg in err, (case, err)
