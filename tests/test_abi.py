@@ -119,3 +119,49 @@ def test_create_validates_arguments_on_the_host(lib, case, kw, msg):
     st, err = _create(lib, **kw)
     assert st == rfb.RFB_ERR_INVALID_ARG, case
     assert msg in err, (case, err)
+
+
+NO_STATUS = {"rfb_soc_last_error", "rfb_soc_batch_last_error", "rfb_soc_kernel_launches",
+             "rfb_status_string", "rfb_solve_opts_default"}
+
+
+def _neutral(t):
+    if t is ctypes.c_double:
+        return 0.5
+    if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_long):
+        return 1
+    return None                      # handles, pointers, structs by pointer
+
+
+def test_every_handle_call_refuses_a_null_handle(lib):
+    """Each declared call whose first argument is a solver or batch handle returns
+    RFB_ERR_INVALID_ARG for a NULL handle (destroy calls return RFB_OK), before any
+    device work; the error getters return a string and the launch counter 0."""
+    seen = 0
+    for name in sorted(_declared()):
+        f = getattr(lib, name)
+        if name in NO_STATUS or not f.argtypes or f.argtypes[0] is not ctypes.c_void_p:
+            continue
+        args = [None] + [_neutral(t) for t in f.argtypes[1:]]
+        want = rfb.RFB_OK if name.endswith("_destroy") else rfb.RFB_ERR_INVALID_ARG
+        assert f(*args) == want, name
+        seen += 1
+    assert seen >= 20, seen
+    assert isinstance(lib.rfb_soc_last_error(None), bytes)
+    assert isinstance(lib.rfb_soc_batch_last_error(None), bytes)
+    assert lib.rfb_soc_kernel_launches(None) == 0
+
+
+def test_batch_create_and_bounded_wait_check_their_arguments(lib):
+    out = ctypes.c_void_p()
+    assert lib.rfb_soc_batch_create(None, 0, ctypes.byref(out)) == rfb.RFB_ERR_INVALID_ARG
+    assert b"at least one handle" in lib.rfb_soc_batch_last_error(None)
+    handles = (ctypes.c_void_p * 2)(None, None)
+    assert lib.rfb_soc_batch_create(handles, 2, ctypes.byref(out)) == rfb.RFB_ERR_INVALID_ARG
+    assert b"NULL handle" in lib.rfb_soc_batch_last_error(None)
+    assert lib.rfb_soc_batch_create(handles, 2, None) == rfb.RFB_ERR_INVALID_ARG
+    gave_up = ctypes.c_int32()
+    for limit, ptr in ((0, ctypes.byref(gave_up)), ((1 << 26) + 1, ctypes.byref(gave_up)),
+                       (100, None)):
+        assert lib.rfb_selftest_bounded_wait(limit, ptr) == rfb.RFB_ERR_INVALID_ARG
+    assert b"spin_limit" in lib.rfb_soc_last_error(None)
