@@ -447,3 +447,102 @@ def large_mixed_case(dims=(256, 256, 512), seed=2, **kw) -> Case:
     0.5 cm/s, eta = -0.05 V, s_in = 0.3, residual 1e-8."""
     return build_case("fiber%dx%dx%d_mixed" % tuple(dims), dims, 0.85, (6.0, 10.0), seed,
                       0.005, -0.05, 0.3, 1e-8, **kw)
+
+
+# --------------------------------------------------------------------------------------
+# Logpile lattice (the paper's benchmark electrode, Sec. IV)
+# --------------------------------------------------------------------------------------
+#
+# A box of 1280 x 640 x 160 um (the paper's flow length x width x height) holding 43 rods
+# of diameter 20 um in seven layers whose axes lie at heights 20, 40, ..., 140 um. Layers
+# 1, 3, 5 and 7 run along the flow, four rods each at widths 128, 256, 384 and 512 um;
+# layers 2, 4 and 6 run across it, nine rods each at flow positions 128, 256, ..., 1152
+# um. Adjacent layers are one diameter apart, so crossing rods touch. In this module's
+# axes the flow runs along z (the paper's x), y is the paper's y and x the paper's z
+# (the stacking height).
+
+LOGPILE_BOX_UM = (1280.0, 640.0, 160.0)   # flow length, width, height
+LOGPILE_ROD_D_UM = 20.0
+LOGPILE_PITCH_UM = 128.0
+LOGPILE_LAYER_UM = 20.0
+LOGPILE_Q_10PA = 0.345e-6 / 3600.0        # m^3/s: 3.45 mL/h at 100 Pa, scaled to 10 Pa
+
+
+def logpile_rods():
+    """The 43 rods: (layer, along, c1_um, c2_um). along = 'z' (with the flow; axis at
+    height c1 and width c2) or 'y' (across it; axis at height c1 and flow position c2)."""
+    rods = []
+    for layer in range(1, 8):
+        height = LOGPILE_LAYER_UM * layer
+        if layer % 2 == 1:
+            for m in range(1, 5):
+                rods.append((layer, "z", height, LOGPILE_PITCH_UM * m))
+        else:
+            for m in range(1, 10):
+                rods.append((layer, "y", height, LOGPILE_PITCH_UM * m))
+    return rods
+
+
+def logpile_dims(h: float):
+    """(nx, ny, nz) of the logpile box at cell size h (which must divide it)."""
+    um = h * 1e6
+    n = [L / um for L in (LOGPILE_BOX_UM[2], LOGPILE_BOX_UM[1], LOGPILE_BOX_UM[0])]
+    dims = tuple(int(round(v)) for v in n)
+    if any(abs(v - d) > 1e-9 * d for v, d in zip(n, dims)):
+        raise ValueError("h = %g m does not divide the 1280 x 640 x 160 um box" % h)
+    return dims
+
+
+def logpile_solid(h: float) -> np.ndarray:
+    """Solid mask (nz, ny, nx) of the logpile at cell size h: a cell is solid when its
+    centre lies within a rod's radius of the rod's axis (distances in cell units)."""
+    nx, ny, nz = logpile_dims(h)
+    um = h * 1e6
+    r = 0.5 * LOGPILE_ROD_D_UM / um
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    z = np.arange(nz) + 0.5
+    solid = np.zeros((nz, ny, nx), dtype=bool)
+    for _, along, c1, c2 in logpile_rods():
+        a, b = c1 / um, c2 / um
+        if along == "z":
+            disk = (x[None, :] - a) ** 2 + (y[:, None] - b) ** 2 <= r * r     # (ny, nx)
+            solid |= disk[None, :, :]
+        else:
+            disk = (x[None, :] - a) ** 2 + (z[:, None] - b) ** 2 <= r * r     # (nz, nx)
+            solid |= disk[:, None, :]
+    return solid
+
+
+def logpile_porosity_exact() -> float:
+    """Fluid fraction of the continuous logpile: the rods are tangent where they cross,
+    so their volumes add: 1 - pi r^2 (16 x 1280 + 27 x 640) / (1280 x 640 x 160)."""
+    r = 0.5 * LOGPILE_ROD_D_UM
+    L, W, H = LOGPILE_BOX_UM
+    n_along = sum(1 for rod in logpile_rods() if rod[1] == "z")
+    n_across = len(logpile_rods()) - n_along
+    return 1.0 - math.pi * r * r * (n_along * L + n_across * W) / (L * W * H)
+
+
+def logpile_case(h: float = H_PAPER, q: float = LOGPILE_Q_10PA, eta: float = 0.0,
+                 s_in: float = 1.73e-7, k0: float = 7.2e-5, tol: float = 1e-6,
+                 flow_device: str = "cpu", flow_tol: float = 1e-12) -> Case:
+    """The paper's reference reaction case on the logpile (Sec. IV): 10 Pa, applied
+    reducing voltage 0 (eta = 0, s_eq = 1/2), the parameter table's k0 and inlet state
+    of charge, tolerance 1e-6 on the residual. The paper's Stokes flow is replaced by the
+    potential flow of this module, rescaled so that the volumetric flow rate through the
+    inlet is q (default: the paper's 3.45 mL/h at 100 Pa scaled linearly to 10 Pa)."""
+    solid = remove_unconnected(logpile_solid(h))
+    U, V, W, info = potential_flow(solid, h, 1.0, tol=flow_tol, device=flow_device)
+    fin = ~solid[0]
+    q1 = h * h * float(np.sum(np.where(fin, W[0], 0.0)))
+    f = q / q1
+    U, V, W = U * f, V * f, W * f
+    info = dict(info)
+    info["q_m3_s"] = q
+    info["n_rods"] = len(logpile_rods())
+    u_mean = f * 1.0
+    dims = logpile_dims(h)
+    return Case(name="logpile%dx%dx%d" % dims, dims=dims, h=h, solid=solid.astype(np.uint8),
+                U=U, V=V, W=W, D=D_SOC, k0=k0, alpha=0.5, T=298.0, n_e=2, c0=20.0,
+                s_in=s_in, eta=eta, tol=tol, u_mean=u_mean, info=info)
