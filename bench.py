@@ -41,12 +41,14 @@ def parse():
     ap.add_argument("--dims", default="256,256,512")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--workload", default="mixed",
-                    choices=["mixed", "batch48", "upsample", "adjoint", "nernst"],
+                    choices=["mixed", "batch48", "upsample", "adjoint", "nernst", "logpile"],
                     help="mixed: the 256x256x512 mixed-precision solve (default); batch48: the "
                          "48-lattice batched workload; upsample: 128x128x256 -> 256x256x512 -> "
                          "512x512x1024 iterative upsampling; adjoint: gradients of I_tot, U "
                          "and U_mt on the 128x128x256 differentiation workload; nernst: the "
-                         "Nernst model against the SBV FP64 solve on 48x48x96 and 128x128x256")
+                         "Nernst model against the SBV FP64 solve on 48x48x96 and 128x128x256; "
+                         "logpile: the paper's reference reaction case on its logpile lattice "
+                         "at 5, 2.5 and 1.25 um")
     ap.add_argument("--fp32-kernel", default="auto",
                     choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
@@ -471,6 +473,64 @@ def run_nernst(args):
     print(json.dumps(out), flush=True)
 
 
+def run_logpile(args):
+    """The paper's reference reaction case on its logpile lattice (Sec. IV): 10 Pa flow
+    rate, applied reducing voltage 0, k0 = 7.2e-5 m/s, s_in = 1.73e-7, residual 1e-6 (the
+    paper's tolerance), potential flow in place of the paper's Stokes flow. Mixed-precision
+    solves at h = 5, 2.5 and 1.25 um (the last is the paper's 1024 x 512 x 128 = 2^26
+    cells), with U, I_tot and U_mt beside the paper's U = 0.243 and I = 0.09 mA, and the
+    FP64 solve of the finest level for comparison. value: cell-updates/s of the timed
+    finest-level mixed solves."""
+    import numpy as np
+    import torch
+
+    from paper_2502_08034_gb300 import _build, rfb, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    tol = 1e-6
+    stream = torch.cuda.current_stream()
+    levels, t_setup = [], time.time()
+    with Clocks(local) as clk:
+        for h in (5e-6, 2.5e-6, 1.25e-6):
+            case = synth.logpile_case(h, flow_device="cuda:%d" % local)
+            with rfb.Solver.from_case(case, stream=stream) as sv:
+                finest = h == 1.25e-6
+                for _ in range(max(1, args.warmup) if finest else 0):
+                    sv.reset_state()
+                    sv.solve(case.s_in, case.eta, tol, precision="mixed")
+                res = []
+                for _ in range(args.steps if finest else 1):
+                    sv.reset_state()
+                    res.append(sv.solve(case.s_in, case.eta, tol, precision="mixed"))
+                s_mixed = sv.get_state() if finest else None
+                u_mt, _ = sv.umt(tol, precision="mixed")
+                row = {"h_um": h * 1e6, "dims": list(case.dims),
+                       "porosity": round(case.porosity, 5), "sweeps": res[-1]["sweeps"],
+                       "time_to_steady_ms": res[-1]["time_ms"], "U": res[-1]["U"],
+                       "I_tot_mA": res[-1]["I_tot"] * 1e3, "U_mt": u_mt,
+                       "mass_balance_rel": res[-1]["mass_balance_rel"]}
+                if finest:
+                    sv.reset_state()
+                    r64 = sv.solve(case.s_in, case.eta, tol, precision="fp64")
+                    row["fp64_time_to_steady_ms"] = r64["time_ms"]
+                    row["mixed_minus_fp64_maxabs_s"] = float(np.abs(sv.get_state() - s_mixed).max())
+                    n_fine, steps_fine = case.n, res
+            levels.append(row)
+    ms = sum(r["time_ms"] for r in steps_fine)
+    cells = n_fine * sum(r["sweeps"] for r in steps_fine)
+    out = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic (the paper's logpile geometry, potential flow)",
+           "config": {"workload": "logpile1024x512x128_sbv_10Pa", "tol": tol,
+                      "precision": "mixed", "q_m3_s": synth.LOGPILE_Q_10PA, "eta_V": 0.0,
+                      "k0_m_s": 7.2e-5},
+           "paper": {"U": 0.243, "I_tot_mA": 0.09}, "levels": levels,
+           "setup_s": time.time() - t_setup, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Differentiation workload: 128x128x256, porosity 0.8, d = 8, lognormal (sigma 0.3)
     area multipliers on wall cells; step = FP64 solve to 1e-12 + U_mt solve + the three
@@ -555,6 +615,9 @@ def main():
         return
     if args.workload == "nernst":
         run_nernst(args)
+        return
+    if args.workload == "logpile":
+        run_logpile(args)
         return
     import numpy as np
     import torch
