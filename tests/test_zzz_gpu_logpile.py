@@ -34,9 +34,10 @@ def _logpile():
 
 # The flow is slow (tau = V_f / Q = 1.25 s), so the residual's FP64 rounding floor is
 # near 4e-14 (the oracle's direct solution has 3.7e-14) and the double-float one of the
-# mixed defects near 4e-11: the tolerances sit above both.
+# mixed defects (tau 2^-44 max_c d_c) is 1.8e-11: the tolerances sit well above both. At
+# residual 1e-9 the oracle's own explicit loop is within 3e-10 of the direct solution.
 @pytest.mark.parametrize("precision,tol,rel,absolute", [("fp64", 1e-12, 1e-10, 0.0),
-                                                        ("mixed", 1e-10, 0.0, 1e-7)])
+                                                        ("mixed", 1e-9, 0.0, 1e-7)])
 def test_logpile_reference_case_matches_oracle(precision, tol, rel, absolute):
     from paper_2502_08034_gb300 import rfb
     case, p, s_ref, o = _logpile()
