@@ -533,15 +533,15 @@ def logpile_case(h: float = H_PAPER, q: float = LOGPILE_Q_10PA, eta: float = 0.0
     potential flow of this module, rescaled so that the volumetric flow rate through the
     inlet is q (default: the paper's 3.45 mL/h at 100 Pa scaled linearly to 10 Pa)."""
     solid = remove_unconnected(logpile_solid(h))
+    # solved at a mean z-velocity of 1 m/s over fluid z-faces, then scaled to the rate q
     U, V, W, info = potential_flow(solid, h, 1.0, tol=flow_tol, device=flow_device)
     fin = ~solid[0]
-    q1 = h * h * float(np.sum(np.where(fin, W[0], 0.0)))
-    f = q / q1
+    f = q / (h * h * float(np.sum(np.where(fin, W[0], 0.0))))
     U, V, W = U * f, V * f, W * f
     info = dict(info)
     info["q_m3_s"] = q
     info["n_rods"] = len(logpile_rods())
-    u_mean = f * 1.0
+    u_mean = f                                  # the scaled mean z-velocity (m/s)
     dims = logpile_dims(h)
     return Case(name="logpile%dx%dx%d" % dims, dims=dims, h=h, solid=solid.astype(np.uint8),
                 U=U, V=V, W=W, D=D_SOC, k0=k0, alpha=0.5, T=298.0, n_e=2, c0=20.0,
