@@ -150,8 +150,15 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
-def _ptr(x, dtype):
-    """(pointer, keepalive, kind) of a numpy array or CUDA torch tensor."""
+def _count(size, n, what):
+    if n is not None and size != n:
+        raise ValueError("%s holds %d values; the lattice needs %d" % (what, size, n))
+
+
+def _ptr(x, dtype, n=None, what="array"):
+    """(pointer, keepalive, kind) of a numpy array or CUDA torch tensor. With ``n`` the
+    array must hold exactly n values (any shape): the C ABI reads that many from the
+    pointer, so a smaller array would be read past its end."""
     if x is None:
         return None, None, None
     if _is_torch(x):
@@ -162,8 +169,10 @@ def _ptr(x, dtype):
             tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
             if x.dtype != tdt or not x.is_contiguous():
                 x = x.to(tdt).contiguous()
+            _count(x.numel(), n, what)
             return c_void_p(x.data_ptr()), x, MEM_DEVICE
     a = np.ascontiguousarray(x, dtype=dtype)
+    _count(a.size, n, what)
     return a.ctypes.data_as(c_void_p), a, MEM_HOST
 
 
@@ -177,8 +186,13 @@ class Solver:
         d = (c_int32 * 3)(*self.dims)
         kin = Kinetics(float(k0), float(alpha), int(n_e), int(kinetics_mode), float(T),
                        float(c0))
-        ptrs = [_ptr(solid, np.uint8), _ptr(U, np.float64), _ptr(V, np.float64),
-                _ptr(W, np.float64), _ptr(area_mult, np.float64)]
+        nx, ny, nz = self.dims
+        N = nx * ny * nz
+        ptrs = [_ptr(solid, np.uint8, N, "solid"),
+                _ptr(U, np.float64, (nx + 1) * ny * nz, "U"),
+                _ptr(V, np.float64, nx * (ny + 1) * nz, "V"),
+                _ptr(W, np.float64, nx * ny * (nz + 1), "W"),
+                _ptr(area_mult, np.float64, N, "area_mult")]
         kinds = {p[2] for p in ptrs if p[2] is not None}
         if len(kinds) != 1:
             raise ValueError("all arrays must be host (numpy) or all CUDA tensors")
@@ -243,7 +257,7 @@ class Solver:
         """eta~ of the last Nernst-model solve (N values, 0 off the electrode cells)."""
         if out is None:
             out = np.empty(self.n_cells, dtype=np.float64)
-        p, keep, kind = _ptr(out, np.float64)
+        p, keep, kind = _ptr(out, np.float64, self.n_cells, "out")
         if kind == MEM_HOST and keep is not out:
             raise ValueError("out must be a contiguous float64 array")
         self._check(lib().rfb_soc_get_overpotential(self.h, p, kind))
@@ -271,14 +285,14 @@ class Solver:
     def get_state(self, out=None):
         if out is None:
             out = np.empty(self.n_cells, dtype=np.float64)
-        p, keep, kind = _ptr(out, np.float64)
+        p, keep, kind = _ptr(out, np.float64, self.n_cells, "out")
         if kind == MEM_HOST and keep is not out:
             raise ValueError("out must be a contiguous float64 array")
         self._check(lib().rfb_soc_get_state(self.h, p, kind))
         return out
 
     def set_state(self, s):
-        p, keep, kind = _ptr(s, np.float64)
+        p, keep, kind = _ptr(s, np.float64, self.n_cells, "state")
         self._check(lib().rfb_soc_set_state(self.h, p, kind))
 
     def set_area_mult(self, m):
@@ -286,7 +300,7 @@ class Solver:
         if m is None:
             self._check(lib().rfb_soc_set_area_mult(self.h, None, MEM_HOST))
             return
-        p, keep, kind = _ptr(m, np.float64)
+        p, keep, kind = _ptr(m, np.float64, self.n_cells, "area_mult")
         self._check(lib().rfb_soc_set_area_mult(self.h, p, kind))
 
     def adjoint(self, objective="I_tot", tol=1e-12, out=None, **opts):
@@ -294,7 +308,7 @@ class Solver:
         obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
         if out is None:
             out = np.empty(self.n_cells, dtype=np.float64)
-        p, keep, kind = _ptr(out, np.float64)
+        p, keep, kind = _ptr(out, np.float64, self.n_cells, "out")
         db = c_double()
         r = SolveResult()
         o = make_opts(**opts)
@@ -370,13 +384,16 @@ class Batch:
 
     def solve(self, s_in, eta, tol, allow_not_converged=False, **opts):
         n = len(self.solvers)
+        s_in, eta, tol = (list(map(float, v)) for v in (s_in, eta, tol))
+        if not len(s_in) == len(eta) == len(tol) == n:
+            raise ValueError("s_in, eta and tol need one value per lattice (%d)" % n)
         opts.setdefault("precision", "mixed")
         D = c_double * n
         res = (SolveResult * n)()
         info = BatchInfo()
         o = make_opts(**opts)
-        st = lib().rfb_soc_batch_solve(self.b, D(*map(float, s_in)), D(*map(float, eta)),
-                                       D(*map(float, tol)), byref(o), res, byref(info))
+        st = lib().rfb_soc_batch_solve(self.b, D(*s_in), D(*eta), D(*tol), byref(o), res,
+                                       byref(info))
         ok = (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,)
         if st not in ok:
             raise RfbError(st, lib().rfb_soc_batch_last_error(self.b).decode())

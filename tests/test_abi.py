@@ -165,3 +165,43 @@ def test_batch_create_and_bounded_wait_check_their_arguments(lib):
                        (100, None)):
         assert lib.rfb_selftest_bounded_wait(limit, ptr) == rfb.RFB_ERR_INVALID_ARG
     assert b"spin_limit" in lib.rfb_soc_last_error(None)
+
+
+@pytest.mark.parametrize("bad", ["solid", "U", "V", "W", "area_mult"])
+def test_binding_checks_array_sizes_before_the_c_call(lib, bad):
+    """The C ABI reads as many values as the lattice needs from each pointer; the binding
+    refuses an array of another size (here one value short) before calling it."""
+    import numpy as np
+    nx, ny, nz = 4, 5, 6
+    N = nx * ny * nz
+    sizes = {"solid": N, "U": (nx + 1) * ny * nz, "V": nx * (ny + 1) * nz,
+             "W": nx * ny * (nz + 1), "area_mult": N}
+    arrays = {k: np.zeros(v - (1 if k == bad else 0)) for k, v in sizes.items()}
+    with pytest.raises(ValueError, match=bad):
+        rfb.Solver((nx, ny, nz), 1e-6, arrays["solid"].astype(np.uint8), arrays["U"],
+                   arrays["V"], arrays["W"], 4e-10, 1e-7, area_mult=arrays["area_mult"])
+
+
+def test_binding_checks_batch_argument_lengths(lib):
+    b = rfb.Batch.__new__(rfb.Batch)          # no device: only the argument check runs
+    b.solvers, b.b = [None, None], None
+    with pytest.raises(ValueError, match="one value per lattice"):
+        b.solve([0.5], [-0.1, -0.1], [1e-8, 1e-8])
+    with pytest.raises(ValueError, match="one value per lattice"):
+        b.solve([0.5, 0.5], [-0.1, -0.1], [1e-8, 1e-8, 1e-8])
+
+
+def test_binding_passes_arrays_of_the_right_size_to_the_c_call(lib):
+    """Arrays in the face layouts of the synthetic inputs pass the size checks and reach
+    rfb_soc_create (which, without a GPU, then reports the CUDA error)."""
+    import numpy as np
+    from paper_2502_08034_gb300 import synth
+    for dims in ((6, 5, 4), (3, 7, 2)):
+        nx, ny, nz = dims
+        solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+        U, V, W = np.zeros((nz, ny, nx + 1)), np.zeros((nz, ny + 1, nx)), np.zeros((nz + 1, ny, nx))
+        try:
+            rfb.Solver(dims, 1e-6, solid, U, V, W, 4e-10, 1e-7, area_mult=np.ones(solid.shape)).close()
+        except rfb.RfbError as e:
+            assert e.status == rfb.RFB_ERR_CUDA, str(e)
+    assert synth.logpile_dims(10e-6) == (16, 64, 128)
