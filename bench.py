@@ -91,17 +91,22 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_digest():
-    """Digest of the kernel sources' code (comments and whitespace removed, so that a
-    comment edit does not void the traffic figures taken on the same code)."""
+def code_digest(sources):
+    """Digest of C/CUDA source texts with comments and whitespace removed."""
     import re
     h = hashlib.sha256()
-    for name in ("soc_kernels.cuh", "sweep_tb.cuh"):
-        src = open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name)).read()
+    for src in sources:
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_digest():
+    """Digest of the kernel sources' code (comments and whitespace removed, so that a
+    comment edit does not void the traffic figures taken on the same code)."""
+    return code_digest(open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name)).read()
+                       for name in ("soc_kernels.cuh", "sweep_tb.cuh"))
 
 
 def kernel_traffic(n_cells, kernel):

@@ -68,3 +68,31 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_code_digest_ignores_comments_and_whitespace_only():
+    src = "__global__ void k(float* a) {\n    a[0] = 1.0f;  // set\n}\n"
+    same = "/* kernel */\n__global__ void k(float* a)\n{ a[0] = 1.0f; }  // other words\n"
+    changed = "__global__ void k(float* a) {\n    a[0] = 2.0f;  // set\n}\n"
+    assert bench.code_digest([src]) == bench.code_digest([same])
+    assert bench.code_digest([src]) != bench.code_digest([changed])
+
+
+def test_kernel_traffic_scales_with_the_cells_and_names_its_kernel():
+    """The committed DRAM bytes per cell of the current kernel code, scaled to a launch's
+    cells; unknown kernels have none."""
+    per, stale = {}, set()
+    for line in open(os.path.join(ROOT, "profiles", "sweep_fp32_traffic.txt")):
+        if line.startswith("kernel="):
+            kv = dict(x.split("=", 1) for x in line.split())
+            if kv["source_sha"] == bench.kernel_source_digest():
+                per[kv["kernel"]] = float(kv["dram_bytes_per_cell"])
+            else:
+                stale.add(kv["kernel"])
+    for kernel in stale - set(per):       # taken on other kernel code: reported as null
+        assert bench.kernel_traffic(1000, kernel) is None
+    for kernel, b in per.items():
+        assert bench.kernel_traffic(1000, kernel) == b * 1000
+        assert bench.kernel_traffic(2 ** 25, kernel) == b * 2 ** 25
+        assert b >= bench.SWEEP_BYTES_PER_CELL - 0.5    # no launch moves less than its inputs
+    assert bench.kernel_traffic(1000, "no_such_kernel") is None
