@@ -526,23 +526,176 @@ def logpile_porosity_exact() -> float:
 
 def logpile_case(h: float = H_PAPER, q: float = LOGPILE_Q_10PA, eta: float = 0.0,
                  s_in: float = 1.73e-7, k0: float = 7.2e-5, tol: float = 1e-6,
-                 flow_device: str = "cpu", flow_tol: float = 1e-12) -> Case:
+                 flow_device: str = "cpu", flow_tol: float = 1e-12, flow: str = "potential",
+                 dp: float = 10.0) -> Case:
     """The paper's reference reaction case on the logpile (Sec. IV): 10 Pa, applied
     reducing voltage 0 (eta = 0, s_eq = 1/2), the parameter table's k0 and inlet state
-    of charge, tolerance 1e-6 on the residual. The paper's Stokes flow is replaced by the
-    potential flow of this module, rescaled so that the volumetric flow rate through the
-    inlet is q (default: the paper's 3.45 mL/h at 100 Pa scaled linearly to 10 Pa)."""
+    of charge, tolerance 1e-6 on the residual.
+    flow = 'potential': the potential flow of this module, rescaled so that the volumetric
+    flow rate through the inlet is q (default: the paper's 3.45 mL/h at 100 Pa scaled
+    linearly to 10 Pa). flow = 'stokes': the Stokes flow at the pressure drop dp (Pa)
+    from ``stokes_flow`` (sparse LU on the CPU: coarse cell sizes only)."""
     solid = remove_unconnected(logpile_solid(h))
-    # solved at a mean z-velocity of 1 m/s over fluid z-faces, then scaled to the rate q
-    U, V, W, info = potential_flow(solid, h, 1.0, tol=flow_tol, device=flow_device)
-    fin = ~solid[0]
-    f = q / (h * h * float(np.sum(np.where(fin, W[0], 0.0))))
-    U, V, W = U * f, V * f, W * f
+    if flow == "stokes":
+        U, V, W, info = stokes_flow(solid, h, dp=dp)
+        q = info["q_m3_s"]
+        f = 1.0
+    elif flow == "potential":
+        # solved at a mean z-velocity of 1 m/s over fluid z-faces, scaled to the rate q
+        U, V, W, info = potential_flow(solid, h, 1.0, tol=flow_tol, device=flow_device)
+        fin = ~solid[0]
+        f = q / (h * h * float(np.sum(np.where(fin, W[0], 0.0))))
+        U, V, W = U * f, V * f, W * f
+    else:
+        raise ValueError("flow must be 'potential' or 'stokes'")
     info = dict(info)
+    info["flow"] = flow
     info["q_m3_s"] = q
     info["n_rods"] = len(logpile_rods())
-    u_mean = f                                  # the scaled mean z-velocity (m/s)
+    fz = np.zeros(W.shape, dtype=bool)
+    fz[1:-1] = (solid[:-1] == 0) & (solid[1:] == 0)
+    u_mean = float(W[fz].mean())                # mean z-velocity over fluid z-faces (m/s)
     dims = logpile_dims(h)
     return Case(name="logpile%dx%dx%d" % dims, dims=dims, h=h, solid=solid.astype(np.uint8),
                 U=U, V=V, W=W, D=D_SOC, k0=k0, alpha=0.5, T=298.0, n_e=2, c0=20.0,
                 s_in=s_in, eta=eta, tol=tol, u_mean=u_mean, info=info)
+
+
+# --------------------------------------------------------------------------------------
+# Stokes flow fixture (CPU, sparse LU; small lattices)
+# --------------------------------------------------------------------------------------
+
+MU_WATER = 8.8891e-4   # Pa s (parameter table)
+
+
+def _face_laplacian(open_, along, h, mu):
+    """A = -mu Lap on the open faces of one velocity component (face array ``open_``,
+    component along array axis ``along``: 0 = z, 1 = y, 2 = x). Neighbour faces:
+    open -> coupled; closed along the component's own axis -> a wall face with velocity 0
+    one cell away; closed across it -> a wall half a cell away (ghost value -u);
+    outside the lattice across z (inlet / outlet planes) -> zero normal gradient;
+    outside across x or y (side walls) -> wall half a cell away."""
+    import scipy.sparse as sp
+    shape = open_.shape
+    idx = -np.ones(shape, dtype=np.int64)
+    idx[open_] = np.arange(int(open_.sum()))
+    n = int(open_.sum())
+    c = mu / (h * h)
+    diag = np.zeros(n)
+    rows, cols = [], []
+    for axis in range(3):
+        for step in (-1, 1):
+            src = [slice(None)] * 3
+            dst = [slice(None)] * 3
+            if step == 1:
+                src[axis], dst[axis] = slice(0, shape[axis] - 1), slice(1, None)
+            else:
+                src[axis], dst[axis] = slice(1, None), slice(0, shape[axis] - 1)
+            a = idx[tuple(src)]
+            b = idx[tuple(dst)]
+            have = a >= 0
+            coupled = have & (b >= 0)
+            rows.append(a[coupled]); cols.append(b[coupled])
+            np.add.at(diag, a[coupled], c)
+            closed = have & (b < 0)
+            np.add.at(diag, a[closed], c if axis == along else 2 * c)
+            # faces on the lattice's last layer along this direction have no neighbour
+            edge = [slice(None)] * 3
+            edge[axis] = shape[axis] - 1 if step == 1 else 0
+            e = idx[tuple(edge)]
+            e = e[e >= 0]
+            if axis != 0:                       # side walls half a cell away
+                np.add.at(diag, e, c if axis == along else 2 * c)
+            # axis 0 (inlet / outlet): zero normal gradient, nothing added
+    r = np.concatenate(rows)
+    q = np.concatenate(cols)
+    A = sp.csr_matrix((np.full(r.size, -c), (r, q)), shape=(n, n)) + sp.diags(diag)
+    return A.tocsc(), idx
+
+
+def stokes_flow(solid: np.ndarray, h: float, dp: float = 1.0, mu: float = MU_WATER,
+                tol: float = 1e-13, max_iter: int = 5000):
+    """Steady Stokes flow through the fluid cells of ``solid`` driven by the pressure drop
+    ``dp`` (Pa) from the inlet to the outlet; at the paper's Reynolds numbers its
+    incompressible Navier-Stokes solve (Sec. III.A, Algorithm 1) reaches this flow, which
+    is linear in the pressure (Sec. IV scales flows between pressures). Staggered grid in
+    this module's face layout: -mu Lap u + grad p = 0 on every open face and div u = 0 in
+    every fluid cell; no slip on fiber faces and side walls (staircase walls), zero normal
+    gradient of velocity at the inlet and outlet planes, and pressures dp and 0 on ghost
+    cell centres one cell before the inlet and past the outlet.
+    Solved by conjugate gradients on the pressure Schur complement S = D A^-1 D^T (SPD:
+    the boundary pressures fix the constant), with sparse LU factors of the three velocity
+    Laplacians A. Returns (U, V, W, info) in m/s."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    solid = solid.astype(bool)
+    fluid = ~solid
+    nz, ny, nx = solid.shape
+    oU = np.zeros((nz, ny, nx + 1), dtype=bool)
+    oU[:, :, 1:nx] = fluid[:, :, :-1] & fluid[:, :, 1:]
+    oV = np.zeros((nz, ny + 1, nx), dtype=bool)
+    oV[:, 1:ny, :] = fluid[:, :-1, :] & fluid[:, 1:, :]
+    oW = np.zeros((nz + 1, ny, nx), dtype=bool)
+    oW[1:nz] = fluid[:-1] & fluid[1:]
+    oW[0] = fluid[0]
+    oW[nz] = fluid[-1]
+    cidx = -np.ones((nz, ny, nx), dtype=np.int64)
+    nf = int(fluid.sum())
+    cidx[fluid] = np.arange(nf)
+
+    blocks, divs, rhs = [], [], []
+    for open_, along in ((oU, 2), (oV, 1), (oW, 0)):
+        A, fidx = _face_laplacian(open_, along, h, mu)
+        n = A.shape[0]
+        # divergence: a face is the high face of the cell below it along its axis (+1/h)
+        # and the low face of the cell above it (-1/h)
+        f_of = fidx[open_]
+        pos = np.argwhere(open_)
+        lo = pos.copy()
+        lo[:, along] -= 1
+        rows, cols, vals = [], [], []
+        for cellpos, sign in ((lo, 1.0), (pos, -1.0)):
+            ok = (cellpos[:, along] >= 0) & (cellpos[:, along] < (nz, ny, nx)[along])
+            cp = cellpos[ok]
+            rows.append(cidx[cp[:, 0], cp[:, 1], cp[:, 2]]); cols.append(f_of[ok])
+            vals.append(np.full(int(ok.sum()), sign / h))
+        D = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(nf, n))
+        b = np.zeros(n)
+        if along == 0:
+            b[fidx[0][oW[0]]] = dp / h            # (p_0 - dp) / h on the inlet faces
+        blocks.append(spla.splu(A))
+        divs.append(D)
+        rhs.append(b)
+
+    def a_inv(vs):
+        return [lu.solve(v) for lu, v in zip(blocks, vs)]
+
+    def s_mul(p):
+        u = a_inv([D.T @ p for D in divs])
+        return sum(D @ x for D, x in zip(divs, u))
+
+    S = spla.LinearOperator((nf, nf), matvec=s_mul, dtype=np.float64)
+    g = -sum(D @ x for D, x in zip(divs, a_inv(rhs)))
+    iters = [0]
+
+    def count(_):
+        iters[0] += 1
+
+    p, info_cg = spla.cg(S, g, rtol=tol, atol=0.0, maxiter=max_iter, callback=count)
+    if info_cg != 0:
+        raise RuntimeError("Stokes pressure CG did not converge (info=%d)" % info_cg)
+    u = a_inv([b + D.T @ p for b, D in zip(rhs, divs)])
+    out = []
+    for open_, x in zip((oU, oV, oW), u):
+        f = np.zeros(open_.shape)
+        f[open_] = x
+        out.append(f)
+    U, V, W = out
+    div = sum(D @ x for D, x in zip(divs, u))
+    q = h * h * float(W[0][oW[0]].sum())
+    # a cell's net outflow (div u h^3) relative to the mean flux of an inlet face
+    mean_face_q = q / max(int(oW[0].sum()), 1)
+    info = {"cg_iters": iters[0], "q_m3_s": q,
+            "max_div_rel": float(np.abs(div).max() * h ** 3 / max(abs(mean_face_q), 1e-300))}
+    return U, V, W, info
