@@ -347,9 +347,13 @@ def newton_steady_state(op: Operator, s0: Optional[np.ndarray] = None, direct_ma
     step of the explicit loop's size) and grows by switched evolution relaxation,
     delta <- delta ||RHS_prev|| / ||RHS||, so the iteration turns into Newton's method near
     the solution. Steps are halved while they would leave (0, 1). Starts from s = s_in
-    (clamped into (0, 1)) unless s0 is given; stops once delta is large (a Newton step)
-    and the step is below rtol max|s|, or below 1e-9 max|s| and no smaller than half the
-    previous one (the rounding floor of the linear solves)."""
+    (clamped into (0, 1)) unless s0 is given; stops once delta >= 1e8 and the step is
+    below rtol max|s|, or below 1e-9 max|s| and no smaller than half the previous one (the
+    rounding floor of the linear solves). At delta >= 1e8 the pseudo-time term D/delta is
+    at most 1e-8 of the diagonal, so the step solves Newton's equation to that accuracy
+    and these tests are as valid as for Newton's method itself; delta cannot be required
+    to grow further, since near the rounding floor ||RHS|| only jitters and the update
+    above stalls."""
     u = op.unknown
     s = initial_state(op, op.s_in) if s0 is None else np.array(s0, dtype=np.float64)
     s[u] = np.clip(s[u], 1e-12, 1.0 - 1e-12)
@@ -373,7 +377,7 @@ def newton_steady_state(op: Operator, s0: Optional[np.ndarray] = None, direct_ma
         rn_new = float(np.linalg.norm(r))
         step = float(np.max(np.abs(ds))) if ds.size else 0.0
         scale = max(1.0, float(np.max(np.abs(s))))
-        newton = delta >= 1e12
+        newton = delta >= 1e8
         if newton and lam == 1.0 and (step <= rtol * scale or
                                       (step <= 1e-9 * scale and step >= 0.5 * prev)):
             return s
