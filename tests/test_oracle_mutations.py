@@ -154,6 +154,17 @@ MUTATIONS = [
        "float(np.sum(np.where(fout, w, 0.0)))",
        "return float(np.mean(s3[-1][fout]))")],
      "test_umt_is_the_fast_kinetics_limit", {}, None),
+    # kinetics mode 1: Newton's method with pseudo-transient continuation
+    ("jacobian_without_reaction_slope",
+     [("    d[k] = op.kappa[k] * rate_uniform_slope(s[k], op.kin.Vt, op.kin.alpha)\n"
+       "    return (op.L + sp.diags(d)).tocsr()",
+       "    d[k] = 0.0 * op.kappa[k] * rate_uniform_slope(s[k], op.kin.Vt, op.kin.alpha)\n"
+       "    return (op.L + sp.diags(d)).tocsr()")],
+     "test_oracle_adjoint_matches_central_differences", dict(objective="I_tot", kmode=1), None),
+    ("pseudo_time_term_sign",
+     [("A = (sp.diags(d / delta) - J).tocsr() if delta < 1e15 else -J",
+       "A = (sp.diags(-d / delta) - J).tocsr() if delta < 1e15 else -J")],
+     "test_uniform_eta_channel_without_diffusion_is_solved_cell_by_cell", dict(alpha=0.5), None),
     # steady state and the explicit loop (Algorithm 7)
     ("steady_state_source_sign",
      [("rhs_u = -(op.b[u] + op.L[u] @ op.fixed)", "rhs_u = (op.b[u] + op.L[u] @ op.fixed)")],
