@@ -2,8 +2,8 @@
 and operating points, the steady state obeys what the paper's PDE fixes for any input:
 exact discrete conservation (I_tot = F_out - F_in, Eq. convergence-bv-flow), the
 discrete maximum principle (s between s_in and s_eq), the explicit pseudo-time loop of
-Algorithm 7 reaching the direct solution, and, for kinetics mode 1, RHS = 0 at Newton's
-state with s inside (s_in, 1)."""
+Algorithm 7 reaching the direct solution, the Nernst model reaching the same state, and,
+for kinetics mode 1, RHS = 0 at Newton's state with s inside (s_in, 1)."""
 import functools
 
 import numpy as np
@@ -81,3 +81,19 @@ def test_uniform_eta_newton_state(seed, s_in, eta, alpha):
     assert s[fl].min() >= s_in - 1e-10 and s[fl].max() < 1.0
     o = soc.outputs(p, op, s)
     assert abs(o.I_tot - (o.F_out - o.F_in)) <= 1e-9 * max(abs(o.F_out), abs(o.I_tot))
+
+
+@settings(max_examples=4, deadline=None, derandomize=True)
+@given(lat=lattices, s_in=st.floats(0.0, 0.95), eta=st.floats(-0.2, 0.05),
+       logk=st.floats(-8.0, -3.0), local=st.booleans())
+def test_nernst_model_reaches_the_sbv_state(lat, s_in, eta, logk, local):
+    """The Nernst model's iteration (relaxed eta~ on Dirichlet electrode cells) stops at
+    the SBV steady state for any operating point, reducing or oxidising, slow or fast
+    kinetics (both models have the same fixed point, Sec. III.C)."""
+    case = _lattice(*lat)
+    p = _problem(case, s_in=s_in, eta=eta, k0=10.0 ** logk)
+    ref = soc.steady_state(soc.assemble(p))
+    s, _, n = soc.nernst_iterate(p, 1.0 if local else 0.5, 1e-11, local_dt=local,
+                                 max_steps=300000)
+    assert n < 300000
+    assert np.abs(s - ref).max() <= 1e-8
