@@ -531,7 +531,8 @@ def run_logpile(args):
            "config": {"workload": "logpile1024x512x128_sbv_10Pa", "tol": tol,
                       "precision": "mixed", "q_m3_s": synth.LOGPILE_Q_10PA, "eta_V": 0.0,
                       "k0_m_s": 7.2e-5},
-           "paper": {"U": 0.243, "I_tot_mA": 0.09}, "levels": levels,
+           "paper": {"U": 0.243, "I_tot_mA": 0.09, "time_steps_to_tol": 125000},
+           "levels": levels,
            "setup_s": time.time() - t_setup, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
