@@ -205,3 +205,86 @@ def test_binding_passes_arrays_of_the_right_size_to_the_c_call(lib):
         except rfb.RfbError as e:
             assert e.status == rfb.RFB_ERR_CUDA, str(e)
     assert synth.logpile_dims(10e-6) == (16, 64, 128)
+
+
+# ------------------------------------------------------- the binding matches the header
+
+def _header_text():
+    txt = open(os.path.join(ROOT, "include", "rfb_soc.h")).read()
+    return re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+
+
+def _header_enums():
+    out = {}
+    for body in re.findall(r"typedef enum \w+ \{(.*?)\}", _header_text(), flags=re.S):
+        for name, val in re.findall(r"(\w+)\s*=\s*(\d+)", body):
+            out[name] = int(val)
+    return out
+
+
+def _header_structs():
+    out = {}
+    for name, body in re.findall(r"typedef struct (\w+) \{(.*?)\}", _header_text(), flags=re.S):
+        fields = []
+        for ctype, fname, arr in re.findall(r"(int32_t|int64_t|double)\s+(\w+)\s*(?:\[(\d+)\])?;",
+                                            body):
+            fields.append((fname, ctype, int(arr) if arr else None))
+        out[name] = fields
+    return out
+
+
+def test_binding_enums_match_the_header():
+    e = _header_enums()
+    assert (e["RFB_OK"], e["RFB_ERR_INVALID_ARG"], e["RFB_ERR_CUDA"], e["RFB_ERR_OOM"],
+            e["RFB_ERR_NOT_CONVERGED"], e["RFB_ERR_NONFINITE"], e["RFB_ERR_STATE"],
+            e["RFB_ERR_UNSUPPORTED"]) == (rfb.RFB_OK, rfb.RFB_ERR_INVALID_ARG, rfb.RFB_ERR_CUDA,
+                                          rfb.RFB_ERR_OOM, rfb.RFB_ERR_NOT_CONVERGED,
+                                          rfb.RFB_ERR_NONFINITE, rfb.RFB_ERR_STATE,
+                                          rfb.RFB_ERR_UNSUPPORTED)
+    assert (e["RFB_MEM_HOST"], e["RFB_MEM_DEVICE"]) == (rfb.MEM_HOST, rfb.MEM_DEVICE)
+    assert rfb.PREC == {"fp64": e["RFB_PREC_FP64"], "mixed": e["RFB_PREC_MIXED"]}
+    assert rfb.INLET == {"face": e["RFB_INLET_FACE"], "ghost": e["RFB_INLET_GHOST"]}
+    assert rfb.DT == {"global": e["RFB_DT_GLOBAL"], "local": e["RFB_DT_LOCAL"]}
+    assert (rfb.KIN_AFFINE, rfb.KIN_UNIFORM_ETA) == (e["RFB_KIN_AFFINE"], e["RFB_KIN_UNIFORM_ETA"])
+    assert rfb.OBJECTIVES == {"I_tot": e["RFB_OBJ_I_TOT"], "U": e["RFB_OBJ_U"],
+                              "U_mt": e["RFB_OBJ_U_MT"]}
+
+
+def test_binding_structs_match_the_header():
+    """Field names, order, types and array lengths of every struct the binding mirrors."""
+    cmap = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+    s = _header_structs()
+    for cname, py in (("rfb_kinetics", rfb.Kinetics), ("rfb_solve_opts", rfb.SolveOpts),
+                      ("rfb_solve_result", rfb.SolveResult), ("rfb_batch_info", rfb.BatchInfo)):
+        want = s[cname]
+        got = py._fields_
+        assert [f[0] for f in got] == [f[0] for f in want], cname
+        for (fname, ftype), (_, ctype, arr) in zip(got, want):
+            if arr is None:
+                assert ftype is cmap[ctype], (cname, fname)
+            else:
+                assert ftype._type_ is cmap[ctype] and ftype._length_ == arr, (cname, fname)
+
+
+def test_binding_argument_types_match_the_header(lib):
+    """Each declared function's parameters against the ctypes argtypes: pointers to
+    pointer types, doubles to c_double, 64-bit integers to c_int64, 32-bit integers and
+    enums to c_int32."""
+    txt = _header_text()
+    protos = re.findall(r"\b(?:rfb_status|void|const char\*|int64_t)\s+(rfb_\w+)\s*\((.*?)\);",
+                        txt, flags=re.S)
+    assert len(protos) >= 25
+    for name, params in protos:
+        f = getattr(lib, name)
+        plist = [p.strip() for p in params.split(",")] if params.strip() else []
+        assert len(plist) == len(f.argtypes), name
+        for p, t in zip(plist, f.argtypes):
+            if "*" in p or "[" in p:
+                assert t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and \
+                    t.__name__.startswith("LP_"), (name, p, t)
+            elif p.startswith("double"):
+                assert t is ctypes.c_double, (name, p, t)
+            elif p.startswith("int64_t"):
+                assert t is ctypes.c_int64, (name, p, t)
+            else:
+                assert t is ctypes.c_int32, (name, p, t)
