@@ -288,3 +288,16 @@ def test_binding_argument_types_match_the_header(lib):
                 assert t is ctypes.c_int64, (name, p, t)
             else:
                 assert t is ctypes.c_int32, (name, p, t)
+
+
+def test_no_fallback_when_the_library_is_missing(monkeypatch, tmp_path):
+    """Without the built CUDA library every entry point raises: there is no CPU path."""
+    import numpy as np
+    monkeypatch.setattr(rfb, "_LIB", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "librfbsoc.so"))
+    with pytest.raises(RuntimeError, match="no fallback"):
+        rfb.lib()
+    z = np.zeros(2 * 2 * 3)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        rfb.Solver((2, 2, 3), 1e-6, z.astype(np.uint8), np.zeros(3 * 2 * 3),
+                   np.zeros(2 * 3 * 3), np.zeros(2 * 2 * 4), 4e-10, 1e-7)
