@@ -76,3 +76,10 @@ def test_logpile_flow_rate_matches_the_paper():
     U, V, W, info = synth.stokes_flow(solid, 10e-6, dp=100.0, tol=1e-9)
     q_ml_h = info["q_m3_s"] * 3600e6
     assert abs(q_ml_h / 3.45 - 1.0) < 0.02, q_ml_h
+    # what the solver's create requires of a flow field: no inflow through the outlet or
+    # outflow through the inlet, nothing through fiber faces or side walls
+    assert np.all(W[0] >= 0.0) and np.all(W[-1] >= 0.0)
+    assert np.all(W[1:-1][solid[1:] | solid[:-1]] == 0.0)
+    assert np.all(U[:, :, 1:-1][solid[:, :, 1:] | solid[:, :, :-1]] == 0.0)
+    assert np.all(V[:, 1:-1, :][solid[:, 1:, :] | solid[:, :-1, :]] == 0.0)
+    assert np.all(U[:, :, [0, -1]] == 0.0) and np.all(V[:, [0, -1], :] == 0.0)
