@@ -145,15 +145,15 @@ MUTATIONS = [
     # U_mt (Eq. umt-def)
     ("umt_electrode_cells_at_zero",
      [("fixed[elec] = 1.0", "fixed[elec] = 0.0")],
-     "test_umt_bounds_and_upper_bound_on_utilisation", {}, None),
+     "test_umt_closed_form_of_a_channel_inside_electrode_cells", dict(inlet_bc="face"), None),
     ("umt_keeps_the_inlet_value",
      [('s_in = 0.0 if mode == "umt" else p.s_in', "s_in = p.s_in")],
-     "test_umt_independent_of_kinetics_and_inlet", {}, None),
+     "test_umt_closed_form_of_a_channel_inside_electrode_cells", dict(inlet_bc="face"), None),
     ("umt_unweighted_outlet_mean",
      [("return float(np.sum(np.where(fout, w * s3[-1], 0.0))) / "
        "float(np.sum(np.where(fout, w, 0.0)))",
        "return float(np.mean(s3[-1][fout]))")],
-     "test_umt_is_the_fast_kinetics_limit", {}, None),
+     "test_umt_closed_form_of_a_channel_inside_electrode_cells", dict(inlet_bc="ghost"), None),
     # kinetics mode 1: Newton's method with pseudo-transient continuation
     ("jacobian_without_reaction_slope",
      [("    d[k] = op.kappa[k] * rate_uniform_slope(s[k], op.kin.Vt, op.kin.alpha)\n"

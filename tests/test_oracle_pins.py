@@ -348,6 +348,32 @@ def test_umt_is_the_fast_kinetics_limit():
     assert np.abs(s[fl] - s_mt[fl]).max() < 1e-5
 
 
+@pytest.mark.parametrize("inlet_bc", ["face", "ghost"])
+def test_umt_closed_form_of_a_channel_inside_electrode_cells(inlet_bc):
+    """5 x 5 x n lattice with a solid outer ring: the centre column touches no fiber; its
+    four neighbours do, so in the U_mt problem (Eqs. np-fast-interior/np-fast-boundary)
+    they are held at 1, and the inlet is at 0. With flow only in the centre column the
+    centre's rows are the 1D channel's with K = 4 D / h^2 towards s* = 1 and E_in = -1, and
+    U_mt (Eq. umt-def) is the centre's outlet value."""
+    n, w, h, D = 30, 0.004, 1.25e-6, 4e-10
+    solid = np.ones((n, 5, 5), dtype=np.uint8)
+    solid[:, 1:4, 1:4] = 0
+    U = np.zeros((n, 5, 6))
+    V = np.zeros((n, 6, 5))
+    W = np.zeros((n + 1, 5, 5))
+    W[:, 2, 2] = w
+    p = soc.Problem(solid, U, V, W, h, D, 0.7, k0=3e-6, eta=-0.1, inlet_bc=inlet_bc)
+    g = 2.0 if inlet_bc == "face" else 1.0
+    e = _closed_form_1d(n, w / h, D / h ** 2, 4 * D / h ** 2, g, -1.0)
+    op = soc.assemble(p, "umt")
+    s = soc.steady_state(op).reshape(solid.shape)
+    assert np.allclose(s[:, 2, 2], 1.0 + e, rtol=0, atol=1e-12)
+    ring = np.ones((5, 5), dtype=bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = ring[2, 2] = False
+    assert np.all(s[:, ring] == 1.0)
+    assert abs(soc.umt(p) - (1.0 + e[-1])) <= 1e-12
+
+
 def test_umt_independent_of_kinetics_and_inlet():
     a = soc.umt(_p3(s_in=0.3, eta=-0.1, k0=1e-7))
     b = soc.umt(_p3(s_in=0.9, eta=-0.02, k0=5e-6))
