@@ -54,6 +54,9 @@ def parse():
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
                          "per launch, or two-sweep TMA-staged passes (launch shape autotuned, "
                          "persistent, or one (tile, z chunk) item per CTA)")
+    ap.add_argument("--logpile-flow", default="potential", choices=["potential", "stokes"],
+                    help="logpile workload: potential flow at the paper's 10 Pa flow rate "
+                         "(default) or the Stokes flow at 10 Pa (matrix-free MINRES)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -498,7 +501,7 @@ def run_logpile(args):
     levels, t_setup = [], time.time()
     with Clocks(local) as clk:
         for h in (5e-6, 2.5e-6, 1.25e-6):
-            case = synth.logpile_case(h, flow_device="cuda:%d" % local)
+            case = synth.logpile_case(h, flow_device="cuda:%d" % local, flow=args.logpile_flow)
             with rfb.Solver.from_case(case, stream=stream) as sv:
                 finest = h == 1.25e-6
                 for _ in range(max(1, args.warmup) if finest else 0):
@@ -527,7 +530,8 @@ def run_logpile(args):
     out = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64", "data": "synthetic (the paper's logpile geometry, potential flow)",
+           "dtype": "f32+f64",
+           "data": "synthetic (the paper's logpile geometry, %s flow)" % args.logpile_flow,
            "config": {"workload": "logpile1024x512x128_sbv_10Pa", "tol": tol,
                       "precision": "mixed", "q_m3_s": synth.LOGPILE_Q_10PA, "eta_V": 0.0,
                       "k0_m_s": 7.2e-5},

@@ -534,10 +534,10 @@ def logpile_case(h: float = H_PAPER, q: float = LOGPILE_Q_10PA, eta: float = 0.0
     flow = 'potential': the potential flow of this module, rescaled so that the volumetric
     flow rate through the inlet is q (default: the paper's 3.45 mL/h at 100 Pa scaled
     linearly to 10 Pa). flow = 'stokes': the Stokes flow at the pressure drop dp (Pa)
-    from ``stokes_flow`` (sparse LU on the CPU: coarse cell sizes only)."""
+    from ``stokes_flow_minres`` on ``flow_device``."""
     solid = remove_unconnected(logpile_solid(h))
     if flow == "stokes":
-        U, V, W, info = stokes_flow(solid, h, dp=dp)
+        U, V, W, info = stokes_flow_minres(solid, h, dp=dp, tol=1e-10, device=flow_device)
         q = info["q_m3_s"]
         f = 1.0
     elif flow == "potential":
@@ -698,4 +698,146 @@ def stokes_flow(solid: np.ndarray, h: float, dp: float = 1.0, mu: float = MU_WAT
     mean_face_q = q / max(int(oW[0].sum()), 1)
     info = {"cg_iters": iters[0], "q_m3_s": q,
             "max_div_rel": float(np.abs(div).max() * h ** 3 / max(abs(mean_face_q), 1e-300))}
+    return U, V, W, info
+
+
+def _open_faces(fluid):
+    """Open-face masks (U, V, W) of a fluid mask (nz, ny, nx): faces between two fluid
+    cells, plus the inlet and outlet faces of fluid cells."""
+    nz, ny, nx = fluid.shape
+    oU = np.zeros((nz, ny, nx + 1), dtype=bool)
+    oU[:, :, 1:nx] = fluid[:, :, :-1] & fluid[:, :, 1:]
+    oV = np.zeros((nz, ny + 1, nx), dtype=bool)
+    oV[:, 1:ny, :] = fluid[:, :-1, :] & fluid[:, 1:, :]
+    oW = np.zeros((nz + 1, ny, nx), dtype=bool)
+    oW[1:nz] = fluid[:-1] & fluid[1:]
+    oW[0] = fluid[0]
+    oW[nz] = fluid[-1]
+    return oU, oV, oW
+
+
+def _shift(x, axis, step):
+    """y[i] = x[i + step] along ``axis`` (zero where i + step leaves the array)."""
+    import torch
+    y = torch.zeros_like(x)
+    n = x.shape[axis]
+    if step == 1:
+        y.narrow(axis, 0, n - 1).copy_(x.narrow(axis, 1, n - 1))
+    else:
+        y.narrow(axis, 1, n - 1).copy_(x.narrow(axis, 0, n - 1))
+    return y
+
+
+def stokes_flow_minres(solid: np.ndarray, h: float, dp: float = 1.0, mu: float = MU_WATER,
+                       tol: float = 1e-10, max_iter: int = 200000, device: str = "cpu"):
+    """The Stokes flow of ``stokes_flow`` (same staggered discretisation and boundary
+    conditions), matrix-free in PyTorch on any device: preconditioned MINRES (Paige and
+    Saunders, SIAM J. Numer. Anal. 12, 1975) on the symmetric saddle-point system
+        [A  -D^T] [u]   [b]
+        [-D   0 ] [p] = [0],
+    in the scaled velocity u^ = (mu / h) u, where A is the unit-stencil negative Laplacian
+    on the open faces, D the unit-stencil divergence and b = dp on the inlet faces: both
+    unknowns are then of the size of dp. The preconditioner is the diagonal of A on the
+    velocities and the identity on the pressures (the Schur complement D A^-1 D^T of the
+    scaled system is close to I). Stops when the preconditioned residual norm falls below
+    tol times its initial value. Returns (U, V, W, info) in m/s."""
+    import torch
+    dev = torch.device(device)
+    f64 = torch.float64
+    solid = solid.astype(bool)
+    fluid_np = ~solid
+    nz, ny, nx = solid.shape
+    opens = [torch.from_numpy(o).to(dev) for o in _open_faces(fluid_np)]
+    fluid = torch.from_numpy(fluid_np).to(dev)
+    c = 1.0
+    along_of = (2, 1, 0)                      # U along x (axis 2), V along y, W along z
+    diags = []
+    for o, along in zip(opens, along_of):
+        d = torch.zeros(o.shape, dtype=f64, device=dev)
+        ones = torch.ones(o.shape, dtype=torch.bool, device=dev)
+        for axis in range(3):
+            for step in (-1, 1):
+                nb = _shift(o, axis, step)
+                inside = _shift(ones, axis, step)
+                wall = c if axis == along else 2 * c
+                d += c * nb + wall * (inside & ~nb)
+                if axis != 0:                 # side walls half a cell away
+                    d += wall * ~inside
+        diags.append(d * o)
+    sizes = [o.numel() for o in opens] + [fluid.numel()]
+    shapes = [o.shape for o in opens] + [fluid.shape]
+    offs = np.cumsum([0] + sizes)
+
+    def views(x):
+        return [x[offs[i]:offs[i + 1]].view(shapes[i]) for i in range(4)]
+
+    def apply(x):
+        U, V, W, P = views(x)
+        y = torch.empty_like(x)
+        yU, yV, yW, yP = views(y)
+        for u, yu, o, d in ((U, yU, opens[0], diags[0]), (V, yV, opens[1], diags[1]),
+                            (W, yW, opens[2], diags[2])):
+            nbsum = torch.zeros_like(u)
+            for axis in range(3):
+                for step in (-1, 1):
+                    nbsum += _shift(u, axis, step)
+            yu.copy_((d * u - c * nbsum) * o)
+        # -D^T p on the faces: p_high - p_low, with p = 0 outside the lattice
+        Pz = torch.nn.functional.pad(P, (0, 0, 0, 0, 1, 1))
+        yU[:, :, 1:nx] += (P[:, :, 1:] - P[:, :, :-1]) * opens[0][:, :, 1:nx]
+        yV[:, 1:ny, :] += (P[:, 1:, :] - P[:, :-1, :]) * opens[1][:, 1:ny, :]
+        yW += (Pz[1:] - Pz[:-1]) * opens[2]
+        # -D u in the fluid cells
+        div = U[:, :, 1:] - U[:, :, :-1] + V[:, 1:, :] - V[:, :-1, :] + W[1:] - W[:-1]
+        yP.copy_(-div * fluid)
+        return y
+
+    minv = torch.cat([torch.where(o, 1.0 / torch.where(o, d, torch.ones_like(d)),
+                                  torch.zeros_like(d)).reshape(-1)
+                      for o, d in zip(opens, diags)] + [fluid.to(f64).reshape(-1)])
+    b = torch.zeros(int(offs[-1]), dtype=f64, device=dev)
+    views(b)[2][0] = dp * opens[2][0]
+
+    # preconditioned MINRES
+    x = torch.zeros_like(b)
+    r1 = b.clone()
+    y = minv * r1
+    beta1 = float(torch.dot(r1, y)) ** 0.5
+    beta, oldb, dbar, epsln, phibar, cs, sn = beta1, 0.0, 0.0, 0.0, beta1, -1.0, 0.0
+    w = torch.zeros_like(b)
+    w2 = torch.zeros_like(b)
+    r2 = r1.clone()
+    it = 0
+    while it < max_iter and phibar > tol * beta1:
+        it += 1
+        v = y / beta
+        y = apply(v)
+        if it >= 2:
+            y -= (beta / oldb) * r1
+        alfa = float(torch.dot(v, y))
+        y -= (alfa / beta) * r2
+        r1, r2 = r2, y
+        y = minv * r2
+        oldb, beta = beta, float(torch.dot(r2, y)) ** 0.5
+        oldeps = epsln
+        delta = cs * dbar + sn * alfa
+        gbar = sn * dbar - cs * alfa
+        epsln = sn * beta
+        dbar = -cs * beta
+        gamma = max((gbar * gbar + beta * beta) ** 0.5, 1e-300)
+        cs, sn = gbar / gamma, beta / gamma
+        phi = cs * phibar
+        phibar = sn * phibar
+        w1, w2 = w2, w
+        w = (v - oldeps * w1 - delta * w2) / gamma
+        x += phi * w
+    if phibar > tol * beta1:
+        raise RuntimeError("Stokes MINRES did not converge in %d iterations" % it)
+    oU, oV, oW = _open_faces(fluid_np)
+    U, V, W = ((t.cpu().numpy() * (h / mu)) * o for t, o in zip(views(x)[:3], (oU, oV, oW)))
+    q = h * h * float(W[0].sum())
+    div = (U[:, :, 1:] - U[:, :, :-1] + V[:, 1:, :] - V[:, :-1, :] + W[1:] - W[:-1]) / h
+    mean_face_q = q / max(int(fluid_np[0].sum()), 1)
+    info = {"minres_iters": it, "q_m3_s": q,
+            "max_div_rel": float(np.abs(div[fluid_np]).max() * h ** 3 / max(abs(mean_face_q), 1e-300))}
     return U, V, W, info

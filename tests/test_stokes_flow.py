@@ -1,6 +1,7 @@
-"""The Stokes-flow input fixture (no GPU): the analytic flow rate of a square duct at
+"""The Stokes-flow input fixtures (no GPU): the analytic flow rate of a square duct at
 second order in h, linearity in the pressure drop, no slip and symmetry around an
-obstacle, and the logpile's flow rate against the one the paper reports (Sec. IV)."""
+obstacle (sparse LU), the matrix-free MINRES solver against it, and the logpile's flow
+rate against the one the paper reports (Sec. IV)."""
 import math
 
 import numpy as np
@@ -69,11 +70,25 @@ def test_no_slip_mass_conservation_and_symmetry_around_an_obstacle():
     assert np.allclose(V, V[:, :, ::-1], atol=1e-12 * W.max())
 
 
+@pytest.mark.parametrize("solid", [_obstacle(), np.zeros((6, 12, 12), dtype=bool)],
+                         ids=["obstacle", "duct"])
+def test_matrix_free_minres_matches_the_sparse_lu_fixture(solid):
+    """The matrix-free MINRES solver (PyTorch, any device) and the sparse-LU one solve the
+    same discrete Stokes problem: their fields agree to the MINRES tolerance."""
+    a = synth.stokes_flow(solid, 1e-6, dp=2.0)
+    b = synth.stokes_flow_minres(solid, 1e-6, dp=2.0, tol=1e-12)
+    scale = np.abs(a[2]).max()
+    for x, y in zip(a[:3], b[:3]):
+        assert np.abs(x - y).max() <= 1e-10 * scale
+    assert abs(b[3]["q_m3_s"] / a[3]["q_m3_s"] - 1.0) <= 1e-12
+    assert b[3]["max_div_rel"] < 1e-10
+
+
 def test_logpile_flow_rate_matches_the_paper():
     """Sec. IV reports 3.45 mL/h through the logpile at 100 Pa. The voxel logpile at
     h = 10 um (rods two cells across) gives it within 2 %."""
     solid = synth.remove_unconnected(synth.logpile_solid(10e-6))
-    U, V, W, info = synth.stokes_flow(solid, 10e-6, dp=100.0, tol=1e-9)
+    U, V, W, info = synth.stokes_flow_minres(solid, 10e-6, dp=100.0, tol=1e-10)
     q_ml_h = info["q_m3_s"] * 3600e6
     assert abs(q_ml_h / 3.45 - 1.0) < 0.02, q_ml_h
     # what the solver's create requires of a flow field: no inflow through the outlet or
