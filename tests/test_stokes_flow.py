@@ -1,7 +1,7 @@
 """The Stokes-flow input fixtures (no GPU): the analytic flow rate of a square duct at
 second order in h, linearity in the pressure drop, no slip and symmetry around an
-obstacle (sparse LU), the matrix-free MINRES solver against it, and the logpile's flow
-rate against the one the paper reports (Sec. IV)."""
+obstacle (sparse LU), the matrix-free MINRES solver against it, and the magnitude of the
+logpile's flow rate against the one the paper reports (Sec. IV)."""
 import math
 
 import numpy as np
@@ -84,13 +84,16 @@ def test_matrix_free_minres_matches_the_sparse_lu_fixture(solid):
     assert b[3]["max_div_rel"] < 1e-10
 
 
-def test_logpile_flow_rate_matches_the_paper():
-    """Sec. IV reports 3.45 mL/h through the logpile at 100 Pa. The voxel logpile at
-    h = 10 um (rods two cells across) gives it within 2 %."""
+def test_logpile_flow_rate_is_of_the_papers_magnitude():
+    """Sec. IV reports 3.45 mL/h through the logpile at 100 Pa (cut cells at 1.25 um). The
+    voxel logpile is not converged at the cell sizes a CPU reaches: 3.457 mL/h at 10 um
+    (rods two cells across) and 2.919 at 5 um. So this checks only the magnitude (within
+    20 %) and what the solver requires of the field; the fixture itself is pinned by the
+    duct, the sparse-LU solve, linearity and symmetry above."""
     solid = synth.remove_unconnected(synth.logpile_solid(10e-6))
     U, V, W, info = synth.stokes_flow_minres(solid, 10e-6, dp=100.0, tol=1e-10)
     q_ml_h = info["q_m3_s"] * 3600e6
-    assert abs(q_ml_h / 3.45 - 1.0) < 0.02, q_ml_h
+    assert abs(q_ml_h / 3.45 - 1.0) < 0.2, q_ml_h
     # what the solver's create requires of a flow field: no inflow through the outlet or
     # outflow through the inlet, nothing through fiber faces or side walls
     assert np.all(W[0] >= 0.0) and np.all(W[-1] >= 0.0)
