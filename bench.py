@@ -62,22 +62,14 @@ def parse():
     return ap.parse_args()
 
 
+from paper_2502_08034_gb300.workflows import reduce_over_ranks, upsample_chain  # noqa: E402
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
-
-
-def reduce_over_ranks(dist, elapsed_ms, units, device="cpu"):
-    """Max of the timed region and sum of the cell updates over ranks (replicas)."""
-    import torch
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
-    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    return float(t.item()), float(u.item())
 
 
 def make_case(dims, device):
@@ -329,19 +321,6 @@ def run_batch(args):
     batch.close()
     for s in solvers:
         s.close()
-
-
-def upsample_chain(solvers, cases, tol, umt=True):
-    """Solve the coarsest level cold, then prolong and solve each finer level (mixed)."""
-    out = []
-    for q, (sv, c) in enumerate(zip(solvers, cases)):
-        if q == 0:
-            sv.reset_state()
-        else:
-            sv.upsample_from(solvers[q - 1])
-        out.append(sv.solve(c.s_in, c.eta, tol, precision="mixed"))
-    u = solvers[-1].umt(tol, precision="mixed") if umt else None
-    return out, u
 
 
 def run_upsample(args):

@@ -220,8 +220,11 @@ rfb_status rfb_soc_step(rfb_soc_handle* h, double s_in, double eta, int64_t n_sw
 rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res);
 
 /*
- * Same outputs as rfb_soc_current, computed by the same FP64 kernel and fixed-order
- * reduction, but without touching any device memory that needs allocating: the
+ * Same outputs as rfb_soc_current, computed in FP64 by the matrix-free check kernel
+ * (coefficients built from the face velocities; rfb_soc_current applies the assembled
+ * operator, so the two agree up to rounding, ~1e-16 of the largest RHS term per cell)
+ * and the same fixed-order reduction, but without touching any device memory that
+ * needs allocating: the
  * per-block partial sums go to a static device array of 65,600 bytes (8192 blocks x 8
  * sums + 8 totals) that every GPU loading this library holds until the process exits.
  * The paper has no counterpart; this exists for callers that cannot allocate at the
@@ -231,8 +234,11 @@ rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res);
  *   res   host struct, filled like rfb_soc_current (sweeps = 0, checks = 1)
  * Errors: RFB_ERR_STATE without a state; RFB_ERR_INVALID_ARG if the lattice needs more
  * than 8192 reduction blocks (about nx*ny > 2,000,000; use rfb_soc_current then).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress
- * with that device current); make that first call before any stream capture begins.
+ * Every call made outside a stream capture looks up the array's device address
+ * (cudaGetSymbolAddress with the handle's device current; after a cudaDeviceReset the
+ * module is reloaded and the address may change). A call during a capture uses the
+ * address of the last uncaptured call on that device, so make the first call on a
+ * device before any stream capture begins (RFB_ERR_STATE otherwise).
  * All calls in the process share the one array and its contents stay behind after a
  * call; calls whose work overlaps on the GPU (other streams, other handles, other host
  * threads) race on it and must be serialised by the caller.

@@ -17,7 +17,8 @@ LIB = os.path.join(HERE, "librfbsoc.so")            # the solver (C ABI of inclu
 SYNTH_LIB = os.path.join(HERE, "librfbsynth.so")    # potential-flow input generator
 TARGETS = {
     LIB: ([os.path.join(CSRC, "rfb_soc.cu")],
-          [os.path.join(CSRC, "soc_kernels.cuh"), os.path.join(ROOT, "include", "rfb_soc.h")]),
+          [os.path.join(CSRC, "soc_kernels.cuh"), os.path.join(CSRC, "sweep_tb.cuh"),
+           os.path.join(ROOT, "include", "rfb_soc.h")]),
     SYNTH_LIB: ([os.path.join(CSRC, "synth_flow.cu")], []),
 }
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

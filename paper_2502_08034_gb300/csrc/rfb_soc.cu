@@ -93,6 +93,8 @@ struct rfb_soc_handle {
     int df_cur = 0;
     float2* d_gdf = nullptr;      // adjoint source as pairs (mixed-precision adjoints)
     double scaled_beta = NAN;
+    double* d_stage = nullptr;    // N doubles: host inputs of set_state / set_area_mult
+                                  // (allocated on the first such call, then reused)
 
     int64_t n_fluid = 0, n_elec = 0;
     double sum_w_in = 0, sum_w_out = 0;     // unscaled sums of inlet / outlet W
@@ -215,20 +217,27 @@ void reduce_readback(rfb_soc_handle* h, int min_slot0) {
     CK(h, cudaStreamSynchronize(h->stream));
 }
 
+// Face velocities times beta / h (FP64 and FP32 copies) for the velocity scale beta;
+// nothing is launched when they already hold that scale. Every kernel that builds
+// coefficients reads these copies, so each entry point that evaluates an operating point
+// calls this first (an intervening U_mt solve or adjoint may have used another scale).
+void rescale_velocities(rfb_soc_handle* h, double beta) {
+    if (h->scaled_beta == beta) return;
+    const double sc = beta / h->h;
+    const int64_t N = h->N;
+    scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_u, h->d_us, h->d_u32, sc, N);
+    LAUNCHED(h);
+    scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_v, h->d_vs, h->d_v32, sc, N);
+    LAUNCHED(h);
+    scale_kernel<<<flat_grid(N + h->nxny), 256, 0, h->stream>>>(h->d_w, h->d_ws, h->d_w32,
+                                                                sc, N + h->nxny);
+    LAUNCHED(h);
+    h->scaled_beta = beta;
+}
+
 // Prepare velocities, tables and dt for an operating point.
 void prepare(rfb_soc_handle* h, OpPoint& op) {
-    if (!(h->scaled_beta == op.beta)) {
-        const double sc = op.beta / h->h;
-        const int64_t N = h->N;
-        scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_u, h->d_us, h->d_u32, sc, N);
-        LAUNCHED(h);
-        scale_kernel<<<flat_grid(N), 256, 0, h->stream>>>(h->d_v, h->d_vs, h->d_v32, sc, N);
-        LAUNCHED(h);
-        scale_kernel<<<flat_grid(N + h->nxny), 256, 0, h->stream>>>(h->d_w, h->d_ws, h->d_w32,
-                                                                    sc, N + h->nxny);
-        LAUNCHED(h);
-        h->scaled_beta = op.beta;
-    }
+    rescale_velocities(h, op.beta);
     kinetics_AB(h->kin, op.eta, &op.A, &op.B, &op.K1);
     Coef<double> C = make_coef<double>(h, op, false, false);
     const bool local = op.dt_mode == RFB_DT_LOCAL;
@@ -886,7 +895,7 @@ void free_all(rfb_soc_handle* h) {
     // the arena holds flags .. partials; the rest are allocated on first use
     void* ptrs[] = {h->d_arena, h->d_m,    h->d_m32,  h->d_lam[0], h->d_lam[1], h->d_g,
                     h->d_grad,  h->d_L64,  h->d_L2F,  h->d_eta,    h->d_elec,   h->d_sdf[0],
-                    h->d_sdf[1], h->d_gdf};
+                    h->d_sdf[1], h->d_gdf,  h->d_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -1171,6 +1180,7 @@ rfb_status rfb_soc_current(rfb_soc_handle* h, rfb_solve_result* res) {
     }
     try {
         OpPoint op = h->op;
+        rescale_velocities(h, op.beta);
         check(h, op, false);
         rfb_solve_result r{};
         r.checks = 1;
@@ -1366,11 +1376,10 @@ rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind ki
     h->have_eta = false;
     try {
         const double* src = s;
-        double* tmp = nullptr;
         if (kind == RFB_MEM_HOST) {
-            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
-            CK(h, cudaMemcpyAsync(tmp, s, h->N * 8, cudaMemcpyHostToDevice, h->stream));
-            src = tmp;
+            if (!h->d_stage) dalloc(h, &h->d_stage, h->N);
+            CK(h, cudaMemcpyAsync(h->d_stage, s, h->N * 8, cudaMemcpyHostToDevice, h->stream));
+            src = h->d_stage;
         }
         CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned long long), h->stream));
         set_state_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(h->d_flags, src, h->d_s[0],
@@ -1379,7 +1388,6 @@ rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind ki
         unsigned long long bad = 0;
         CK(h, cudaMemcpyAsync(&bad, h->d_err, sizeof bad, cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
-        if (tmp) cudaFree(tmp);
         h->s_cur = 0;
         h->have_state = true;
         h->s_converged = false;
@@ -1437,19 +1445,17 @@ rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kin
     try {
         // validate on the device (count of entries that are not finite and > 0) before
         // anything is replaced; NULL restores 1 everywhere
-        const double* src = nullptr;
-        double* tmp = nullptr;
-        if (m && kind == RFB_MEM_HOST) {
-            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
-            CK(h, cudaMemcpyAsync(tmp, m, h->N * 8, cudaMemcpyHostToDevice, h->stream));
-            src = tmp;
-        } else if (m) {
-            src = m;
-        } else {
-            CK(h, cudaMalloc((void**)&tmp, h->N * 8));
-            fill_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(tmp, 1.0, h->N);
-            LAUNCHED(h);
-            src = tmp;
+        const double* src = m;
+        if (!m || kind == RFB_MEM_HOST) {
+            if (!h->d_stage) dalloc(h, &h->d_stage, h->N);
+            if (m) {
+                CK(h, cudaMemcpyAsync(h->d_stage, m, h->N * 8, cudaMemcpyHostToDevice,
+                                      h->stream));
+            } else {
+                fill_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(h->d_stage, 1.0, h->N);
+                LAUNCHED(h);
+            }
+            src = h->d_stage;
         }
         const int sblocks = (int)std::min<int64_t>(h->nblocks, 2048);
         stats_kernel<<<sblocks, 256, 0, h->stream>>>(h->d_flags, h->d_w, src, h->N, h->nxny,
@@ -1461,7 +1467,6 @@ rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kin
                               h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
         if (h->h_red[4] > 0) {
-            if (tmp) cudaFree(tmp);
             set_err(h, "area_mult must be finite and > 0 (%.0f cells are not)", h->h_red[4]);
             return RFB_ERR_INVALID_ARG;
         }
@@ -1472,7 +1477,6 @@ rfb_status rfb_soc_set_area_mult(rfb_soc_handle* h, const double* m, rfb_mem_kin
         scale_kernel<<<flat_grid(h->N), 256, 0, h->stream>>>(src, h->d_m, h->d_m32, 1.0, h->N);
         LAUNCHED(h);
         CK(h, cudaStreamSynchronize(h->stream));
-        cudaFree(tmp);
         h->s_converged = false;   // the operator changed; the state stays as a warm start
         ++h->area_version;
     } catch (Fail f) {
@@ -1761,9 +1765,11 @@ rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
 // they want the outputs: a runtime whose caching allocator already owns the device's
 // memory budget, or a monitor on a latency-critical path that must not pay for the
 // implicit device synchronisation of cudaMalloc/cudaFree. rfb_soc_current_noalloc serves
-// them: the same FP64 check kernel and fixed-order reduction, but the scratch is the
-// file-scope array below, present on every device that loads this library until the
-// process exits.
+// them: the matrix-free FP64 check kernel (check_kernel, which builds each cell's
+// coefficients from the face velocities; rfb_soc_current runs check64c_kernel on the
+// assembled operator, so the two agree up to rounding) and the same fixed-order
+// reduction, but the scratch is the file-scope array below, present on every device that
+// loads this library until the process exits.
 // =====================================================================================
 namespace {
 
@@ -1774,16 +1780,30 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * N
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[256] = {};   // device address of g_noalloc_scratch, per device
 
-// Device address of the scratch on h's device, looked up once per device with that
-// device current (h's device is made current by guard()). In host code the symbol's
-// name is only a host-side stand-in, so kernels must be given this address.
+// Device address of the scratch on h's device, looked up with that device current (h's
+// device is made current by guard()). In host code the symbol's name is only a host-side
+// stand-in, so kernels must be given this address. It is looked up again on every call
+// made outside a stream capture (a cudaDeviceReset reloads the module, and the array may
+// then sit elsewhere); during a capture the address from the last uncaptured call on
+// that device is used, so the first call on a device must come before any capture.
 rfb_status noalloc_scratch(rfb_soc_handle* h, double** out) {
     if (h->device < 0 || h->device >= 256) {
         set_err(h, "device ordinal %d out of range", h->device);
         return RFB_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(h->stream, &cap);
+    if (ce != cudaSuccess) {
+        set_err(h, "cudaStreamIsCapturing failed: %s", cudaGetErrorString(ce));
+        return RFB_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[h->device]) {
+    if (cap != cudaStreamCaptureStatusNone && !g_noalloc_addr[h->device]) {
+        set_err(h, "the first rfb_soc_current_noalloc call on a device must come before any "
+                "stream capture");
+        return RFB_ERR_STATE;
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -1821,6 +1841,7 @@ extern "C" rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_resul
         // call, and finalize_kernel writes every final slot, so nothing left over from an
         // earlier call is read and nothing has to be cleared first.
         const OpPoint op = h->op;
+        rescale_velocities(h, op.beta);   // allocates nothing
         Coef<double> C = make_coef<double>(h, op, false, false);
         double* partials = scratch;
         double* sums = scratch + NOALLOC_MAX_BLOCKS * NRED;

@@ -55,3 +55,20 @@ def test_timeout_stops_an_adjoint_and_a_batch():
         with pytest.raises(rfb.RfbError) as e:
             sv.solve(case.s_in, case.eta, 1e-8, timeout_ms=-1)
         assert e.value.status == rfb.RFB_ERR_INVALID_ARG
+
+
+def test_outputs_after_a_umt_solve_at_another_velocity_scale():
+    """rfb_soc_current evaluates the last solve's operating point, velocity scale
+    included, even after a U_mt solve (or an adjoint) used another scale in between."""
+    from paper_2502_08034_gb300 import rfb
+    from tests._cases import fiber_case
+    case = fiber_case((16, 16, 32))
+    with rfb.Solver.from_case(case) as sv:
+        r = sv.solve(case.s_in, case.eta, 1e-12, precision="fp64", velocity_scale=1.0)
+        before = sv.current()
+        sv.umt(1e-10, precision="fp64", velocity_scale=2.0)
+        after = sv.current()
+    for k in ("residual", "I_tot", "F_in", "F_out", "F_in_adv", "U", "outlet_mean",
+              "mass_balance_rel"):
+        assert after[k] == before[k], k
+    assert before["I_tot"] == pytest.approx(r["I_tot"], rel=1e-12)

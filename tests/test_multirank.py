@@ -19,11 +19,11 @@ def _free_port():
 def _worker(rank, world, port, q):
     import torch.distributed as dist
 
-    import bench
+    from paper_2502_08034_gb300 import workflows
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    t, u = bench.reduce_over_ranks(dist, 100.0 + 50.0 * rank, 1000 * (rank + 1))
+    t, u = workflows.reduce_over_ranks(dist, 100.0 + 50.0 * rank, 1000 * (rank + 1))
     q.put((rank, t, u))
     dist.barrier()
     dist.destroy_process_group()
@@ -46,5 +46,5 @@ def test_replicas_reduce_max_time_and_sum_units():
 
 
 def test_single_rank_passthrough():
-    import bench
-    assert bench.reduce_over_ranks(None, 12.5, 7) == (12.5, 7.0)
+    from paper_2502_08034_gb300 import workflows
+    assert workflows.reduce_over_ranks(None, 12.5, 7) == (12.5, 7.0)
