@@ -334,8 +334,7 @@ def run_upsample(args):
     torch.cuda.set_device(local)
     _build.build()
     t0 = time.time()
-    cases = synth.multilevel_cases((512, 512, 1024), 3, 0.82, 8.0, 5, 0.01, -0.10, 0.5,
-                                   args.tol, flow_device="cuda:%d" % local)
+    cases = synth.upsampling_cases(flow_device="cuda:%d" % local)
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream()
     solvers = [rfb.Solver.from_case(c, device_inputs=True, stream=stream) for c in cases]

@@ -522,8 +522,33 @@ def _advection_only(p: Problem, mode: str) -> Operator:
     return assemble(q, mode=mode)
 
 
-def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
-    """Adjoint state and gradients at the steady state s (solved here if None)."""
+def transposed_iterate(A: sp.spmatrix, g: np.ndarray, cfl: float, tol: float,
+                       max_steps: int = 10_000_000, check_every: int = 100):
+    """Explicit pseudo-time iteration of A^T lam + g = 0 with the local step
+    dt_c = cfl / d_c, d_c = -A_cc (A and A^T share their diagonal): lam <- lam +
+    dt (A^T lam + g), from lam = 0, the forward loop of Algorithm 7 applied to the
+    transposed operator, until ||A^T lam + g||_2 <= tol ||g||_2. Returns (lam, steps)."""
+    At = A.T.tocsr()
+    d = -A.diagonal()
+    dt = cfl / d
+    lam = np.zeros(A.shape[0])
+    gn = float(np.linalg.norm(g))
+    n = 0
+    while n < max_steps:
+        lam = lam + dt * (At @ lam + g)
+        n += 1
+        if n % check_every == 0 and float(np.linalg.norm(At @ lam + g)) <= tol * gn:
+            break
+    return lam, n
+
+
+def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot", direct_max: int = 40000,
+            rtol: float = 1e-14, iter_tol: float = 1e-13) -> dict:
+    """Adjoint state and gradients at the steady state s (solved here if None).
+
+    L^T lam = -dJ/ds: sparse LU up to ``direct_max`` unknowns; larger affine problems
+    (kinetics mode 0) by the explicit transposed iteration ``transposed_iterate`` to a
+    relative residual of ``iter_tol`` (the forward pseudo-time loop applied to L^T)."""
     mode = "umt" if objective == "U_mt" else "sbv"
     op = assemble(p, mode)
     if s is None:
@@ -560,7 +585,13 @@ def adjoint(p: Problem, s: np.ndarray, objective: str = "I_tot") -> dict:
         raise ValueError(objective)
     Luu = jacobian(op, s)[u][:, u]
     lam = np.zeros(N)
-    lam[u] = spla.spsolve(Luu.T.tocsc(), -g[u])
+    if Luu.shape[0] <= direct_max:
+        lam[u] = spla.spsolve(Luu.T.tocsc(), -g[u])
+    elif not op.nonlinear:
+        lam[u], _ = transposed_iterate(Luu, g[u], 0.4, iter_tol)
+    else:
+        raise ValueError("the oracle's kinetics-mode-1 adjoint is direct only (<= %d unknowns)"
+                         % direct_max)
     # gradients
     dm = np.zeros(N)
     if objective == "I_tot":

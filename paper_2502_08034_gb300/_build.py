@@ -15,12 +15,15 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librfbsoc.so")            # the solver (C ABI of include/rfb_soc.h)
 SYNTH_LIB = os.path.join(HERE, "librfbsynth.so")    # potential-flow input generator
+HOST_SYNTH_LIB = os.path.join(HERE, "librfbsynth_host.so")   # the same on the host CPU
 TARGETS = {
     LIB: ([os.path.join(CSRC, "rfb_soc.cu")],
           [os.path.join(CSRC, "soc_kernels.cuh"), os.path.join(CSRC, "sweep_tb.cuh"),
            os.path.join(ROOT, "include", "rfb_soc.h")]),
     SYNTH_LIB: ([os.path.join(CSRC, "synth_flow.cu")], []),
+    HOST_SYNTH_LIB: ([os.path.join(CSRC, "synth_flow_cpu.c")], []),
 }
+HOST_TARGETS = {HOST_SYNTH_LIB}   # plain C (gcc), no CUDA
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -41,6 +44,10 @@ def cuda_lib_dir() -> str:
 
 def command(out: str = LIB, extra=(), target: str = LIB):
     sources = TARGETS[target][0]
+    if target in HOST_TARGETS:
+        # fixed-order sums and no contraction into FMA: the same result on every host
+        return [os.environ.get("CC", "gcc"), "-O2", "-fopenmp", "-ffp-contract=off", "-shared",
+                "-fPIC", *extra, "-o", out, *sources, "-lm"]
     return [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
             "-cudart", "shared", "-I", os.path.join(ROOT, "include"),
             "-Xlinker", "-rpath," + cuda_lib_dir(), *extra, "-o", out, *sources]
@@ -65,14 +72,14 @@ def _build_one(target: str, force: bool, verbose: bool):
                                          text=True)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile both libraries (in parallel); returns the solver library path."""
-    jobs = [j for j in (_build_one(t, force, verbose) for t in TARGETS) if j]
+def build(force: bool = False, verbose: bool = False, targets=None) -> str:
+    """Compile the libraries (in parallel); returns the solver library path."""
+    jobs = [j for j in (_build_one(t, force, verbose) for t in (targets or TARGETS)) if j]
     errors = []
     for target, tmp, proc in jobs:
         out, err = proc.communicate()
         if proc.returncode != 0:
-            errors.append("nvcc failed for %s:\n%s%s" % (os.path.basename(target), out, err))
+            errors.append("build failed for %s:\n%s%s" % (os.path.basename(target), out, err))
         else:
             os.replace(tmp, target)
     if errors:

@@ -154,106 +154,46 @@ def remove_unconnected(solid: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------------------
 
 def potential_flow(solid: np.ndarray, h: float, u_mean: float, tol: float = 1e-12,
-                   device: str = "cpu", max_iter: int = 200000, check_every: int = 25):
+                   device: str = "cpu", max_iter: int = 200000, check_every: int = 25,
+                   threads: int = 0):
     """Discrete potential flow on the fluid cells of ``solid``.
 
     Returns (U, V, W, info) as float64 numpy arrays in the face layouts of this module;
     info holds the CG iteration count and the achieved max |div u| / u_mean.
-    On a CUDA device the native fixture solver (librfbsynth.so) runs; on the CPU a torch
-    CG of the same equations."""
+    On a CUDA device the native fixture solver (librfbsynth.so) runs; on the CPU its host
+    counterpart (librfbsynth_host.so, OpenMP, ``threads`` <= 0: the default count), the
+    same equations and stopping rule, with results independent of the thread count."""
     if str(device).startswith("cuda"):
         return _potential_flow_native(solid, h, u_mean, tol, max_iter, device)
-    import torch
+    return _potential_flow_host(solid, h, u_mean, tol, max_iter, max(check_every, 1) * 8,
+                                threads)
 
-    dev = torch.device(device)
-    f = torch.from_numpy(~solid).to(dev)
-    nz, ny, nx = f.shape
-    fd = f.double()
-    gx = (f[:, :, 1:] & f[:, :, :-1]).double()
-    gy = (f[:, 1:, :] & f[:, :-1, :]).double()
-    gz = (f[1:] & f[:-1]).double()
-    gin = fd[0]
-    gout = fd[-1]
-    diag = torch.zeros_like(fd)
-    diag[:, :, 1:] += gx
-    diag[:, :, :-1] += gx
-    diag[:, 1:, :] += gy
-    diag[:, :-1, :] += gy
-    diag[1:] += gz
-    diag[:-1] += gz
-    diag[0] += 2.0 * gin
-    diag[-1] += 2.0 * gout
-    inv_diag = torch.where(diag > 0, 1.0 / torch.where(diag > 0, diag, torch.ones_like(diag)),
-                           torch.zeros_like(diag))
 
-    def apply_a(p):
-        out = diag * p
-        t = gx * (p[:, :, 1:]); out[:, :, :-1] -= t
-        t = gx * (p[:, :, :-1]); out[:, :, 1:] -= t
-        t = gy * (p[:, 1:, :]); out[:, :-1, :] -= t
-        t = gy * (p[:, :-1, :]); out[:, 1:, :] -= t
-        t = gz * p[1:]; out[:-1] -= t
-        t = gz * p[:-1]; out[1:] -= t
-        return out
+def _potential_flow_host(solid, h, u_mean, tol, max_iter, check_every, threads):
+    import ctypes
 
-    b = torch.zeros_like(fd)
-    b[0] = 2.0 * gin
-    # initial guess: linear profile in z on fluid cells
-    zc = (torch.arange(nz, device=dev, dtype=torch.float64) + 0.5) / nz
-    x = (1.0 - zc)[:, None, None] * fd
-    r = b - apply_a(x)
-    z = inv_diag * r
-    p = z.clone()
-    rz = torch.sum(r * z)
+    from . import _build
 
-    def w_mean_unscaled(xv):
-        wz = torch.zeros((nz + 1, ny, nx), dtype=torch.float64, device=dev)
-        wz[0] = 2.0 * (1.0 - xv[0]) * gin / h
-        wz[-1] = 2.0 * xv[-1] * gout / h
-        wz[1:-1] = -(xv[1:] - xv[:-1]) * gz / h
-        cnt = gin.sum() + gout.sum() + gz.sum()
-        return wz, float(wz.sum() / cnt)
-
-    it = 0
-    achieved = float("inf")
-    while it < max_iter:
-        for _ in range(check_every):
-            ap = apply_a(p)
-            alpha = rz / torch.sum(p * ap)
-            x += alpha * p
-            r -= alpha * ap
-            z = inv_diag * r
-            rz_new = torch.sum(r * z)
-            p = z + (rz_new / rz) * p
-            rz = rz_new
-            it += 1
-        rtrue = b - apply_a(x)
-        _, wm = w_mean_unscaled(x)
-        achieved = float(rtrue.abs().max()) / (h * wm)
-        if achieved < 0.5 * tol:
-            break
-        if float(r.abs().max()) < 0.05 * tol * h * wm:
-            # recursive residual has drifted below the true one: restart from x
-            r = rtrue
-            z = inv_diag * r
-            p = z.clone()
-            rz = torch.sum(r * z)
-
-    wz, wm = w_mean_unscaled(x)
-    sigma = u_mean / wm
-    U = torch.zeros((nz, ny, nx + 1), dtype=torch.float64, device=dev)
-    V = torch.zeros((nz, ny + 1, nx), dtype=torch.float64, device=dev)
-    U[:, :, 1:-1] = -(x[:, :, 1:] - x[:, :, :-1]) * gx / h * sigma
-    V[:, 1:-1, :] = -(x[:, 1:, :] - x[:, :-1, :]) * gy / h * sigma
-    W = wz * sigma
-    # inflow / outflow through the inlet and outlet planes is >= 0 in the exact solution
-    W[0] = torch.clamp(W[0], min=0.0)
-    W[-1] = torch.clamp(W[-1], min=0.0)
-    div = (U[:, :, 1:] - U[:, :, :-1]) + (V[:, 1:, :] - V[:, :-1, :]) + (W[1:] - W[:-1])
-    div = div * fd
-    info = {"cg_iters": it, "max_div_rel": float(div.abs().max()) / u_mean,
-            "superficial_q": float(W[0].sum()) / (nx * ny)}
-    return U.cpu().numpy(), V.cpu().numpy(), W.cpu().numpy(), info
+    if not os.path.exists(_build.HOST_SYNTH_LIB):
+        _build.build(targets=[_build.HOST_SYNTH_LIB])
+    lib = ctypes.CDLL(_build.HOST_SYNTH_LIB)
+    f = lib.rfb_synth_potential_flow_cpu
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [ctypes.c_int] * 2 + \
+        [ctypes.c_void_p] * 5 + [ctypes.c_int]
+    nz, ny, nx = solid.shape
+    sol = np.ascontiguousarray(solid, dtype=np.uint8)
+    U = np.empty((nz, ny, nx + 1))
+    V = np.empty((nz, ny + 1, nx))
+    W = np.empty((nz + 1, ny, nx))
+    info = np.zeros(4)
+    rc = f(nx, ny, nz, h, u_mean, tol, max_iter, check_every, sol.ctypes.data, U.ctypes.data,
+           V.ctypes.data, W.ctypes.data, info.ctypes.data, int(threads))
+    if rc not in (0, 3):
+        raise RuntimeError("host potential-flow solver failed (code %d)" % rc)
+    out = {"cg_iters": int(info[0]), "max_div_rel": float(info[1]),
+           "true_residual_rel": float(info[2]), "superficial_q": float(info[3])}
+    return U, V, W, out
 
 
 def _potential_flow_native(solid, h, u_mean, tol, max_iter, device):
@@ -345,15 +285,18 @@ def build_case(name: str, dims, porosity: float, diameter, seed: int, u_mean: fl
 def multilevel_cases(fine_dims, levels: int, porosity: float, diameter, seed: int,
                      u_mean: float, eta: float, s_in: float, tol: float,
                      h_fine: float = H_PAPER, flow_device: str = "cpu", k0: float = 1e-7,
-                     name: str = "fiber"):
+                     name: str = "fiber", only_level=None):
     """The same analytic fibers rasterised at ``levels`` resolutions, coarsest first.
 
     Fibers are drawn once in finest-level cell units (porosity target at the finest
     level); level l has dims fine_dims / 2^(levels-1-l) and cell size h_fine times the
-    same factor. Each level gets its own flood fill and potential flow."""
+    same factor. Each level gets its own flood fill and potential flow. ``only_level``
+    (an index) builds that level alone and returns a one-element list."""
     fibers, solid_f = generate_fibers(seed, fine_dims, porosity, diameter)
     out = []
     for lev in range(levels):
+        if only_level is not None and lev != only_level:
+            continue
         f = 2 ** (levels - 1 - lev)
         dims = tuple(int(d) // f for d in fine_dims)
         solid = solid_f if f == 1 else rasterise(fibers, dims, scale=float(f))
@@ -366,6 +309,14 @@ def multilevel_cases(fine_dims, levels: int, porosity: float, diameter, seed: in
                         alpha=0.5, T=298.0, n_e=2, c0=20.0, s_in=s_in, eta=eta, tol=tol,
                         u_mean=u_mean, info=info))
     return out
+
+
+def upsampling_cases(flow_device: str = "cpu", only_level=None):
+    """The upsampling workload: 128x128x256 (h = 5 um) -> 256x256x512 -> 512x512x1024
+    (h = 1.25 um), porosity 0.82 and d = 8 at the finest level, seed 5, 1 cm/s,
+    eta = -0.10 V, s_in = 0.5, residual 1e-8 at each level."""
+    return multilevel_cases((512, 512, 1024), 3, 0.82, 8.0, 5, 0.01, -0.10, 0.5, 1e-8,
+                            flow_device=flow_device, only_level=only_level)
 
 
 def lognormal_area_mult(solid: np.ndarray, sigma: float = 0.3, seed: int = 40) -> np.ndarray:

@@ -120,8 +120,7 @@ def test_upsampling_workload_512x512x1024_full_size():
     balance, the maximum principle and U <= U_mt."""
     from paper_2502_08034_gb300 import rfb, synth
     from paper_2502_08034_gb300.workflows import upsample_chain
-    cases = synth.multilevel_cases((512, 512, 1024), 3, 0.82, 8.0, 5, 0.01, -0.10, 0.5, 1e-8,
-                                   flow_device="cuda")
+    cases = synth.upsampling_cases(flow_device="cuda")
     solvers = [rfb.Solver.from_case(c, device_inputs=True) for c in cases]
     try:
         levels, _ = upsample_chain(solvers, cases, 1e-8, umt=False)

@@ -10,6 +10,7 @@ import math
 import os
 
 import numpy as np
+import scipy.sparse.linalg as spla
 import pytest
 
 from oracle import soc
@@ -662,3 +663,68 @@ def test_nernst_model_fast_kinetics_limit():
 def test_nernst_model_needs_alpha_one_half():
     with pytest.raises(ValueError):
         soc.nernst_iterate(_nernst_problem(alpha=0.3), 0.5, 1e-8)
+
+
+@pytest.mark.parametrize("objective", ["I_tot", "U", "U_mt"])
+def test_large_problem_adjoint_iteration_equals_the_direct_adjoint(objective):
+    """The oracle's path for adjoints beyond its direct-solve size (the explicit
+    transposed iteration with local steps) reaches the sparse-LU adjoint: forced here on
+    a small lattice with area multipliers (direct_max = 0), to 1e-9 relative in lam and
+    in both gradients."""
+    import dataclasses
+    base = _p3((12, 10, 20))
+    rng = np.random.default_rng(3)
+    nw = soc.n_wall(base.solid.astype(bool)).ravel()
+    fl = base.solid.ravel() == 0
+    m = np.where(fl & (nw > 0), np.exp(0.3 * rng.standard_normal(base.solid.size)), 1.0)
+    p = dataclasses.replace(base, area_mult=m.reshape(base.solid.shape))
+    mode = "umt" if objective == "U_mt" else "sbv"
+    s = soc.steady_state(soc.assemble(p, mode))
+    a = soc.adjoint(p, s, objective)
+    b = soc.adjoint(p, s, objective, direct_max=0, iter_tol=1e-14)
+    assert np.abs(b["lam"] - a["lam"]).max() <= 1e-9 * np.abs(a["lam"]).max()
+    if objective != "U_mt":
+        assert np.abs(b["d_area_mult"] - a["d_area_mult"]).max() <= \
+            1e-9 * np.abs(a["d_area_mult"]).max()
+    assert abs(b["d_beta"] - a["d_beta"]) <= 1e-9 * abs(a["d_beta"])
+
+
+def test_transposed_iteration_is_the_transpose_solve():
+    """transposed_iterate solves A^T x + g = 0 for a nonsymmetric M-matrix (upwind
+    advection): the result satisfies the transposed system, and it differs from the
+    solution of the untransposed one."""
+    p = _p3((8, 8, 12))
+    op = soc.assemble(p)
+    u = op.unknown
+    A = op.L[u][:, u].tocsr()
+    g = np.random.default_rng(5).standard_normal(A.shape[0])
+    x, n = soc.transposed_iterate(A, g, 0.4, 1e-13)
+    assert n > 0
+    assert np.linalg.norm(A.T @ x + g) <= 1e-12 * np.linalg.norm(g)
+    y = spla.spsolve(A.tocsc(), -g)
+    assert np.abs(x - y).max() > 1e-3 * np.abs(y).max()
+
+
+def test_host_potential_flow_is_divergence_free_and_thread_independent():
+    """The host potential-flow input generator: divergence-free to its tolerance, no flow
+    through fibers or side walls, inflow only at the inlet and outflow only at the
+    outlet, mean W over fluid z-faces equal to the requested value, and the same bits
+    with one thread as with eight."""
+    from paper_2502_08034_gb300 import synth
+    _, solid = synth.generate_fibers(2, (24, 20, 40), 0.8, 4.0)
+    solid = synth.remove_unconnected(solid)
+    U1, V1, W1, i1 = synth.potential_flow(solid, 1e-6, 0.003, threads=1)
+    U8, V8, W8, i8 = synth.potential_flow(solid, 1e-6, 0.003, threads=8)
+    assert np.array_equal(U1, U8) and np.array_equal(V1, V8) and np.array_equal(W1, W8)
+    assert i1["max_div_rel"] < 1e-11
+    fl = solid == 0
+    div = (U1[:, :, 1:] - U1[:, :, :-1]) + (V1[:, 1:, :] - V1[:, :-1, :]) + (W1[1:] - W1[:-1])
+    assert np.abs(div[fl]).max() < 1e-11 * 0.003
+    assert np.all(U1[:, :, 0] == 0) and np.all(U1[:, :, -1] == 0)
+    assert np.all(V1[:, 0, :] == 0) and np.all(V1[:, -1, :] == 0)
+    assert np.all(W1[0] >= 0) and np.all(W1[-1] >= 0)
+    sx = solid.astype(bool)
+    assert np.all(U1[:, :, 1:-1][sx[:, :, 1:] | sx[:, :, :-1]] == 0)
+    assert np.all(W1[1:-1][sx[1:] | sx[:-1]] == 0)
+    zf = np.concatenate([fl[:1], fl[1:] & fl[:-1], fl[-1:]])
+    assert abs(W1[zf].mean() - 0.003) < 1e-15
