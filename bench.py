@@ -26,9 +26,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GCell-updates/s + time-to-steady (res 1e-8) of SOC sweep, % HBM peak, vs FP64"
 UNIT = "GCell-updates/s"
-# algorithmic bytes per cell of one FP32 correction sweep: delta in + out (8), FP32
-# forcing r (4), three FP32 face velocities (12), one mask bit (1/8)
+# algorithmic bytes per cell of one FP32 correction launch (one sweep or a two-sweep
+# pass), global-step kernels of the batched path: delta in + out (8), FP32 forcing r (4),
+# three FP32 face velocities (12), one mask bit (1/8)
 SWEEP_BYTES_PER_CELL = 4 + 4 + 4 + 12 + 0.125
+# local-step kernels (every single-lattice workload): the same with the FP32 step field
+# (4) in place of the mask
+DT_SWEEP_BYTES_PER_CELL = 4 + 4 + 4 + 12 + 4
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -101,7 +105,7 @@ def kernel_source_digest():
     """Digest of the kernel sources' code (comments and whitespace removed, so that a
     comment edit does not void the traffic figures taken on the same code)."""
     return code_digest(open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name)).read()
-                       for name in ("soc_kernels.cuh", "sweep_tb.cuh"))
+                       for name in ("soc_kernels.cuh", "sweep_tb.cuh", "sweep_dt.cuh"))
 
 
 def kernel_traffic(n_cells, kernel):
@@ -365,8 +369,8 @@ def run_upsample(args):
     two_sweep = bool(kname) and kname.startswith("blocked")
     launches_fine = (fr["sweeps"] + 1) // 2 if two_sweep else fr["sweeps"]
     # algorithmic bytes per launch (a two-sweep pass reads and writes each cell once)
-    achieved = SWEEP_BYTES_PER_CELL * N * launches_fine / (fr["sweep_ms"] / 1e3) / 1e9
-    effective = SWEEP_BYTES_PER_CELL * N * fr["sweeps"] / (fr["sweep_ms"] / 1e3) / 1e9
+    achieved = DT_SWEEP_BYTES_PER_CELL * N * launches_fine / (fr["sweep_ms"] / 1e3) / 1e9
+    effective = DT_SWEEP_BYTES_PER_CELL * N * fr["sweeps"] / (fr["sweep_ms"] / 1e3) / 1e9
     out = {"metric": METRIC, "value": cells / (elapsed / 1e3) / 1e9, "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -382,12 +386,12 @@ def run_upsample(args):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
                         "kernel": "%s on the finest level" % (
-                            "sweep32tb_kernel (two-sweep pass, %s launch)" % kname.split("_")[1]
-                            if two_sweep else "sweep32v_kernel (one sweep)"),
-                        "bytes_per_cell_per_launch": SWEEP_BYTES_PER_CELL,
+                            "sweep32tbd_kernel (two-sweep pass, %s launch)" % kname.split("_")[1]
+                            if two_sweep else "sweep32d_kernel (one sweep)"),
+                        "bytes_per_cell_per_launch": DT_SWEEP_BYTES_PER_CELL,
                         "peak_kind": peak_kind},
            "effective_bandwidth": {"value": effective, "unit": "GB/s", "frac": effective / peak,
-                                   "note": "24.125 B per cell per sweep x sweeps/s, finest level"},
+                                   "note": "28 B per cell per sweep x sweeps/s, finest level"},
            "clocks": clk.summary(), "setup_s": setup_s}
     print(json.dumps(out), flush=True)
     for s in solvers:
@@ -662,15 +666,15 @@ def main():
     sweep_ms = sum(r["sweep_ms"] for r in results)
     peak, peak_kind = peak_hbm()
     # algorithmic bytes per launch: a launch reads each cell's correction, forcing, three
-    # face velocities and mask once and writes the correction once, whether it applies
+    # face velocities and step once and writes the correction once, whether it applies
     # one sweep or a two-sweep pass
     kname, tuned_plain_ms, tuned_blocked_ms = sv.tuned_fp32_kernel()
     if args.fp32_kernel not in ("auto", "blocked"):
         kname = args.fp32_kernel
     two_sweep = kname.startswith("blocked")   # about one launch per two sweeps
     kernel_launches = (sweeps + 1) // 2 if two_sweep else sweeps
-    achieved = SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
-    effective = SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
+    achieved = DT_SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
+    effective = DT_SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
     traffic = kernel_traffic(N, kname)
     # measured DRAM bytes per launch over the launch time: the kernel's % of HBM peak
     launch_s = (sweep_ms / 1e3) / max(1, kernel_launches)
@@ -754,17 +758,17 @@ def main():
                "mass_balance_rel": last["mass_balance_rel"],
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                            "kernel": ("sweep32tb_kernel (two-sweep TMA-staged pass, %s "
+                            "kernel": ("sweep32tbd_kernel (two-sweep TMA-staged pass, %s "
                                        "launch)" % kname.split("_")[1] if two_sweep
-                                       else "sweep32v_kernel (one sweep)"),
+                                       else "sweep32d_kernel (one sweep)"),
                             "autotuner_ms_per_sweep": {"plain": tuned_plain_ms,
                                                        "blocked": tuned_blocked_ms},
-                            "bytes_per_cell_per_launch": SWEEP_BYTES_PER_CELL,
+                            "bytes_per_cell_per_launch": DT_SWEEP_BYTES_PER_CELL,
                             "dram_frac": dram_frac, "nominal_peak_gbs": 7900.0,
                             "peak_kind": peak_kind},
                "effective_bandwidth": {"value": effective, "unit": "GB/s",
                                        "frac": effective / peak,
-                                       "note": "24.125 B per cell per sweep x sweeps/s"},
+                                       "note": "28 B per cell per sweep x sweeps/s"},
                "sweep_kernel_ms_per_sweep": sweep_ms / sweeps,
                "check_ms_per_check": (sum(r["check_ms"] for r in results) /
                                       max(1, sum(r["checks"] - 1 for r in results))),

@@ -4,6 +4,7 @@
 #include "rfb_soc.h"
 #include "soc_kernels.cuh"
 #include "sweep_tb.cuh"
+#include "sweep_dt.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -120,7 +121,7 @@ struct rfb_soc_handle {
     } tb_launch[2];
     int tb_variant = -1;      // -1 not chosen yet
     bool tm_ready = false;
-    CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f;
+    CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f, tm_t;
     float* tm_delta_ptr[2] = {nullptr, nullptr};
     double tb_tuned_plain_ms = 0, tb_tuned_tb_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -418,9 +419,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool tb_eligible(const rfb_soc_handle* h) {
-    // 16-byte TMA rows for the 8-bit mask; the blocked kernel streams no area multiplier
-    return (h->nx % 16) == 0 && h->d_m32 == nullptr && h->nz >= 2;
+// Two-sweep passes: with local steps the step-field pass (sweep_dt.cuh; 16-byte FP32
+// rows: nx % 4 == 0, any area multipliers, since they enter only through the step);
+// with the global step the mask-byte pass (sweep_tb.cuh; 16-byte rows of the 8-bit mask,
+// no area multiplier streamed).
+bool tb_eligible(const rfb_soc_handle* h, bool local) {
+    if (h->nz < 2) return false;
+    return local ? (h->nx % 4) == 0 : ((h->nx % 16) == 0 && h->d_m32 == nullptr);
 }
 
 void tb_encode(rfb_soc_handle* h, CUtensorMap* m, CUtensorMapDataType t, size_t esize, void* ptr,
@@ -463,6 +468,10 @@ void tb_prepare(rfb_soc_handle* h) {
     if (!attr_set[1]) {
         CK(h, cudaFuncSetAttribute(sweep32tb_kernel<true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TBD_SMEM));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TBD_SMEM));
         attr_set[1] = true;
     }
     for (int q = 0; q < 2; ++q) {
@@ -474,7 +483,9 @@ void tb_prepare(rfb_soc_handle* h) {
     tb_encode(h, &h->tm_u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz, TB_BW);
     tb_encode(h, &h->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz, TB_BW);
     tb_encode(h, &h->tm_w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1, TB_BW);
-    tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz, TB_BWM);
+    if (h->nx % 16 == 0)   // the mask byte of the global-step pass
+        tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz, TB_BWM);
+    tb_encode(h, &h->tm_t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_dtc, h->nz, TB_BW);
     // One CTA per SM fits (152 KB of shared memory each).
     // Shape 0, persistent: the tile-major (tile, plane) space in equal shares of at least
     // 16 planes (every z segment pays a two-plane prologue): no partial last wave, but
@@ -507,10 +518,31 @@ void tb_prepare(rfb_soc_handle* h) {
 
 unsigned int* tb_err_word(rfb_soc_handle* h) { return reinterpret_cast<unsigned int*>(h->d_err + 3); }
 
-// one two-sweep pass from delta[cur] into delta[cur ^ 1]
-void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur, bool local) {
+// one two-sweep pass from delta[cur] into delta[cur ^ 1] (tr: of the transposed
+// operator; local steps only)
+void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur, bool local,
+             bool tr = false) {
     const CUtensorMap& td = (h->d_delta[cur] == h->tm_delta_ptr[0]) ? h->tm_delta[0]
                                                                      : h->tm_delta[1];
+    if (local) {
+        TBDArgs A{};
+        A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
+        const auto& S = h->tb_launch[h->tb_variant > 0 ? 1 : 0];
+        A.lc = S.lc; A.total = S.total; A.per = S.per;
+        A.d_in = h->d_delta[cur];
+        A.d_out = h->d_delta[cur ^ 1];
+        A.omc = (float)(1.0 - op.cfl);
+        A.Dh = C.Dh;
+        A.err = tb_err_word(h);
+        if (tr)
+            sweep32tbd_kernel<true><<<S.grid, TB_THREADS, TBD_SMEM, h->stream>>>(
+                td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+        else
+            sweep32tbd_kernel<false><<<S.grid, TB_THREADS, TBD_SMEM, h->stream>>>(
+                td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+        LAUNCHED(h);
+        return;
+    }
     TBArgs A{};
     A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
     const auto& S = h->tb_launch[h->tb_variant > 0 ? 1 : 0];
@@ -529,14 +561,24 @@ void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur
     LAUNCHED(h);
 }
 
-// one plain sweep from delta[cur] into delta[cur ^ 1]
+DArgs dargs(const rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C) {
+    DArgs A{};
+    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz; A.nxny = h->nxny;
+    A.u = h->d_u32; A.v = h->d_v32; A.w = h->d_w32; A.dt = h->d_dtc;
+    A.omc = (float)(1.0 - op.cfl);
+    A.Dh = C.Dh;
+    return A;
+}
+
+// one plain sweep from delta[cur] into delta[cur ^ 1] (local steps: the step-field
+// kernel, whose updates are bitwise those of the two-sweep pass)
 void plain_sweep(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur,
                  bool local) {
     const bool vec = (h->nx % 4) == 0;
     Lattice L = lattice(h);
     if (vec && local)
-        sweep32v_kernel<true><<<h->vgrid, h->vblock, 0, h->stream>>>(
-            L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+        sweep32d_kernel<false><<<h->vgrid, h->vblock, 0, h->stream>>>(
+            dargs(h, op, C), h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->vkchunk);
     else if (vec)
         sweep32v_kernel<false><<<h->vgrid, h->vblock, 0, h->stream>>>(
             L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
@@ -580,8 +622,9 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = fal
 }
 
 // n FP32 correction sweeps of the transposed operator (adjoint), delta <- delta +
-// dt (L^T delta + r), from delta = 0; the result is left in d_delta[0]. One-sweep kernel
-// only (nx % 4 == 0).
+// dt (L^T delta + r), from delta = 0; the result is left in d_delta[0] (nx % 4 == 0).
+// With local steps: two-sweep passes of the step-field kernel (plus one plain sweep when
+// n is odd).
 void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int64_t n) {
     const size_t bytes = (size_t)h->N * sizeof(float);
     CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
@@ -589,10 +632,19 @@ void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C
     const bool local = op.dt_mode == RFB_DT_LOCAL;
     Lattice L = lattice(h);
     int cur = 0;
-    for (int64_t q = 0; q < n; ++q) {
+    int64_t q = 0;
+    if (local && tb_eligible(h, true)) {
+        tb_prepare(h);
+        if (h->tb_variant < 0) h->tb_variant = 1;   // chunked shape unless tuned
+        for (; q + 2 <= n; q += 2) {
+            tb_pass(h, op, C, cur, true, true);
+            cur ^= 1;
+        }
+    }
+    for (; q < n; ++q) {
         if (local)
-            sweep32v_kernel<true, true><<<h->vgrid, h->vblock, 0, h->stream>>>(
-                L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
+            sweep32d_kernel<true><<<h->vgrid, h->vblock, 0, h->stream>>>(
+                dargs(h, op, C), h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, h->vkchunk);
         else
             sweep32v_kernel<false, true><<<h->vgrid, h->vblock, 0, h->stream>>>(
                 L, C, h->d_delta[cur], h->d_delta[cur ^ 1], h->d_r32, (float)op.cfl, h->vkchunk);
@@ -628,7 +680,7 @@ std::mutex g_tune_mu;
 // launch shape of the two-sweep pass (CUDA events, on the current forcing) and keep the
 // fastest (tb_only: choose between the two-sweep shapes only).
 void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false) {
-    if (!tb_eligible(h)) { h->tb_mode = 0; return; }
+    if (!tb_eligible(h, op.dt_mode == RFB_DT_LOCAL)) { h->tb_mode = 0; return; }
     const TuneKey key{h->nx, h->ny, h->nz, h->d_m32 != nullptr,
                       op.dt_mode == RFB_DT_LOCAL, h->device};
     {
@@ -703,8 +755,9 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
                    "or 3 / 4 (two-sweep passes, persistent / chunked launch)");
         return false;
     }
-    if (o->fp32_kernel >= 2 && !tb_eligible(h)) {
-        set_err(h, "two-sweep passes need nx %% 16 == 0 and no area multiplier");
+    if (o->fp32_kernel >= 2 && !tb_eligible(h, o->dt_mode == RFB_DT_LOCAL)) {
+        set_err(h, "two-sweep passes need nz >= 2 and nx %% 4 == 0 (local steps), or nx %% 16 "
+                   "== 0 and no area multiplier (global step)");
         return false;
     }
     if (o->max_sweeps == 0) o->max_sweeps = 50000000;
@@ -1619,6 +1672,7 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
                 LAUNCHED(h);
                 check64();
             };
+            CK(h, cudaMemsetAsync(tb_err_word(h), 0, sizeof(unsigned int), h->stream));
             df_check(false);
             bool joined = false;
             while (true) {
@@ -1645,6 +1699,14 @@ rfb_status rfb_soc_adjoint(rfb_soc_handle* h, rfb_objective obj, double tol,
                 const bool bad = st == RFB_ERR_NONFINITE;
                 join_and_check();
                 if (!bad && h->h_red[6] > 0) st = RFB_ERR_NONFINITE;
+            }
+            unsigned int tb_bad = 0;
+            CK(h, cudaMemcpyAsync(&tb_bad, tb_err_word(h), sizeof tb_bad, cudaMemcpyDeviceToHost,
+                                  h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            if (tb_bad) {
+                set_err(h, "a TMA stage of the two-sweep kernel did not arrive in time");
+                st = RFB_ERR_CUDA;
             }
         }
         while (!mixed) {

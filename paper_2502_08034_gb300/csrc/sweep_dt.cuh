@@ -1,0 +1,310 @@
+// FP32 correction sweeps with a stored per-cell step (local pseudo-time stepping).
+//
+// With the local step dt_c = C_CFL / d_c (d_c the diagonal of -L) one explicit update of
+// the homogeneous correction equation is
+//     delta'_c = (1 - C_CFL) delta_c
+//              + dt_c (r_c + sum_f q_in,f delta_f + (D/h^2) sum_f delta_f),
+// q_in,f the inflow through face f (beta/h times the face velocity where it points into
+// the cell, else 0) and the sums over the six neighbours. Solid and out-of-domain
+// neighbours hold delta = 0 and their faces carry no velocity, so no face needs a mask
+// test; cells that are not updated (solid, or electrode cells of U_mt) have dt_c = 0 and
+// keep delta = 0, the value every correction cycle starts from. The step field is the
+// one the FP64 path uses (written by the diagonal pass of every operating point), so the
+// kernels stream the step instead of a mask byte and recompute no diagonal: a cell update
+// is 20 FP32 instructions. For the transposed operator (adjoint corrections) the
+// coefficient towards a neighbour is this cell's outflow through the shared face (the
+// neighbour's inflow from it), with the same diagonal.
+//
+// sweep32d_kernel applies one sweep; sweep32tbd_kernel two sweeps per pass over HBM,
+// planes staged by TMA through a three-stage mbarrier ring (the scheme of sweep_tb.cuh,
+// with the step plane in place of the mask plane). Both evaluate every update with
+// dt_update below in the same operation order, so a pass is bitwise two sweeps.
+#pragma once
+
+#include "sweep_tb.cuh"
+
+namespace rfb {
+
+// Face weights of one cell's update: the inflow through each face (TR: the outflow),
+// -x, +x, -y, +y, -z, +z, and the cell's step.
+struct CoefD {
+    float f[6];
+    float dt;
+};
+
+template <bool TR>
+__device__ __forceinline__ CoefD dt_coef(float dt, float uL, float uH, float vL, float vH,
+                                         float wL, float wH) {
+    CoefD k;
+    const float sg = TR ? -1.f : 1.f;
+    k.f[0] = fmaxf(sg * uL, 0.f);
+    k.f[1] = fmaxf(-sg * uH, 0.f);
+    k.f[2] = fmaxf(sg * vL, 0.f);
+    k.f[3] = fmaxf(-sg * vH, 0.f);
+    k.f[4] = fmaxf(sg * wL, 0.f);
+    k.f[5] = fmaxf(-sg * wH, 0.f);
+    k.dt = dt;
+    return k;
+}
+
+// one update (omc = 1 - C_CFL, Dh = D/h^2)
+__device__ __forceinline__ float dt_update(const CoefD& k, float omc, float Dh, float sc,
+                                           float xm, float xp, float ym, float yp, float zm,
+                                           float zp, float r) {
+    float acc = r;
+    acc = fmaf(k.f[0], xm, acc);
+    acc = fmaf(k.f[1], xp, acc);
+    acc = fmaf(k.f[2], ym, acc);
+    acc = fmaf(k.f[3], yp, acc);
+    acc = fmaf(k.f[4], zm, acc);
+    acc = fmaf(k.f[5], zp, acc);
+    const float sum = ((xm + xp) + (ym + yp)) + (zm + zp);
+    acc = fmaf(Dh, sum, acc);
+    return fmaf(k.dt, acc, omc * sc);
+}
+
+struct DArgs {
+    int nx, ny, nz;
+    int64_t nxny;
+    const float* __restrict__ u;    // FP32 face velocities * beta / h (low faces)
+    const float* __restrict__ v;
+    const float* __restrict__ w;    // nz + 1 planes
+    const float* __restrict__ dt;   // per-cell step (0: not updated)
+    float omc, Dh;
+};
+
+// One sweep over the planes kb .. ke-1 of the columns (i0 .. i0+3, j), i0 % 4 == 0,
+// nx % 4 == 0; every load of a plane is issued before its arithmetic.
+template <bool TR>
+__global__ void __launch_bounds__(VBX * VBY)
+sweep32d_kernel(DArgs A, const float* __restrict__ s, float* __restrict__ s_out,
+                const float* __restrict__ force, int kchunk) {
+    const int i0 = 4 * (blockIdx.x * VBX + threadIdx.x);
+    const int j = blockIdx.y * VBY + threadIdx.y;
+    if (i0 >= A.nx || j >= A.ny) return;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, A.nz);
+    const int nx = A.nx, nz = A.nz;
+    const int64_t nxny = A.nxny;
+    const bool has_xm = i0 > 0, has_xp = i0 + 4 < nx;
+    const bool has_ym = j > 0, has_yp = j + 1 < A.ny;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t c = (int64_t)i0 + (int64_t)nx * j + nxny * kb;
+    float4 d_prev = kb > 0 ? ldg4(s + c - nxny) : zero4;   // plane -1: outside, 0
+    float4 d_cur = ldg4(s + c);
+    float4 wL = ldg4(A.w + c);
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const float4 d_next = k == nz - 1 ? zero4 : ldg4(s + c + nxny);
+        const float4 wH = ldg4(A.w + c + nxny);
+        const float4 d_ym = has_ym ? ldg4(s + c - nx) : zero4;
+        const float4 d_yp = has_yp ? ldg4(s + c + nx) : zero4;
+        const float d_xm = has_xm ? __ldg(s + c - 1) : 0.f;
+        const float d_xp = has_xp ? __ldg(s + c + 4) : 0.f;
+        const float4 u4 = ldg4(A.u + c);
+        const float u_nx = has_xp ? __ldg(A.u + c + 4) : 0.f;
+        const float4 v4 = ldg4(A.v + c);
+        const float4 vH4 = has_yp ? ldg4(A.v + c + nx) : zero4;
+        const float4 r4 = ldg4(force + c);
+        const float4 t4 = ldg4(A.dt + c);
+        float out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const CoefD kc = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? u_nx : el(u4, e + 1),
+                                         el(v4, e), el(vH4, e), el(wL, e), el(wH, e));
+            out[e] = dt_update(kc, A.omc, A.Dh, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
+                               e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
+                               el(d_prev, e), el(d_next, e), el(r4, e));
+        }
+        *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
+        d_prev = d_cur;
+        d_cur = d_next;
+        wL = wH;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Two sweeps per pass. Tile, staged boxes, thread layout, launch shapes and the bounded
+// mbarrier waits are those of sweep32tb_kernel (sweep_tb.cuh); a stage holds six FP32
+// planes (delta, forcing, u, v, w, step).
+// ---------------------------------------------------------------------------------
+constexpr int TBD_STAGE = 6 * TB_F32;
+constexpr int TBD_L1 = TB_NSTAGE * TBD_STAGE;       // offset of the two level-1 planes
+constexpr int TBD_BAR = TBD_L1 + 2 * TB_F32;        // offset of the stage barriers
+constexpr int TBD_SMEM = TBD_BAR + 64 + 128;        // + alignment slack for the base
+constexpr uint32_t TBD_TX_BYTES = 6 * TB_F32;
+
+struct TBDArgs {
+    int nx, ny, nz;
+    int lc;                           // planes per z chunk (nz: one chunk)
+    int64_t total;                    // tiles x chunks x lc (chunk-major, tile fastest)
+    int64_t per;                      // planes of that space per CTA
+    const float* __restrict__ d_in;   // delta read by this pass (prologue plane)
+    float* __restrict__ d_out;
+    float omc, Dh;
+    unsigned int* err;                // set if a stage never arrives
+};
+
+template <bool TR>
+__global__ void __launch_bounds__(TB_THREADS, 1)
+sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_r,
+                  const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
+                  const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_t,
+                  TBDArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TBD_BAR);
+    const int tid = threadIdx.x;
+    const int tx = tid % TB_GX, ty = tid / TB_GX;
+    const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const bool interior = tx >= 1 && tx < 1 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
+    const int64_t nxny = (int64_t)nx * ny;
+    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
+    const int gx = (nx + TB_TXI - 1) / TB_TXI;
+    const float omc = A.omc, Dh = A.Dh;
+
+    auto stage = [&](int s) { return smem + s * TBD_STAGE; };
+    uint32_t phase = 0;   // parity of each stage's next completion
+    uint32_t pend = 0;    // stages with a load in flight (every thread tracks the same set)
+    auto wait = [&](int s) -> bool {                   // bounded wait for stage s
+        if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, TB_SPIN_LIMIT, A.err)) return false;
+        phase ^= 1u << s;
+        pend &= ~(1u << s);
+        return true;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < TB_NSTAGE; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int tiles = gx * ((ny + TB_TYI - 1) / TB_TYI);
+    const int64_t q1 = min((int64_t)(blockIdx.x + 1) * A.per, A.total);
+    bool ok = true;
+    for (int64_t q = (int64_t)blockIdx.x * A.per; q < q1 && ok;) {
+        const int64_t item = q / A.lc;
+        const int zl = (int)(q % A.lc);
+        const int tile = (int)(item % tiles);
+        const int kb = (int)(item / tiles) * A.lc + zl;
+        const int64_t item_end = (item + 1) * A.lc;
+        if (kb >= nz) { q = item_end; continue; }     // padding of a short last chunk
+        const int ke = (int)min((int64_t)nz, kb + (min(q1, item_end) - q));
+        q = min(q1, item_end);
+        const int x0 = TB_TXI * (tile % gx) - 4;       // box origin (4-cell aligned)
+        const int y0 = TB_TYI * (tile / gx) - 2;
+        const int i0 = x0 + bxx, j = y0 + byy;
+        const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+        auto issue = [&](int p, int s) {               // plane p -> stage s
+            pend |= 1u << s;
+            if (tid != 0) return;                      // one thread issues the copies
+            unsigned char* S = stage(s);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[s], TBD_TX_BYTES);
+            tma_load_3d(S, &tm_d, x0, y0, p, &bar[s]);
+            tma_load_3d(S + TB_F32, &tm_r, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
+            tma_load_3d(S + 5 * TB_F32, &tm_t, x0, y0, p, &bar[s]);
+        };
+        __syncthreads();   // the previous segment's readers are done with every stage
+        for (int s = 0; s < TB_NSTAGE; ++s) issue(kb - 1 + s, s);       // kb-1, kb, kb+1
+
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 l1_m2 = zero4, l1_m1 = zero4;           // own level 1 at z-2, z-1
+        // Two register sets that swap roles every step (the loop is unrolled by two):
+        // weights, forcing and own level-0 value of the step's plane (written) and of the
+        // plane before it (read).
+        CoefD kcA[4], kcB[4];
+        float4 rA = zero4, rB = zero4, dA = zero4, dB = zero4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            for (int s = 0; s < 6; ++s) kcB[e].f[s] = 0.f;
+            kcB[e].dt = 0.f;
+        }
+        if (in_dom && kb >= 2) dB = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
+        bool good = wait(0);
+        int s0 = 0;                                    // stage holding plane z
+
+        auto step = [&](int z, CoefD (&kc)[4], float4& rr, float4& dc,
+                        const CoefD (&pkc)[4], const float4& prr, const float4& pdc) -> bool {
+            const int s1 = s0 == TB_NSTAGE - 1 ? 0 : s0 + 1;
+            if (good) good = wait(s1);
+            const float* D0 = reinterpret_cast<const float*>(stage(s0));
+            const float* R0 = D0 + TB_PLANE;
+            const float* U0 = R0 + TB_PLANE;
+            const float* V0 = U0 + TB_PLANE;
+            const float* W0 = V0 + TB_PLANE;
+            const float* T0 = W0 + TB_PLANE;
+            const float* D1 = reinterpret_cast<const float*>(stage(s1));
+            const float* W1 = D1 + 4 * TB_PLANE;
+            // ---- level 1 at plane z
+            dc = lds4(D0 + o);
+            const float4 dn = lds4(D1 + o);
+            const float4 u4 = lds4(U0 + o);
+            const float un = U0[o + 4];
+            const float4 v4 = lds4(V0 + o);
+            const float4 vh4 = lds4(V0 + o + TB_BW);
+            const float4 wl4 = lds4(W0 + o);
+            const float4 wh4 = lds4(W1 + o);
+            const float4 t4 = lds4(T0 + o);
+            rr = lds4(R0 + o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                kc[e] = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? un : el(u4, e + 1),
+                                    el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
+            float4 l1 = dc;
+            if (in_dom && z >= 0 && z < nz) {
+                const float dxm = D0[o - 1], dxp = D0[o + 4];
+                const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+                float out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    out[e] = dt_update(kc[e], omc, Dh, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
+                                       e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                       el(pdc, e), el(dn, e), el(rr, e));
+                l1 = make_float4(out[0], out[1], out[2], out[3]);
+            }
+            float* L1w = reinterpret_cast<float*>(smem + TBD_L1) + (z & 1) * TB_PLANE;
+            *reinterpret_cast<float4*>(L1w + o) = l1;
+            // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
+            const int zz = z - 1;
+            if (zz >= kb && interior && in_dom) {
+                const float* L1r =
+                    reinterpret_cast<const float*>(smem + TBD_L1) + (zz & 1) * TB_PLANE;
+                const float lxm = L1r[o - 1], lxp = L1r[o + 4];
+                const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
+                float out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    out[e] = dt_update(pkc[e], omc, Dh, el(l1_m1, e),
+                                       e == 0 ? lxm : el(l1_m1, e - 1),
+                                       e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
+                                       el(l1_m2, e), el(l1, e), el(prr, e));
+                *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
+                    make_float4(out[0], out[1], out[2], out[3]);
+            }
+            l1_m2 = l1_m1;
+            l1_m1 = l1;
+            // ---- all threads are done with stage s0: refill it with plane z + 3
+            if (!__syncthreads_and(good)) return false;
+            if (z + 3 <= ke + 1) issue(z + 3, s0);
+            s0 = s1;
+            return true;
+        };
+
+        for (int z = kb - 1; z <= ke; z += 2) {
+            if (!step(z, kcA, rA, dA, kcB, rB, dB)) { ok = false; break; }
+            if (z + 1 > ke) break;
+            if (!step(z + 1, kcB, rB, dB, kcA, rA, dA)) { ok = false; break; }
+        }
+    }
+    if (!ok) {
+        for (int s = 0; s < TB_NSTAGE; ++s)
+            if (pend & (1u << s)) (void)wait(s);
+    }
+}
+
+}  // namespace rfb

@@ -79,16 +79,41 @@ def test_mixed_solve_with_two_sweep_passes_matches_oracle(dims):
     assert np.abs(s - ref).max() < 1e-7
 
 
-def test_two_sweep_passes_need_a_16_multiple_and_no_area_multiplier():
+def test_two_sweep_pass_eligibility():
+    """Local steps: the step-field pass takes nx % 4 == 0 and area multipliers (they enter
+    through the step only); the global step keeps the mask-byte pass's nx % 16 == 0 and
+    no multiplier; lattices outside that fall back to one-sweep launches under auto."""
     from paper_2502_08034_gb300 import rfb, synth
     case = _case((36, 20, 24))
     with rfb.Solver.from_case(case) as sv:
+        sv.solve(case.s_in, case.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
         with pytest.raises(rfb.RfbError) as e:
-            sv.solve(case.s_in, case.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
+            sv.solve(case.s_in, case.eta, 1e-8, precision="mixed", fp32_kernel="blocked",
+                     dt_mode="global")
         assert e.value.status == rfb.RFB_ERR_INVALID_ARG
     c2 = _case((48, 48, 96))
     m = synth.lognormal_area_mult(c2.solid)
     with rfb.Solver.from_case(c2, area_mult=m) as sv:
+        sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
         with pytest.raises(rfb.RfbError):
-            sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed", fp32_kernel="blocked")
-        sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed")   # auto falls back
+            sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed", fp32_kernel="blocked",
+                     dt_mode="global")
+        sv.solve(c2.s_in, c2.eta, 1e-8, precision="mixed", dt_mode="global")   # auto
+
+
+@pytest.mark.parametrize("dims", [(36, 20, 24), (52, 44, 30)])
+def test_step_field_pass_is_bitwise_with_area_multipliers_and_nx_multiple_of_4(dims):
+    """The step-field pass (local steps) on lattices whose nx is a multiple of 4 but not
+    of 16, with lognormal area multipliers: both launch shapes give the bits of one-sweep
+    launches."""
+    from paper_2502_08034_gb300 import rfb, synth
+    case = _case(dims)
+    m = synth.lognormal_area_mult(case.solid, 0.3, 40)
+    states = []
+    for kernel in ("plain", "blocked_persistent", "blocked_chunked"):
+        with rfb.Solver.from_case(case, area_mult=m) as sv:
+            for n in (6, 9):
+                sv.step(case.s_in, case.eta, n, precision="mixed", fp32_kernel=kernel)
+            states.append(sv.get_state())
+    for st in states[1:]:
+        assert np.array_equal(states[0], st)
