@@ -54,10 +54,12 @@ def parse():
                          "logpile: the paper's reference reaction case on its logpile lattice "
                          "at 5, 2.5 and 1.25 um")
     ap.add_argument("--fp32-kernel", default="auto",
-                    choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked"],
+                    choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked",
+                             "blocked4_persistent", "blocked4_chunked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
                          "per launch, or two-sweep TMA-staged passes (launch shape autotuned, "
-                         "persistent, or one (tile, z chunk) item per CTA)")
+                         "persistent, or one (tile, z chunk) item per CTA; blocked4: four TMA "
+                         "stages)")
     ap.add_argument("--logpile-flow", default="potential", choices=["potential", "stokes"],
                     help="logpile workload: potential flow at the paper's 10 Pa flow rate "
                          "(default) or the Stokes flow at 10 Pa (matrix-free MINRES)")
@@ -221,6 +223,66 @@ def oracle_sample(case, n_planes=16, sweeps=40, repeats=1):
     return n * sweeps / best / 1e9, best, n, sweeps
 
 
+_SLAB_BARRIER = None
+
+
+def _slab_init(barrier):
+    global _SLAB_BARRIER
+    _SLAB_BARRIER = barrier
+
+
+def _oracle_slab(task):
+    """One worker of the all-core oracle figure: assemble the oracle operator of a slab of
+    z-planes, wait for every worker, then time its explicit FP64 sweeps."""
+    import numpy as np
+
+    from oracle import soc
+    solid, U, V, W, h, D, s_in, k0, eta, sweeps = task
+    p = soc.Problem(np.ascontiguousarray(solid), U, V, W, h, D, s_in, k0=k0, eta=eta)
+    op = soc.assemble(p)
+    s0 = soc.initial_state(op, s_in)
+    _SLAB_BARRIER.wait()
+    t0 = time.perf_counter()
+    soc.explicit_iterate(op, 0.4, 0.0, s0=s0, max_steps=sweeps, check_every=sweeps + 1,
+                         local_dt=True)
+    return solid.size * sweeps, time.perf_counter() - t0
+
+
+def oracle_all_cores(case, n_planes=16, sweeps=20):
+    """The oracle on every host core: one process per core (spawned, not forked), each
+    sweeping its own slab of ``n_planes`` z-planes of the workload at the same time.
+    Returns (cell-updates/s over all workers, workers, seconds of the slowest)."""
+    import multiprocessing as mp
+    workers = max(1, min(os.cpu_count() or 1, case.dims[2] // n_planes))
+    tasks = []
+    for q in range(workers):
+        a, b = q * n_planes, (q + 1) * n_planes
+        tasks.append((case.solid[a:b].copy(), case.U[a:b].copy(), case.V[a:b].copy(),
+                      case.W[a:b + 1].copy(), case.h, case.D, case.s_in, case.k0, case.eta,
+                      sweeps))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    with ctx.Pool(workers, initializer=_slab_init, initargs=(barrier,)) as pool:
+        res = pool.map(_oracle_slab, tasks)
+    slowest = max(t for _, t in res)
+    return sum(n for n, _ in res) / slowest / 1e9, workers, slowest
+
+
+def oracle_time_to_steady(case, tol):
+    """Serial wall time of the oracle's Algorithm 7 loop (local steps, FP64 CSR, one
+    core) from the cold start s = s_in to tau RMS(RHS) < tol, with its sweep count."""
+    import numpy as np
+
+    from oracle import soc
+    p = soc.Problem(np.ascontiguousarray(case.solid), case.U, case.V, case.W, case.h, case.D,
+                    case.s_in, k0=case.k0, eta=case.eta)
+    op = soc.assemble(p)
+    t0 = time.perf_counter()
+    _, n = soc.explicit_iterate(op, 0.4, tol, s0=soc.initial_state(op, case.s_in),
+                                check_every=50, local_dt=True)
+    return time.perf_counter() - t0, n
+
+
 def run_reference(args, dims):
     rank, world, local = dist_env()
     if rank != 0:
@@ -362,6 +424,35 @@ def run_upsample(args):
     # cold start of the finest level for comparison
     fine.reset_state()
     cold = fine.solve(cases[-1].s_in, cases[-1].eta, args.tol, precision="mixed")
+
+    # What the warm start saves, level by level: the residual every 200 sweeps of each
+    # level's solve from a cold start (s = s_in) and from the prolonged coarser solution,
+    # for the 256x256x512 level (prolonged from 128x128x256, whose fibers are 2 cells
+    # across) and the 512x512x1024 level (prolonged from 256x256x512, fibers 4 cells across)
+    def history(sv, case, warm_from):
+        if warm_from is None:
+            sv.reset_state()
+        else:
+            sv.upsample_from(warm_from)
+        hist = []
+        for _ in range(200):
+            r = sv.step(case.s_in, case.eta, 200, precision="mixed")
+            hist.append(r["residual"])
+            if r["residual"] <= args.tol:
+                break
+        return hist
+
+    upsample_gain = []
+    for q in (1, 2):
+        solvers[q - 1].reset_state()
+        upsample_chain(solvers[:q], cases[:q], args.tol, umt=False)
+        warm = history(solvers[q], cases[q], solvers[q - 1])
+        coldh = history(solvers[q], cases[q], None)
+        upsample_gain.append({"level": list(cases[q].dims), "from": list(cases[q - 1].dims),
+                              "coarse_fiber_cells": 8.0 / 2 ** (2 - (q - 1)),
+                              "residual_every_200_sweeps_warm": warm,
+                              "residual_every_200_sweeps_cold": coldh,
+                              "sweeps_warm": 200 * len(warm), "sweeps_cold": 200 * len(coldh)})
     peak, peak_kind = peak_hbm()
     N = cases[-1].n
     fr = levels[-1]
@@ -383,6 +474,7 @@ def run_upsample(args):
                       "mass_balance_rel": fr["mass_balance_rel"], "U_mt": u_mt,
                       "U_mt_sweeps": ru["sweeps"]},
            "cold_start_finest": {"sweeps": cold["sweeps"], "time_ms": cold["time_ms"]},
+           "upsample_gain": upsample_gain,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
                         "kernel": "%s on the finest level" % (
@@ -467,10 +559,11 @@ def run_logpile(args):
     """The paper's reference reaction case on its logpile lattice (Sec. IV): 10 Pa flow
     rate, applied reducing voltage 0, k0 = 7.2e-5 m/s, s_in = 1.73e-7, residual 1e-6 (the
     paper's tolerance), potential flow in place of the paper's Stokes flow. Mixed-precision
-    solves at h = 5, 2.5 and 1.25 um (the last is the paper's 1024 x 512 x 128 = 2^26
+    solves at h = 10, 5, 2.5 and 1.25 um (the last is the paper's 1024 x 512 x 128 = 2^26
     cells), with U, I_tot and U_mt beside the paper's U = 0.243 and I = 0.09 mA, and the
-    FP64 solve of the finest level for comparison. value: cell-updates/s of the timed
-    finest-level mixed solves."""
+    FP64 solve of the finest level for comparison; at 10 and 5 um also the Butler-Volmer
+    model with electromigration refined from the SBV state, beside the paper's model
+    comparison. value: cell-updates/s of the timed finest-level mixed solves."""
     import numpy as np
     import torch
 
@@ -482,7 +575,7 @@ def run_logpile(args):
     stream = torch.cuda.current_stream()
     levels, t_setup = [], time.time()
     with Clocks(local) as clk:
-        for h in (5e-6, 2.5e-6, 1.25e-6):
+        for h in (10e-6, 5e-6, 2.5e-6, 1.25e-6):
             case = synth.logpile_case(h, flow_device="cuda:%d" % local, flow=args.logpile_flow)
             with rfb.Solver.from_case(case, stream=stream) as sv:
                 finest = h == 1.25e-6
@@ -500,6 +593,25 @@ def run_logpile(args):
                        "time_to_steady_ms": res[-1]["time_ms"], "U": res[-1]["U"],
                        "I_tot_mA": res[-1]["I_tot"] * 1e3, "U_mt": u_mt,
                        "mass_balance_rel": res[-1]["mass_balance_rel"]}
+                if h >= 5e-6:
+                    # the Butler-Volmer model with electromigration refined from the SBV
+                    # state (Sec. III.C), against the paper's model comparison (Sec. V:
+                    # RMS difference of s from SBV 8.61e-4; phi_L mean 0.16 mV, max 0.47 mV)
+                    sv.reset_state()
+                    sv.solve(case.s_in, case.eta, 1e-10, precision="fp64")
+                    s_sbv = sv.get_state()
+                    rb = sv.solve_bv(case.s_in, case.eta, 1e-8, start="sbv")
+                    g = sv.get_bv_state()
+                    fl = case.solid.ravel() == 0
+                    s_bv = g["R"][fl] / (g["O"][fl] + g["R"][fl])
+                    row["bv"] = {"rms_s_minus_sbv": float(np.sqrt(np.mean((s_bv - s_sbv[fl]) ** 2))),
+                                 "phi_mean_mV": rb["phi_mean"] * 1e3,
+                                 "phi_min_mV": rb["phi_min"] * 1e3,
+                                 "phi_max_mV": rb["phi_max"] * 1e3, "U": rb["U"],
+                                 "I_tot_mA": rb["I_tot"] * 1e3, "sweeps": rb["sweeps"],
+                                 "potential_solves": rb["cycles"],
+                                 "cg_iterations": rb["cg_iterations"],
+                                 "time_ms": rb["time_ms"], "residual": rb["residual"]}
                 if finest:
                     sv.reset_state()
                     r64 = sv.solve(case.s_in, case.eta, tol, precision="fp64")
@@ -517,7 +629,9 @@ def run_logpile(args):
            "config": {"workload": "logpile1024x512x128_sbv_10Pa", "tol": tol,
                       "precision": "mixed", "q_m3_s": synth.LOGPILE_Q_10PA, "eta_V": 0.0,
                       "k0_m_s": 7.2e-5},
-           "paper": {"U": 0.243, "I_tot_mA": 0.09, "time_steps_to_tol": 125000},
+           "paper": {"U": 0.243, "I_tot_mA": 0.09, "time_steps_to_tol": 125000,
+                     "bv_rms_s_minus_sbv": 8.61e-4, "bv_phi_mean_mV": 0.16,
+                     "bv_phi_max_mV": 0.47},
            "levels": levels,
            "setup_s": time.time() - t_setup, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
@@ -733,11 +847,34 @@ def main():
                "ms_per_step": {"create": parts[0] / reps, "solve": parts[1] / reps,
                                "state_to_host": parts[2] / reps, "destroy": parts[3] / reps}}
         if rank == 0 and world == 1:
+            from paper_2502_08034_gb300 import synth
             rate, sec, n_s, sw = oracle_sample(case, sweeps=40)
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "explicit FP64 CSR sweeps (scipy, 1 thread) on the first 16 "
                              "z-planes (%d cells) of the workload, %d sweeps, %.1f s" %
                              (n_s, sw, sec), "host": host_cpu()}
+            # the same sweeps on every core at once (one slab of 16 planes per process)
+            arate, workers, asec = oracle_all_cores(case)
+            cpu["all_cores"] = {"value": arate, "unit": UNIT, "cores": workers,
+                                "sample": "%d processes, each 20 sweeps of its own 16-plane "
+                                          "slab, %.1f s for the slowest" % (workers, asec)}
+            # serial time to steady state: measured on the small workloads, extrapolated
+            # (serial rate x the sweeps the same local-step iteration needs) on this one
+            small = {}
+            c1 = synth.fiber_channel_case(flow_device="cuda:%d" % local)
+            t1, n1 = oracle_time_to_steady(c1, c1.tol)
+            small["fiber48x48x96_tol1e-10"] = {"seconds": t1, "sweeps": n1, "measured": True}
+            q0 = synth.batch_instance_params(0)
+            c0 = synth.build_case("batch00", q0["dims"], q0["porosity"], 8.0, q0["seed"],
+                                  q0["u_mean"], q0["eta"], q0["s_in"], args.tol,
+                                  flow_device="cuda:%d" % local)
+            t0_, n0 = oracle_time_to_steady(c0, args.tol)
+            small["batch_lattice0_64x64x64_tol%g" % args.tol] = {"seconds": t0_, "sweeps": n0,
+                                                                 "measured": True}
+            small["this_workload"] = {"seconds": N * sweeps / args.steps / (rate * 1e9),
+                                      "sweeps": sweeps / args.steps, "measured": False,
+                                      "note": "extrapolated: serial rate x sweeps to tol"}
+            cpu["time_to_steady_serial"] = small
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -759,8 +896,10 @@ def main():
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                             "kernel": ("sweep32tbd_kernel (two-sweep TMA-staged pass, %s "
-                                       "launch)" % kname.split("_")[1] if two_sweep
-                                       else "sweep32d_kernel (one sweep)"),
+                                       "launch, %d TMA stages)" % (
+                                           kname.split("_")[1],
+                                           4 if kname.startswith("blocked4") else 3)
+                                       if two_sweep else "sweep32d_kernel (one sweep)"),
                             "autotuner_ms_per_sweep": {"plain": tuned_plain_ms,
                                                        "blocked": tuned_blocked_ms},
                             "bytes_per_cell_per_launch": DT_SWEEP_BYTES_PER_CELL,

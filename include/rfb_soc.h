@@ -113,10 +113,12 @@ typedef struct rfb_solve_opts {
                                the lattice (once per lattice shape, dt mode
                                and device in a process), 1 = one sweep per launch,
                                2 = two sweeps per pass (TMA-staged, temporally blocked;
-                               needs nx % 16 == 0 and no area multiplier), launch shape
-                               chosen by timing; 3 = two-sweep passes in a persistent
-                               launch (one CTA per SM, equal shares); 4 = two-sweep passes,
-                               one (tile, z chunk) item per CTA */
+                               local steps: nx % 4 == 0; global step: nx % 16 == 0 and no
+                               area multiplier), launch shape and TMA stage count chosen
+                               by timing; 3 = two-sweep passes in a persistent launch (one
+                               CTA per SM, equal shares); 4 = two-sweep passes, one
+                               (tile, z chunk) item per CTA; 5 / 6 = as 3 / 4 with four
+                               TMA stages instead of three (local steps only) */
     int32_t timeout_ms;     /* > 0: stop after the first FP64 check at or past this much
                                wall time since the call began and return
                                RFB_ERR_NOT_CONVERGED (the state is valid); 0 = none */
@@ -341,9 +343,14 @@ typedef struct rfb_batch_info {
     int32_t grid_blocks;       /* resident blocks of the persistent launch */
     double sweep_ms;           /* autotuner: device time of one sweep of the batch */
     double check_ms;           /* autotuner: device time of one FP64 check of the batch */
-    int64_t cycles;            /* graph replays of this solve */
+    int64_t cycles;            /* correction cycles of this solve */
     double time_ms;            /* wall time of this solve */
     int64_t launches;          /* kernels launched by this batch so far */
+    int64_t graph_launches;    /* graph launches of this solve, each followed by one host
+                                  wait: without opts.timeout_ms a launch runs up to 64
+                                  cycles in a device-driven loop (a conditional while node
+                                  whose condition a kernel sets once every lattice has
+                                  converged); with a timeout, one cycle per launch */
 } rfb_batch_info;
 
 /* hs: n handles (distinct, same device, nx % 4 == 0), not owned; they must outlive the
@@ -405,6 +412,76 @@ rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double overpoten
  * set_state drop it). */
 rfb_status rfb_soc_get_overpotential(rfb_soc_handle* h, double* eta_t, rfb_mem_kind kind);
 
+/* Parameters of the Butler-Volmer model with electromigration (rfb_soc_solve_bv); zero
+ * fields take the default in brackets. */
+typedef struct rfb_bv_params {
+    double D_H;        /* proton diffusivity [m^2/s] (9.3e-9, parameter table) */
+    double D_X;        /* HSO4- diffusivity [m^2/s] (1.38e-9; the table's second proton
+                          row, read as the counter-ion) */
+    double c_H_in;     /* inlet proton concentration [mol/m^3] (50 c0: 1 M sulfuric acid
+                          against 20 mM quinone, Sec. II.B) */
+    double cg_rtol;    /* each potential solve stops at max|residual| <= cg_rtol
+                          max|right-hand side| (1e-13) */
+    int32_t cycle;     /* species sweeps between potential solves (100) */
+    int32_t max_cg;    /* conjugate-gradient iterations per potential solve (100000) */
+    int32_t start;     /* 0: from the handle's converged SBV state at the same operating
+                          point when there is one (model refinement, Sec. III.C), else from
+                          s = s_in; 1: SBV state required (RFB_ERR_STATE without one);
+                          2: from s = s_in */
+    int32_t reserved;  /* must be 0 */
+} rfb_bv_params;
+
+typedef struct rfb_bv_result {
+    int64_t sweeps;          /* species sweeps */
+    int64_t cycles;          /* potential solves */
+    int64_t cg_iterations;   /* conjugate-gradient iterations, all solves */
+    double residual;         /* max over O, R, H of tau RMS(RHS_j) / scale_j, scale c0
+                                for the quinones and c_H_in for protons */
+    double dphi;             /* largest change of phi in the last potential solve [V] */
+    double I_tot;            /* n_e F h^3 sum S [A] (Eq. I-tot-def) */
+    double U;                /* I_tot / (n_e F c0 Q (1 - s_in)) (Eq. utilization-def) */
+    double s_out;            /* flow-weighted outlet mean of s = C_R / (C_O + C_R) */
+    double I_membrane;       /* protons' migration current through the membrane [A] */
+    double phi_mean;         /* mean of phi_L over fluid cells [V] */
+    double phi_min;          /* smallest phi_L [V] */
+    double phi_max;          /* largest phi_L [V] */
+    double time_ms;
+} rfb_bv_result;
+
+/*
+ * Steady state of the Butler-Volmer model with electromigration (Sec. II.C, Eqs.
+ * nernst-planck, poisson-phi, kappa, electroneutrality; Algorithm 2 in steady form) on
+ * the handle's lattice, flow and kinetics: oxidised and reduced quinone (charge -2,
+ * diffusivity D), protons (+1, D_H) and the electrolyte potential phi_L, with HSO4- by
+ * electroneutrality. The source is the Butler-Volmer rate with the overpotential of
+ * Eq. etat-from-s-bv, k0 a (C_O e^{alpha V_c} - C_R e^{(alpha-1) V_c}),
+ * V_c = V~ + n_e phi_L / V_T; O + 2 H+ + 2 e- -> R. Boundaries: inlet concentrations
+ * (1 - s_in) c0, s_in c0, c_H_in and zero normal field; zero-gradient outlet; no flux
+ * and zero normal field at side walls and fibers; the membrane (phi_L = 0) is the low-x
+ * face of the cells i = 0, crossed by protons only (migration, C_H of the cell, half a
+ * cell). The potential equation is solved as div(kappa grad phi) with face
+ * conductivities from Eq. kappa, as the discrete charge balance of the species fluxes.
+ * Species: FP64 explicit pseudo-time sweeps at a fixed potential (local steps, opts.cfl);
+ * every bv->cycle sweeps the potential is solved by conjugate gradients on the device.
+ * Converged when res->residual <= tol and the last potential solve changed phi by at most
+ * tol V_T / n_e. Needs kinetics mode 0, opts.precision FP64, opts.dt_mode local.
+ *   bv    nullable (defaults)
+ *   res   nullable
+ * Returns RFB_OK, RFB_ERR_NOT_CONVERGED (opts.max_sweeps or opts.timeout_ms; the state is
+ * valid), RFB_ERR_NONFINITE, RFB_ERR_INVALID_ARG, RFB_ERR_STATE (start = 1 without an SBV
+ * state). The SOC state of the handle is not changed; rfb_soc_get_bv_state reads the
+ * result.
+ */
+rfb_status rfb_soc_solve_bv(rfb_soc_handle* h, double s_in, double overpotential, double tol,
+                            const rfb_bv_params* bv, const rfb_solve_opts* opts,
+                            rfb_bv_result* res);
+
+/* The last rfb_soc_solve_bv state: C_O, C_R, C_H [mol/m^3] and phi_L [V], N doubles each
+ * (host or device per kind; any pointer may be NULL), 0 on solid cells. RFB_ERR_STATE if
+ * there is none. */
+rfb_status rfb_soc_get_bv_state(rfb_soc_handle* h, double* c_o, double* c_r, double* c_h,
+                                double* phi, rfb_mem_kind kind);
+
 /* Self-test of the bounded waits of the two-sweep pass (no counterpart in the paper):
  * launches one block on the current device that waits, through the same bounded
  * mbarrier wait as the pass, on a barrier nothing completes, polling at most spin_limit
@@ -415,7 +492,8 @@ rfb_status rfb_selftest_bounded_wait(int64_t spin_limit, int32_t* gave_up);
 
 /* The FP32 correction kernel the handle's autotuner chose for RFB_PREC_MIXED solves with
  * fp32_kernel = 0 or 2, as an opts.fp32_kernel value: 0 = not chosen yet, 1 = one sweep
- * per launch, 3 / 4 = two-sweep passes in the persistent / chunked launch shape; and the
+ * per launch, 3 / 4 = two-sweep passes in the persistent / chunked launch shape, 5 / 6 the
+ * same with four TMA stages; and the
  * timed device milliseconds per sweep of the one-sweep kernel and of the faster two-sweep
  * shape (0 if not timed). Any output pointer may be NULL. */
 rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,

@@ -5,6 +5,7 @@
 #include "soc_kernels.cuh"
 #include "sweep_tb.cuh"
 #include "sweep_dt.cuh"
+#include "bv_kernels.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -96,6 +97,12 @@ struct rfb_soc_handle {
     double scaled_beta = NAN;
     double* d_stage = nullptr;    // N doubles: host inputs of set_state / set_area_mult
                                   // (allocated on the first such call, then reused)
+    // Butler-Volmer model (one allocation on first use): O, R, H ping-pong, phi, phi_old,
+    // potential right-hand side, kappa_c, membrane kappa, CG r, z, p, q, 1/diag
+    double* d_bv = nullptr;
+    double* d_bvpart = nullptr;   // BV_NB x NRED partials + 16 CG scalars
+    int bv_cur = 0;
+    bool have_bv = false;
 
     int64_t n_fluid = 0, n_elec = 0;
     double sum_w_in = 0, sum_w_out = 0;     // unscaled sums of inlet / outlet W
@@ -119,7 +126,8 @@ struct rfb_soc_handle {
         int64_t per = 0;      // positions per CTA
         dim3 grid;
     } tb_launch[2];
-    int tb_variant = -1;      // -1 not chosen yet
+    int tb_variant = -1;      // -1 not chosen yet; bit 0 the launch shape, bit 1 (step-
+                              // field pass only) four TMA stages instead of three
     bool tm_ready = false;
     CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f, tm_t;
     float* tm_delta_ptr[2] = {nullptr, nullptr};
@@ -468,10 +476,14 @@ void tb_prepare(rfb_soc_handle* h) {
     if (!attr_set[1]) {
         CK(h, cudaFuncSetAttribute(sweep32tb_kernel<true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
-        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TBD_SMEM));
-        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, TBD_SMEM));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<false, 3>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<3>()));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<true, 3>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<3>()));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<false, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<4>()));
+        CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<true, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<4>()));
         attr_set[1] = true;
     }
     for (int q = 0; q < 2; ++q) {
@@ -527,25 +539,32 @@ void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur
     if (local) {
         TBDArgs A{};
         A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
-        const auto& S = h->tb_launch[h->tb_variant > 0 ? 1 : 0];
+        const auto& S = h->tb_launch[std::max(h->tb_variant, 0) & 1];
         A.lc = S.lc; A.total = S.total; A.per = S.per;
         A.d_in = h->d_delta[cur];
         A.d_out = h->d_delta[cur ^ 1];
         A.omc = (float)(1.0 - op.cfl);
         A.Dh = C.Dh;
         A.err = tb_err_word(h);
-        if (tr)
-            sweep32tbd_kernel<true><<<S.grid, TB_THREADS, TBD_SMEM, h->stream>>>(
+        const bool four = h->tb_variant >= 2;
+        if (tr && four)
+            sweep32tbd_kernel<true, 4><<<S.grid, TB_THREADS, tbd_smem<4>(), h->stream>>>(
+                td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+        else if (tr)
+            sweep32tbd_kernel<true, 3><<<S.grid, TB_THREADS, tbd_smem<3>(), h->stream>>>(
+                td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+        else if (four)
+            sweep32tbd_kernel<false, 4><<<S.grid, TB_THREADS, tbd_smem<4>(), h->stream>>>(
                 td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
         else
-            sweep32tbd_kernel<false><<<S.grid, TB_THREADS, TBD_SMEM, h->stream>>>(
+            sweep32tbd_kernel<false, 3><<<S.grid, TB_THREADS, tbd_smem<3>(), h->stream>>>(
                 td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
         LAUNCHED(h);
         return;
     }
     TBArgs A{};
     A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
-    const auto& S = h->tb_launch[h->tb_variant > 0 ? 1 : 0];
+    const auto& S = h->tb_launch[std::max(h->tb_variant, 0) & 1];
     A.lc = S.lc; A.total = S.total; A.per = S.per;
     A.d_in = h->d_delta[cur];
     A.d_out = h->d_delta[cur ^ 1];
@@ -677,8 +696,9 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 std::mutex g_tune_mu;
 
 // Project-written autotuner for one lattice: time 8 plain sweeps and 8 sweeps of each
-// launch shape of the two-sweep pass (CUDA events, on the current forcing) and keep the
-// fastest (tb_only: choose between the two-sweep shapes only).
+// launch shape of the two-sweep pass (with local steps: with three and with four TMA
+// stages) by CUDA events on the current forcing and keep the fastest (tb_only: choose
+// between the two-sweep variants only).
 void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false) {
     if (!tb_eligible(h, op.dt_mode == RFB_DT_LOCAL)) { h->tb_mode = 0; return; }
     const TuneKey key{h->nx, h->ny, h->nz, h->d_m32 != nullptr,
@@ -694,8 +714,10 @@ void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false
             return;
         }
     }
-    float ms[3] = {INFINITY, INFINITY, INFINITY};   // plain, shape 0, shape 1
-    for (int cand = tb_only ? 1 : 0; cand < 3; ++cand) {
+    // candidates: plain, then two-sweep variants 0 .. nvar-1
+    const int nvar = op.dt_mode == RFB_DT_LOCAL ? 4 : 2;
+    float ms[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    for (int cand = tb_only ? 1 : 0; cand <= nvar; ++cand) {
         if (cand > 0) h->tb_variant = cand - 1;
         sweeps32(h, op, 2, cand > 0);   // warm-up (and tensor maps)
         CK(h, cudaEventRecord(h->ev[0], h->stream));
@@ -704,8 +726,11 @@ void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false
         CK(h, cudaEventSynchronize(h->ev[1]));
         CK(h, cudaEventElapsedTime(&ms[cand], h->ev[0], h->ev[1]));
     }
-    h->tb_variant = ms[2] < ms[1] ? 1 : 0;
-    const float tb = std::min(ms[1], ms[2]);
+    int bestv = 0;
+    for (int v = 1; v < nvar; ++v)
+        if (ms[1 + v] < ms[1 + bestv]) bestv = v;
+    h->tb_variant = bestv;
+    const float tb = ms[1 + bestv];
     h->tb_tuned_plain_ms = ms[0] / 8;
     h->tb_tuned_tb_ms = tb / 8;
     if (!tb_only) h->tb_mode = tb < ms[0] ? 1 : 0;
@@ -750,9 +775,11 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
     for (int q = 0; q < 6; ++q)
         if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
     if (o->timeout_ms < 0) { set_err(h, "opts.timeout_ms must be >= 0"); return false; }
-    if (o->fp32_kernel < 0 || o->fp32_kernel > 4) {
-        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep), 2 (two-sweep passes) "
-                   "or 3 / 4 (two-sweep passes, persistent / chunked launch)");
+    if (o->fp32_kernel < 0 || o->fp32_kernel > 6 ||
+        (o->fp32_kernel >= 5 && o->dt_mode != RFB_DT_LOCAL)) {
+        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep), 2 (two-sweep passes), "
+                   "3 / 4 (two-sweep passes, persistent / chunked launch) or, with local "
+                   "steps, 5 / 6 (the same with four TMA stages)");
         return false;
     }
     if (o->fp32_kernel >= 2 && !tb_eligible(h, o->dt_mode == RFB_DT_LOCAL)) {
@@ -838,7 +865,8 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
             if (h->tb_variant < 0) tune_fp32_kernel(h, op, true);
             use_tb = true;
         } else if (o.fp32_kernel >= 3) {
-            h->tb_variant = o.fp32_kernel - 3;   // a forced shape (kept for later calls)
+            // a forced shape (kept for later calls); 5 / 6 with four TMA stages
+            h->tb_variant = o.fp32_kernel <= 4 ? o.fp32_kernel - 3 : (o.fp32_kernel - 5) | 2;
             use_tb = true;
         } else if (o.fp32_kernel == 0) {
             if (h->tb_mode < 0) tune_fp32_kernel(h, op);
@@ -948,7 +976,7 @@ void free_all(rfb_soc_handle* h) {
     // the arena holds flags .. partials; the rest are allocated on first use
     void* ptrs[] = {h->d_arena, h->d_m,    h->d_m32,  h->d_lam[0], h->d_lam[1], h->d_g,
                     h->d_grad,  h->d_L64,  h->d_L2F,  h->d_eta,    h->d_elec,   h->d_sdf[0],
-                    h->d_sdf[1], h->d_gdf,  h->d_stage};
+                    h->d_sdf[1], h->d_gdf,  h->d_stage,  h->d_bv,     h->d_bvpart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -1369,6 +1397,282 @@ rfb_status rfb_soc_solve_nernst(rfb_soc_handle* h, double s_in, double eta, doub
     } catch (Fail f) {
         return f.st;
     }
+}
+
+namespace {
+
+// N-double fields of the Butler-Volmer state in h->d_bv: 0-1 O, 2-3 R, 4-5 H
+// (ping-pong), 6 phi, 7 phi before the last potential solve, 8 right-hand side of the
+// potential equation, 9 kappa_c, 10 membrane kappa, 11-14 CG r, z, p, q; then 1/diag.
+constexpr int BV_FIELDS = 15;
+double* bv_field(rfb_soc_handle* h, int q) { return h->d_bv + (size_t)q * h->N; }
+
+}  // namespace
+
+rfb_status rfb_soc_solve_bv(rfb_soc_handle* h, double s_in, double eta, double tol,
+                            const rfb_bv_params* bvp, const rfb_solve_opts* opts,
+                            rfb_bv_result* res) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    rfb_solve_opts o;
+    if (!read_opts(h, opts, &o)) return RFB_ERR_INVALID_ARG;
+    if (!(s_in >= 0 && s_in <= 1)) { set_err(h, "s_in must be in [0, 1]"); return RFB_ERR_INVALID_ARG; }
+    if (!std::isfinite(eta)) { set_err(h, "eta must be finite"); return RFB_ERR_INVALID_ARG; }
+    if (!(tol > 0)) { set_err(h, "tol must be > 0"); return RFB_ERR_INVALID_ARG; }
+    if (o.precision != RFB_PREC_FP64 || o.dt_mode != RFB_DT_LOCAL || h->kin.mode != RFB_KIN_AFFINE) {
+        set_err(h, "the Butler-Volmer model needs RFB_PREC_FP64, local steps and kinetics mode 0");
+        return RFB_ERR_INVALID_ARG;
+    }
+    rfb_bv_params P{};
+    if (bvp) P = *bvp;
+    if (P.D_H == 0) P.D_H = 9.3e-9;
+    if (P.D_X == 0) P.D_X = 1.38e-9;
+    if (P.c_H_in == 0) P.c_H_in = 50.0 * h->kin.c0;
+    if (P.cg_rtol == 0) P.cg_rtol = 1e-13;
+    if (P.cycle == 0) P.cycle = 100;
+    if (P.max_cg == 0) P.max_cg = 100000;
+    const double cX_in = P.c_H_in - 2.0 * h->kin.c0;
+    if (!(P.D_H > 0) || !(P.D_X > 0) || !std::isfinite(P.D_H + P.D_X) || !(cX_in > 0) ||
+        !std::isfinite(P.c_H_in) || !(P.cg_rtol > 0 && P.cg_rtol < 1) || P.cycle < 1 ||
+        P.max_cg < 1 || P.start < 0 || P.start > 2 || P.reserved != 0) {
+        set_err(h, "bad rfb_bv_params (diffusivities > 0, c_H_in > 2 c0, 0 < cg_rtol < 1, "
+                "cycle, max_cg >= 1, start 0..2, reserved 0)");
+        return RFB_ERR_INVALID_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        OpPoint op = make_op(o, s_in, eta, false);
+        // model refinement needs the converged SBV state of this operating point
+        const bool sbv_ok = h->have_state && h->s_converged && h->op.valid &&
+                            h->op.s_in == s_in && h->op.eta == eta && h->op.beta == op.beta &&
+                            h->op.inlet_bc == op.inlet_bc;
+        if (P.start == 1 && !sbv_ok) {
+            set_err(h, "no converged SBV state at this operating point to refine");
+            return RFB_ERR_STATE;
+        }
+        const bool from_sbv = sbv_ok && P.start != 2;
+        prepare(h, op);   // velocities * beta / h; op.A, op.B
+        const int64_t N = h->N;
+        if (!h->d_bv) {
+            dalloc(h, &h->d_bv, (size_t)BV_FIELDS * N + N);   // + 1/diag of the CG
+            dalloc(h, &h->d_bvpart, (size_t)BV_NB * NRED + 16);
+        }
+        double* dinv = h->d_bv + (size_t)BV_FIELDS * N;
+        double* part = h->d_bvpart;
+        double* sc = h->d_bvpart + (size_t)BV_NB * NRED;   // CG scalars (3) + spare
+        const double VT = R_GAS * h->kin.T / FARADAY;
+        const double hh = h->h * h->h;
+        const double c0 = h->kin.c0;
+        BVArgs A{};
+        A.nx = h->nx; A.ny = h->ny; A.nz = h->nz; A.nxny = h->nxny; A.N = N;
+        A.flags = h->d_flags;
+        A.u = h->d_us; A.v = h->d_vs; A.w = h->d_ws; A.m = h->d_m;
+        const double gin = op.inlet_bc == RFB_INLET_GHOST ? 1.0 : 2.0;
+        const double Dsp[3] = {h->D, h->D, P.D_H};
+        const double zsp[3] = {-2.0, -2.0, 1.0};
+        const double cin[3] = {(1.0 - s_in) * c0, s_in * c0, P.c_H_in};
+        const double nst[3] = {-1.0, 1.0, -2.0};
+        for (int q = 0; q < 3; ++q) {
+            A.sp[q].Dh = Dsp[q] / hh;
+            A.sp[q].gDh = gin * Dsp[q] / hh;
+            A.sp[q].g = zsp[q] * Dsp[q] * FARADAY / (R_GAS * h->kin.T * hh);
+            A.sp[q].c_in = cin[q];
+            A.sp[q].nst = nst[q];
+            A.sp[q].zD = zsp[q] * Dsp[q];
+            A.sp[q].membrane = q == 2;
+        }
+        A.x_zD = -P.D_X;
+        A.x_cin = cX_in;
+        A.lap_in = gin;
+        A.kap0 = h->kin.k0 / h->h;
+        A.alpha = h->kin.alpha;
+        A.Vt = h->kin.n_e * (-eta) / VT;
+        A.ne_VT = h->kin.n_e / VT;
+        A.F = FARADAY;
+        A.pre = FARADAY * FARADAY / (R_GAS * h->kin.T);
+        A.D4 = 4.0 * h->D;
+        A.D_H = P.D_H;
+        A.D_X = P.D_X;
+        A.ne_F = h->kin.n_e * FARADAY;
+        A.h2 = hh;
+        A.cfl = op.cfl;
+        h->bv_cur = 0;
+        bv_init_kernel<<<flat_grid(N), BV_TPB, 0, h->stream>>>(
+            A, from_sbv ? h->d_s[h->s_cur] : nullptr, s_in, c0, bv_field(h, 0),
+            bv_field(h, 2), bv_field(h, 4), bv_field(h, 6));
+        LAUNCHED(h);
+        h->have_bv = true;
+        // tau = V_f / Q as in the SBV residual
+        const double Q = op.beta * h->sum_w_in * hh;
+        const double tau = Q > 0 ? (double)h->n_fluid * hh * h->h / Q
+                                 : std::pow(h->nz * h->h, 2) / h->D;
+        const double scale[3] = {c0, c0, P.c_H_in};
+        std::vector<double> hp((size_t)BV_NB * BV_STATS);
+        double hred[NRED];
+        rfb_bv_result r{};
+        rfb_status st = RFB_OK;
+        auto check = [&]() {   // species residuals and outputs at (C, phi)
+            const int cur = h->bv_cur;
+            bv_check_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(
+                A, bv_field(h, 0 + cur), bv_field(h, 2 + cur), bv_field(h, 4 + cur),
+                bv_field(h, 6), bv_field(h, 8), bv_field(h, 9), bv_field(h, 10), part);
+            LAUNCHED(h);
+            finalize_kernel<<<1, 256, 0, h->stream>>>(part, BV_NB, h->d_red, 0);
+            LAUNCHED(h);
+            CK(h, cudaMemcpyAsync(hred, h->d_red, sizeof hred, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            double resid = 0.0;
+            for (int q = 0; q < 3; ++q)
+                resid = std::max(resid, tau * std::sqrt(hred[q] / (double)h->n_fluid) / scale[q]);
+            r.residual = std::isfinite(hred[0] + hred[1] + hred[2]) ? resid : NAN;
+            r.I_tot = h->kin.n_e * FARADAY * hh * h->h * hred[3];
+            const double denom = h->kin.n_e * FARADAY * c0 * Q * (1.0 - s_in);
+            r.U = denom != 0 ? r.I_tot / denom : NAN;
+            r.s_out = hred[5] != 0 ? hred[4] / hred[5] : NAN;
+            r.I_membrane = hred[6] * h->h;
+            return hred[7];   // max |right-hand side of the potential equation|
+        };
+        // conjugate gradients on -K phi = -bphi, warm-started from the current phi;
+        // returns the largest change of phi
+        auto potential = [&](double bmax) -> double {
+            double* phi = bv_field(h, 6);
+            CK(h, cudaMemcpyAsync(bv_field(h, 7), phi, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+            double* rr = bv_field(h, 11);
+            double* zz = bv_field(h, 12);
+            double* pp = bv_field(h, 13);
+            double* qq = bv_field(h, 14);
+            bv_cg_start_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(A, bv_field(h, 9), bv_field(h, 10),
+                                                                 bv_field(h, 8), phi, rr, zz, pp,
+                                                                 dinv, part);
+            LAUNCHED(h);
+            bv_sum_kernel<<<1, BV_TPB, 0, h->stream>>>(part, BV_NB, sc + 0);
+            LAUNCHED(h);
+            int it = 0;
+            double stats[BV_STATS] = {0, 0, 0, 0, 0, 0};
+            auto read_stats = [&]() {
+                bv_potential_stats_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(
+                    A, bv_field(h, 9), bv_field(h, 10), bv_field(h, 8), phi, bv_field(h, 7), part);
+                LAUNCHED(h);
+                CK(h, cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost,
+                                      h->stream));
+                CK(h, cudaStreamSynchronize(h->stream));
+                stats[0] = stats[1] = stats[2] = stats[5] = 0.0;
+                stats[3] = INFINITY; stats[4] = -INFINITY;
+                for (int b = 0; b < BV_NB; ++b) {
+                    const double* q = &hp[(size_t)b * BV_STATS];
+                    stats[0] = std::max(stats[0], q[0]);
+                    stats[1] = std::max(stats[1], q[1]);
+                    stats[2] += q[2];
+                    stats[3] = std::min(stats[3], q[3]);
+                    stats[4] = std::max(stats[4], q[4]);
+                    stats[5] = std::max(stats[5], q[5]);
+                }
+            };
+            // done at cg_rtol of the right-hand side, or at the rounding floor of the
+            // residual (64 eps of the largest diag |phi| term), or when 20 checks in a row
+            // brought no halving (stagnation at that floor)
+            auto done_cg = [&]() {
+                return stats[0] <= std::max(P.cg_rtol * bmax, 64.0 * 2.2e-16 * stats[5]);
+            };
+            read_stats();
+            double best = stats[0];
+            int stall = 0;
+            while (!done_cg() && it < P.max_cg && stall < 20) {
+                for (int k = 0; k < 50 && it < P.max_cg; ++k, ++it) {
+                    bv_cg_matvec_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(
+                        A, bv_field(h, 9), bv_field(h, 10), pp, qq, part);
+                    bv_sum_kernel<<<1, BV_TPB, 0, h->stream>>>(part, BV_NB, sc + 1);
+                    bv_cg_update_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(N, sc, phi, rr, zz, pp,
+                                                                          qq, dinv, part);
+                    bv_sum_kernel<<<1, BV_TPB, 0, h->stream>>>(part, BV_NB, sc + 2);
+                    bv_cg_direction_kernel<<<BV_NB, BV_TPB, 0, h->stream>>>(N, sc, pp, zz);
+                    bv_copy_scalar_kernel<<<1, 1, 0, h->stream>>>(sc);
+                    h->launches += 6;
+                }
+                read_stats();
+                if (!std::isfinite(stats[0])) break;
+                if (stats[0] < 0.5 * best) { best = stats[0]; stall = 0; }
+                else ++stall;
+            }
+            r.cg_iterations += it;
+            r.phi_mean = stats[2] / (double)h->n_fluid;
+            r.phi_min = stats[3];
+            r.phi_max = stats[4];
+            if (!done_cg() && std::isfinite(stats[0]) && stall < 20) {
+                set_err(h, "potential solve: max residual %.3e after %d iterations", stats[0], it);
+            }
+            return stats[1];
+        };
+        // From a cold start the species first relax at phi = 0 (the SBV problem) until
+        // their residual is below 1e-3 (or tol): a potential solved from the far-from-
+        // steady reaction currents of s = s_in would feed back exponentially through the
+        // source. From the SBV state the potential is solved at once.
+        bool potential_on = from_sbv;
+        int64_t done = 0;
+        while (true) {
+            const double bmax = check();
+            if (!potential_on && r.residual <= std::max(1e-3, tol)) potential_on = true;
+            if (potential_on) {
+                r.dphi = potential(bmax);
+                ++r.cycles;
+                check();
+            } else {
+                r.dphi = INFINITY;
+            }
+            if (!std::isfinite(r.residual) || (potential_on && !std::isfinite(r.dphi))) {
+                st = RFB_ERR_NONFINITE;
+                break;
+            }
+            if (r.residual <= tol && r.dphi <= tol * VT / h->kin.n_e) break;
+            if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
+                                        std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
+                set_err(h, "opts.timeout_ms reached after %lld sweeps", (long long)done);
+                st = RFB_ERR_NOT_CONVERGED;
+                break;
+            }
+            const int64_t n = std::min<int64_t>(P.cycle, o.max_sweeps - done);
+            for (int64_t q = 0; q < n; ++q) {
+                const int cur = h->bv_cur;
+                bv_sweep_kernel<<<flat_grid(N), BV_TPB, 0, h->stream>>>(
+                    A, bv_field(h, 0 + cur), bv_field(h, 2 + cur), bv_field(h, 4 + cur),
+                    bv_field(h, 6), bv_field(h, 1 - cur), bv_field(h, 3 - cur),
+                    bv_field(h, 5 - cur));
+                LAUNCHED(h);
+                h->bv_cur ^= 1;
+            }
+            done += n;
+        }
+        r.sweeps = done;
+        r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (res) *res = r;
+        return st;
+    } catch (Fail f) {
+        return f.st;
+    }
+}
+
+rfb_status rfb_soc_get_bv_state(rfb_soc_handle* h, double* c_o, double* c_r, double* c_h,
+                                double* phi, rfb_mem_kind kind) {
+    rfb_status g = guard(h);
+    if (g) return g;
+    if (kind != RFB_MEM_HOST && kind != RFB_MEM_DEVICE) { set_err(h, "bad kind"); return RFB_ERR_INVALID_ARG; }
+    if (!h->have_bv) { set_err(h, "no Butler-Volmer state: call rfb_soc_solve_bv first"); return RFB_ERR_STATE; }
+    try {
+        double* outs[4] = {c_o, c_r, c_h, phi};
+        const int fld[4] = {0 + h->bv_cur, 2 + h->bv_cur, 4 + h->bv_cur, 6};
+        for (int q = 0; q < 4; ++q) {
+            if (!outs[q]) continue;
+            CK(h, cudaMemcpyAsync(outs[q], bv_field(h, fld[q]), h->N * 8,
+                                  kind == RFB_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                       : cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+    } catch (Fail f) {
+        return f.st;
+    }
+    return RFB_OK;
 }
 
 rfb_status rfb_soc_get_overpotential(rfb_soc_handle* h, double* eta_t, rfb_mem_kind kind) {
@@ -1810,7 +2114,10 @@ rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
     if (!h) return RFB_ERR_INVALID_ARG;
     int32_t k = 0;
     if (h->tb_mode == 0) k = 1;
-    else if (h->tb_mode == 1 || h->tb_variant >= 0) k = 3 + std::max(h->tb_variant, 0);
+    else if (h->tb_mode == 1 || h->tb_variant >= 0) {
+        const int v = std::max(h->tb_variant, 0);
+        k = (v & 2 ? 5 : 3) + (v & 1);
+    }
     if (kernel) *kernel = k;
     if (plain_ms_per_sweep) *plain_ms_per_sweep = h->tb_tuned_plain_ms;
     if (blocked_ms_per_sweep) *blocked_ms_per_sweep = h->tb_tuned_tb_ms;
@@ -1929,6 +2236,36 @@ extern "C" rfb_status rfb_soc_current_noalloc(rfb_soc_handle* h, rfb_solve_resul
 // =====================================================================================
 // Batches (many lattices, one persistent launch per sweep, one CUDA graph per cycle)
 // =====================================================================================
+namespace {
+
+// Cycle budget of one launch of the device-driven batch loop (set by the host before each
+// launch) and the cycles run (counted on the device).
+struct BatchLoop {
+    int cycles;
+    int max_cycles;
+    int n_inst;
+    int pad_;
+};
+
+// Last node of the loop body: counts the cycle and sets the while node's condition, 1 while
+// a lattice is still active (not converged, finite) and the budget is not spent.
+__global__ void batch_loop_kernel(const BatchCtl* __restrict__ ctl, BatchLoop* __restrict__ lp,
+                                  cudaGraphConditionalHandle hc) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < lp->n_inst; q += blockDim.x)
+        if (!ctl[q].converged && !ctl[q].nonfinite) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int c = lp->cycles + 1;
+        lp->cycles = c;
+        cudaGraphSetConditional(hc, (any && c < lp->max_cycles) ? 1u : 0u);
+    }
+}
+
+}  // namespace
+
 struct rfb_batch {
     std::vector<rfb_soc_handle*> hs;
     int device = 0;
@@ -1952,6 +2289,12 @@ struct rfb_batch {
     double tuned_sweep_ms = 0, tuned_check_ms = 0;
     cudaGraphExec_t exec = nullptr;
     int exec_every = 0;
+    // device-driven loop: a graph whose while node repeats the cycle until every lattice
+    // has converged or the launch's cycle budget is spent
+    cudaGraphExec_t loop_exec = nullptr;
+    int loop_every = 0;
+    BatchLoop* d_loop = nullptr;
+    BatchLoop* h_loop = nullptr;         // pinned
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::string err;
     int64_t launches = 0;
@@ -2019,6 +2362,7 @@ void build_items(rfb_batch* b, int kchunk) {
     b->n_items = (int)items.size();
     b->items_kchunk = kchunk;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
 }
 
 void batch_sweeps(rfb_batch* b, int n, bool local) {
@@ -2047,14 +2391,59 @@ void batch_check(rfb_batch* b, bool fused, int sweeps_done) {
 }
 
 // One correction cycle: delta = 0, `every` sweeps, fused FP64 check, bookkeeping, and
-// the control block copied to the host.
-void batch_cycle(rfb_batch* b, int every, bool local) {
+// (to_host) the control block copied to the host.
+void batch_cycle(rfb_batch* b, int every, bool local, bool to_host = true) {
     batch_zero_kernel<<<152 * 4, 256, 0, b->stream>>>(b->d_insts, (int)b->hs.size());
     BLAUNCHED(b);
     batch_sweeps(b, every, local);
     batch_check(b, true, every);
-    BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->hs.size() * sizeof(BatchCtl),
-                           cudaMemcpyDeviceToHost, b->stream));
+    if (to_host)
+        BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->hs.size() * sizeof(BatchCtl),
+                               cudaMemcpyDeviceToHost, b->stream));
+}
+
+// The device-driven solve graph: one conditional while node whose body is a cycle
+// followed by batch_loop_kernel, which counts the cycle and keeps the loop going while a
+// lattice is still active and the launch's cycle budget (BatchLoop::max_cycles, written
+// by the host before each launch) is not spent. No host round trip between cycles.
+void build_loop_graph(rfb_batch* b, int every, bool local) {
+    if (b->loop_exec && b->loop_every == every) return;
+    if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaGraphCreate(&g, 0));
+    try {
+        cudaGraphConditionalHandle hc;
+        BCK(b, cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        BCK(b, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        BCK(b, cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = b->launches;
+        try {
+            batch_cycle(b, every, local, false);
+            batch_loop_kernel<<<1, 32, 0, b->stream>>>(b->d_ctl, b->d_loop, hc);
+            BLAUNCHED(b);
+        } catch (Fail) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(b->stream, &dummy);
+            throw;
+        }
+        b->launches = l0;   // counted when run
+        cudaGraph_t captured = nullptr;
+        BCK(b, cudaStreamEndCapture(b->stream, &captured));
+        BCK(b, cudaGraphInstantiate(&b->loop_exec, g, 0));
+    } catch (Fail) {
+        cudaGraphDestroy(g);
+        throw;
+    }
+    cudaGraphDestroy(g);
+    b->loop_every = every;
 }
 
 // Project-written autotuner: for each candidate z-chunk of the work items, time a few
@@ -2133,6 +2522,8 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
         BCK(b, cudaMalloc((void**)&b->d_insts, n * sizeof(BatchInst)));
         BCK(b, cudaMalloc((void**)&b->d_ctl, n * sizeof(BatchCtl)));
         BCK(b, cudaMallocHost((void**)&b->h_ctl, n * sizeof(BatchCtl)));
+        BCK(b, cudaMalloc((void**)&b->d_loop, sizeof(BatchLoop)));
+        BCK(b, cudaMallocHost((void**)&b->h_loop, sizeof(BatchLoop)));
         BCK(b, cudaEventCreate(&b->ev[0]));
         BCK(b, cudaEventCreate(&b->ev[1]));
         int sms = 152, per = 4;
@@ -2154,10 +2545,12 @@ rfb_status rfb_soc_batch_destroy(rfb_batch* b) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    void* ptrs[] = {b->d_insts, b->d_ctl, b->d_items, b->d_item_begin, b->d_partials};
+    if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
+    void* ptrs[] = {b->d_insts, b->d_ctl, b->d_items, b->d_item_begin, b->d_partials, b->d_loop};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->h_loop) cudaFreeHost(b->h_loop);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->stream && b->own_stream) cudaStreamDestroy(b->stream);
@@ -2245,8 +2638,21 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl), cudaMemcpyDeviceToHost,
                                b->stream));
         BCK(b, cudaStreamSynchronize(b->stream));
-        // capture one cycle as a CUDA graph (rebuilt when the cycle length changes)
-        if (!b->exec || b->exec_every != every) {
+        int64_t done = 0;
+        rfb_status st = RFB_OK;
+        auto all_done = [&]() {
+            for (int q = 0; q < n; ++q)
+                if (!b->h_ctl[q].converged && !b->h_ctl[q].nonfinite) return false;
+            return true;
+        };
+        // Without a timeout the cycles run in a device-driven loop (a conditional while
+        // node): one graph launch runs up to 64 cycles and stops by itself once every
+        // lattice has converged, so the host waits once per launch, not once per cycle.
+        // A timeout needs the host between cycles: one captured cycle per launch.
+        const bool device_loop = o.timeout_ms == 0;
+        if (device_loop) {
+            build_loop_graph(b, every, local);
+        } else if (!b->exec || b->exec_every != every) {
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             cudaGraph_t g = nullptr;
             BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -2264,15 +2670,31 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             cudaGraphDestroy(g);
             b->exec_every = every;
         }
-        int64_t done = 0;
-        rfb_status st = RFB_OK;
-        auto all_done = [&]() {
-            for (int q = 0; q < n; ++q)
-                if (!b->h_ctl[q].converged && !b->h_ctl[q].nonfinite) return false;
-            return true;
-        };
+        int64_t graph_launches = 0;
         while (!all_done()) {
             if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+            if (device_loop) {
+                const int64_t left = (o.max_sweeps - done + every - 1) / every;
+                BatchLoop lp{0, (int)std::min<int64_t>(64, left), n, 0};
+                *b->h_loop = lp;
+                BCK(b, cudaMemcpyAsync(b->d_loop, b->h_loop, sizeof(BatchLoop),
+                                       cudaMemcpyHostToDevice, b->stream));
+                BCK(b, cudaGraphLaunch(b->loop_exec, b->stream));
+                BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl),
+                                       cudaMemcpyDeviceToHost, b->stream));
+                BCK(b, cudaMemcpyAsync(b->h_loop, b->d_loop, sizeof(BatchLoop),
+                                       cudaMemcpyDeviceToHost, b->stream));
+                BCK(b, cudaStreamSynchronize(b->stream));
+                const int cyc = b->h_loop->cycles;
+                b->launches += (int64_t)cyc * (every + 4);
+                done += (int64_t)cyc * every;
+                ++graph_launches;
+                if (cyc < 1) {
+                    bset_err(b, "the device-driven batch loop ran no cycle");
+                    throw Fail{RFB_ERR_CUDA};
+                }
+                continue;
+            }
             if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
                                         std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
                 bset_err(b, "opts.timeout_ms reached after %lld sweeps", (long long)done);
@@ -2283,6 +2705,7 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             b->launches += every + 3;
             BCK(b, cudaStreamSynchronize(b->stream));
             done += every;
+            ++graph_launches;
         }
         BCK(b, cudaMemcpy(insts.data(), b->d_insts, n * sizeof(BatchInst), cudaMemcpyDeviceToHost));
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2309,6 +2732,7 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             info->sweep_ms = b->tuned_sweep_ms;
             info->check_ms = b->tuned_check_ms;
             info->cycles = done / every;
+            info->graph_launches = graph_launches;
             info->time_ms = ms;
             info->launches = b->launches;
         }
@@ -2332,6 +2756,7 @@ extern "C" rfb_status rfb_soc_batch_set_stream(rfb_batch* b, void* stream) {
         BCK(b, cudaSetDevice(b->device));
         BCK(b, cudaStreamSynchronize(b->stream));
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
         if (b->own_stream) { cudaStreamDestroy(b->stream); b->own_stream = false; }
         b->stream = (cudaStream_t)stream;
     } catch (Fail f) {

@@ -16,8 +16,9 @@
 // neighbour's inflow from it), with the same diagonal.
 //
 // sweep32d_kernel applies one sweep; sweep32tbd_kernel two sweeps per pass over HBM,
-// planes staged by TMA through a three-stage mbarrier ring (the scheme of sweep_tb.cuh,
-// with the step plane in place of the mask plane). Both evaluate every update with
+// planes staged by TMA through a three- or four-stage mbarrier ring (the scheme of
+// sweep_tb.cuh, with the step plane in place of the mask plane; four stages keep three
+// planes in flight and use 221 KB of shared memory). Both evaluate every update with
 // dt_update below in the same operation order, so a pass is bitwise two sweeps.
 #pragma once
 
@@ -128,9 +129,10 @@ sweep32d_kernel(DArgs A, const float* __restrict__ s, float* __restrict__ s_out,
 // planes (delta, forcing, u, v, w, step).
 // ---------------------------------------------------------------------------------
 constexpr int TBD_STAGE = 6 * TB_F32;
-constexpr int TBD_L1 = TB_NSTAGE * TBD_STAGE;       // offset of the two level-1 planes
-constexpr int TBD_BAR = TBD_L1 + 2 * TB_F32;        // offset of the stage barriers
-constexpr int TBD_SMEM = TBD_BAR + 64 + 128;        // + alignment slack for the base
+template <int NST> __host__ __device__ constexpr int tbd_l1() { return NST * TBD_STAGE; }   // level-1 planes
+template <int NST> __host__ __device__ constexpr int tbd_bar() { return tbd_l1<NST>() + 2 * TB_F32; }   // barriers
+template <int NST> __host__ __device__ constexpr int tbd_smem() { return tbd_bar<NST>() + 64 + 128; }  // + slack
+static_assert(tbd_smem<4>() <= 232448, "four stages fit the 227 KB a CTA may use");
 constexpr uint32_t TBD_TX_BYTES = 6 * TB_F32;
 
 struct TBDArgs {
@@ -144,7 +146,7 @@ struct TBDArgs {
     unsigned int* err;                // set if a stage never arrives
 };
 
-template <bool TR>
+template <bool TR, int NST>
 __global__ void __launch_bounds__(TB_THREADS, 1)
 sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_r,
                   const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_v,
@@ -153,7 +155,7 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TBD_BAR);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tbd_bar<NST>());
     const int tid = threadIdx.x;
     const int tx = tid % TB_GX, ty = tid / TB_GX;
     const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
@@ -175,7 +177,7 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
     };
 
     if (tid == 0) {
-        for (int s = 0; s < TB_NSTAGE; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -210,7 +212,7 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
             tma_load_3d(S + 5 * TB_F32, &tm_t, x0, y0, p, &bar[s]);
         };
         __syncthreads();   // the previous segment's readers are done with every stage
-        for (int s = 0; s < TB_NSTAGE; ++s) issue(kb - 1 + s, s);       // kb-1, kb, kb+1
+        for (int s = 0; s < NST; ++s) issue(kb - 1 + s, s);             // kb-1, kb, ...
 
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 l1_m2 = zero4, l1_m1 = zero4;           // own level 1 at z-2, z-1
@@ -230,7 +232,7 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
 
         auto step = [&](int z, CoefD (&kc)[4], float4& rr, float4& dc,
                         const CoefD (&pkc)[4], const float4& prr, const float4& pdc) -> bool {
-            const int s1 = s0 == TB_NSTAGE - 1 ? 0 : s0 + 1;
+            const int s1 = s0 == NST - 1 ? 0 : s0 + 1;
             if (good) good = wait(s1);
             const float* D0 = reinterpret_cast<const float*>(stage(s0));
             const float* R0 = D0 + TB_PLANE;
@@ -267,13 +269,13 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
                                        el(pdc, e), el(dn, e), el(rr, e));
                 l1 = make_float4(out[0], out[1], out[2], out[3]);
             }
-            float* L1w = reinterpret_cast<float*>(smem + TBD_L1) + (z & 1) * TB_PLANE;
+            float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST>()) + (z & 1) * TB_PLANE;
             *reinterpret_cast<float4*>(L1w + o) = l1;
             // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
             const int zz = z - 1;
             if (zz >= kb && interior && in_dom) {
                 const float* L1r =
-                    reinterpret_cast<const float*>(smem + TBD_L1) + (zz & 1) * TB_PLANE;
+                    reinterpret_cast<const float*>(smem + tbd_l1<NST>()) + (zz & 1) * TB_PLANE;
                 const float lxm = L1r[o - 1], lxp = L1r[o + 4];
                 const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
                 float out[4];
@@ -288,9 +290,9 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
             }
             l1_m2 = l1_m1;
             l1_m1 = l1;
-            // ---- all threads are done with stage s0: refill it with plane z + 3
+            // ---- all threads are done with stage s0: refill it with plane z + NST
             if (!__syncthreads_and(good)) return false;
-            if (z + 3 <= ke + 1) issue(z + 3, s0);
+            if (z + NST <= ke + 1) issue(z + NST, s0);
             s0 = s1;
             return true;
         };
@@ -302,7 +304,7 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
         }
     }
     if (!ok) {
-        for (int s = 0; s < TB_NSTAGE; ++s)
+        for (int s = 0; s < NST; ++s)
             if (pend & (1u << s)) (void)wait(s);
     }
 }

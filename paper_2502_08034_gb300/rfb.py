@@ -50,6 +50,25 @@ class SolveResult(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class BVParams(ctypes.Structure):
+    _fields_ = [("D_H", c_double), ("D_X", c_double), ("c_H_in", c_double),
+                ("cg_rtol", c_double), ("cycle", c_int32), ("max_cg", c_int32),
+                ("start", c_int32), ("reserved", c_int32)]
+
+
+class BVResult(ctypes.Structure):
+    _fields_ = [("sweeps", c_int64), ("cycles", c_int64), ("cg_iterations", c_int64),
+                ("residual", c_double), ("dphi", c_double), ("I_tot", c_double),
+                ("U", c_double), ("s_out", c_double), ("I_membrane", c_double),
+                ("phi_mean", c_double), ("phi_min", c_double), ("phi_max", c_double),
+                ("time_ms", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+BV_START = {"auto": 0, "sbv": 1, "cold": 2}
+
 _LIB = None
 
 
@@ -107,6 +126,9 @@ def lib():
         L.rfb_soc_solve_nernst.argtypes = [H, c_double, c_double, c_double, c_double,
                                            POINTER(SolveOpts), POINTER(SolveResult)]
         L.rfb_soc_get_overpotential.argtypes = [H, c_void_p, c_int]
+        L.rfb_soc_solve_bv.argtypes = [H, c_double, c_double, c_double, POINTER(BVParams),
+                                       POINTER(SolveOpts), POINTER(BVResult)]
+        L.rfb_soc_get_bv_state.argtypes = [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int]
         for name in ("rfb_soc_create", "rfb_soc_destroy", "rfb_soc_set_stream", "rfb_soc_solve",
                      "rfb_soc_step", "rfb_soc_current", "rfb_soc_umt", "rfb_soc_get_state",
                      "rfb_soc_set_state", "rfb_soc_info", "rfb_soc_reset_state",
@@ -114,7 +136,7 @@ def lib():
                      "rfb_soc_adjoint", "rfb_soc_batch_create", "rfb_soc_batch_solve",
                      "rfb_soc_batch_destroy", "rfb_soc_tuned_fp32_kernel",
                      "rfb_selftest_bounded_wait", "rfb_soc_solve_nernst",
-                     "rfb_soc_get_overpotential"):
+                     "rfb_soc_get_overpotential", "rfb_soc_solve_bv", "rfb_soc_get_bv_state"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -127,7 +149,7 @@ class RfbError(RuntimeError):
 
 
 FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2, "blocked_persistent": 3,
-               "blocked_chunked": 4}
+               "blocked_chunked": 4, "blocked4_persistent": 5, "blocked4_chunked": 6}
 
 
 def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
@@ -253,6 +275,29 @@ class Solver:
         out["status"] = st
         return out
 
+    def solve_bv(self, s_in, eta, tol, D_H=0.0, D_X=0.0, c_H_in=0.0, cg_rtol=0.0, cycle=0,
+                 max_cg=0, start="auto", allow_not_converged=False, **opts) -> dict:
+        """rfb_soc_solve_bv: the Butler-Volmer model with electromigration (FP64); zero
+        parameters take the library's defaults."""
+        q = BVParams(float(D_H), float(D_X), float(c_H_in), float(cg_rtol), int(cycle),
+                     int(max_cg), BV_START[start] if isinstance(start, str) else int(start), 0)
+        r = BVResult()
+        o = make_opts(**opts)
+        st = lib().rfb_soc_solve_bv(self.h, float(s_in), float(eta), float(tol), byref(q),
+                                    byref(o), byref(r))
+        self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
+        out = r.as_dict()
+        out["status"] = st
+        return out
+
+    def get_bv_state(self) -> dict:
+        """The last Butler-Volmer state: C_O, C_R, C_H [mol/m^3] and phi [V] (host arrays)."""
+        out = {k: np.empty(self.n_cells, dtype=np.float64) for k in ("O", "R", "H", "phi")}
+        self._check(lib().rfb_soc_get_bv_state(
+            self.h, out["O"].ctypes.data, out["R"].ctypes.data, out["H"].ctypes.data,
+            out["phi"].ctypes.data, MEM_HOST))
+        return out
+
     def get_overpotential(self, out=None):
         """eta~ of the last Nernst-model solve (N values, 0 off the electrode cells)."""
         if out is None:
@@ -334,7 +379,8 @@ class Solver:
         """(name, plain ms/sweep, blocked ms/sweep) chosen by the autotuner."""
         k, a, b = c_int32(), c_double(), c_double()
         self._check(lib().rfb_soc_tuned_fp32_kernel(self.h, byref(k), byref(a), byref(b)))
-        names = {0: None, 1: "plain", 3: "blocked_persistent", 4: "blocked_chunked"}
+        names = {0: None, 1: "plain", 3: "blocked_persistent", 4: "blocked_chunked",
+                 5: "blocked4_persistent", 6: "blocked4_chunked"}
         return names[k.value], a.value, b.value
 
     def close(self):
@@ -358,7 +404,8 @@ class Solver:
 class BatchInfo(ctypes.Structure):
     _fields_ = [("kchunk", c_int32), ("sweeps_per_cycle", c_int32), ("n_items", c_int32),
                 ("grid_blocks", c_int32), ("sweep_ms", c_double), ("check_ms", c_double),
-                ("cycles", c_int64), ("time_ms", c_double), ("launches", c_int64)]
+                ("cycles", c_int64), ("time_ms", c_double), ("launches", c_int64),
+                ("graph_launches", c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -255,7 +255,8 @@ def test_binding_structs_match_the_header():
     cmap = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
     s = _header_structs()
     for cname, py in (("rfb_kinetics", rfb.Kinetics), ("rfb_solve_opts", rfb.SolveOpts),
-                      ("rfb_solve_result", rfb.SolveResult), ("rfb_batch_info", rfb.BatchInfo)):
+                      ("rfb_solve_result", rfb.SolveResult), ("rfb_batch_info", rfb.BatchInfo),
+                      ("rfb_bv_params", rfb.BVParams), ("rfb_bv_result", rfb.BVResult)):
         want = s[cname]
         got = py._fields_
         assert [f[0] for f in got] == [f[0] for f in want], cname

@@ -96,3 +96,15 @@ def test_kernel_traffic_scales_with_the_cells_and_names_its_kernel():
         assert bench.kernel_traffic(2 ** 25, kernel) == b * 2 ** 25
         assert b >= bench.SWEEP_BYTES_PER_CELL - 0.5    # no launch moves less than its inputs
     assert bench.kernel_traffic(1000, "no_such_kernel") is None
+
+
+def test_oracle_baselines_on_every_core_and_to_steady_state():
+    """The CPU baseline's all-core figure runs one spawned process per slab at once and
+    adds their cell updates; the serial time to steady state runs the oracle's loop to the
+    tolerance."""
+    from tests._cases import fiber_case
+    case = fiber_case((16, 16, 32))
+    rate, workers, sec = bench.oracle_all_cores(case, n_planes=8, sweeps=5)
+    assert workers == min(os.cpu_count() or 1, 4) and rate > 0 and sec > 0
+    t, n = bench.oracle_time_to_steady(case, 1e-8)
+    assert t > 0 and 0 < n < 100000

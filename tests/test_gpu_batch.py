@@ -1,5 +1,6 @@
-"""Batched solves (one persistent launch per sweep over every lattice, CUDA-graph cycles,
-autotuned work items) against the oracle and against one-lattice solves."""
+"""Batched solves (one persistent launch per sweep over every lattice, CUDA-graph cycles
+driven from the device, autotuned work items) against the oracle and against one-lattice
+solves."""
 import functools
 
 import numpy as np
@@ -50,6 +51,33 @@ def test_small_batch_matches_oracle_and_single_solves():
     finally:
         for s in solvers:
             s.close()
+
+
+def test_device_driven_loop_equals_the_host_driven_cycles():
+    """Without a timeout the cycles run in the device-driven loop (a conditional while
+    node; a few graph launches for the whole solve); with one, one captured cycle per
+    launch with the host in between. Both run the same cycles: bitwise the same states,
+    sweep counts and residuals."""
+    from paper_2502_08034_gb300 import rfb
+    cases = _small_batch()
+    out = []
+    for timeout in (0, 600000):
+        solvers = [rfb.Solver.from_case(c) for c in cases]
+        try:
+            with rfb.Batch(solvers) as b:
+                res, info = b.solve([c.s_in for c in cases], [c.eta for c in cases],
+                                    [1e-10] * len(cases), check_every=40, timeout_ms=timeout)
+            out.append(([s.get_state() for s in solvers], res, info))
+        finally:
+            for s in solvers:
+                s.close()
+    (sa, ra, ia), (sb, rb, ib) = out
+    assert ia["cycles"] == ib["cycles"] and ib["graph_launches"] == ib["cycles"]
+    assert ia["graph_launches"] == -(-ia["cycles"] // 64) < ia["cycles"]
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    for x, y in zip(ra, rb):
+        assert x["sweeps"] == y["sweeps"] and x["residual"] == y["residual"]
 
 
 def test_batch_second_solve_reuses_tuning_and_warm_starts():

@@ -36,7 +36,10 @@ def test_two_sweep_pass_is_bitwise_two_sweeps(dims, dt_mode):
     from paper_2502_08034_gb300 import rfb
     case = _case(dims)
     states = []
-    for kernel in ("plain", "blocked_persistent", "blocked_chunked", "blocked"):
+    kernels = ["plain", "blocked_persistent", "blocked_chunked", "blocked"]
+    if dt_mode == "local":      # the step-field pass also runs with four TMA stages
+        kernels += ["blocked4_persistent", "blocked4_chunked"]
+    for kernel in kernels:
         with rfb.Solver.from_case(case) as sv:
             for n in (6, 10, 4):      # several correction cycles
                 sv.step(case.s_in, case.eta, n, precision="mixed", dt_mode=dt_mode,
@@ -110,7 +113,8 @@ def test_step_field_pass_is_bitwise_with_area_multipliers_and_nx_multiple_of_4(d
     case = _case(dims)
     m = synth.lognormal_area_mult(case.solid, 0.3, 40)
     states = []
-    for kernel in ("plain", "blocked_persistent", "blocked_chunked"):
+    for kernel in ("plain", "blocked_persistent", "blocked_chunked", "blocked4_persistent",
+                   "blocked4_chunked"):
         with rfb.Solver.from_case(case, area_mult=m) as sv:
             for n in (6, 9):
                 sv.step(case.s_in, case.eta, n, precision="mixed", fp32_kernel=kernel)

@@ -1,0 +1,133 @@
+"""Full-size lattices against the oracle, element by element.
+
+tests/golden/make_fullsize.py ran the CPU oracle on the same seeded inputs and stored its
+steady states at 100,000 sampled fluid cells plus every fluid cell of the inlet and
+outlet planes, its outputs, U_mt and (differentiation lattice) gradients. Here the same
+inputs are rebuilt with the GPU potential-flow fixture, checked against the flow samples
+of the file (both flows sit at the CG rounding floor, ~1e-13 of the mean velocity apart),
+and solved through the C ABI:
+  - in the benchmark's configuration (mixed precision, autotuned FP32 kernel, local
+    steps, residual 1e-8): max |s - s_oracle| <= 1e-6 at the samples, outputs within 1e-6;
+  - on the FP64 path to residual 1e-12: max |s - s_oracle| <= 1e-10 max |s_oracle|,
+    I_tot and U within 1e-10;
+  - adjoint gradients (FP64) within 1e-9 of the oracle's, mixed-precision ones within
+    1e-8.
+"""
+import functools
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_08034_gb300 import _build
+    _build.build()
+
+
+@functools.lru_cache(maxsize=None)
+def _gold(name):
+    with np.load(os.path.join(GOLDEN, "fullsize_%s.npz" % name)) as z:
+        return {k: z[k] for k in z.files}
+
+
+def _check_flow(case, g):
+    """The GPU-built potential flow agrees with the one the oracle was given."""
+    assert int((case.solid == 0).sum()) == int(g["n_fluid"])
+    q = case.info["superficial_q"]
+    assert abs(q - float(g["flow_q"])) <= 1e-10 * float(g["flow_q"])
+    for key, arr in (("W", case.W), ("U", case.U), ("V", case.V)):
+        got = arr.ravel()[g["flow_%s_idx" % key]]
+        assert np.abs(got - g["flow_%s" % key]).max() <= 1e-10 * case.u_mean, key
+
+
+def _check_state(s, r, g, tol_s, tol_out, relative):
+    idx = g["idx"]
+    ref = g["s"]
+    err = float(np.abs(s[idx] - ref).max())
+    if relative:
+        err /= float(np.abs(ref).max())
+    assert err <= tol_s, err
+    for k in ("I_tot", "U", "F_out"):
+        assert abs(r[k] - float(g[k])) <= tol_out * abs(float(g[k])), (k, r[k], float(g[k]))
+    return err
+
+
+def test_benchmark_lattice_256x256x512_against_the_oracle():
+    from paper_2502_08034_gb300 import rfb, synth
+    g = _gold("mixed256")
+    case = synth.large_mixed_case(flow_device="cuda")
+    _check_flow(case, g)
+    with rfb.Solver.from_case(case, device_inputs=True) as sv:
+        r = sv.solve(case.s_in, case.eta, case.tol, precision="mixed")
+        assert r["residual"] <= case.tol
+        e_mixed = _check_state(sv.get_state(), r, g, 1e-6, 1e-6, False)
+        u_mt, _ = sv.umt(case.tol, precision="mixed")
+        assert abs(u_mt - float(g["U_mt"])) <= 1e-6
+        sv.reset_state()
+        r64 = sv.solve(case.s_in, case.eta, 1e-12, precision="fp64")
+        e64 = _check_state(sv.get_state(), r64, g, 1e-10, 1e-10, True)
+        u64, _ = sv.umt(1e-12, precision="fp64")
+        assert abs(u64 - float(g["U_mt"])) <= 1e-10
+    print("256x256x512: mixed max|ds| %.2e, FP64 max rel %.2e, U_mt %.2e / %.2e" % (
+        e_mixed, e64, abs(u_mt - float(g["U_mt"])), abs(u64 - float(g["U_mt"]))))
+
+
+def test_differentiation_lattice_128x128x256_against_the_oracle():
+    from paper_2502_08034_gb300 import rfb, synth
+    g = _gold("adjoint128")
+    case = synth.adjoint_case(flow_device="cuda")
+    m = synth.lognormal_area_mult(case.solid, 0.3, 40)
+    _check_flow(case, g)
+    gi = g["grad_idx"]
+    with rfb.Solver.from_case(case, area_mult=m, device_inputs=True) as sv:
+        r = sv.solve(case.s_in, case.eta, 1e-12, precision="fp64")
+        _check_state(sv.get_state(), r, g, 1e-10, 1e-10, True)
+        for obj in ("I_tot", "U"):
+            want_m, want_b = g["dm_%s" % obj], float(g["dbeta_%s" % obj])
+            dm, db, _ = sv.adjoint(obj, 1e-12)
+            assert np.abs(dm[gi] - want_m).max() <= 1e-9 * np.abs(want_m).max(), obj
+            assert abs(db - want_b) <= 1e-9 * abs(want_b), obj
+            dm, db, _ = sv.adjoint(obj, 1e-10, precision="mixed")
+            assert np.abs(dm[gi] - want_m).max() <= 1e-8 * np.abs(want_m).max(), obj
+            assert abs(db - want_b) <= 1e-8 * abs(want_b), obj
+        u, _ = sv.umt(1e-12, precision="fp64")
+        assert abs(u - float(g["U_mt"])) <= 1e-10
+        dm, db, _ = sv.adjoint("U_mt", 1e-12)
+        assert np.all(dm == 0.0)
+        want_b = float(g["dbeta_U_mt"])
+        assert abs(db - want_b) <= 1e-9 * abs(want_b)
+        # the mixed-precision forward solve in the differentiation workload's setting
+        sv.reset_state()
+        rm = sv.solve(case.s_in, case.eta, 1e-8, precision="mixed")
+        _check_state(sv.get_state(), rm, g, 1e-6, 1e-6, False)
+
+
+def test_upsampled_level_256x256x512_against_the_oracle():
+    """The 256x256x512 level of the upsampling workload, reached as in the workload: the
+    128x128x256 level solved cold, prolonged, and solved warm (mixed precision, residual
+    1e-8); then the FP64 path from the same warm start to residual 1e-12."""
+    from paper_2502_08034_gb300 import rfb, synth
+    g = _gold("upsample256")
+    coarse = synth.upsampling_cases(flow_device="cuda", only_level=0)[0]
+    fine = synth.upsampling_cases(flow_device="cuda", only_level=1)[0]
+    _check_flow(fine, g)
+    with rfb.Solver.from_case(coarse, device_inputs=True) as sc, \
+            rfb.Solver.from_case(fine, device_inputs=True) as sf:
+        sc.solve(coarse.s_in, coarse.eta, 1e-8, precision="mixed")
+        sf.upsample_from(sc)
+        r = sf.solve(fine.s_in, fine.eta, 1e-8, precision="mixed")
+        _check_state(sf.get_state(), r, g, 1e-6, 1e-6, False)
+        u_mt, _ = sf.umt(1e-8, precision="mixed")
+        assert abs(u_mt - float(g["U_mt"])) <= 1e-6
+        sf.upsample_from(sc)
+        r64 = sf.solve(fine.s_in, fine.eta, 1e-12, precision="fp64")
+        _check_state(sf.get_state(), r64, g, 1e-10, 1e-10, True)
