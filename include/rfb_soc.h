@@ -337,7 +337,8 @@ rfb_status rfb_soc_set_state(rfb_soc_handle* h, const double* s, rfb_mem_kind ki
 typedef struct rfb_batch rfb_batch;
 
 typedef struct rfb_batch_info {
-    int32_t kchunk;            /* z planes per work item (autotuned) */
+    int32_t kchunk;            /* z planes per work item of the one-sweep kernel
+                                  (autotuned) */
     int32_t sweeps_per_cycle;  /* sweeps between FP64 checks (autotuned or opts) */
     int32_t n_items;           /* work items over all lattices */
     int32_t grid_blocks;       /* resident blocks of the persistent launch */
@@ -351,6 +352,9 @@ typedef struct rfb_batch_info {
                                   cycles in a device-driven loop (a conditional while node
                                   whose condition a kernel sets once every lattice has
                                   converged); with a timeout, one cycle per launch */
+    int32_t pass_stages;       /* 0: the one-sweep kernel ran; 3 / 4: the batched two-sweep
+                                  pass with that many TMA stages */
+    int32_t pass_chunk;        /* z planes per work item of the two-sweep pass */
 } rfb_batch_info;
 
 /* hs: n handles (distinct, same device, nx % 4 == 0), not owned; they must outlive the
@@ -361,9 +365,13 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
  * opts (nullable) must select RFB_PREC_MIXED (the default of this call is still the
  * opts default, so pass opts with precision = RFB_PREC_MIXED); velocity_scale, cfl,
  * dt_mode, inlet_bc, max_sweeps (per lattice) and check_every (0 = autotuned) apply to
- * all. Each handle warm-starts from its state if it has one. res (nullable, n entries)
- * and info (nullable) are filled. Returns RFB_ERR_NOT_CONVERGED if max_sweeps ran out
- * first; the states of every handle are valid either way. */
+ * all. opts.fp32_kernel: 0 = the faster of the one-sweep kernel over every lattice and
+ * the batched two-sweep TMA pass (local steps only; timed once per batch), 1 = the
+ * one-sweep kernel, 2..6 = the two-sweep pass (RFB_ERR_INVALID_ARG with the global
+ * step). With the two-sweep pass the sweeps per cycle are a multiple of 4. Each handle
+ * warm-starts from its state if it has one. res (nullable, n entries) and info
+ * (nullable) are filled. Returns RFB_ERR_NOT_CONVERGED if max_sweeps ran out first;
+ * the states of every handle are valid either way. */
 rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* eta,
                                const double* tol, const rfb_solve_opts* opts,
                                rfb_solve_result* res, rfb_batch_info* info);

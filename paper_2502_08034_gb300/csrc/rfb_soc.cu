@@ -2295,6 +2295,16 @@ struct rfb_batch {
     int loop_every = 0;
     BatchLoop* d_loop = nullptr;
     BatchLoop* h_loop = nullptr;         // pinned
+    // two-sweep passes over every lattice (local steps, every lattice nz >= 2): per-lattice
+    // tensor maps, (lattice, tile, z chunk) items, chunk length and stage count (autotuned)
+    BatchTBD* d_tbd = nullptr;
+    BatchTBItem* d_tbitems = nullptr;
+    int n_tbitems = 0;
+    int tb_lc = 0;                       // chunk length of the built item list
+    int tb_nst = 0;                      // 0: one-sweep kernel; 3 / 4: passes, stages
+    int tb_grid = 0;                     // CTAs of the pass (one per SM)
+    int tuned_mode = -1;                 // kernel choice the tuning was made for
+    unsigned int* d_tberr = nullptr;     // set if a stage of a pass never arrives
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::string err;
     int64_t launches = 0;
@@ -2365,7 +2375,42 @@ void build_items(rfb_batch* b, int kchunk) {
     if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
 }
 
+// Items of the batched two-sweep pass for a z-chunk length: per lattice, chunk-major
+// with the tiles of a chunk consecutive.
+void build_tb_items(rfb_batch* b, int lc) {
+    if (b->tb_lc == lc) return;
+    std::vector<BatchTBItem> items;
+    for (size_t q = 0; q < b->hs.size(); ++q) {
+        const rfb_soc_handle* h = b->hs[q];
+        const int tiles = ((h->nx + TB_TXI - 1) / TB_TXI) * ((h->ny + TB_TYI - 1) / TB_TYI);
+        for (int kb = 0; kb < h->nz; kb += lc)
+            for (int t = 0; t < tiles; ++t)
+                items.push_back(BatchTBItem{(int)q, t, kb, std::min(kb + lc, h->nz)});
+    }
+    if (b->d_tbitems) cudaFree(b->d_tbitems);
+    b->d_tbitems = nullptr;
+    BCK(b, cudaMalloc((void**)&b->d_tbitems, items.size() * sizeof(BatchTBItem)));
+    BCK(b, cudaMemcpy(b->d_tbitems, items.data(), items.size() * sizeof(BatchTBItem),
+                      cudaMemcpyHostToDevice));
+    b->n_tbitems = (int)items.size();
+    b->tb_lc = lc;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
+}
+
 void batch_sweeps(rfb_batch* b, int n, bool local) {
+    if (b->tb_nst) {   // two-sweep passes (n even); pass p reads delta[p & 1]
+        for (int q = 0; q < n / 2; ++q) {
+            if (b->tb_nst == 4)
+                batch_tbd_kernel<4><<<b->tb_grid, TB_THREADS, tbd_smem<4>(), b->stream>>>(
+                    b->d_tbd, b->d_insts, b->d_tbitems, b->n_tbitems, q & 1, b->d_tberr);
+            else
+                batch_tbd_kernel<3><<<b->tb_grid, TB_THREADS, tbd_smem<3>(), b->stream>>>(
+                    b->d_tbd, b->d_insts, b->d_tbitems, b->n_tbitems, q & 1, b->d_tberr);
+            BLAUNCHED(b);
+        }
+        return;
+    }
     for (int q = 0; q < n; ++q) {
         if (local)
             batch_sweep_kernel<true><<<b->grid_blocks, dim3(VBX, VBY), 0, b->stream>>>(
@@ -2449,7 +2494,8 @@ void build_loop_graph(rfb_batch* b, int every, bool local) {
 // Project-written autotuner: for each candidate z-chunk of the work items, time a few
 // persistent sweeps of the whole batch (CUDA events) and keep the fastest; then set the
 // sweeps per cycle so that the FP64 check costs about 3% of a cycle.
-void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0) {
+// mode: 0 fastest of both kernels, 1 one-sweep kernel only, 2 two-sweep passes only
+void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0, int mode) {
     // candidates: z-chunk of the items x grid size (1x / 2x the resident blocks, walking
     // the item list persistently, or one block per item)
     const int cands[] = {8, 16, 32, 64};
@@ -2476,6 +2522,33 @@ void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0) {
     b->tuned_grid = best_grid;
     b->tuned_kchunk = best_k;
     b->tuned_sweep_ms = best / 4.0;
+    // two-sweep passes (local steps and tensor maps in place): chunk length x stages
+    b->tb_nst = 0;
+    if (mode == 2) best = 1e30f;
+    if (b->d_tbd && mode != 1) {
+        float best_tb = 1e30f;
+        int bl = 0, bn = 0;
+        for (int lc : {16, 32, 64}) {
+            build_tb_items(b, lc);
+            for (int nst : {3, 4}) {
+                b->tb_nst = nst;
+                batch_sweeps(b, 2, local);   // warm-up
+                BCK(b, cudaEventRecord(b->ev[0], b->stream));
+                batch_sweeps(b, 4, local);
+                BCK(b, cudaEventRecord(b->ev[1], b->stream));
+                BCK(b, cudaEventSynchronize(b->ev[1]));
+                float ms = 0;
+                BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+                if (ms < best_tb) { best_tb = ms; bl = lc; bn = nst; }
+            }
+        }
+        b->tb_nst = 0;
+        if (best_tb < best || mode == 2) {
+            build_tb_items(b, bl);
+            b->tb_nst = bn;
+            b->tuned_sweep_ms = best_tb / 4.0;
+        }
+    }
     BCK(b, cudaEventRecord(b->ev[0], b->stream));
     batch_check_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
         b->d_insts, b->d_items, b->n_items, b->d_partials);
@@ -2487,6 +2560,7 @@ void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0) {
     b->tuned_check_ms = cms;
     int every = (int)std::ceil(cms / (0.03 * std::max(1e-6, b->tuned_sweep_ms)));
     every = std::max(20, std::min(400, every + (every & 1)));
+    if (b->tb_nst) every = (every + 3) / 4 * 4;   // whole passes, result in delta[0]
     b->tuned_every = every;
     // the tuning sweeps touched delta only; restore the descriptors (cur / active)
     BCK(b, cudaMemcpy(b->d_insts, insts0.data(), insts0.size() * sizeof(BatchInst),
@@ -2524,6 +2598,7 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
         BCK(b, cudaMallocHost((void**)&b->h_ctl, n * sizeof(BatchCtl)));
         BCK(b, cudaMalloc((void**)&b->d_loop, sizeof(BatchLoop)));
         BCK(b, cudaMallocHost((void**)&b->h_loop, sizeof(BatchLoop)));
+        BCK(b, cudaMalloc((void**)&b->d_tberr, sizeof(unsigned int)));
         BCK(b, cudaEventCreate(&b->ev[0]));
         BCK(b, cudaEventCreate(&b->ev[1]));
         int sms = 152, per = 4;
@@ -2546,7 +2621,8 @@ rfb_status rfb_soc_batch_destroy(rfb_batch* b) {
     cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
-    void* ptrs[] = {b->d_insts, b->d_ctl, b->d_items, b->d_item_begin, b->d_partials, b->d_loop};
+    void* ptrs[] = {b->d_insts, b->d_ctl,  b->d_items,  b->d_item_begin, b->d_partials,
+                    b->d_loop,  b->d_tbd,  b->d_tbitems, b->d_tberr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -2626,13 +2702,72 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         }
         BCK(b, cudaMemcpy(b->d_insts, insts.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice));
         BCK(b, cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(BatchCtl), cudaMemcpyHostToDevice));
-        if (!b->tuned_kchunk) autotune(b, local, insts);
+        // tensor maps of the two-sweep passes (local steps; re-encoded every solve, since a
+        // handle's own solves may have swapped its two correction buffers)
+        bool tb_ok = local;
+        for (int q = 0; q < n && tb_ok; ++q) tb_ok = tb_eligible(b->hs[q], true);
+        if (tb_ok) {
+            static bool attr = false;
+            if (!attr) {
+                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tbd_smem<3>()));
+                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<4>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tbd_smem<4>()));
+                attr = true;
+            }
+            std::vector<BatchTBD> tbd(n);
+            for (int q = 0; q < n; ++q) {
+                rfb_soc_handle* h = b->hs[q];
+                BatchTBD& T = tbd[q];
+                std::memset(&T, 0, sizeof T);
+                try {
+                    for (int p = 0; p < 2; ++p)
+                        tb_encode(h, &T.td[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                  insts[q].delta[p], h->nz, TB_BW);
+                    tb_encode(h, &T.tr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz, TB_BW);
+                    tb_encode(h, &T.tu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz, TB_BW);
+                    tb_encode(h, &T.tv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz, TB_BW);
+                    tb_encode(h, &T.tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1,
+                              TB_BW);
+                    tb_encode(h, &T.tt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_dtc, h->nz, TB_BW);
+                } catch (Fail f) {
+                    bset_err(b, "lattice %d: %s", q, h->err.c_str());
+                    throw;
+                }
+                T.nx = h->nx; T.ny = h->ny; T.nz = h->nz;
+                T.omc = (float)(1.0 - ops[q].cfl);
+                T.Dh = insts[q].C32.Dh;
+            }
+            if (!b->d_tbd) BCK(b, cudaMalloc((void**)&b->d_tbd, n * sizeof(BatchTBD)));
+            BCK(b, cudaMemcpy(b->d_tbd, tbd.data(), n * sizeof(BatchTBD), cudaMemcpyHostToDevice));
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+            b->tb_grid = sms;
+        } else if (b->tb_nst) {
+            b->tb_nst = 0;   // a global step: the one-sweep kernel (the graphs hold passes)
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+            if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
+        }
+        BCK(b, cudaMemsetAsync(b->d_tberr, 0, sizeof(unsigned int), b->stream));
+        // opts.fp32_kernel: 0 the faster, 1 the one-sweep kernel, 2 two-sweep passes
+        const int mode = o.fp32_kernel == 1 ? 1 : o.fp32_kernel >= 2 ? 2 : 0;
+        if (mode == 2 && !tb_ok) {
+            bset_err(b, "two-sweep passes need local steps and nz >= 2 in every lattice");
+            return RFB_ERR_INVALID_ARG;
+        }
+        if (!b->tuned_kchunk || b->tuned_mode != mode) {
+            autotune(b, local, insts, mode);
+            b->tuned_mode = mode;
+        }
         else {
             build_items(b, b->tuned_kchunk);
             b->grid_blocks = std::max(1, std::min(b->tuned_grid, b->n_items));
         }
-        const int every = o.check_every > 0 ? std::max(2, o.check_every + (o.check_every & 1))
-                                            : b->tuned_every;
+        int every = o.check_every > 0 ? std::max(2, o.check_every + (o.check_every & 1))
+                                      : b->tuned_every;
+        if (b->tb_nst) every = (every + 3) / 4 * 4;   // whole passes, result in delta[0]
         // residual of the starting states (forcing for the first cycle)
         batch_check(b, false, 0);
         BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl), cudaMemcpyDeviceToHost,
@@ -2708,6 +2843,12 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             ++graph_launches;
         }
         BCK(b, cudaMemcpy(insts.data(), b->d_insts, n * sizeof(BatchInst), cudaMemcpyDeviceToHost));
+        unsigned int tb_bad = 0;
+        BCK(b, cudaMemcpy(&tb_bad, b->d_tberr, sizeof tb_bad, cudaMemcpyDeviceToHost));
+        if (tb_bad) {
+            bset_err(b, "a TMA stage of the batched two-sweep pass did not arrive in time");
+            st = RFB_ERR_CUDA;
+        }
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         for (int q = 0; q < n; ++q) {
             rfb_soc_handle* h = b->hs[q];
@@ -2733,6 +2874,8 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             info->check_ms = b->tuned_check_ms;
             info->cycles = done / every;
             info->graph_launches = graph_launches;
+            info->pass_stages = b->tb_nst;
+            info->pass_chunk = b->tb_nst ? b->tb_lc : 0;
             info->time_ms = ms;
             info->launches = b->launches;
         }

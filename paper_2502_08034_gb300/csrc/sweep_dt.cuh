@@ -146,6 +146,195 @@ struct TBDArgs {
     unsigned int* err;                // set if a stage never arrives
 };
 
+// One lattice as the pass sees it: its six tensor maps (delta, forcing, u, v, w, step;
+// generic addresses of kernel parameters or of global memory) and sizes.
+struct TBDField {
+    const CUtensorMap* d;
+    const CUtensorMap* r;
+    const CUtensorMap* u;
+    const CUtensorMap* v;
+    const CUtensorMap* w;
+    const CUtensorMap* t;
+    int nx, ny, nz;
+    const float* d_in;                // delta read by this pass (prologue plane)
+    float* d_out;
+    float omc, Dh;
+};
+
+// Per-CTA state of the pass: the stage ring in shared memory, the parity of each stage's
+// next completion and the stages with a copy in flight (every thread tracks the same).
+template <int NST>
+struct TBDRing {
+    unsigned char* smem;
+    uint64_t* bar;
+    uint32_t phase, pend;
+    unsigned int* err;
+    __device__ __forceinline__ unsigned char* stage(int s) const { return smem + s * TBD_STAGE; }
+    __device__ __forceinline__ bool wait(int s) {          // bounded wait for stage s
+        if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, TB_SPIN_LIMIT, err)) return false;
+        phase ^= 1u << s;
+        pend &= ~(1u << s);
+        return true;
+    }
+};
+
+template <int NST>
+__device__ __forceinline__ TBDRing<NST> tbd_ring_init(unsigned char* smem_raw, unsigned int* err) {
+    TBDRing<NST> R;
+    R.smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    R.bar = reinterpret_cast<uint64_t*>(R.smem + tbd_bar<NST>());
+    R.phase = 0;
+    R.pend = 0;
+    R.err = err;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&R.bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    return R;
+}
+
+// error path (a stage never arrived): wait, again with the limit, for the copies still
+// in flight into this CTA's shared memory before the kernel returns
+template <int NST>
+__device__ __forceinline__ void tbd_ring_drain(TBDRing<NST>& R) {
+    for (int s = 0; s < NST; ++s)
+        if (R.pend & (1u << s)) (void)R.wait(s);
+}
+
+// Two sweeps over planes kb .. ke-1 of one tile of lattice F, from F.d_in into F.d_out.
+// Every stage issued is waited for, so the ring is empty when it returns; false if a
+// wait gave up (the CTA decides together at its step barrier).
+template <bool TR, int NST>
+__device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, int tile,
+                                            int kb, int ke) {
+    const int tid = threadIdx.x;
+    const int tx = tid % TB_GX, ty = tid / TB_GX;
+    const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
+    const int nx = F.nx, ny = F.ny, nz = F.nz;
+    const bool interior = tx >= 1 && tx < 1 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
+    const int64_t nxny = (int64_t)nx * ny;
+    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
+    const int gx = (nx + TB_TXI - 1) / TB_TXI;
+    const float omc = F.omc, Dh = F.Dh;
+    unsigned char* smem = R.smem;
+    const int x0 = TB_TXI * (tile % gx) - 4;           // box origin (4-cell aligned)
+    const int y0 = TB_TYI * (tile / gx) - 2;
+    const int i0 = x0 + bxx, j = y0 + byy;
+    const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+    auto issue = [&](int p, int s) {                   // plane p -> stage s
+        R.pend |= 1u << s;
+        if (tid != 0) return;                          // one thread issues the copies
+        unsigned char* S = R.stage(s);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&R.bar[s], TBD_TX_BYTES);
+        tma_load_3d(S, F.d, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + TB_F32, F.r, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 2 * TB_F32, F.u, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 3 * TB_F32, F.v, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 4 * TB_F32, F.w, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 5 * TB_F32, F.t, x0, y0, p, &R.bar[s]);
+    };
+    __syncthreads();   // the previous segment's readers are done with every stage
+    for (int s = 0; s < NST; ++s) issue(kb - 1 + s, s);                 // kb-1, kb, ...
+
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
+    // Two register sets that swap roles every step (the loop is unrolled by two):
+    // weights, forcing and own level-0 value of the step's plane (written) and of the
+    // plane before it (read).
+    CoefD kcA[4], kcB[4];
+    float4 rA = zero4, rB = zero4, dA = zero4, dB = zero4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        for (int s = 0; s < 6; ++s) kcB[e].f[s] = 0.f;
+        kcB[e].dt = 0.f;
+    }
+    if (in_dom && kb >= 2) dB = ldg4(F.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
+    bool good = R.wait(0);
+    int s0 = 0;                                        // stage holding plane z
+
+    auto step = [&](int z, CoefD (&kc)[4], float4& rr, float4& dc,
+                    const CoefD (&pkc)[4], const float4& prr, const float4& pdc) -> bool {
+        const int s1 = s0 == NST - 1 ? 0 : s0 + 1;
+        if (good) good = R.wait(s1);
+        const float* D0 = reinterpret_cast<const float*>(R.stage(s0));
+        const float* R0 = D0 + TB_PLANE;
+        const float* U0 = R0 + TB_PLANE;
+        const float* V0 = U0 + TB_PLANE;
+        const float* W0 = V0 + TB_PLANE;
+        const float* T0 = W0 + TB_PLANE;
+        const float* D1 = reinterpret_cast<const float*>(R.stage(s1));
+        const float* W1 = D1 + 4 * TB_PLANE;
+        // ---- level 1 at plane z
+        dc = lds4(D0 + o);
+        const float4 dn = lds4(D1 + o);
+        const float4 u4 = lds4(U0 + o);
+        const float un = U0[o + 4];
+        const float4 v4 = lds4(V0 + o);
+        const float4 vh4 = lds4(V0 + o + TB_BW);
+        const float4 wl4 = lds4(W0 + o);
+        const float4 wh4 = lds4(W1 + o);
+        const float4 t4 = lds4(T0 + o);
+        rr = lds4(R0 + o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            kc[e] = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? un : el(u4, e + 1),
+                                el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
+        float4 l1 = dc;
+        if (in_dom && z >= 0 && z < nz) {
+            const float dxm = D0[o - 1], dxp = D0[o + 4];
+            const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                out[e] = dt_update(kc[e], omc, Dh, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
+                                   e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                   el(pdc, e), el(dn, e), el(rr, e));
+            l1 = make_float4(out[0], out[1], out[2], out[3]);
+        }
+        float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST>()) + (z & 1) * TB_PLANE;
+        *reinterpret_cast<float4*>(L1w + o) = l1;
+        // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
+        const int zz = z - 1;
+        if (zz >= kb && interior && in_dom) {
+            const float* L1r =
+                reinterpret_cast<const float*>(smem + tbd_l1<NST>()) + (zz & 1) * TB_PLANE;
+            const float lxm = L1r[o - 1], lxp = L1r[o + 4];
+            const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                out[e] = dt_update(pkc[e], omc, Dh, el(l1_m1, e),
+                                   e == 0 ? lxm : el(l1_m1, e - 1),
+                                   e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
+                                   el(l1_m2, e), el(l1, e), el(prr, e));
+            *reinterpret_cast<float4*>(F.d_out + i0 + (int64_t)nx * j + nxny * zz) =
+                make_float4(out[0], out[1], out[2], out[3]);
+        }
+        l1_m2 = l1_m1;
+        l1_m1 = l1;
+        // ---- all threads are done with stage s0: refill it with plane z + NST
+        if (!__syncthreads_and(good)) return false;
+        if (z + NST <= ke + 1) issue(z + NST, s0);
+        s0 = s1;
+        return true;
+    };
+
+    for (int z = kb - 1; z <= ke; z += 2) {
+        if (!step(z, kcA, rA, dA, kcB, rB, dB)) return false;
+        if (z + 1 > ke) break;
+        if (!step(z + 1, kcB, rB, dB, kcA, rA, dA)) return false;
+    }
+    return true;
+}
+
+// One pass over one lattice: this CTA's share of the linear index
+// ((chunk * tiles + tile) * lc + plane in chunk), walked as one z segment per
+// (chunk, tile) item it touches; positions past nz in the last chunk are skipped. With
+// one chunk and per = tiles * nz / CTAs this is a persistent launch with equal shares;
+// with per = lc every CTA takes one item and neighbouring tiles run together.
 template <bool TR, int NST>
 __global__ void __launch_bounds__(TB_THREADS, 1)
 sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_r,
@@ -153,36 +342,11 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
                   const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_t,
                   TBDArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tbd_bar<NST>());
-    const int tid = threadIdx.x;
-    const int tx = tid % TB_GX, ty = tid / TB_GX;
-    const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
-    const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const bool interior = tx >= 1 && tx < 1 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
-    const int64_t nxny = (int64_t)nx * ny;
-    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
-    const int gx = (nx + TB_TXI - 1) / TB_TXI;
-    const float omc = A.omc, Dh = A.Dh;
-
-    auto stage = [&](int s) { return smem + s * TBD_STAGE; };
-    uint32_t phase = 0;   // parity of each stage's next completion
-    uint32_t pend = 0;    // stages with a load in flight (every thread tracks the same set)
-    auto wait = [&](int s) -> bool {                   // bounded wait for stage s
-        if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, TB_SPIN_LIMIT, A.err)) return false;
-        phase ^= 1u << s;
-        pend &= ~(1u << s);
-        return true;
-    };
-
-    if (tid == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    const int tiles = gx * ((ny + TB_TYI - 1) / TB_TYI);
+    TBDRing<NST> R = tbd_ring_init<NST>(smem_raw, A.err);
+    const TBDField F{&tm_d, &tm_r, &tm_u, &tm_v, &tm_w, &tm_t, A.nx, A.ny, A.nz,
+                     A.d_in, A.d_out, A.omc, A.Dh};
+    const int gx = (A.nx + TB_TXI - 1) / TB_TXI;
+    const int tiles = gx * ((A.ny + TB_TYI - 1) / TB_TYI);
     const int64_t q1 = min((int64_t)(blockIdx.x + 1) * A.per, A.total);
     bool ok = true;
     for (int64_t q = (int64_t)blockIdx.x * A.per; q < q1 && ok;) {
@@ -191,122 +355,51 @@ sweep32tbd_kernel(const __grid_constant__ CUtensorMap tm_d, const __grid_constan
         const int tile = (int)(item % tiles);
         const int kb = (int)(item / tiles) * A.lc + zl;
         const int64_t item_end = (item + 1) * A.lc;
-        if (kb >= nz) { q = item_end; continue; }     // padding of a short last chunk
-        const int ke = (int)min((int64_t)nz, kb + (min(q1, item_end) - q));
+        if (kb >= A.nz) { q = item_end; continue; }   // padding of a short last chunk
+        const int ke = (int)min((int64_t)A.nz, kb + (min(q1, item_end) - q));
         q = min(q1, item_end);
-        const int x0 = TB_TXI * (tile % gx) - 4;       // box origin (4-cell aligned)
-        const int y0 = TB_TYI * (tile / gx) - 2;
-        const int i0 = x0 + bxx, j = y0 + byy;
-        const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
-        auto issue = [&](int p, int s) {               // plane p -> stage s
-            pend |= 1u << s;
-            if (tid != 0) return;                      // one thread issues the copies
-            unsigned char* S = stage(s);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[s], TBD_TX_BYTES);
-            tma_load_3d(S, &tm_d, x0, y0, p, &bar[s]);
-            tma_load_3d(S + TB_F32, &tm_r, x0, y0, p, &bar[s]);
-            tma_load_3d(S + 2 * TB_F32, &tm_u, x0, y0, p, &bar[s]);
-            tma_load_3d(S + 3 * TB_F32, &tm_v, x0, y0, p, &bar[s]);
-            tma_load_3d(S + 4 * TB_F32, &tm_w, x0, y0, p, &bar[s]);
-            tma_load_3d(S + 5 * TB_F32, &tm_t, x0, y0, p, &bar[s]);
-        };
-        __syncthreads();   // the previous segment's readers are done with every stage
-        for (int s = 0; s < NST; ++s) issue(kb - 1 + s, s);             // kb-1, kb, ...
-
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 l1_m2 = zero4, l1_m1 = zero4;           // own level 1 at z-2, z-1
-        // Two register sets that swap roles every step (the loop is unrolled by two):
-        // weights, forcing and own level-0 value of the step's plane (written) and of the
-        // plane before it (read).
-        CoefD kcA[4], kcB[4];
-        float4 rA = zero4, rB = zero4, dA = zero4, dB = zero4;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            for (int s = 0; s < 6; ++s) kcB[e].f[s] = 0.f;
-            kcB[e].dt = 0.f;
-        }
-        if (in_dom && kb >= 2) dB = ldg4(A.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
-        bool good = wait(0);
-        int s0 = 0;                                    // stage holding plane z
-
-        auto step = [&](int z, CoefD (&kc)[4], float4& rr, float4& dc,
-                        const CoefD (&pkc)[4], const float4& prr, const float4& pdc) -> bool {
-            const int s1 = s0 == NST - 1 ? 0 : s0 + 1;
-            if (good) good = wait(s1);
-            const float* D0 = reinterpret_cast<const float*>(stage(s0));
-            const float* R0 = D0 + TB_PLANE;
-            const float* U0 = R0 + TB_PLANE;
-            const float* V0 = U0 + TB_PLANE;
-            const float* W0 = V0 + TB_PLANE;
-            const float* T0 = W0 + TB_PLANE;
-            const float* D1 = reinterpret_cast<const float*>(stage(s1));
-            const float* W1 = D1 + 4 * TB_PLANE;
-            // ---- level 1 at plane z
-            dc = lds4(D0 + o);
-            const float4 dn = lds4(D1 + o);
-            const float4 u4 = lds4(U0 + o);
-            const float un = U0[o + 4];
-            const float4 v4 = lds4(V0 + o);
-            const float4 vh4 = lds4(V0 + o + TB_BW);
-            const float4 wl4 = lds4(W0 + o);
-            const float4 wh4 = lds4(W1 + o);
-            const float4 t4 = lds4(T0 + o);
-            rr = lds4(R0 + o);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                kc[e] = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? un : el(u4, e + 1),
-                                    el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
-            float4 l1 = dc;
-            if (in_dom && z >= 0 && z < nz) {
-                const float dxm = D0[o - 1], dxp = D0[o + 4];
-                const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
-                float out[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    out[e] = dt_update(kc[e], omc, Dh, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
-                                       e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                       el(pdc, e), el(dn, e), el(rr, e));
-                l1 = make_float4(out[0], out[1], out[2], out[3]);
-            }
-            float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST>()) + (z & 1) * TB_PLANE;
-            *reinterpret_cast<float4*>(L1w + o) = l1;
-            // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
-            const int zz = z - 1;
-            if (zz >= kb && interior && in_dom) {
-                const float* L1r =
-                    reinterpret_cast<const float*>(smem + tbd_l1<NST>()) + (zz & 1) * TB_PLANE;
-                const float lxm = L1r[o - 1], lxp = L1r[o + 4];
-                const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
-                float out[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    out[e] = dt_update(pkc[e], omc, Dh, el(l1_m1, e),
-                                       e == 0 ? lxm : el(l1_m1, e - 1),
-                                       e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
-                                       el(l1_m2, e), el(l1, e), el(prr, e));
-                *reinterpret_cast<float4*>(A.d_out + i0 + (int64_t)nx * j + nxny * zz) =
-                    make_float4(out[0], out[1], out[2], out[3]);
-            }
-            l1_m2 = l1_m1;
-            l1_m1 = l1;
-            // ---- all threads are done with stage s0: refill it with plane z + NST
-            if (!__syncthreads_and(good)) return false;
-            if (z + NST <= ke + 1) issue(z + NST, s0);
-            s0 = s1;
-            return true;
-        };
-
-        for (int z = kb - 1; z <= ke; z += 2) {
-            if (!step(z, kcA, rA, dA, kcB, rB, dB)) { ok = false; break; }
-            if (z + 1 > ke) break;
-            if (!step(z + 1, kcB, rB, dB, kcA, rA, dA)) { ok = false; break; }
-        }
+        ok = tbd_segment<TR, NST>(R, F, tile, kb, ke);
     }
-    if (!ok) {
-        for (int s = 0; s < NST; ++s)
-            if (pend & (1u << s)) (void)wait(s);
+    if (!ok) tbd_ring_drain<NST>(R);
+}
+
+// ---------------------------------------------------------------------------------
+// Batched two-sweep pass: many lattices in one launch. Work items are (lattice, tile, z
+// chunk), lattice-major with neighbouring tiles of a chunk next to each other; one CTA per
+// SM walks the item list in a fixed round-robin order. Each lattice's tensor maps live
+// in global memory (written by the host before the launch); lattices that have converged
+// are skipped (their flag is read from the batch's descriptors, which the check kernels
+// update), so a captured graph keeps working as lattices drop out.
+// ---------------------------------------------------------------------------------
+struct BatchTBD {
+    CUtensorMap td[2];                // delta buffer 0 and 1
+    CUtensorMap tr, tu, tv, tw, tt;   // forcing, u, v, w, step
+    int nx, ny, nz, pad_;
+    float omc, Dh;
+};
+
+struct BatchTBItem {
+    int inst, tile, kb, ke;           // planes kb .. ke-1 of one tile of one lattice
+};
+
+template <int NST>
+__global__ void __launch_bounds__(TB_THREADS, 1)
+batch_tbd_kernel(const BatchTBD* __restrict__ lat, const BatchInst* __restrict__ insts,
+                 const BatchTBItem* __restrict__ items, int n_items, int parity,
+                 unsigned int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    TBDRing<NST> R = tbd_ring_init<NST>(smem_raw, err);
+    bool ok = true;
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        const BatchTBItem it = items[w];
+        const BatchInst* I = insts + it.inst;
+        if (!I->active) continue;   // uniform over the CTA
+        const BatchTBD* L = lat + it.inst;
+        const TBDField F{&L->td[parity], &L->tr, &L->tu, &L->tv, &L->tw, &L->tt, L->nx, L->ny,
+                         L->nz, I->delta[parity], I->delta[parity ^ 1], L->omc, L->Dh};
+        ok = tbd_segment<false, NST>(R, F, it.tile, it.kb, it.ke);
     }
+    if (!ok) tbd_ring_drain<NST>(R);
 }
 
 }  // namespace rfb

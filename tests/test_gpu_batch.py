@@ -80,6 +80,29 @@ def test_device_driven_loop_equals_the_host_driven_cycles():
         assert x["sweeps"] == y["sweeps"] and x["residual"] == y["residual"]
 
 
+def test_batched_two_sweep_pass_and_one_sweep_kernel_reach_the_oracle():
+    """The batched two-sweep TMA pass (per-lattice tensor maps in global memory, items of
+    every lattice in one launch) and the one-sweep kernel over every lattice both reach
+    the oracle's steady states."""
+    from paper_2502_08034_gb300 import rfb
+    cases = _small_batch()
+    refs = [soc.steady_state(soc.assemble(problem_from_case(c, soc))) for c in cases]
+    for kernel in ("blocked", "plain"):
+        solvers = [rfb.Solver.from_case(c) for c in cases]
+        try:
+            with rfb.Batch(solvers) as b:
+                res, info = b.solve([c.s_in for c in cases], [c.eta for c in cases],
+                                    [1e-10] * len(cases), fp32_kernel=kernel)
+            if kernel == "blocked":
+                assert info["sweeps_per_cycle"] % 4 == 0
+            for c, r, sv, ref in zip(cases, res, solvers, refs):
+                assert r["residual"] <= 1e-10
+                assert np.abs(sv.get_state() - ref).max() < 1e-6, (kernel, c.name)
+        finally:
+            for s in solvers:
+                s.close()
+
+
 def test_batch_second_solve_reuses_tuning_and_warm_starts():
     from paper_2502_08034_gb300 import rfb
     cases = _small_batch()[:3]
