@@ -472,7 +472,10 @@ typedef struct rfb_bv_result {
  * Species: FP64 explicit pseudo-time sweeps at a fixed potential (local steps, opts.cfl);
  * every bv->cycle sweeps the potential is solved by conjugate gradients on the device.
  * Converged when res->residual <= tol and the last potential solve changed phi by at most
- * tol V_T / n_e. Needs kinetics mode 0, opts.precision FP64, opts.dt_mode local.
+ * tol V_T / n_e and reached its own tolerance (or the rounding floor of its residual; a
+ * solve cut off by max_cg does not count). From a cold start (start = 2, or no SBV state)
+ * the species first relax at phi = 0 to residual 1e-3. Needs kinetics mode 0,
+ * opts.precision FP64, opts.dt_mode local.
  *   bv    nullable (defaults)
  *   res   nullable
  * Returns RFB_OK, RFB_ERR_NOT_CONVERGED (opts.max_sweeps or opts.timeout_ms; the state is

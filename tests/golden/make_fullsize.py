@@ -23,7 +23,8 @@ Each file holds, besides the operating point:
     <= 1e-13, or <= 1e-12 where FP64 rounding stops the loop first) at 100,000 seeded
     fluid cells plus every
     fluid cell of the inlet and outlet planes, and the outputs (Sec. II.C);
-  - U_mt (Eq. umt-def) from the same loop on the U_mt operator;
+  - U_mt (Eq. umt-def) from the same loop on the U_mt operator (benchmark and
+    differentiation lattices);
   - for adjoint128: dI/dm at the 64 finite-difference voxels (seed 41) and at 20,000
     sampled wall cells, d/dbeta of I_tot, U and U_mt (the oracle's explicit transposed
     iteration to a relative residual of 1e-13).
@@ -144,11 +145,13 @@ def make(name):
                I_tot=o.I_tot, F_in=o.F_in, F_out=o.F_out, F_in_adv=o.F_in_adv, U=o.U,
                mass_balance_rel=o.mass_balance_rel, **flow_samples(case))
     del op
-    # U_mt (Eq. umt-def): reaction off, s_in = 0, electrode cells held at 1
-    opm = soc.assemble(p, mode="umt")
-    sm, _, _ = solve(opm, 0.0, direct)
-    rec["U_mt"] = soc.umt(p, sm)
-    del opm
+    sm = None
+    if name != "upsample256":   # U_mt at full size: the benchmark and differentiation lattices
+        # U_mt (Eq. umt-def): reaction off, s_in = 0, electrode cells held at 1
+        opm = soc.assemble(p, mode="umt")
+        sm, _, _ = solve(opm, 0.0, direct)
+        rec["U_mt"] = soc.umt(p, sm)
+        del opm
     if name == "adjoint128":
         fl = case.solid.ravel() == 0
         nw = soc.n_wall(case.solid.astype(bool)).ravel()
@@ -166,8 +169,8 @@ def make(name):
         rec["fd_voxels"] = vox
         rec["grad_idx"] = wsel
     np.savez_compressed(out_path(name), **rec)
-    print("%s written (%.0f s): I_tot %.6e U %.6e U_mt %.9f" % (
-        out_path(name), time.time() - t0, o.I_tot, o.U, rec["U_mt"]), flush=True)
+    print("%s written (%.0f s): I_tot %.6e U %.6e U_mt %s" % (
+        out_path(name), time.time() - t0, o.I_tot, o.U, rec.get("U_mt")), flush=True)
 
 
 if __name__ == "__main__":
