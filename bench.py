@@ -33,6 +33,19 @@ SWEEP_BYTES_PER_CELL = 4 + 4 + 4 + 12 + 0.125
 # local-step kernels (every single-lattice workload): the same with the FP32 step field
 # (4) in place of the mask
 DT_SWEEP_BYTES_PER_CELL = 4 + 4 + 4 + 12 + 4
+
+
+def pass_kernel(kname):
+    """(sweeps per launch, kernel description) of an FP32 kernel name of the binding."""
+    if not kname or kname == "plain":
+        return 1, "sweep32d_kernel (one sweep)"
+    shape = kname.rsplit("_", 1)[1]
+    if kname.startswith("three_sweep"):
+        return 3, ("sweep32t3_kernel (three-sweep TMA-staged pass, coefficients of the older "
+                   "levels in tensor memory, %s launch, %d delta stages)" % (
+                       shape, 5 if kname.startswith("three_sweep5") else 4))
+    return 2, ("sweep32tbd_kernel (two-sweep TMA-staged pass, %s launch, %d TMA stages)" % (
+        shape, 4 if kname.startswith("blocked4") else 3))
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -57,11 +70,14 @@ def parse():
                     help="logpile workload: cell sizes in um (each must divide the box)")
     ap.add_argument("--fp32-kernel", default="auto",
                     choices=["auto", "plain", "blocked", "blocked_persistent", "blocked_chunked",
-                             "blocked4_persistent", "blocked4_chunked"],
+                             "blocked4_persistent", "blocked4_chunked",
+                             "three_sweep_persistent", "three_sweep_chunked",
+                             "three_sweep5_persistent", "three_sweep5_chunked"],
                     help="FP32 correction kernel: chosen by the autotuner (default), one sweep "
-                         "per launch, or two-sweep TMA-staged passes (launch shape autotuned, "
-                         "persistent, or one (tile, z chunk) item per CTA; blocked4: four TMA "
-                         "stages)")
+                         "per launch, or TMA-staged passes (variant autotuned; two-sweep "
+                         "passes persistent, or one (tile, z chunk) item per CTA; blocked4: "
+                         "four TMA stages; three_sweep: three sweeps a pass with four (or "
+                         "five) delta stages)")
     ap.add_argument("--logpile-flow", default="potential", choices=["potential", "stokes"],
                     help="logpile workload: potential flow at the paper's 10 Pa flow rate "
                          "(default) or the Stokes flow at 10 Pa (matrix-free MINRES)")
@@ -105,11 +121,15 @@ def code_digest(sources):
     return h.hexdigest()[:16]
 
 
-def kernel_source_digest():
+def kernel_source_digest(kernel=None):
     """Digest of the kernel sources' code (comments and whitespace removed, so that a
-    comment edit does not void the traffic figures taken on the same code)."""
+    comment edit does not void the traffic figures taken on the same code); the
+    three-sweep pass adds its own header."""
+    names = ["soc_kernels.cuh", "sweep_tb.cuh", "sweep_dt.cuh"]
+    if kernel and kernel.startswith("three_sweep"):
+        names.append("sweep_t3.cuh")
     return code_digest(open(os.path.join(ROOT, "paper_2502_08034_gb300", "csrc", name)).read()
-                       for name in ("soc_kernels.cuh", "sweep_tb.cuh", "sweep_dt.cuh"))
+                       for name in names)
 
 
 def kernel_traffic(n_cells, kernel):
@@ -118,7 +138,7 @@ def kernel_traffic(n_cells, kernel):
     p = os.path.join(ROOT, "profiles", "sweep_fp32_traffic.txt")
     if not os.path.exists(p):
         return None
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(kernel)
     for line in open(p):
         parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if (parts.get("source_sha") == digest and parts.get("kernel") == kernel
@@ -466,9 +486,9 @@ def run_upsample(args):
     N = cases[-1].n
     fr = levels[-1]
     kname, _, _ = fine.tuned_fp32_kernel()
-    two_sweep = bool(kname) and kname.startswith("blocked")
-    launches_fine = (fr["sweeps"] + 1) // 2 if two_sweep else fr["sweeps"]
-    # algorithmic bytes per launch (a two-sweep pass reads and writes each cell once)
+    depth, kdesc = pass_kernel(kname)
+    launches_fine = (fr["sweeps"] + depth - 1) // depth
+    # algorithmic bytes per launch (a pass reads and writes each cell once)
     achieved = DT_SWEEP_BYTES_PER_CELL * N * launches_fine / (fr["sweep_ms"] / 1e3) / 1e9
     effective = DT_SWEEP_BYTES_PER_CELL * N * fr["sweeps"] / (fr["sweep_ms"] / 1e3) / 1e9
     out = {"metric": METRIC, "value": cells / (elapsed / 1e3) / 1e9, "unit": UNIT,
@@ -486,10 +506,8 @@ def run_upsample(args):
            "upsample_gain": upsample_gain,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak,
-                        "traffic": kernel_traffic(N, kname) if two_sweep else None,
-                        "kernel": "%s on the finest level" % (
-                            "sweep32tbd_kernel (two-sweep pass, %s launch)" % kname.split("_")[1]
-                            if two_sweep else "sweep32d_kernel (one sweep)"),
+                        "traffic": kernel_traffic(N, kname) if depth > 1 else None,
+                        "kernel": "%s on the finest level" % kdesc,
                         "bytes_per_cell_per_launch": DT_SWEEP_BYTES_PER_CELL,
                         "peak_kind": peak_kind},
            "effective_bandwidth": {"value": effective, "unit": "GB/s", "frac": effective / peak,
@@ -568,7 +586,8 @@ def run_nernst(args):
 def run_logpile(args):
     """The paper's reference reaction case on its logpile lattice (Sec. IV): 10 Pa flow
     rate, applied reducing voltage 0, k0 = 7.2e-5 m/s, s_in = 1.73e-7, residual 1e-6 (the
-    paper's tolerance), potential flow in place of the paper's Stokes flow. Mixed-precision
+    paper's tolerance), with potential flow scaled to the paper's 10 Pa flow rate or
+    (--logpile-flow stokes) the Stokes flow at 10 Pa on each lattice. Mixed-precision
     solves at h = 10, 5, 2.5 and 1.25 um (the last is the paper's 1024 x 512 x 128 = 2^26
     cells), with U, I_tot and U_mt beside the paper's U = 0.243 and I = 0.09 mA, and the
     FP64 solve of the finest level for comparison; at 10 and 5 um also the Butler-Volmer
@@ -599,7 +618,8 @@ def run_logpile(args):
                 s_mixed = sv.get_state() if finest else None
                 u_mt, _ = sv.umt(tol, precision="mixed")
                 row = {"h_um": h * 1e6, "dims": list(case.dims),
-                       "porosity": round(case.porosity, 5), "sweeps": res[-1]["sweeps"],
+                       "porosity": round(case.porosity, 5),
+                       "q_mL_h": case.info["q_m3_s"] * 3.6e9, "sweeps": res[-1]["sweeps"],
                        "time_to_steady_ms": res[-1]["time_ms"], "U": res[-1]["U"],
                        "I_tot_mA": res[-1]["I_tot"] * 1e3, "U_mt": u_mt,
                        "mass_balance_rel": res[-1]["mass_balance_rel"]}
@@ -637,8 +657,10 @@ def run_logpile(args):
            "dtype": "f32+f64",
            "data": "synthetic (the paper's logpile geometry, %s flow)" % args.logpile_flow,
            "config": {"workload": "logpile1024x512x128_sbv_10Pa", "tol": tol,
-                      "precision": "mixed", "q_m3_s": synth.LOGPILE_Q_10PA, "eta_V": 0.0,
-                      "k0_m_s": 7.2e-5},
+                      "precision": "mixed", "flow": args.logpile_flow,
+                      "q_m3_s": (synth.LOGPILE_Q_10PA if args.logpile_flow == "potential"
+                                 else "the Stokes flow rate at 10 Pa of each level (q_mL_h)"),
+                      "eta_V": 0.0, "k0_m_s": 7.2e-5},
            "paper": {"U": 0.243, "I_tot_mA": 0.09, "time_steps_to_tol": 125000,
                      "bv_rms_s_minus_sbv": 8.61e-4, "bv_phi_mean_mV": 0.16,
                      "bv_phi_max_mV": 0.47},
@@ -795,8 +817,8 @@ def main():
     kname, tuned_plain_ms, tuned_blocked_ms = sv.tuned_fp32_kernel()
     if args.fp32_kernel not in ("auto", "blocked"):
         kname = args.fp32_kernel
-    two_sweep = kname.startswith("blocked")   # about one launch per two sweeps
-    kernel_launches = (sweeps + 1) // 2 if two_sweep else sweeps
+    depth, kdesc = pass_kernel(kname)   # one launch per `depth` sweeps
+    kernel_launches = (sweeps + depth - 1) // depth
     achieved = DT_SWEEP_BYTES_PER_CELL * N * kernel_launches / (sweep_ms / 1e3) / 1e9
     effective = DT_SWEEP_BYTES_PER_CELL * N * sweeps / (sweep_ms / 1e3) / 1e9
     traffic = kernel_traffic(N, kname)
@@ -905,11 +927,7 @@ def main():
                "mass_balance_rel": last["mass_balance_rel"],
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                            "kernel": ("sweep32tbd_kernel (two-sweep TMA-staged pass, %s "
-                                       "launch, %d TMA stages)" % (
-                                           kname.split("_")[1],
-                                           4 if kname.startswith("blocked4") else 3)
-                                       if two_sweep else "sweep32d_kernel (one sweep)"),
+                            "kernel": kdesc, "sweeps_per_launch": depth,
                             "autotuner_ms_per_sweep": {"plain": tuned_plain_ms,
                                                        "blocked": tuned_blocked_ms},
                             "bytes_per_cell_per_launch": DT_SWEEP_BYTES_PER_CELL,

@@ -112,13 +112,19 @@ typedef struct rfb_solve_opts {
     int32_t fp32_kernel;    /* RFB_PREC_MIXED only: 0 = chosen by timing the kernels on
                                the lattice (once per lattice shape, dt mode
                                and device in a process), 1 = one sweep per launch,
-                               2 = two sweeps per pass (TMA-staged, temporally blocked;
-                               local steps: nx % 4 == 0; global step: nx % 16 == 0 and no
-                               area multiplier), launch shape and TMA stage count chosen
-                               by timing; 3 = two-sweep passes in a persistent launch (one
+                               2 = several sweeps per pass (TMA-staged, temporally
+                               blocked; local steps: nx % 4 == 0; global step: nx % 16
+                               == 0 and no area multiplier), the pass variant chosen by
+                               timing; 3 = two-sweep passes in a persistent launch (one
                                CTA per SM, equal shares); 4 = two-sweep passes, one
-                               (tile, z chunk) item per CTA; 5 / 6 = as 3 / 4 with four
-                               TMA stages instead of three (local steps only) */
+                               (tile, z chunk) item per CTA; local steps only: 5 / 6 = as
+                               3 / 4 with four TMA stages instead of three; 7 / 8 =
+                               three-sweep passes (128 x 10 tiles, the update
+                               coefficients of the two older levels in tensor memory),
+                               persistent / chunked; 9 / 10 = as 7 / 8 with five delta
+                               stages instead of four. Every pass is bitwise the same
+                               number of one-sweep launches; check intervals are whole
+                               passes */
     int32_t timeout_ms;     /* > 0: stop after the first FP64 check at or past this much
                                wall time since the call began and return
                                RFB_ERR_NOT_CONVERGED (the state is valid); 0 = none */
@@ -502,11 +508,11 @@ rfb_status rfb_soc_get_bv_state(rfb_soc_handle* h, double* c_o, double* c_r, dou
 rfb_status rfb_selftest_bounded_wait(int64_t spin_limit, int32_t* gave_up);
 
 /* The FP32 correction kernel the handle's autotuner chose for RFB_PREC_MIXED solves with
- * fp32_kernel = 0 or 2, as an opts.fp32_kernel value: 0 = not chosen yet, 1 = one sweep
- * per launch, 3 / 4 = two-sweep passes in the persistent / chunked launch shape, 5 / 6 the
- * same with four TMA stages; and the
- * timed device milliseconds per sweep of the one-sweep kernel and of the faster two-sweep
- * shape (0 if not timed). Any output pointer may be NULL. */
+ * fp32_kernel = 0 or 2 (or the one a solve forced), as an opts.fp32_kernel value: 0 = not
+ * chosen yet, 1 = one sweep per launch, 3 / 4 = two-sweep passes in the persistent /
+ * chunked launch shape, 5 / 6 the same with four TMA stages, 7 .. 10 three-sweep passes;
+ * and the timed device milliseconds per sweep of the one-sweep kernel and of the fastest
+ * pass variant (0 if not timed). Any output pointer may be NULL. */
 rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
                                      double* plain_ms_per_sweep,
                                      double* blocked_ms_per_sweep);

@@ -18,8 +18,9 @@ SYNTH_LIB = os.path.join(HERE, "librfbsynth.so")    # potential-flow input gener
 HOST_SYNTH_LIB = os.path.join(HERE, "librfbsynth_host.so")   # the same on the host CPU
 TARGETS = {
     LIB: ([os.path.join(CSRC, "rfb_soc.cu")],
-          [os.path.join(CSRC, "soc_kernels.cuh"), os.path.join(CSRC, "sweep_tb.cuh"),
-           os.path.join(ROOT, "include", "rfb_soc.h")]),
+          # every kernel header of csrc/ and the C ABI header
+          sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")) +
+          [os.path.join(ROOT, "include", "rfb_soc.h")]),
     SYNTH_LIB: ([os.path.join(CSRC, "synth_flow.cu")], []),
     HOST_SYNTH_LIB: ([os.path.join(CSRC, "synth_flow_cpu.c")], []),
 }

@@ -5,6 +5,7 @@
 #include "soc_kernels.cuh"
 #include "sweep_tb.cuh"
 #include "sweep_dt.cuh"
+#include "sweep_t3.cuh"
 #include "bv_kernels.cuh"
 
 #include <cuda.h>
@@ -125,9 +126,11 @@ struct rfb_soc_handle {
         int64_t total = 0;    // tiles x chunks x lc
         int64_t per = 0;      // positions per CTA
         dim3 grid;
-    } tb_launch[2];
-    int tb_variant = -1;      // -1 not chosen yet; bit 0 the launch shape, bit 1 (step-
-                              // field pass only) four TMA stages instead of three
+    } tb_launch[4];           // 2, 3: the same shapes for the three-sweep pass
+    int tb_variant = -1;      // -1 not chosen yet; bit 0 the launch shape; step-field
+                              // passes only: bit 1 one more TMA stage of delta (two-sweep:
+                              // four instead of three; three-sweep: five instead of four),
+                              // bit 2 three sweeps per pass instead of two
     bool tm_ready = false;
     CUtensorMap tm_delta[2], tm_r, tm_u, tm_v, tm_w, tm_f, tm_t;
     float* tm_delta_ptr[2] = {nullptr, nullptr};
@@ -484,6 +487,14 @@ void tb_prepare(rfb_soc_handle* h) {
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<4>()));
         CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<true, 4>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tbd_smem<4>()));
+        CK(h, cudaFuncSetAttribute(sweep32t3_kernel<false, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<4>()));
+        CK(h, cudaFuncSetAttribute(sweep32t3_kernel<true, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<4>()));
+        CK(h, cudaFuncSetAttribute(sweep32t3_kernel<false, 5>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<5>()));
+        CK(h, cudaFuncSetAttribute(sweep32t3_kernel<true, 5>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<5>()));
         attr_set[1] = true;
     }
     for (int q = 0; q < 2; ++q) {
@@ -498,40 +509,47 @@ void tb_prepare(rfb_soc_handle* h) {
     if (h->nx % 16 == 0)   // the mask byte of the global-step pass
         tb_encode(h, &h->tm_f, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, h->d_mask32, h->nz, TB_BWM);
     tb_encode(h, &h->tm_t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_dtc, h->nz, TB_BW);
-    // One CTA per SM fits (152 KB of shared memory each).
+    // One CTA per SM fits (152 to 227 KB of shared memory each).
     // Shape 0, persistent: the tile-major (tile, plane) space in equal shares of at least
-    // 16 planes (every z segment pays a two-plane prologue): no partial last wave, but
-    // CTAs on neighbouring tiles run at different planes and do not share halo rows in L2.
+    // 16 planes (every z segment pays a prologue of k planes, k the sweeps of a pass): no
+    // partial last wave, but CTAs on neighbouring tiles run at different planes and do not
+    // share halo rows in L2.
     // Shape 1, chunked: one (tile, z chunk) item per CTA in chunk-major order, so that
-    // neighbouring tiles run together; the chunk count minimises waves x (chunk + 2).
-    const int64_t tiles = (int64_t)((h->nx + TB_TXI - 1) / TB_TXI) *
-                          ((h->ny + TB_TYI - 1) / TB_TYI);
+    // neighbouring tiles run together; the chunk count minimises waves x (chunk + k).
     int sms = 152;
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    auto& P = h->tb_launch[0];
-    P.lc = h->nz;
-    P.total = tiles * h->nz;
-    P.per = std::max<int64_t>((P.total + sms - 1) / sms, 16);
-    P.grid = dim3((unsigned)((P.total + P.per - 1) / P.per));
-    int best_c = 1;
-    double best = INFINITY;
-    for (int c = 1; c <= std::max(1, h->nz / 8); ++c) {
-        const int lc = (h->nz + c - 1) / c, cc = (h->nz + lc - 1) / lc;
-        const double cost = std::ceil((double)(tiles * cc) / sms) * (lc + 2);
-        if (cost < best) { best = cost; best_c = cc; }
+    for (int k = 2; k <= 3; ++k) {
+        const int rows = k == 2 ? TB_TYI : T3_TYI;
+        const int64_t tiles = (int64_t)((h->nx + TB_TXI - 1) / TB_TXI) *
+                              ((h->ny + rows - 1) / rows);
+        auto& P = h->tb_launch[2 * (k - 2)];
+        P.lc = h->nz;
+        P.total = tiles * h->nz;
+        P.per = std::max<int64_t>((P.total + sms - 1) / sms, 16);
+        P.grid = dim3((unsigned)((P.total + P.per - 1) / P.per));
+        int best_c = 1;
+        double best = INFINITY;
+        for (int c = 1; c <= std::max(1, h->nz / 8); ++c) {
+            const int lc = (h->nz + c - 1) / c, cc = (h->nz + lc - 1) / lc;
+            const double cost = std::ceil((double)(tiles * cc) / sms) * (lc + k);
+            if (cost < best) { best = cost; best_c = cc; }
+        }
+        auto& Q = h->tb_launch[2 * (k - 2) + 1];
+        Q.lc = (h->nz + best_c - 1) / best_c;
+        Q.total = tiles * best_c * Q.lc;
+        Q.per = Q.lc;
+        Q.grid = dim3((unsigned)(tiles * best_c));
     }
-    auto& Q = h->tb_launch[1];
-    Q.lc = (h->nz + best_c - 1) / best_c;
-    Q.total = tiles * best_c * Q.lc;
-    Q.per = Q.lc;
-    Q.grid = dim3((unsigned)(tiles * best_c));
     h->tm_ready = true;
 }
 
 unsigned int* tb_err_word(rfb_soc_handle* h) { return reinterpret_cast<unsigned int*>(h->d_err + 3); }
 
-// one two-sweep pass from delta[cur] into delta[cur ^ 1] (tr: of the transposed
-// operator; local steps only)
+// sweeps of one pass of the chosen variant
+int tb_depth(const rfb_soc_handle* h) { return h->tb_variant >= 4 ? 3 : 2; }
+
+// one pass (two or three sweeps) from delta[cur] into delta[cur ^ 1] (tr: of the
+// transposed operator; local steps only)
 void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur, bool local,
              bool tr = false) {
     const CUtensorMap& td = (h->d_delta[cur] == h->tm_delta_ptr[0]) ? h->tm_delta[0]
@@ -539,14 +557,31 @@ void tb_pass(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int cur
     if (local) {
         TBDArgs A{};
         A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
-        const auto& S = h->tb_launch[std::max(h->tb_variant, 0) & 1];
+        const int v = std::max(h->tb_variant, 0);
+        const auto& S = h->tb_launch[v >= 4 ? 2 + (v & 1) : v & 1];
         A.lc = S.lc; A.total = S.total; A.per = S.per;
         A.d_in = h->d_delta[cur];
         A.d_out = h->d_delta[cur ^ 1];
         A.omc = (float)(1.0 - op.cfl);
         A.Dh = C.Dh;
         A.err = tb_err_word(h);
-        const bool four = h->tb_variant >= 2;
+        const bool four = (v & 2) != 0;
+        if (v >= 4) {
+            if (tr && four)
+                sweep32t3_kernel<true, 5><<<S.grid, T3_THREADS, t3_smem<5>(), h->stream>>>(
+                    td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+            else if (tr)
+                sweep32t3_kernel<true, 4><<<S.grid, T3_THREADS, t3_smem<4>(), h->stream>>>(
+                    td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+            else if (four)
+                sweep32t3_kernel<false, 5><<<S.grid, T3_THREADS, t3_smem<5>(), h->stream>>>(
+                    td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+            else
+                sweep32t3_kernel<false, 4><<<S.grid, T3_THREADS, t3_smem<4>(), h->stream>>>(
+                    td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
+            LAUNCHED(h);
+            return;
+        }
         if (tr && four)
             sweep32tbd_kernel<true, 4><<<S.grid, TB_THREADS, tbd_smem<4>(), h->stream>>>(
                 td, h->tm_r, h->tm_u, h->tm_v, h->tm_w, h->tm_t, A);
@@ -608,8 +643,8 @@ void plain_sweep(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int
 }
 
 // n FP32 correction sweeps delta <- delta + dt (L delta + r), starting from delta = 0.
-// The result is left in d_delta[0]. use_tb: two-sweep passes (plus one plain sweep when
-// n is odd).
+// The result is left in d_delta[0]. use_tb: passes of the chosen variant (two or three
+// sweeps each), plain sweeps for the remainder.
 void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = false) {
     const size_t bytes = (size_t)h->N * sizeof(float);
     CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
@@ -622,7 +657,8 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = fal
     int64_t q = 0;
     if (use_tb) {
         tb_prepare(h);
-        for (; q + 2 <= n; q += 2) {
+        const int k = tb_depth(h);
+        for (; q + k <= n; q += k) {
             tb_pass(h, op, C, cur, local);
             cur ^= 1;
         }
@@ -642,8 +678,8 @@ void sweeps32(rfb_soc_handle* h, const OpPoint& op, int64_t n, bool use_tb = fal
 
 // n FP32 correction sweeps of the transposed operator (adjoint), delta <- delta +
 // dt (L^T delta + r), from delta = 0; the result is left in d_delta[0] (nx % 4 == 0).
-// With local steps: two-sweep passes of the step-field kernel (plus one plain sweep when
-// n is odd).
+// With local steps: passes of the step-field kernels (two or three sweeps each, the
+// variant the autotuner chose), plain sweeps for the remainder.
 void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C, int64_t n) {
     const size_t bytes = (size_t)h->N * sizeof(float);
     CK(h, cudaMemsetAsync(h->d_delta[0], 0, bytes, h->stream));
@@ -655,7 +691,8 @@ void sweeps32_adjoint(rfb_soc_handle* h, const OpPoint& op, const Coef<float>& C
     if (local && tb_eligible(h, true)) {
         tb_prepare(h);
         if (h->tb_variant < 0) h->tb_variant = 1;   // chunked shape unless tuned
-        for (; q + 2 <= n; q += 2) {
+        const int k = tb_depth(h);
+        for (; q + k <= n; q += k) {
             tb_pass(h, op, C, cur, true, true);
             cur ^= 1;
         }
@@ -695,10 +732,11 @@ struct TuneVal {
 std::map<TuneKey, TuneVal> g_tune_cache;
 std::mutex g_tune_mu;
 
-// Project-written autotuner for one lattice: time 8 plain sweeps and 8 sweeps of each
+// Project-written autotuner for one lattice: time 12 plain sweeps and 12 sweeps of each
 // launch shape of the two-sweep pass (with local steps: with three and with four TMA
-// stages) by CUDA events on the current forcing and keep the fastest (tb_only: choose
-// between the two-sweep variants only).
+// stages, and the three-sweep pass with four and five delta stages) by CUDA events on
+// the current forcing and keep the fastest (tb_only: choose between the pass variants
+// only).
 void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false) {
     if (!tb_eligible(h, op.dt_mode == RFB_DT_LOCAL)) { h->tb_mode = 0; return; }
     const TuneKey key{h->nx, h->ny, h->nz, h->d_m32 != nullptr,
@@ -714,14 +752,15 @@ void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false
             return;
         }
     }
-    // candidates: plain, then two-sweep variants 0 .. nvar-1
-    const int nvar = op.dt_mode == RFB_DT_LOCAL ? 4 : 2;
-    float ms[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    // candidates: plain, then pass variants 0 .. nvar-1 (12 sweeps: whole passes of each)
+    const int nvar = op.dt_mode == RFB_DT_LOCAL ? 8 : 2;
+    float ms[9];
+    for (float& m : ms) m = INFINITY;
     for (int cand = tb_only ? 1 : 0; cand <= nvar; ++cand) {
         if (cand > 0) h->tb_variant = cand - 1;
-        sweeps32(h, op, 2, cand > 0);   // warm-up (and tensor maps)
+        sweeps32(h, op, 6, cand > 0);   // warm-up (and tensor maps)
         CK(h, cudaEventRecord(h->ev[0], h->stream));
-        sweeps32(h, op, 8, cand > 0);
+        sweeps32(h, op, 12, cand > 0);
         CK(h, cudaEventRecord(h->ev[1], h->stream));
         CK(h, cudaEventSynchronize(h->ev[1]));
         CK(h, cudaEventElapsedTime(&ms[cand], h->ev[0], h->ev[1]));
@@ -731,8 +770,8 @@ void tune_fp32_kernel(rfb_soc_handle* h, const OpPoint& op, bool tb_only = false
         if (ms[1 + v] < ms[1 + bestv]) bestv = v;
     h->tb_variant = bestv;
     const float tb = ms[1 + bestv];
-    h->tb_tuned_plain_ms = ms[0] / 8;
-    h->tb_tuned_tb_ms = tb / 8;
+    h->tb_tuned_plain_ms = ms[0] / 12;
+    h->tb_tuned_tb_ms = tb / 12;
     if (!tb_only) h->tb_mode = tb < ms[0] ? 1 : 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = TuneVal{tb_only ? -1 : h->tb_mode, h->tb_variant, h->tb_tuned_plain_ms,
@@ -775,11 +814,12 @@ bool read_opts(rfb_soc_handle* h, const rfb_solve_opts* in, rfb_solve_opts* o) {
     for (int q = 0; q < 6; ++q)
         if (o->reserved[q] != 0) { set_err(h, "opts.reserved must be zero"); return false; }
     if (o->timeout_ms < 0) { set_err(h, "opts.timeout_ms must be >= 0"); return false; }
-    if (o->fp32_kernel < 0 || o->fp32_kernel > 6 ||
+    if (o->fp32_kernel < 0 || o->fp32_kernel > 10 ||
         (o->fp32_kernel >= 5 && o->dt_mode != RFB_DT_LOCAL)) {
-        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep), 2 (two-sweep passes), "
-                   "3 / 4 (two-sweep passes, persistent / chunked launch) or, with local "
-                   "steps, 5 / 6 (the same with four TMA stages)");
+        set_err(h, "opts.fp32_kernel must be 0 (auto), 1 (one sweep), 2 (passes), 3 / 4 "
+                   "(two-sweep passes, persistent / chunked launch) or, with local steps, "
+                   "5 / 6 (the same with four TMA stages), 7 / 8 (three-sweep passes) or "
+                   "9 / 10 (three-sweep passes with five delta stages)");
         return false;
     }
     if (o->fp32_kernel >= 2 && !tb_eligible(h, o->dt_mode == RFB_DT_LOCAL)) {
@@ -823,7 +863,7 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         set_err(h, "kinetics mode 1 (nonlinear source) runs in RFB_PREC_FP64 only");
         throw Fail{RFB_ERR_INVALID_ARG};
     }
-    const int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, o.precision);
+    int64_t every = o.check_every > 0 ? o.check_every : default_check_every(h, o.precision);
     rfb_solve_result r{};
     rfb_status st = RFB_OK;
     int64_t done = 0;
@@ -865,8 +905,12 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
             if (h->tb_variant < 0) tune_fp32_kernel(h, op, true);
             use_tb = true;
         } else if (o.fp32_kernel >= 3) {
-            // a forced shape (kept for later calls); 5 / 6 with four TMA stages
-            h->tb_variant = o.fp32_kernel <= 4 ? o.fp32_kernel - 3 : (o.fp32_kernel - 5) | 2;
+            // a forced variant (kept for later calls): 3 / 4 and 5 / 6 two-sweep passes with
+            // three / four TMA stages, 7 / 8 and 9 / 10 three-sweep passes with four / five
+            h->tb_variant = o.fp32_kernel <= 4 ? o.fp32_kernel - 3
+                            : o.fp32_kernel <= 6 ? (o.fp32_kernel - 5) | 2
+                            : o.fp32_kernel <= 8 ? (o.fp32_kernel - 7) | 4
+                                                  : (o.fp32_kernel - 9) | 6;
             use_tb = true;
         } else if (o.fp32_kernel == 0) {
             if (h->tb_mode < 0) tune_fp32_kernel(h, op);
@@ -874,13 +918,17 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
         }
         if (use_tb) CK(h, cudaMemsetAsync(tb_err_word(h), 0, sizeof(unsigned int), h->stream));
     }
+    // sweeps per pass: the default interval and the shortened ones are whole passes
+    const int depth = use_tb ? tb_depth(h) : 1;
+    if (o.check_every == 0) every = std::max<int64_t>(depth, every / depth * depth);
     // Check interval: `every` sweeps, shortened near the end. The residual of these
     // transport problems does not decay geometrically early on (it stays up while the
     // inlet state is carried through the lattice, then falls faster), so a crossing
     // extrapolated from the last two checks lies too late there and the interval stays at
     // `every`; in the geometric tail the extrapolation is accurate, and the next check is
-    // placed just past the predicted crossing of tol (at least 16 sweeps, even) instead of
-    // up to `every` sweeps beyond it. One check costs about 9 FP32 sweeps.
+    // placed just past the predicted crossing of tol (at least 16 sweeps, whole passes) instead of
+    // up to `every` sweeps beyond it; intervals are whole passes of the FP32 kernel. One
+    // check costs about 9 to 13 FP32 sweeps.
     int64_t next_every = every;
     while (true) {
         if (r.nonfinite > 0) { st = RFB_ERR_NONFINITE; break; }
@@ -945,7 +993,8 @@ rfb_status drive(rfb_soc_handle* h, const rfb_solve_opts& o, OpPoint& op, bool u
             const double rate = std::log(res_before / r.residual) / (double)n;   // per sweep
             const double need = std::log(r.residual / tol) / rate;
             int64_t k = (int64_t)std::ceil(1.1 * need) + 2;
-            k = std::max<int64_t>(16, k + (k & 1));
+            k = std::max<int64_t>(16, k);
+            k = (k + depth - 1) / depth * depth;
             next_every = std::min(every, k);
         }
     }
@@ -2132,7 +2181,7 @@ rfb_status rfb_soc_tuned_fp32_kernel(const rfb_soc_handle* h, int32_t* kernel,
     if (h->tb_mode == 0) k = 1;
     else if (h->tb_mode == 1 || h->tb_variant >= 0) {
         const int v = std::max(h->tb_variant, 0);
-        k = (v & 2 ? 5 : 3) + (v & 1);
+        k = (v & 4 ? (v & 2 ? 9 : 7) : (v & 2 ? 5 : 3)) + (v & 1);
     }
     if (kernel) *kernel = k;
     if (plain_ms_per_sweep) *plain_ms_per_sweep = h->tb_tuned_plain_ms;

@@ -149,7 +149,9 @@ class RfbError(RuntimeError):
 
 
 FP32_KERNEL = {"auto": 0, "plain": 1, "blocked": 2, "blocked_persistent": 3,
-               "blocked_chunked": 4, "blocked4_persistent": 5, "blocked4_chunked": 6}
+               "blocked_chunked": 4, "blocked4_persistent": 5, "blocked4_chunked": 6,
+               "three_sweep_persistent": 7, "three_sweep_chunked": 8,
+               "three_sweep5_persistent": 9, "three_sweep5_chunked": 10}
 
 
 def make_opts(precision="fp64", inlet_bc="face", dt_mode="local", check_every=0, cfl=0.4,
@@ -379,8 +381,8 @@ class Solver:
         """(name, plain ms/sweep, blocked ms/sweep) chosen by the autotuner."""
         k, a, b = c_int32(), c_double(), c_double()
         self._check(lib().rfb_soc_tuned_fp32_kernel(self.h, byref(k), byref(a), byref(b)))
-        names = {0: None, 1: "plain", 3: "blocked_persistent", 4: "blocked_chunked",
-                 5: "blocked4_persistent", 6: "blocked4_chunked"}
+        names = {0: None, 1: "plain"}
+        names.update({v: k for k, v in FP32_KERNEL.items() if v >= 3})
         return names[k.value], a.value, b.value
 
     def close(self):

@@ -85,7 +85,7 @@ def test_kernel_traffic_scales_with_the_cells_and_names_its_kernel():
     for line in open(os.path.join(ROOT, "profiles", "sweep_fp32_traffic.txt")):
         if line.startswith("kernel="):
             kv = dict(x.split("=", 1) for x in line.split())
-            if kv["source_sha"] == bench.kernel_source_digest():
+            if kv["source_sha"] == bench.kernel_source_digest(kv["kernel"]):
                 per[kv["kernel"]] = float(kv["dram_bytes_per_cell"])
             else:
                 stale.add(kv["kernel"])

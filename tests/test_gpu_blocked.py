@@ -1,7 +1,8 @@
-"""The two-sweep (temporally blocked, TMA-staged) FP32 correction pass is bitwise two
-one-sweep launches, on lattices with several tiles, ragged tile edges in y, odd z
-extents and both pseudo-time step modes; and mixed-precision solves with it match the
-oracle."""
+"""The temporally blocked, TMA-staged FP32 correction passes (two sweeps, and with local
+steps three sweeps with tensor-memory coefficients) are bitwise the same number of
+one-sweep launches, on lattices with several tiles, ragged tile edges in y, odd z extents
+and both pseudo-time step modes, for the operator and its transpose; and mixed-precision
+solves with them match the oracle."""
 import functools
 
 import numpy as np
@@ -22,6 +23,11 @@ def _built():
     _build.build()
 
 
+# the step-field pass variants (local steps only)
+THREE_AND_FOUR = ["blocked4_persistent", "blocked4_chunked", "three_sweep_persistent",
+                  "three_sweep_chunked", "three_sweep5_persistent", "three_sweep5_chunked"]
+
+
 @functools.lru_cache(maxsize=None)
 def _case(dims, seed=7, d=4.0):
     from paper_2502_08034_gb300 import synth
@@ -37,8 +43,8 @@ def test_two_sweep_pass_is_bitwise_two_sweeps(dims, dt_mode):
     case = _case(dims)
     states = []
     kernels = ["plain", "blocked_persistent", "blocked_chunked", "blocked"]
-    if dt_mode == "local":      # the step-field pass also runs with four TMA stages
-        kernels += ["blocked4_persistent", "blocked4_chunked"]
+    if dt_mode == "local":      # the step-field passes: four TMA stages, three sweeps
+        kernels += THREE_AND_FOUR
     for kernel in kernels:
         with rfb.Solver.from_case(case) as sv:
             for n in (6, 10, 4):      # several correction cycles
@@ -113,11 +119,44 @@ def test_step_field_pass_is_bitwise_with_area_multipliers_and_nx_multiple_of_4(d
     case = _case(dims)
     m = synth.lognormal_area_mult(case.solid, 0.3, 40)
     states = []
-    for kernel in ("plain", "blocked_persistent", "blocked_chunked", "blocked4_persistent",
-                   "blocked4_chunked"):
+    for kernel in ["plain", "blocked_persistent", "blocked_chunked"] + THREE_AND_FOUR:
         with rfb.Solver.from_case(case, area_mult=m) as sv:
             for n in (6, 9):
                 sv.step(case.s_in, case.eta, n, precision="mixed", fp32_kernel=kernel)
             states.append(sv.get_state())
     for st in states[1:]:
         assert np.array_equal(states[0], st)
+
+
+@pytest.mark.parametrize("dims", [(48, 48, 96), (64, 40, 37), (144, 30, 21)])
+def test_transposed_passes_are_bitwise_the_same_sweeps(dims):
+    """Mixed adjoint corrections (transposed operator) through the two-sweep and the
+    three-sweep passes: with 12 sweeps per cycle (whole passes of either) the adjoint and
+    its gradients are the same bits."""
+    from paper_2502_08034_gb300 import rfb, synth
+    case = _case(dims)
+    m = synth.lognormal_area_mult(case.solid, 0.3, 40)
+    outs = []
+    for kernel in ["blocked_chunked"] + THREE_AND_FOUR:
+        with rfb.Solver.from_case(case, area_mult=m) as sv:
+            # 6 mixed sweeps choose the pass variant (the same bits for every variant)
+            sv.step(case.s_in, case.eta, 6, precision="mixed", fp32_kernel=kernel)
+            sv.solve(case.s_in, case.eta, 1e-13, precision="fp64", max_sweeps=400000)
+            dm, db, r = sv.adjoint("I_tot", 1e-11, precision="mixed", check_every=12)
+            outs.append((dm.copy(), db, r["sweeps"]))
+    for dm, db, n in outs[1:]:
+        assert n == outs[0][2] and db == outs[0][1] and np.array_equal(dm, outs[0][0])
+
+
+def test_three_sweep_pass_mixed_solve_matches_oracle():
+    """A mixed solve through the three-sweep pass reaches the oracle's steady state."""
+    from paper_2502_08034_gb300 import rfb
+    case = _case((64, 40, 37))
+    ref = soc.steady_state(soc.assemble(problem_from_case(case, soc)))
+    for kernel in ("three_sweep_persistent", "three_sweep_chunked"):
+        with rfb.Solver.from_case(case) as sv:
+            r = sv.solve(case.s_in, case.eta, 1e-11, precision="mixed", fp32_kernel=kernel)
+            assert sv.tuned_fp32_kernel()[0] == kernel
+            s = sv.get_state()
+        assert r["residual"] <= 1e-11
+        assert np.abs(s - ref).max() < 1e-7
