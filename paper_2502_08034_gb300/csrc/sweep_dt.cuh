@@ -5,63 +5,65 @@
 //     delta'_c = (1 - C_CFL) delta_c
 //              + dt_c (r_c + sum_f q_in,f delta_f + (D/h^2) sum_f delta_f),
 // q_in,f the inflow through face f (beta/h times the face velocity where it points into
-// the cell, else 0) and the sums over the six neighbours. Solid and out-of-domain
-// neighbours hold delta = 0 and their faces carry no velocity, so no face needs a mask
-// test; cells that are not updated (solid, or electrode cells of U_mt) have dt_c = 0 and
-// keep delta = 0, the value every correction cycle starts from. The step field is the
-// one the FP64 path uses (written by the diagonal pass of every operating point), so the
-// kernels stream the step instead of a mask byte and recompute no diagonal: a cell update
-// is 20 FP32 instructions. For the transposed operator (adjoint corrections) the
-// coefficient towards a neighbour is this cell's outflow through the shared face (the
-// neighbour's inflow from it), with the same diagonal.
+// the cell, else 0) and the sums over the six neighbours. The kernels evaluate it with
+// the step distributed over the terms,
+//     delta'_c = (1 - C_CFL) delta_c + dt_c r_c + sum_f a_f delta_f,
+//     a_f = dt_c (q_in,f + D/h^2),
+// so that the per-cell weights a_f and dt_c r_c, formed once per pass, make every further
+// update of the cell seven FMAs. Solid and out-of-domain neighbours hold delta = 0 and
+// their faces carry no velocity, so no face needs a mask test; cells that are not updated
+// (solid, or electrode cells of U_mt) have dt_c = 0 and keep delta = 0, the value every
+// correction cycle starts from. The step field is the one the FP64 path uses (written by
+// the diagonal pass of every operating point), so the kernels stream the step instead of
+// a mask byte and recompute no diagonal. For the transposed operator (adjoint
+// corrections) the coefficient towards a neighbour is this cell's outflow through the
+// shared face (the neighbour's inflow from it), with the same diagonal.
 //
 // sweep32d_kernel applies one sweep; sweep32tbd_kernel two sweeps per pass over HBM,
 // planes staged by TMA through a three- or four-stage mbarrier ring (the scheme of
 // sweep_tb.cuh, with the step plane in place of the mask plane; four stages keep three
 // planes in flight and use 221 KB of shared memory). Both evaluate every update with
-// dt_update below in the same operation order, so a pass is bitwise two sweeps.
+// dt_coef and dt_update below in the same operation order, so a pass is bitwise two
+// sweeps.
 #pragma once
 
 #include "sweep_tb.cuh"
 
 namespace rfb {
 
-// Face weights of one cell's update: the inflow through each face (TR: the outflow),
-// -x, +x, -y, +y, -z, +z, and the cell's step.
+// Weights of one cell's update towards its neighbours -x, +x, -y, +y, -z, +z:
+// a_f = dt (q_f + D/h^2), q_f the inflow through face f (TR: the outflow).
 struct CoefD {
-    float f[6];
-    float dt;
+    float a[6];
 };
 
 template <bool TR>
-__device__ __forceinline__ CoefD dt_coef(float dt, float uL, float uH, float vL, float vH,
-                                         float wL, float wH) {
+__device__ __forceinline__ CoefD dt_coef(float dt, float Dh, float uL, float uH, float vL,
+                                         float vH, float wL, float wH) {
     CoefD k;
     const float sg = TR ? -1.f : 1.f;
-    k.f[0] = fmaxf(sg * uL, 0.f);
-    k.f[1] = fmaxf(-sg * uH, 0.f);
-    k.f[2] = fmaxf(sg * vL, 0.f);
-    k.f[3] = fmaxf(-sg * vH, 0.f);
-    k.f[4] = fmaxf(sg * wL, 0.f);
-    k.f[5] = fmaxf(-sg * wH, 0.f);
-    k.dt = dt;
+    const float dtD = dt * Dh;
+    k.a[0] = fmaf(dt, fmaxf(sg * uL, 0.f), dtD);
+    k.a[1] = fmaf(dt, fmaxf(-sg * uH, 0.f), dtD);
+    k.a[2] = fmaf(dt, fmaxf(sg * vL, 0.f), dtD);
+    k.a[3] = fmaf(dt, fmaxf(-sg * vH, 0.f), dtD);
+    k.a[4] = fmaf(dt, fmaxf(sg * wL, 0.f), dtD);
+    k.a[5] = fmaf(dt, fmaxf(-sg * wH, 0.f), dtD);
     return k;
 }
 
-// one update (omc = 1 - C_CFL, Dh = D/h^2)
-__device__ __forceinline__ float dt_update(const CoefD& k, float omc, float Dh, float sc,
+// one update (omc = 1 - C_CFL, dtr = dt r)
+__device__ __forceinline__ float dt_update(const CoefD& k, float omc, float sc, float dtr,
                                            float xm, float xp, float ym, float yp, float zm,
-                                           float zp, float r) {
-    float acc = r;
-    acc = fmaf(k.f[0], xm, acc);
-    acc = fmaf(k.f[1], xp, acc);
-    acc = fmaf(k.f[2], ym, acc);
-    acc = fmaf(k.f[3], yp, acc);
-    acc = fmaf(k.f[4], zm, acc);
-    acc = fmaf(k.f[5], zp, acc);
-    const float sum = ((xm + xp) + (ym + yp)) + (zm + zp);
-    acc = fmaf(Dh, sum, acc);
-    return fmaf(k.dt, acc, omc * sc);
+                                           float zp) {
+    float acc = fmaf(omc, sc, dtr);
+    acc = fmaf(k.a[0], xm, acc);
+    acc = fmaf(k.a[1], xp, acc);
+    acc = fmaf(k.a[2], ym, acc);
+    acc = fmaf(k.a[3], yp, acc);
+    acc = fmaf(k.a[4], zm, acc);
+    acc = fmaf(k.a[5], zp, acc);
+    return acc;
 }
 
 struct DArgs {
@@ -110,11 +112,12 @@ sweep32d_kernel(DArgs A, const float* __restrict__ s, float* __restrict__ s_out,
         float out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const CoefD kc = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? u_nx : el(u4, e + 1),
-                                         el(v4, e), el(vH4, e), el(wL, e), el(wH, e));
-            out[e] = dt_update(kc, A.omc, A.Dh, el(d_cur, e), e == 0 ? d_xm : el(d_cur, e - 1),
-                               e == 3 ? d_xp : el(d_cur, e + 1), el(d_ym, e), el(d_yp, e),
-                               el(d_prev, e), el(d_next, e), el(r4, e));
+            const CoefD kc = dt_coef<TR>(el(t4, e), A.Dh, el(u4, e),
+                                         e == 3 ? u_nx : el(u4, e + 1), el(v4, e), el(vH4, e),
+                                         el(wL, e), el(wH, e));
+            out[e] = dt_update(kc, A.omc, el(d_cur, e), el(t4, e) * el(r4, e),
+                               e == 0 ? d_xm : el(d_cur, e - 1), e == 3 ? d_xp : el(d_cur, e + 1),
+                               el(d_ym, e), el(d_yp, e), el(d_prev, e), el(d_next, e));
         }
         *reinterpret_cast<float4*>(s_out + c) = make_float4(out[0], out[1], out[2], out[3]);
         d_prev = d_cur;
@@ -242,15 +245,13 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 l1_m2 = zero4, l1_m1 = zero4;               // own level 1 at z-2, z-1
     // Two register sets that swap roles every step (the loop is unrolled by two):
-    // weights, forcing and own level-0 value of the step's plane (written) and of the
-    // plane before it (read).
+    // weights, step times forcing and own level-0 value of the step's plane (written) and
+    // of the plane before it (read).
     CoefD kcA[4], kcB[4];
     float4 rA = zero4, rB = zero4, dA = zero4, dB = zero4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        for (int s = 0; s < 6; ++s) kcB[e].f[s] = 0.f;
-        kcB[e].dt = 0.f;
-    }
+    for (int e = 0; e < 4; ++e)
+        for (int s = 0; s < 6; ++s) kcB[e].a[s] = 0.f;
     if (in_dom && kb >= 2) dB = ldg4(F.d_in + i0 + (int64_t)nx * j + nxny * (kb - 2));
     bool good = R.wait(0);
     int s0 = 0;                                        // stage holding plane z
@@ -277,10 +278,11 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
         const float4 wl4 = lds4(W0 + o);
         const float4 wh4 = lds4(W1 + o);
         const float4 t4 = lds4(T0 + o);
-        rr = lds4(R0 + o);
+        const float4 r4 = lds4(R0 + o);
+        rr = make_float4(t4.x * r4.x, t4.y * r4.y, t4.z * r4.z, t4.w * r4.w);
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            kc[e] = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? un : el(u4, e + 1),
+            kc[e] = dt_coef<TR>(el(t4, e), Dh, el(u4, e), e == 3 ? un : el(u4, e + 1),
                                 el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
         float4 l1 = dc;
         if (in_dom && z >= 0 && z < nz) {
@@ -289,9 +291,9 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = dt_update(kc[e], omc, Dh, el(dc, e), e == 0 ? dxm : el(dc, e - 1),
-                                   e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                   el(pdc, e), el(dn, e), el(rr, e));
+                out[e] = dt_update(kc[e], omc, el(dc, e), el(rr, e),
+                                   e == 0 ? dxm : el(dc, e - 1), e == 3 ? dxp : el(dc, e + 1),
+                                   el(dym, e), el(dyp, e), el(pdc, e), el(dn, e));
             l1 = make_float4(out[0], out[1], out[2], out[3]);
         }
         float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST>()) + (z & 1) * TB_PLANE;
@@ -306,10 +308,10 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                out[e] = dt_update(pkc[e], omc, Dh, el(l1_m1, e),
+                out[e] = dt_update(pkc[e], omc, el(l1_m1, e), el(prr, e),
                                    e == 0 ? lxm : el(l1_m1, e - 1),
                                    e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e), el(lyp, e),
-                                   el(l1_m2, e), el(l1, e), el(prr, e));
+                                   el(l1_m2, e), el(l1, e));
             *reinterpret_cast<float4*>(F.d_out + i0 + (int64_t)nx * j + nxny * zz) =
                 make_float4(out[0], out[1], out[2], out[3]);
         }

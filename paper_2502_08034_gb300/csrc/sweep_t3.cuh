@@ -14,20 +14,22 @@
 // A level-l value is valid l cells inside the box, so the 4 halo columns and 3 halo rows
 // leave the interior exact after three sweeps.
 //
-// Each level needs the face weights, step and forcing of its plane. Level 1 derives them
-// from the staged planes; the staged plane is then released, and the 32 words of a
-// thread's four cells are stored in tensor memory (tcgen05.st, 32 lanes x 32 columns per
-// warp), from where levels 2 and 3 load them one and two steps later (tcgen05.ld). Tensor
-// memory (256 KB per SM, unused by this pass otherwise) thus holds three planes of
-// coefficients that would not fit next to the staged planes in shared memory nor in the
-// register file at 480 threads.
+// Each level needs the update weights of its plane (a_f and dt r, sweep_dt.cuh). Level 1
+// derives them from the staged planes; the staged plane is then released, and the 28
+// words of a thread's four cells are stored in tensor memory (tcgen05.st, 32 lanes x 32
+// columns per warp), from where levels 2 and 3 load them one and two steps later
+// (tcgen05.ld). Tensor memory (256 KB per SM, unused by this pass otherwise) thus holds
+// three planes of weights that would not fit next to the staged planes in shared memory
+// nor in the register file at 480 threads. The 4 threads past the 476 that own cells
+// repeat the first four cell groups of the last row, so that every thread runs the same
+// instructions; they store nothing.
 //
 // Staging: delta and w (read at planes z and z+1) go through one mbarrier ring of NA
 // stages, forcing, u, v and step (read at plane z only) through a second ring of NB = 3
 // stages, so both keep two planes in flight while the CTA works on plane z.
 //
-// Every update is dt_update with the same operands in the same order as the one-sweep
-// kernel, so a pass is bitwise three sweeps.
+// Every update is dt_coef and dt_update with the same operands in the same order as the
+// one-sweep kernel, so a pass is bitwise three sweeps.
 #pragma once
 
 #include "sweep_dt.cuh"
@@ -116,29 +118,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
                  : "memory");
 }
 
-// the 32 words of four cells: seven per cell (six face weights, step), then the forcing
-__device__ __forceinline__ void t3_pack(const CoefD (&kc)[4], const float4& rr,
+// the words of four cells: seven per cell (six weights a_f, then dt r), four unused
+__device__ __forceinline__ void t3_pack(const CoefD (&kc)[4], const float (&dtr)[4],
                                         uint32_t (&v)[32]) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) v[7 * e + f] = __float_as_uint(kc[e].f[f]);
-        v[7 * e + 6] = __float_as_uint(kc[e].dt);
+        for (int f = 0; f < 6; ++f) v[7 * e + f] = __float_as_uint(kc[e].a[f]);
+        v[7 * e + 6] = __float_as_uint(dtr[e]);
     }
-    v[28] = __float_as_uint(rr.x);
-    v[29] = __float_as_uint(rr.y);
-    v[30] = __float_as_uint(rr.z);
-    v[31] = __float_as_uint(rr.w);
+    v[28] = v[29] = v[30] = v[31] = 0u;
 }
-__device__ __forceinline__ void t3_unpack(const uint32_t (&v)[32], CoefD (&kc)[4], float4& rr) {
+__device__ __forceinline__ CoefD t3_coef(const uint32_t (&v)[32], int e) {
+    CoefD k;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-#pragma unroll
-        for (int f = 0; f < 6; ++f) kc[e].f[f] = __uint_as_float(v[7 * e + f]);
-        kc[e].dt = __uint_as_float(v[7 * e + 6]);
-    }
-    rr = make_float4(__uint_as_float(v[28]), __uint_as_float(v[29]), __uint_as_float(v[30]),
-                     __uint_as_float(v[31]));
+    for (int f = 0; f < 6; ++f) k.a[f] = __uint_as_float(v[7 * e + f]);
+    return k;
+}
+__device__ __forceinline__ float t3_dtr(const uint32_t (&v)[32], int e) {
+    return __uint_as_float(v[7 * e + 6]);
 }
 
 // Stage rings: NA (delta, w) stages, then T3_NB (forcing, u, v, step) stages; barrier q
@@ -171,8 +169,9 @@ struct T3Ring {
 template <bool TR, int NA>
 __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uint32_t tmem,
                                            int tile, int kb, int ke) {
-    const int tid = threadIdx.x;
-    const bool act = tid < TB_THREADS;                 // the last 4 threads hold no cells
+    const int tid0 = threadIdx.x;
+    const bool act = tid0 < TB_THREADS;                // the last 4 threads store nothing
+    const int tid = act ? tid0 : tid0 - TB_GX;         // ... and repeat row 13's first groups
     const int tx = tid % TB_GX, ty = tid / TB_GX;
     const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
     const bool lv2 = act && ty >= 1 && ty <= 12;       // box rows 2 .. 13
@@ -185,12 +184,12 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
     const int x0 = TB_TXI * (tile % gx) - 4;           // box origin (4-cell aligned)
     const int y0 = T3_TYI * (tile / gx) - 3;
     const int i0 = x0 + bxx, j = y0 + byy;
-    const bool in_dom = act && i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+    const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
     float* L1 = reinterpret_cast<float*>(R.smem + t3_l1<NA>());
     float* L2 = reinterpret_cast<float*>(R.smem + t3_l2<NA>());
     auto issue_a = [&](int p, int s) {                 // delta, w of plane p -> stage s
         R.pend |= 1u << s;
-        if (tid != 0) return;
+        if (tid0 != 0) return;
         unsigned char* S = R.a(s);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&R.bar[s], T3_ASTAGE);
@@ -199,7 +198,7 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
     };
     auto issue_b = [&](int p, int s) {                 // forcing, u, v, step -> stage s
         R.pend |= 1u << (NA + s);
-        if (tid != 0) return;
+        if (tid0 != 0) return;
         unsigned char* S = R.b(s);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&R.bar[NA + s], T3_BSTAGE);
@@ -223,7 +222,7 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
     if (in_dom && zf >= 1) pdc = ldg4(F.d_in + i0 + (int64_t)nx * j + nxny * (zf - 1));
     bool good = R.wait(0);
     int a0 = 0, b0 = 0;                                // stages holding plane z
-    int sl0 = 0, sl1 = 2, sl2 = 1;                     // coefficient slots of z, z-1, z-2
+    int sl0 = 0, sl1 = 2, sl2 = 1;                     // weight slots of z, z-1, z-2
 
     for (int z = zf; z <= ke + 1; ++z) {
         const int a1 = a0 == NA - 1 ? 0 : a0 + 1;
@@ -238,48 +237,41 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
         const float* U0 = R0 + TB_PLANE;
         const float* V0 = U0 + TB_PLANE;
         const float* T0 = V0 + TB_PLANE;
-        float4 dc = zero4, l1 = zero4;
+        const float4 dc = lds4(D0 + o);
+        float4 l1 = dc;
         {
-            uint32_t kw[32];
+            const float4 dn = lds4(D1 + o);
+            const float4 u4 = lds4(U0 + o);
+            const float un = U0[o + 4];
+            const float4 v4 = lds4(V0 + o);
+            const float4 vh4 = lds4(V0 + o + TB_BW);
+            const float4 wl4 = lds4(W0 + o);
+            const float4 wh4 = lds4(W1 + o);
+            const float4 t4 = lds4(T0 + o);
+            const float4 r4 = lds4(R0 + o);
             CoefD kc[4];
-            float4 rr = zero4;
+            float dtr[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-#pragma unroll
-                for (int f = 0; f < 6; ++f) kc[e].f[f] = 0.f;
-                kc[e].dt = 0.f;
+                kc[e] = dt_coef<TR>(el(t4, e), Dh, el(u4, e), e == 3 ? un : el(u4, e + 1),
+                                    el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
+                dtr[e] = el(t4, e) * el(r4, e);
             }
-            if (act) {
-                dc = lds4(D0 + o);
-                const float4 dn = lds4(D1 + o);
-                const float4 u4 = lds4(U0 + o);
-                const float un = U0[o + 4];
-                const float4 v4 = lds4(V0 + o);
-                const float4 vh4 = lds4(V0 + o + TB_BW);
-                const float4 wl4 = lds4(W0 + o);
-                const float4 wh4 = lds4(W1 + o);
-                const float4 t4 = lds4(T0 + o);
-                rr = lds4(R0 + o);
+            if (in_dom && z >= 0 && z < nz) {
+                const float dxm = D0[o - 1], dxp = D0[o + 4];
+                const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+                float out[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    kc[e] = dt_coef<TR>(el(t4, e), el(u4, e), e == 3 ? un : el(u4, e + 1),
-                                        el(v4, e), el(vh4, e), el(wl4, e), el(wh4, e));
-                l1 = dc;
-                if (in_dom && z >= 0 && z < nz) {
-                    const float dxm = D0[o - 1], dxp = D0[o + 4];
-                    const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
-                    float out[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        out[e] = dt_update(kc[e], omc, Dh, el(dc, e),
-                                           e == 0 ? dxm : el(dc, e - 1),
-                                           e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
-                                           el(pdc, e), el(dn, e), el(rr, e));
-                    l1 = make_float4(out[0], out[1], out[2], out[3]);
-                }
-                *reinterpret_cast<float4*>(L1 + (z & 1) * TB_PLANE + o) = l1;
+                    out[e] = dt_update(kc[e], omc, el(dc, e), dtr[e],
+                                       e == 0 ? dxm : el(dc, e - 1),
+                                       e == 3 ? dxp : el(dc, e + 1), el(dym, e), el(dyp, e),
+                                       el(pdc, e), el(dn, e));
+                l1 = make_float4(out[0], out[1], out[2], out[3]);
             }
-            t3_pack(kc, rr, kw);
+            if (act) *reinterpret_cast<float4*>(L1 + (z & 1) * TB_PLANE + o) = l1;
+            uint32_t kw[32];
+            t3_pack(kc, dtr, kw);
             tmem_st32(tmem + sl0 * T3_SLOT_COLS, kw);
         }
         // ---- level 2 at plane z-1 (the level-1 plane z-1 was stored last step)
@@ -290,19 +282,16 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
             const int zz = z - 1;
             if (lv2) {
                 if (in_dom && zz >= 0 && zz < nz) {
-                    CoefD kc[4];
-                    float4 rr;
-                    t3_unpack(kw, kc, rr);
                     const float* P = L1 + (zz & 1) * TB_PLANE;
                     const float lxm = P[o - 1], lxp = P[o + 4];
                     const float4 lym = lds4(P + o - TB_BW), lyp = lds4(P + o + TB_BW);
                     float out[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        out[e] = dt_update(kc[e], omc, Dh, el(l1_m1, e),
+                        out[e] = dt_update(t3_coef(kw, e), omc, el(l1_m1, e), t3_dtr(kw, e),
                                            e == 0 ? lxm : el(l1_m1, e - 1),
                                            e == 3 ? lxp : el(l1_m1, e + 1), el(lym, e),
-                                           el(lyp, e), el(l1_m2, e), el(l1, e), el(rr, e));
+                                           el(lyp, e), el(l1_m2, e), el(l1, e));
                     l2 = make_float4(out[0], out[1], out[2], out[3]);
                 }
                 *reinterpret_cast<float4*>(L2 + (zz & 1) * TB_PLANE + o) = l2;
@@ -314,19 +303,16 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
             tmem_ld32(tmem + sl2 * T3_SLOT_COLS, kw);
             const int zz = z - 2;                      // kb <= zz < ke <= nz
             if (lv3 && in_dom) {
-                CoefD kc[4];
-                float4 rr;
-                t3_unpack(kw, kc, rr);
                 const float* P = L2 + (zz & 1) * TB_PLANE;
                 const float lxm = P[o - 1], lxp = P[o + 4];
                 const float4 lym = lds4(P + o - TB_BW), lyp = lds4(P + o + TB_BW);
                 float out[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    out[e] = dt_update(kc[e], omc, Dh, el(l2_m1, e),
+                    out[e] = dt_update(t3_coef(kw, e), omc, el(l2_m1, e), t3_dtr(kw, e),
                                        e == 0 ? lxm : el(l2_m1, e - 1),
                                        e == 3 ? lxp : el(l2_m1, e + 1), el(lym, e), el(lyp, e),
-                                       el(l2_m2, e), el(l2, e), el(rr, e));
+                                       el(l2_m2, e), el(l2, e));
                 *reinterpret_cast<float4*>(F.d_out + i0 + (int64_t)nx * j + nxny * zz) =
                     make_float4(out[0], out[1], out[2], out[3]);
             }
@@ -336,8 +322,8 @@ __device__ __forceinline__ bool t3_segment(T3Ring<NA>& R, const TBDField& F, uin
         l1_m1 = l1;
         l2_m2 = l2_m1;
         l2_m1 = l2;
-        // ---- this step's coefficients are in tensor memory, and all threads are done
-        // with the stages of plane z: refill them
+        // ---- this step's weights are in tensor memory, and all threads are done with
+        // the stages of plane z: refill them
         tmem_wait_st();
         if (!__syncthreads_and(good)) return false;
         if (z + NA <= ke + 2) issue_a(z + NA, a0);
