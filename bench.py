@@ -842,7 +842,15 @@ def main():
                           "GCell_updates_per_s": N * r64["sweeps"] / r64["time_ms"] / 1e6,
                           "sweep_kernel_GCell_per_s": N * r64["sweeps"] / r64["sweep_ms"] / 1e6}
         extras["mixed_vs_fp64_speedup"] = r64["time_ms"] / r32["time_ms"]
-        extras["mixed_minus_fp64_maxabs_s"] = float(np.abs(s32[fluid] - s64[fluid]).max())
+        # both states are at residual <= tol but stop after different sweep counts (the
+        # check schedules differ), so they differ by the iteration's remaining error there
+        extras["mixed_minus_fp64_at_tol_maxabs_s"] = float(np.abs(s32[fluid] - s64[fluid]).max())
+        # the precision alone: the FP64 path after the mixed solve's number of sweeps
+        sv.reset_state()
+        sv.step(case.s_in, case.eta, r32["sweeps"], precision="fp64")
+        s64n = sv.get_state()
+        extras["mixed_minus_fp64_same_sweeps_maxabs_s"] = float(
+            np.abs(s32[fluid] - s64n[fluid]).max())
         u, ru = sv.umt(args.tol, precision="mixed")
         extras["U_mt"] = u
         extras["U_mt_time_ms"] = ru["time_ms"]
