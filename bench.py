@@ -404,7 +404,9 @@ def run_batch(args):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
                         "kernel": ("batch_tbd_kernel (two-sweep pass over all 48 lattices, "
-                                   "%d TMA stages)" % info["pass_stages"] if passes else
+                                   "%d-column tiles, %d TMA stages)" % (
+                                       info["pass_tile_cols"], info["pass_stages"])
+                                   if passes else
                                    "batch_sweep_kernel (one sweep of all 48 lattices)"),
                         "note": "per sweep: algorithmic bytes of a launch / launches per sweep",
                         "peak_kind": peak_kind},

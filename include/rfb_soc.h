@@ -361,6 +361,10 @@ typedef struct rfb_batch_info {
     int32_t pass_stages;       /* 0: the one-sweep kernel ran; 3 / 4: the batched two-sweep
                                   pass with that many TMA stages */
     int32_t pass_chunk;        /* z planes per work item of the two-sweep pass */
+    int32_t pass_tile_cols;    /* interior columns of a tile of the two-sweep pass: 128 (one
+                                  CTA per SM), or 64 (two CTAs per SM; narrow lattices waste
+                                  less of a tile); 0 with the one-sweep kernel */
+    int32_t reserved_;         /* 0 */
 } rfb_batch_info;
 
 /* hs: n handles (distinct, same device, nx % 4 == 0), not owned; they must outlive the
@@ -373,8 +377,11 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
  * dt_mode, inlet_bc, max_sweeps (per lattice) and check_every (0 = autotuned) apply to
  * all. opts.fp32_kernel: 0 = the faster of the one-sweep kernel over every lattice and
  * the batched two-sweep TMA pass (local steps only; timed once per batch), 1 = the
- * one-sweep kernel, 2..6 = the two-sweep pass (RFB_ERR_INVALID_ARG with the global
- * step). With the two-sweep pass the sweeps per cycle are a multiple of 4. Each handle
+ * one-sweep kernel, 2 = the two-sweep pass with the tile width (128 or 64 columns), TMA
+ * stage count and z chunk timed, 3..6 = the two-sweep pass with 128-column tiles, 7 / 8 =
+ * with 64-column tiles (two CTAs per SM); 2..8 give RFB_ERR_INVALID_ARG with the global
+ * step, larger values always. With the two-sweep pass the sweeps per cycle are a multiple
+ * of 4. Each handle
  * warm-starts from its state if it has one. res (nullable, n entries) and info
  * (nullable) are filled. Returns RFB_ERR_NOT_CONVERGED if max_sweeps ran out first;
  * the states of every handle are valid either way. */

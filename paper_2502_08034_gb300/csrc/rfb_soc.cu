@@ -2366,13 +2366,16 @@ struct rfb_batch {
     BatchLoop* d_loop = nullptr;
     BatchLoop* h_loop = nullptr;         // pinned
     // two-sweep passes over every lattice (local steps, every lattice nz >= 2): per-lattice
-    // tensor maps, (lattice, tile, z chunk) items, chunk length and stage count (autotuned)
-    BatchTBD* d_tbd = nullptr;
+    // tensor maps (boxes for 128- and for 64-column tiles), (lattice, tile, z chunk) items,
+    // tile width, chunk length and stage count (autotuned)
+    BatchTBD* d_tbd = nullptr;           // 136-column boxes
+    BatchTBD* d_tbdn = nullptr;          // 72-column boxes
     BatchTBItem* d_tbitems = nullptr;
     int n_tbitems = 0;
     int tb_lc = 0;                       // chunk length of the built item list
+    int tb_txi = 128;                    // interior columns of a tile (128 or 64)
     int tb_nst = 0;                      // 0: one-sweep kernel; 3 / 4: passes, stages
-    int tb_grid = 0;                     // CTAs of the pass (one per SM)
+    int sms = 152;
     int tuned_mode = -1;                 // kernel choice the tuning was made for
     unsigned int* d_tberr = nullptr;     // set if a stage of a pass never arrives
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -2445,14 +2448,14 @@ void build_items(rfb_batch* b, int kchunk) {
     if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
 }
 
-// Items of the batched two-sweep pass for a z-chunk length: per lattice, chunk-major
-// with the tiles of a chunk consecutive.
-void build_tb_items(rfb_batch* b, int lc) {
-    if (b->tb_lc == lc) return;
+// Items of the batched two-sweep pass for a z-chunk length and tile width: per lattice,
+// chunk-major with the tiles of a chunk consecutive.
+void build_tb_items(rfb_batch* b, int lc, int txi) {
+    if (b->tb_lc == lc && b->tb_txi == txi) return;
     std::vector<BatchTBItem> items;
     for (size_t q = 0; q < b->hs.size(); ++q) {
         const rfb_soc_handle* h = b->hs[q];
-        const int tiles = ((h->nx + TB_TXI - 1) / TB_TXI) * ((h->ny + TB_TYI - 1) / TB_TYI);
+        const int tiles = ((h->nx + txi - 1) / txi) * ((h->ny + TB_TYI - 1) / TB_TYI);
         for (int kb = 0; kb < h->nz; kb += lc)
             for (int t = 0; t < tiles; ++t)
                 items.push_back(BatchTBItem{(int)q, t, kb, std::min(kb + lc, h->nz)});
@@ -2464,6 +2467,7 @@ void build_tb_items(rfb_batch* b, int lc) {
                       cudaMemcpyHostToDevice));
     b->n_tbitems = (int)items.size();
     b->tb_lc = lc;
+    b->tb_txi = txi;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
 }
@@ -2471,11 +2475,15 @@ void build_tb_items(rfb_batch* b, int lc) {
 void batch_sweeps(rfb_batch* b, int n, bool local) {
     if (b->tb_nst) {   // two-sweep passes (n even); pass p reads delta[p & 1]
         for (int q = 0; q < n / 2; ++q) {
-            if (b->tb_nst == 4)
-                batch_tbd_kernel<4><<<b->tb_grid, TB_THREADS, tbd_smem<4>(), b->stream>>>(
+            if (b->tb_txi == 64)   // two CTAs per SM
+                batch_tbd_kernel<3, 64><<<2 * b->sms, TBDGeom<64>::THREADS, tbd_smem<3, 64>(),
+                                          b->stream>>>(b->d_tbdn, b->d_insts, b->d_tbitems,
+                                                       b->n_tbitems, q & 1, b->d_tberr);
+            else if (b->tb_nst == 4)
+                batch_tbd_kernel<4, 128><<<b->sms, TB_THREADS, tbd_smem<4>(), b->stream>>>(
                     b->d_tbd, b->d_insts, b->d_tbitems, b->n_tbitems, q & 1, b->d_tberr);
             else
-                batch_tbd_kernel<3><<<b->tb_grid, TB_THREADS, tbd_smem<3>(), b->stream>>>(
+                batch_tbd_kernel<3, 128><<<b->sms, TB_THREADS, tbd_smem<3>(), b->stream>>>(
                     b->d_tbd, b->d_insts, b->d_tbitems, b->n_tbitems, q & 1, b->d_tberr);
             BLAUNCHED(b);
         }
@@ -2592,16 +2600,20 @@ void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0, int mode
     b->tuned_grid = best_grid;
     b->tuned_kchunk = best_k;
     b->tuned_sweep_ms = best / 4.0;
-    // two-sweep passes (local steps and tensor maps in place): chunk length x stages
+    // two-sweep passes (local steps and tensor maps in place): chunk length x (tile width,
+    // stages): 128-column tiles with three or four stages (one CTA per SM), 64-column tiles
+    // with three (two CTAs per SM; lattices narrower than 128 columns waste less of a tile)
     b->tb_nst = 0;
-    if (mode == 2) best = 1e30f;
+    if (mode >= 2) best = 1e30f;
     if (b->d_tbd && mode != 1) {
         float best_tb = 1e30f;
-        int bl = 0, bn = 0;
+        int bl = 0, bn = 0, bw = 128;
+        const int shapes[3][2] = {{128, 3}, {128, 4}, {64, 3}};
         for (int lc : {16, 32, 64}) {
-            build_tb_items(b, lc);
-            for (int nst : {3, 4}) {
-                b->tb_nst = nst;
+            for (const auto& sh : shapes) {
+                if ((mode == 3 && sh[0] != 128) || (mode == 4 && sh[0] != 64)) continue;
+                build_tb_items(b, lc, sh[0]);
+                b->tb_nst = sh[1];
                 batch_sweeps(b, 2, local);   // warm-up
                 BCK(b, cudaEventRecord(b->ev[0], b->stream));
                 batch_sweeps(b, 4, local);
@@ -2609,12 +2621,12 @@ void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0, int mode
                 BCK(b, cudaEventSynchronize(b->ev[1]));
                 float ms = 0;
                 BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
-                if (ms < best_tb) { best_tb = ms; bl = lc; bn = nst; }
+                if (ms < best_tb) { best_tb = ms; bl = lc; bn = sh[1]; bw = sh[0]; }
             }
         }
         b->tb_nst = 0;
-        if (best_tb < best || mode == 2) {
-            build_tb_items(b, bl);
+        if (best_tb < best || mode >= 2) {
+            build_tb_items(b, bl, bw);
             b->tb_nst = bn;
             b->tuned_sweep_ms = best_tb / 4.0;
         }
@@ -2692,7 +2704,7 @@ rfb_status rfb_soc_batch_destroy(rfb_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
     void* ptrs[] = {b->d_insts, b->d_ctl,  b->d_items,  b->d_item_begin, b->d_partials,
-                    b->d_loop,  b->d_tbd,  b->d_tbitems, b->d_tberr};
+                    b->d_loop,  b->d_tbd,  b->d_tbdn, b->d_tbitems, b->d_tberr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -2779,51 +2791,63 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         if (tb_ok) {
             static bool attr = false;
             if (!attr) {
-                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3>,
+                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3, 128>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             tbd_smem<3>()));
-                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<4>,
+                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<4, 128>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             tbd_smem<4>()));
+                BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3, 64>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tbd_smem<3, 64>()));
                 attr = true;
             }
-            std::vector<BatchTBD> tbd(n);
-            for (int q = 0; q < n; ++q) {
-                rfb_soc_handle* h = b->hs[q];
-                BatchTBD& T = tbd[q];
-                std::memset(&T, 0, sizeof T);
-                try {
-                    for (int p = 0; p < 2; ++p)
-                        tb_encode(h, &T.td[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
-                                  insts[q].delta[p], h->nz, TB_BW);
-                    tb_encode(h, &T.tr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz, TB_BW);
-                    tb_encode(h, &T.tu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz, TB_BW);
-                    tb_encode(h, &T.tv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz, TB_BW);
-                    tb_encode(h, &T.tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32, h->nz + 1,
-                              TB_BW);
-                    tb_encode(h, &T.tt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_dtc, h->nz, TB_BW);
-                } catch (Fail f) {
-                    bset_err(b, "lattice %d: %s", q, h->err.c_str());
-                    throw;
+            for (int wide = 0; wide < 2; ++wide) {   // 72- then 136-column boxes
+                const int bw = wide ? TB_BW : TBDGeom<64>::BW;
+                std::vector<BatchTBD> tbd(n);
+                for (int q = 0; q < n; ++q) {
+                    rfb_soc_handle* h = b->hs[q];
+                    BatchTBD& T = tbd[q];
+                    std::memset(&T, 0, sizeof T);
+                    try {
+                        for (int p = 0; p < 2; ++p)
+                            tb_encode(h, &T.td[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                      insts[q].delta[p], h->nz, bw);
+                        tb_encode(h, &T.tr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_r32, h->nz, bw);
+                        tb_encode(h, &T.tu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_u32, h->nz, bw);
+                        tb_encode(h, &T.tv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_v32, h->nz, bw);
+                        tb_encode(h, &T.tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_w32,
+                                  h->nz + 1, bw);
+                        tb_encode(h, &T.tt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_dtc, h->nz, bw);
+                    } catch (Fail f) {
+                        bset_err(b, "lattice %d: %s", q, h->err.c_str());
+                        throw;
+                    }
+                    T.nx = h->nx; T.ny = h->ny; T.nz = h->nz;
+                    T.omc = (float)(1.0 - ops[q].cfl);
+                    T.Dh = insts[q].C32.Dh;
                 }
-                T.nx = h->nx; T.ny = h->ny; T.nz = h->nz;
-                T.omc = (float)(1.0 - ops[q].cfl);
-                T.Dh = insts[q].C32.Dh;
+                BatchTBD*& dst = wide ? b->d_tbd : b->d_tbdn;
+                if (!dst) BCK(b, cudaMalloc((void**)&dst, n * sizeof(BatchTBD)));
+                BCK(b, cudaMemcpy(dst, tbd.data(), n * sizeof(BatchTBD), cudaMemcpyHostToDevice));
             }
-            if (!b->d_tbd) BCK(b, cudaMalloc((void**)&b->d_tbd, n * sizeof(BatchTBD)));
-            BCK(b, cudaMemcpy(b->d_tbd, tbd.data(), n * sizeof(BatchTBD), cudaMemcpyHostToDevice));
-            int sms = 152;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-            b->tb_grid = sms;
+            cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
         } else if (b->tb_nst) {
             b->tb_nst = 0;   // a global step: the one-sweep kernel (the graphs hold passes)
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
         }
         BCK(b, cudaMemsetAsync(b->d_tberr, 0, sizeof(unsigned int), b->stream));
-        // opts.fp32_kernel: 0 the faster, 1 the one-sweep kernel, 2 two-sweep passes
-        const int mode = o.fp32_kernel == 1 ? 1 : o.fp32_kernel >= 2 ? 2 : 0;
-        if (mode == 2 && !tb_ok) {
+        // opts.fp32_kernel: 0 the faster, 1 the one-sweep kernel, 2 two-sweep passes (tile
+        // width, stages and chunk timed), 3 .. 6 passes with 128-column tiles, 7 / 8 passes
+        // with 64-column tiles (mode 3 and 4 below)
+        if (o.fp32_kernel > 8) {
+            bset_err(b, "opts.fp32_kernel of a batch must be 0 .. 8");
+            return RFB_ERR_INVALID_ARG;
+        }
+        const int k32 = o.fp32_kernel;
+        const int mode = k32 <= 2 ? k32 : k32 <= 6 ? 3 : 4;
+        if (mode >= 2 && !tb_ok) {
             bset_err(b, "two-sweep passes need local steps and nz >= 2 in every lattice");
             return RFB_ERR_INVALID_ARG;
         }
@@ -2946,6 +2970,7 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             info->graph_launches = graph_launches;
             info->pass_stages = b->tb_nst;
             info->pass_chunk = b->tb_nst ? b->tb_lc : 0;
+            info->pass_tile_cols = b->tb_nst ? b->tb_txi : 0;
             info->time_ms = ms;
             info->launches = b->launches;
         }

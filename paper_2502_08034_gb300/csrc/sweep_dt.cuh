@@ -131,12 +131,30 @@ sweep32d_kernel(DArgs A, const float* __restrict__ s, float* __restrict__ s_out,
 // mbarrier waits are those of sweep32tb_kernel (sweep_tb.cuh); a stage holds six FP32
 // planes (delta, forcing, u, v, w, step).
 // ---------------------------------------------------------------------------------
-constexpr int TBD_STAGE = 6 * TB_F32;
-template <int NST> __host__ __device__ constexpr int tbd_l1() { return NST * TBD_STAGE; }   // level-1 planes
-template <int NST> __host__ __device__ constexpr int tbd_bar() { return tbd_l1<NST>() + 2 * TB_F32; }   // barriers
-template <int NST> __host__ __device__ constexpr int tbd_smem() { return tbd_bar<NST>() + 64 + 128; }  // + slack
+// Tile geometry: TXI interior columns (128, or 64 for narrow lattices in batches), the 12
+// interior rows of sweep_tb.cuh, boxes of TXI + 8 columns and 16 rows, one thread per 4
+// cells of the box columns on 14 rows.
+template <int TXI>
+struct TBDGeom {
+    static_assert(TXI % 4 == 0, "4-cell groups");
+    static constexpr int BW = TXI + 8;           // staged columns
+    static constexpr int GX = BW / 4;            // thread columns
+    static constexpr int THREADS = GX * TB_GY;   // 476 (TXI = 128) or 252 (TXI = 64)
+    static constexpr int PLANE = BW * TB_BH;
+    static constexpr int F32 = PLANE * 4;        // bytes of one staged FP32 plane
+    static constexpr int STAGE = 6 * F32;        // delta, forcing, u, v, w, step
+    static_assert(F32 % 128 == 0, "stage buffers stay 128-B aligned");
+};
+static_assert(TBDGeom<128>::F32 == TB_F32 && TBDGeom<128>::THREADS == TB_THREADS, "geometry");
+constexpr int TBD_STAGE = TBDGeom<128>::STAGE;
+template <int NST, int TXI = 128>
+__host__ __device__ constexpr int tbd_l1() { return NST * TBDGeom<TXI>::STAGE; }   // level-1 planes
+template <int NST, int TXI = 128>
+__host__ __device__ constexpr int tbd_bar() { return tbd_l1<NST, TXI>() + 2 * TBDGeom<TXI>::F32; }
+template <int NST, int TXI = 128>
+__host__ __device__ constexpr int tbd_smem() { return tbd_bar<NST, TXI>() + 64 + 128; }   // + slack
 static_assert(tbd_smem<4>() <= 232448, "four stages fit the 227 KB a CTA may use");
-constexpr uint32_t TBD_TX_BYTES = 6 * TB_F32;
+static_assert(2 * tbd_smem<3, 64>() <= 233472, "two narrow three-stage CTAs fit an SM");
 
 struct TBDArgs {
     int nx, ny, nz;
@@ -166,13 +184,15 @@ struct TBDField {
 
 // Per-CTA state of the pass: the stage ring in shared memory, the parity of each stage's
 // next completion and the stages with a copy in flight (every thread tracks the same).
-template <int NST>
+template <int NST, int TXI = 128>
 struct TBDRing {
     unsigned char* smem;
     uint64_t* bar;
     uint32_t phase, pend;
     unsigned int* err;
-    __device__ __forceinline__ unsigned char* stage(int s) const { return smem + s * TBD_STAGE; }
+    __device__ __forceinline__ unsigned char* stage(int s) const {
+        return smem + s * TBDGeom<TXI>::STAGE;
+    }
     __device__ __forceinline__ bool wait(int s) {          // bounded wait for stage s
         if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, TB_SPIN_LIMIT, err)) return false;
         phase ^= 1u << s;
@@ -181,12 +201,13 @@ struct TBDRing {
     }
 };
 
-template <int NST>
-__device__ __forceinline__ TBDRing<NST> tbd_ring_init(unsigned char* smem_raw, unsigned int* err) {
-    TBDRing<NST> R;
+template <int NST, int TXI = 128>
+__device__ __forceinline__ TBDRing<NST, TXI> tbd_ring_init(unsigned char* smem_raw,
+                                                           unsigned int* err) {
+    TBDRing<NST, TXI> R;
     R.smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    R.bar = reinterpret_cast<uint64_t*>(R.smem + tbd_bar<NST>());
+    R.bar = reinterpret_cast<uint64_t*>(R.smem + tbd_bar<NST, TXI>());
     R.phase = 0;
     R.pend = 0;
     R.err = err;
@@ -200,8 +221,8 @@ __device__ __forceinline__ TBDRing<NST> tbd_ring_init(unsigned char* smem_raw, u
 
 // error path (a stage never arrived): wait, again with the limit, for the copies still
 // in flight into this CTA's shared memory before the kernel returns
-template <int NST>
-__device__ __forceinline__ void tbd_ring_drain(TBDRing<NST>& R) {
+template <int NST, int TXI>
+__device__ __forceinline__ void tbd_ring_drain(TBDRing<NST, TXI>& R) {
     for (int s = 0; s < NST; ++s)
         if (R.pend & (1u << s)) (void)R.wait(s);
 }
@@ -209,20 +230,21 @@ __device__ __forceinline__ void tbd_ring_drain(TBDRing<NST>& R) {
 // Two sweeps over planes kb .. ke-1 of one tile of lattice F, from F.d_in into F.d_out.
 // Every stage issued is waited for, so the ring is empty when it returns; false if a
 // wait gave up (the CTA decides together at its step barrier).
-template <bool TR, int NST>
-__device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, int tile,
+template <bool TR, int NST, int TXI = 128>
+__device__ __forceinline__ bool tbd_segment(TBDRing<NST, TXI>& R, const TBDField& F, int tile,
                                             int kb, int ke) {
+    using G = TBDGeom<TXI>;
     const int tid = threadIdx.x;
-    const int tx = tid % TB_GX, ty = tid / TB_GX;
+    const int tx = tid % G::GX, ty = tid / G::GX;
     const int bxx = 4 * tx, byy = 1 + ty;              // this thread's cells in the box
     const int nx = F.nx, ny = F.ny, nz = F.nz;
-    const bool interior = tx >= 1 && tx < 1 + TB_TXI / 4 && ty >= 1 && ty <= TB_TYI;
+    const bool interior = tx >= 1 && tx < 1 + TXI / 4 && ty >= 1 && ty <= TB_TYI;
     const int64_t nxny = (int64_t)nx * ny;
-    const int o = byy * TB_BW + bxx;                   // offset in a staged plane
-    const int gx = (nx + TB_TXI - 1) / TB_TXI;
+    const int o = byy * G::BW + bxx;                   // offset in a staged plane
+    const int gx = (nx + TXI - 1) / TXI;
     const float omc = F.omc, Dh = F.Dh;
     unsigned char* smem = R.smem;
-    const int x0 = TB_TXI * (tile % gx) - 4;           // box origin (4-cell aligned)
+    const int x0 = TXI * (tile % gx) - 4;           // box origin (4-cell aligned)
     const int y0 = TB_TYI * (tile / gx) - 2;
     const int i0 = x0 + bxx, j = y0 + byy;
     const bool in_dom = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
@@ -231,13 +253,13 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
         if (tid != 0) return;                          // one thread issues the copies
         unsigned char* S = R.stage(s);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&R.bar[s], TBD_TX_BYTES);
+        mbar_expect_tx(&R.bar[s], G::STAGE);
         tma_load_3d(S, F.d, x0, y0, p, &R.bar[s]);
-        tma_load_3d(S + TB_F32, F.r, x0, y0, p, &R.bar[s]);
-        tma_load_3d(S + 2 * TB_F32, F.u, x0, y0, p, &R.bar[s]);
-        tma_load_3d(S + 3 * TB_F32, F.v, x0, y0, p, &R.bar[s]);
-        tma_load_3d(S + 4 * TB_F32, F.w, x0, y0, p, &R.bar[s]);
-        tma_load_3d(S + 5 * TB_F32, F.t, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + G::F32, F.r, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 2 * G::F32, F.u, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 3 * G::F32, F.v, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 4 * G::F32, F.w, x0, y0, p, &R.bar[s]);
+        tma_load_3d(S + 5 * G::F32, F.t, x0, y0, p, &R.bar[s]);
     };
     __syncthreads();   // the previous segment's readers are done with every stage
     for (int s = 0; s < NST; ++s) issue(kb - 1 + s, s);                 // kb-1, kb, ...
@@ -261,20 +283,20 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
         const int s1 = s0 == NST - 1 ? 0 : s0 + 1;
         if (good) good = R.wait(s1);
         const float* D0 = reinterpret_cast<const float*>(R.stage(s0));
-        const float* R0 = D0 + TB_PLANE;
-        const float* U0 = R0 + TB_PLANE;
-        const float* V0 = U0 + TB_PLANE;
-        const float* W0 = V0 + TB_PLANE;
-        const float* T0 = W0 + TB_PLANE;
+        const float* R0 = D0 + G::PLANE;
+        const float* U0 = R0 + G::PLANE;
+        const float* V0 = U0 + G::PLANE;
+        const float* W0 = V0 + G::PLANE;
+        const float* T0 = W0 + G::PLANE;
         const float* D1 = reinterpret_cast<const float*>(R.stage(s1));
-        const float* W1 = D1 + 4 * TB_PLANE;
+        const float* W1 = D1 + 4 * G::PLANE;
         // ---- level 1 at plane z
         dc = lds4(D0 + o);
         const float4 dn = lds4(D1 + o);
         const float4 u4 = lds4(U0 + o);
         const float un = U0[o + 4];
         const float4 v4 = lds4(V0 + o);
-        const float4 vh4 = lds4(V0 + o + TB_BW);
+        const float4 vh4 = lds4(V0 + o + G::BW);
         const float4 wl4 = lds4(W0 + o);
         const float4 wh4 = lds4(W1 + o);
         const float4 t4 = lds4(T0 + o);
@@ -287,7 +309,7 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
         float4 l1 = dc;
         if (in_dom && z >= 0 && z < nz) {
             const float dxm = D0[o - 1], dxp = D0[o + 4];
-            const float4 dym = lds4(D0 + o - TB_BW), dyp = lds4(D0 + o + TB_BW);
+            const float4 dym = lds4(D0 + o - G::BW), dyp = lds4(D0 + o + G::BW);
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -296,15 +318,15 @@ __device__ __forceinline__ bool tbd_segment(TBDRing<NST>& R, const TBDField& F, 
                                    el(dym, e), el(dyp, e), el(pdc, e), el(dn, e));
             l1 = make_float4(out[0], out[1], out[2], out[3]);
         }
-        float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST>()) + (z & 1) * TB_PLANE;
+        float* L1w = reinterpret_cast<float*>(smem + tbd_l1<NST, TXI>()) + (z & 1) * G::PLANE;
         *reinterpret_cast<float4*>(L1w + o) = l1;
         // ---- level 2 at plane z-1 (its level-1 neighbours were stored last step)
         const int zz = z - 1;
         if (zz >= kb && interior && in_dom) {
             const float* L1r =
-                reinterpret_cast<const float*>(smem + tbd_l1<NST>()) + (zz & 1) * TB_PLANE;
+                reinterpret_cast<const float*>(smem + tbd_l1<NST, TXI>()) + (zz & 1) * G::PLANE;
             const float lxm = L1r[o - 1], lxp = L1r[o + 4];
-            const float4 lym = lds4(L1r + o - TB_BW), lyp = lds4(L1r + o + TB_BW);
+            const float4 lym = lds4(L1r + o - G::BW), lyp = lds4(L1r + o + G::BW);
             float out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -384,13 +406,13 @@ struct BatchTBItem {
     int inst, tile, kb, ke;           // planes kb .. ke-1 of one tile of one lattice
 };
 
-template <int NST>
-__global__ void __launch_bounds__(TB_THREADS, 1)
+template <int NST, int TXI>
+__global__ void __launch_bounds__(TBDGeom<TXI>::THREADS, TXI == 64 ? 2 : 1)
 batch_tbd_kernel(const BatchTBD* __restrict__ lat, const BatchInst* __restrict__ insts,
                  const BatchTBItem* __restrict__ items, int n_items, int parity,
                  unsigned int* err) {
     extern __shared__ unsigned char smem_raw[];
-    TBDRing<NST> R = tbd_ring_init<NST>(smem_raw, err);
+    TBDRing<NST, TXI> R = tbd_ring_init<NST, TXI>(smem_raw, err);
     bool ok = true;
     for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
         const BatchTBItem it = items[w];
@@ -399,7 +421,7 @@ batch_tbd_kernel(const BatchTBD* __restrict__ lat, const BatchInst* __restrict__
         const BatchTBD* L = lat + it.inst;
         const TBDField F{&L->td[parity], &L->tr, &L->tu, &L->tv, &L->tw, &L->tt, L->nx, L->ny,
                          L->nz, I->delta[parity], I->delta[parity ^ 1], L->omc, L->Dh};
-        ok = tbd_segment<false, NST>(R, F, it.tile, it.kb, it.ke);
+        ok = tbd_segment<false, NST, TXI>(R, F, it.tile, it.kb, it.ke);
     }
     if (!ok) tbd_ring_drain<NST>(R);
 }

@@ -166,3 +166,34 @@ def test_batched_workload_48_lattices_full_size():
             s.close()
     ref = soc.steady_state(soc.assemble(problem_from_case(cases[0], soc)))
     assert np.abs(s0 - ref).max() < 1e-6
+
+
+def test_batched_pass_64_and_128_column_tiles_are_the_same_sweeps():
+    """The batched two-sweep pass with 64-column tiles (two CTAs per SM) and with
+    128-column tiles, on lattices several narrow tiles wide with ragged last tiles in x and
+    y: the same bits for the same cycles, and the oracle's steady states."""
+    from paper_2502_08034_gb300 import rfb, synth
+    dims = [(100, 28, 20), (148, 16, 24), (68, 30, 18)]
+    cases = [synth.build_case("bt%dx%dx%d" % d, d, 0.8, 4.0, 11 + q, 0.01, -0.1, 0.4, 1e-10)
+             for q, d in enumerate(dims)]
+    refs = [soc.steady_state(soc.assemble(problem_from_case(c, soc))) for c in cases]
+    out = []
+    for kernel in (3, 7):                   # 128-column tiles, 64-column tiles
+        solvers = [rfb.Solver.from_case(c) for c in cases]
+        try:
+            with rfb.Batch(solvers) as b:
+                res, info = b.solve([c.s_in for c in cases], [c.eta for c in cases],
+                                    [1e-10] * len(cases), fp32_kernel=kernel, check_every=40)
+            assert info["pass_tile_cols"] == (128 if kernel == 3 else 64)
+            assert info["pass_stages"] > 0
+            out.append(([s.get_state() for s in solvers], [r["sweeps"] for r in res]))
+            for c, r, sv, ref in zip(cases, res, solvers, refs):
+                assert r["residual"] <= 1e-10
+                assert np.abs(sv.get_state() - ref).max() < 1e-7, (kernel, c.name)
+        finally:
+            for s in solvers:
+                s.close()
+    (sa, na), (sb, nb) = out
+    assert na == nb
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
