@@ -364,7 +364,10 @@ typedef struct rfb_batch_info {
     int32_t pass_tile_cols;    /* interior columns of a tile of the two-sweep pass: 128 (one
                                   CTA per SM), or 64 (two CTAs per SM; narrow lattices waste
                                   less of a tile); 0 with the one-sweep kernel */
-    int32_t reserved_;         /* 0 */
+    int32_t df_cycles;         /* cycles whose defects were formed in double-float (FP32
+                                  pairs, as in a single mixed solve), before the states
+                                  were joined and checked in FP64; the rest of the cycles
+                                  checked in FP64 */
 } rfb_batch_info;
 
 /* hs: n handles (distinct, same device, nx % 4 == 0), not owned; they must outlive the
@@ -381,10 +384,15 @@ rfb_status rfb_soc_batch_create(rfb_soc_handle* const* hs, int n, rfb_batch** ou
  * stage count and z chunk timed, 3..6 = the two-sweep pass with 128-column tiles, 7 / 8 =
  * with 64-column tiles (two CTAs per SM); 2..8 give RFB_ERR_INVALID_ARG with the global
  * step, larger values always. With the two-sweep pass the sweeps per cycle are a multiple
- * of 4. Each handle
- * warm-starts from its state if it has one. res (nullable, n entries) and info
- * (nullable) are filled. Returns RFB_ERR_NOT_CONVERGED if max_sweeps ran out first;
- * the states of every handle are valid either way. */
+ * of 4. The defects of the cycles are formed in double-float until every lattice has
+ * reached its tol or, where tol lies below what double-float defects resolve (10 x tau
+ * 2^-44 max_c d_c), that level (info->df_cycles); the states are then joined and checked
+ * in FP64, and a lattice above its tol there continues with FP64 checks, so every result
+ * is FP64-confirmed (the handles need the memory of a mixed solve: the assembled operator
+ * as FP64 and as FP32 pairs, and a double-float state). Each handle warm-starts from its
+ * state if it has one. res (nullable, n entries) and info (nullable) are filled. Returns
+ * RFB_ERR_NOT_CONVERGED if max_sweeps ran out first; the states of every handle are
+ * valid either way. */
 rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* eta,
                                const double* tol, const rfb_solve_opts* opts,
                                rfb_solve_result* res, rfb_batch_info* info);

@@ -2359,10 +2359,14 @@ struct rfb_batch {
     double tuned_sweep_ms = 0, tuned_check_ms = 0;
     cudaGraphExec_t exec = nullptr;
     int exec_every = 0;
+    bool exec_df = false;
+    // defects in double-float (check_df arithmetic) during the cycles, FP64 once at the end
+    bool df = false;
     // device-driven loop: a graph whose while node repeats the cycle until every lattice
     // has converged or the launch's cycle budget is spent
     cudaGraphExec_t loop_exec = nullptr;
     int loop_every = 0;
+    bool loop_df = false;
     BatchLoop* d_loop = nullptr;
     BatchLoop* h_loop = nullptr;         // pinned
     // two-sweep passes over every lattice (local steps, every lattice nz >= 2): per-lattice
@@ -2500,14 +2504,26 @@ void batch_sweeps(rfb_batch* b, int n, bool local) {
     }
 }
 
-void batch_check(rfb_batch* b, bool fused, int sweeps_done) {
-    if (fused)
+// the check kernel of every active lattice (double-float defects when b->df, else FP64),
+// item partials only
+void batch_check_items(rfb_batch* b, bool fused) {
+    if (b->df && fused)
+        batch_check_df_kernel<true><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
+            b->d_insts, b->d_items, b->n_items, b->d_partials);
+    else if (b->df)
+        batch_check_df_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
+            b->d_insts, b->d_items, b->n_items, b->d_partials);
+    else if (fused)
         batch_check_kernel<true><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
             b->d_insts, b->d_items, b->n_items, b->d_partials);
     else
         batch_check_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
             b->d_insts, b->d_items, b->n_items, b->d_partials);
     BLAUNCHED(b);
+}
+
+void batch_check(rfb_batch* b, bool fused, int sweeps_done) {
+    batch_check_items(b, fused);
     batch_finalize_kernel<<<(int)b->hs.size(), 256, 0, b->stream>>>(
         b->d_insts, b->d_item_begin, b->d_partials, b->d_ctl, fused ? 1 : 0, sweeps_done);
     BLAUNCHED(b);
@@ -2530,7 +2546,7 @@ void batch_cycle(rfb_batch* b, int every, bool local, bool to_host = true) {
 // lattice is still active and the launch's cycle budget (BatchLoop::max_cycles, written
 // by the host before each launch) is not spent. No host round trip between cycles.
 void build_loop_graph(rfb_batch* b, int every, bool local) {
-    if (b->loop_exec && b->loop_every == every) return;
+    if (b->loop_exec && b->loop_every == every && b->loop_df == b->df) return;
     if (b->loop_exec) { cudaGraphExecDestroy(b->loop_exec); b->loop_exec = nullptr; }
     cudaGraph_t g = nullptr;
     BCK(b, cudaGraphCreate(&g, 0));
@@ -2567,6 +2583,7 @@ void build_loop_graph(rfb_batch* b, int every, bool local) {
     }
     cudaGraphDestroy(g);
     b->loop_every = every;
+    b->loop_df = b->df;
 }
 
 // Project-written autotuner: for each candidate z-chunk of the work items, time a few
@@ -2632,9 +2649,7 @@ void autotune(rfb_batch* b, bool local, std::vector<BatchInst>& insts0, int mode
         }
     }
     BCK(b, cudaEventRecord(b->ev[0], b->stream));
-    batch_check_kernel<false><<<b->grid_blocks, dim3(BX, BY), 0, b->stream>>>(
-        b->d_insts, b->d_items, b->n_items, b->d_partials);
-    BLAUNCHED(b);
+    batch_check_items(b, false);
     BCK(b, cudaEventRecord(b->ev[1], b->stream));
     BCK(b, cudaEventSynchronize(b->ev[1]));
     float cms = 0;
@@ -2782,6 +2797,37 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             k.tau = Q > 0 ? (double)h->n_fluid * h3 / Q : std::pow(h->nz * h->h, 2) / h->D;
             k.n_unknown = (double)h->n_fluid;
         }
+        // Defects in double-float (as in a single mixed solve): the states are double-float
+        // pairs during these cycles, and a lattice leaves them at its tol or, if that lies
+        // below what double-float defects resolve, at 10 x tau 2^-44 max_c d_c. Then every
+        // state is joined and checked in FP64; lattices still above their tol continue
+        // with FP64 checks.
+        b->df = true;
+        for (int q = 0; q < n; ++q)
+            ctl[q].tol = std::max(tol[q], 10.0 * ctl[q].tau * std::ldexp(1.0, -44) *
+                                              (ops[q].cfl / ops[q].dt));
+        int64_t df_cycles = 0;
+        std::vector<int> cur0(n);
+        for (int q = 0; q < n; ++q) {
+            rfb_soc_handle* h = b->hs[q];
+            cur0[q] = h->s_cur;
+            try {
+                ensure_L2F(h, ops[q]);
+                df_begin(h, false);
+                CK(h, cudaStreamSynchronize(h->stream));
+            } catch (Fail f) {
+                bset_err(b, "lattice %d: %s", q, h->err.c_str());
+                throw;
+            }
+            BatchInst& I = insts[q];
+            const size_t N = h->N;
+            for (int f = 0; f < 6; ++f) I.K2.f[f] = h->d_L2F + f * N;
+            I.K2.diag = h->d_L2F + 6 * N;
+            I.K2.b = h->d_L2F + 7 * N;
+            I.sdf[0] = h->d_sdf[0];
+            I.sdf[1] = h->d_sdf[1];
+            I.cur = 0;
+        }
         BCK(b, cudaMemcpy(b->d_insts, insts.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice));
         BCK(b, cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(BatchCtl), cudaMemcpyHostToDevice));
         // tensor maps of the two-sweep passes (local steps; re-encoded every solve, since a
@@ -2874,67 +2920,99 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
                 if (!b->h_ctl[q].converged && !b->h_ctl[q].nonfinite) return false;
             return true;
         };
-        // Without a timeout the cycles run in a device-driven loop (a conditional while
-        // node): one graph launch runs up to 64 cycles and stops by itself once every
-        // lattice has converged, so the host waits once per launch, not once per cycle.
-        // A timeout needs the host between cycles: one captured cycle per launch.
-        const bool device_loop = o.timeout_ms == 0;
-        if (device_loop) {
-            build_loop_graph(b, every, local);
-        } else if (!b->exec || b->exec_every != every) {
-            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-            cudaGraph_t g = nullptr;
-            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            const int64_t l0 = b->launches;
-            try {
-                batch_cycle(b, every, local);
-            } catch (Fail) {
-                cudaStreamEndCapture(b->stream, &g);
-                if (g) cudaGraphDestroy(g);
-                throw;
-            }
-            b->launches = l0;   // counted when replayed
-            BCK(b, cudaStreamEndCapture(b->stream, &g));
-            BCK(b, cudaGraphInstantiate(&b->exec, g, 0));
-            cudaGraphDestroy(g);
-            b->exec_every = every;
-        }
         int64_t graph_launches = 0;
-        while (!all_done()) {
-            if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+        const bool device_loop = o.timeout_ms == 0;
+        for (int phase = 0; phase < 2; ++phase) {
+            // Without a timeout the cycles run in a device-driven loop (a conditional while
+            // node): one graph launch runs up to 64 cycles and stops by itself once every
+            // lattice has converged, so the host waits once per launch, not once per cycle.
+            // A timeout needs the host between cycles: one captured cycle per launch.
             if (device_loop) {
-                const int64_t left = (o.max_sweeps - done + every - 1) / every;
-                BatchLoop lp{0, (int)std::min<int64_t>(64, left), n, 0};
-                *b->h_loop = lp;
-                BCK(b, cudaMemcpyAsync(b->d_loop, b->h_loop, sizeof(BatchLoop),
-                                       cudaMemcpyHostToDevice, b->stream));
-                BCK(b, cudaGraphLaunch(b->loop_exec, b->stream));
-                BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl),
-                                       cudaMemcpyDeviceToHost, b->stream));
-                BCK(b, cudaMemcpyAsync(b->h_loop, b->d_loop, sizeof(BatchLoop),
-                                       cudaMemcpyDeviceToHost, b->stream));
-                BCK(b, cudaStreamSynchronize(b->stream));
-                const int cyc = b->h_loop->cycles;
-                b->launches += (int64_t)cyc * (every + 4);
-                done += (int64_t)cyc * every;
-                ++graph_launches;
-                if (cyc < 1) {
-                    bset_err(b, "the device-driven batch loop ran no cycle");
-                    throw Fail{RFB_ERR_CUDA};
+                build_loop_graph(b, every, local);
+            } else if (!b->exec || b->exec_every != every || b->exec_df != b->df) {
+                if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+                cudaGraph_t g = nullptr;
+                BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                const int64_t l0 = b->launches;
+                try {
+                    batch_cycle(b, every, local);
+                } catch (Fail) {
+                    cudaStreamEndCapture(b->stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    throw;
                 }
-                continue;
+                b->launches = l0;   // counted when replayed
+                BCK(b, cudaStreamEndCapture(b->stream, &g));
+                BCK(b, cudaGraphInstantiate(&b->exec, g, 0));
+                cudaGraphDestroy(g);
+                b->exec_every = every;
+                b->exec_df = b->df;
             }
-            if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
-                                        std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
-                bset_err(b, "opts.timeout_ms reached after %lld sweeps", (long long)done);
-                st = RFB_ERR_NOT_CONVERGED;
-                break;
+            while (!all_done()) {
+                if (done >= o.max_sweeps) { st = RFB_ERR_NOT_CONVERGED; break; }
+                if (device_loop) {
+                    const int64_t left = (o.max_sweeps - done + every - 1) / every;
+                    BatchLoop lp{0, (int)std::min<int64_t>(64, left), n, 0};
+                    *b->h_loop = lp;
+                    BCK(b, cudaMemcpyAsync(b->d_loop, b->h_loop, sizeof(BatchLoop),
+                                           cudaMemcpyHostToDevice, b->stream));
+                    BCK(b, cudaGraphLaunch(b->loop_exec, b->stream));
+                    BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl),
+                                           cudaMemcpyDeviceToHost, b->stream));
+                    BCK(b, cudaMemcpyAsync(b->h_loop, b->d_loop, sizeof(BatchLoop),
+                                           cudaMemcpyDeviceToHost, b->stream));
+                    BCK(b, cudaStreamSynchronize(b->stream));
+                    const int cyc = b->h_loop->cycles;
+                    b->launches += (int64_t)cyc * (every + 4);
+                    done += (int64_t)cyc * every;
+                    ++graph_launches;
+                    if (cyc < 1) {
+                        bset_err(b, "the device-driven batch loop ran no cycle");
+                        throw Fail{RFB_ERR_CUDA};
+                    }
+                    continue;
+                }
+                if (o.timeout_ms > 0 && std::chrono::duration<double, std::milli>(
+                                            std::chrono::steady_clock::now() - t0).count() >= o.timeout_ms) {
+                    bset_err(b, "opts.timeout_ms reached after %lld sweeps", (long long)done);
+                    st = RFB_ERR_NOT_CONVERGED;
+                    break;
+                }
+                BCK(b, cudaGraphLaunch(b->exec, b->stream));
+                b->launches += every + 3;
+                BCK(b, cudaStreamSynchronize(b->stream));
+                done += every;
+                ++graph_launches;
             }
-            BCK(b, cudaGraphLaunch(b->exec, b->stream));
-            b->launches += every + 3;
+            if (!b->df) break;
+            df_cycles = done / every;
+            // double-float phase over: join every state, then check in FP64 against the
+            // lattice's own tol (lattices that left the phase are checked again; any above
+            // their tol continue with FP64 checks)
+            BCK(b, cudaMemcpy(insts.data(), b->d_insts, n * sizeof(BatchInst),
+                              cudaMemcpyDeviceToHost));
+            for (int q = 0; q < n; ++q) {
+                rfb_soc_handle* h = b->hs[q];
+                join64_kernel<<<flat_grid(h->N), 256, 0, b->stream>>>(
+                    h->d_sdf[insts[q].cur], h->d_s[cur0[q]], h->N);
+                BLAUNCHED(b);
+                insts[q].cur = cur0[q];
+                b->h_ctl[q].tol = tol[q];
+                if (b->h_ctl[q].converged) {
+                    insts[q].active = 1;
+                    b->h_ctl[q].converged = 0;
+                }
+            }
+            BCK(b, cudaMemcpyAsync(b->d_insts, insts.data(), n * sizeof(BatchInst),
+                                   cudaMemcpyHostToDevice, b->stream));
+            BCK(b, cudaMemcpyAsync(b->d_ctl, b->h_ctl, n * sizeof(BatchCtl),
+                                   cudaMemcpyHostToDevice, b->stream));
+            b->df = false;
+            batch_check(b, false, 0);
+            BCK(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(BatchCtl),
+                                   cudaMemcpyDeviceToHost, b->stream));
             BCK(b, cudaStreamSynchronize(b->stream));
-            done += every;
-            ++graph_launches;
+            if (st != RFB_OK) break;
         }
         BCK(b, cudaMemcpy(insts.data(), b->d_insts, n * sizeof(BatchInst), cudaMemcpyDeviceToHost));
         unsigned int tb_bad = 0;
@@ -2971,6 +3049,7 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
             info->pass_stages = b->tb_nst;
             info->pass_chunk = b->tb_nst ? b->tb_lc : 0;
             info->pass_tile_cols = b->tb_nst ? b->tb_txi : 0;
+            info->df_cycles = (int32_t)df_cycles;
             info->time_ms = ms;
             info->launches = b->launches;
         }

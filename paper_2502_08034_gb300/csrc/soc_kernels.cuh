@@ -432,6 +432,13 @@ sweep32v_kernel(Lattice L, Coef<float> C, const float* __restrict__ s,
 // skipped (their `active` flag lives in device memory, so a captured CUDA graph keeps
 // working as lattices drop out).
 // ---------------------------------------------------------------------------------
+// The assembled operator as double-float pairs (check_df_kernel below)
+struct L2F {
+    const float2* __restrict__ f[6];   // neighbour coefficients as (hi, lo)
+    const float2* __restrict__ diag;
+    const float2* __restrict__ b;
+};
+
 struct BatchInst {
     Lattice L;
     Coef<float> C32;       // correction sweep coefficients (homogeneous operator)
@@ -439,9 +446,11 @@ struct BatchInst {
     float* delta[2];
     float* r32;
     double* s64[2];
+    L2F K2;                // double-float operator (double-float checks)
+    float2* sdf[2];        // double-float state (double-float checks)
     float cfl;
     int active;            // 1 while the lattice has not converged
-    int cur;               // which s64 buffer holds the state
+    int cur;               // which s64 (sdf with double-float checks) buffer holds the state
     int pad_;
 };
 
@@ -1088,11 +1097,6 @@ check64c_kernel(Lattice L, Coef<double> C, L64 K, const double* __restrict__ s,
 // a defect is about 2^-47 of its largest term, far below the tolerances of a solve; the
 // last check of every mixed solve is the FP64 one.
 // ---------------------------------------------------------------------------------
-struct L2F {
-    const float2* __restrict__ f[6];   // neighbour coefficients as (hi, lo)
-    const float2* __restrict__ diag;
-    const float2* __restrict__ b;
-};
 
 __device__ __forceinline__ float2 two_sum(float a, float b) {      // a + b = s + e exactly
     const float s = a + b;
@@ -1141,6 +1145,60 @@ __global__ void join64_kernel(const float2* __restrict__ in, double* __restrict_
 // FP32 forcing (its high part), with the reductions the iteration needs: 0 sum RHS^2,
 // 6 count of non-finite values, 7 max |RHS| (slots 1-5 stay 0). FUSE: the state is
 // s + delta, written to s_new (every cell).
+// One column (i, j), planes kb .. ke-1, of the double-float defect; accumulates the sum of
+// squares, the largest magnitude and the non-finite count over unknown cells.
+template <bool FUSE>
+__device__ __forceinline__ void check_df_column(const Lattice& L, const L2F& K,
+                                                const float2* __restrict__ s,
+                                                const float* __restrict__ delta,
+                                                float2* __restrict__ s_new,
+                                                float* __restrict__ r_out, int umt, int i,
+                                                int j, int kb, int ke, float& sum2, float& vmax,
+                                                int& bad) {
+    const int nx = L.nx, nxny = L.nxny;
+    const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
+    const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
+    auto val = [&](int64_t cc) -> float2 {
+        return FUSE ? df_add_f(s[cc], delta[cc]) : s[cc];
+    };
+    const float2 zero = make_float2(0.f, 0.f);
+    int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
+    float2 s_prev = kb > 0 ? val(c - nxny) : zero;
+    float2 s_cur = val(c);
+#pragma unroll 2
+    for (int k = kb; k < ke; ++k, c += nxny) {
+        const float2 s_next = (k + 1 < L.nz) ? val(c + nxny) : zero;
+        const unsigned f = L.flags[c];
+        if (FUSE) s_new[c] = s_cur;
+        if (f & F_FLUID) {
+            if (!(umt && (f & F_ELEC))) {
+                float2 r = df_fma(K.diag[c], s_cur, K.b[c]);
+                r = df_fma(K.f[0][c], val(c + oxm), r);
+                r = df_fma(K.f[1][c], val(c + oxp), r);
+                r = df_fma(K.f[2][c], val(c + oym), r);
+                r = df_fma(K.f[3][c], val(c + oyp), r);
+                r = df_fma(K.f[4][c], s_prev, r);
+                r = df_fma(K.f[5][c], s_next, r);
+                r_out[c] = r.x;
+                const float q = r.x * r.x;
+                if (isfinite(q)) {
+                    sum2 += q;
+                    vmax = fmaxf(vmax, fabsf(r.x));
+                } else {
+                    ++bad;
+                }
+            } else {
+                r_out[c] = 0.f;
+            }
+        }
+        s_prev = s_cur;
+        s_cur = s_next;
+    }
+}
+
+// Defect r = b + L s in double-float (s [+ delta] as pairs), written as the FP32 forcing;
+// reductions 0 sum r^2, 6 non-finite count, 7 max |r| over unknown cells. FUSE: s + delta
+// is the state, written to s_new (every cell).
 template <bool FUSE>
 __global__ void __launch_bounds__(BX * BY, 4)
 check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __restrict__ delta,
@@ -1152,46 +1210,8 @@ check_df_kernel(Lattice L, L2F K, const float2* __restrict__ s, const float* __r
     const int j = blockIdx.y * BY + threadIdx.y;
     if (i < L.nx && j < L.ny) {
         const int kb = blockIdx.z * kchunk;
-        const int ke = min(kb + kchunk, L.nz);
-        const int nx = L.nx, nxny = L.nxny;
-        const int64_t oxm = i > 0 ? -1 : 0, oxp = i + 1 < nx ? 1 : 0;
-        const int64_t oym = j > 0 ? -nx : 0, oyp = j + 1 < L.ny ? nx : 0;
-        auto val = [&](int64_t cc) -> float2 {
-            return FUSE ? df_add_f(s[cc], delta[cc]) : s[cc];
-        };
-        const float2 zero = make_float2(0.f, 0.f);
-        int64_t c = (int64_t)i + (int64_t)nx * j + (int64_t)nxny * kb;
-        float2 s_prev = kb > 0 ? val(c - nxny) : zero;
-        float2 s_cur = val(c);
-#pragma unroll 2
-        for (int k = kb; k < ke; ++k, c += nxny) {
-            const float2 s_next = (k + 1 < L.nz) ? val(c + nxny) : zero;
-            const unsigned f = L.flags[c];
-            if (FUSE) s_new[c] = s_cur;
-            if (f & F_FLUID) {
-                if (!(umt && (f & F_ELEC))) {
-                    float2 r = df_fma(K.diag[c], s_cur, K.b[c]);
-                    r = df_fma(K.f[0][c], val(c + oxm), r);
-                    r = df_fma(K.f[1][c], val(c + oxp), r);
-                    r = df_fma(K.f[2][c], val(c + oym), r);
-                    r = df_fma(K.f[3][c], val(c + oyp), r);
-                    r = df_fma(K.f[4][c], s_prev, r);
-                    r = df_fma(K.f[5][c], s_next, r);
-                    r_out[c] = r.x;
-                    const float q = r.x * r.x;
-                    if (isfinite(q)) {
-                        sum2 += q;
-                        vmax = fmaxf(vmax, fabsf(r.x));
-                    } else {
-                        ++bad;
-                    }
-                } else {
-                    r_out[c] = 0.f;
-                }
-            }
-            s_prev = s_cur;
-            s_cur = s_next;
-        }
+        check_df_column<FUSE>(L, K, s, delta, s_new, r_out, umt, i, j, kb,
+                              min(kb + kchunk, L.nz), sum2, vmax, bad);
     }
     double acc[NRED] = {(double)sum2, 0.0, 0.0, 0.0, 0.0, 0.0, (double)bad, (double)vmax};
     const int64_t bid = (int64_t)blockIdx.x + (int64_t)gridDim.x *
@@ -1290,16 +1310,48 @@ batch_check_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restr
         if (t < 8) { tA[t] = I->C64.rA[t]; tB[t] = I->C64.rB[t]; }
         __syncthreads();
         if (active) {
-            // the item's 1024 cells of the flattened plane, 4 consecutive cells a thread
-            const int64_t cell0 = 4 * ((int64_t)it.bx + t);
+            // the item's 1024 cells of the flattened plane, 4 a thread 256 cells apart
+            // (consecutive threads on consecutive cells: coalesced)
             for (int q = 0; q < 4; ++q) {
-                const int64_t cell = cell0 + q;
+                const int64_t cell = 4 * (int64_t)it.bx + 256 * q + t;
                 if (cell < (int64_t)L.nxny)
                     check_column<FUSE, true>(L, C, tA, tB, s, d0, s_new, r32, acc,
                                              (int)(cell % L.nx), (int)(cell / L.nx), it.kb,
                                              it.ke);
             }
         }
+        block_reduce_store(acc, partials + (int64_t)w * NRED);
+    }
+}
+
+// Batched double-float check (FUSE: state = sdf[cur] + delta[0] written to sdf[cur ^ 1],
+// FP32 forcing refreshed), one work item per loop trip: the work items of
+// batch_check_kernel, the arithmetic of check_df_kernel. Items of inactive lattices write
+// zero partials.
+template <bool FUSE>
+__global__ void __launch_bounds__(BX * BY, 3)
+batch_check_df_kernel(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items,
+                      int n_items, double* __restrict__ partials) {
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const BatchInst* I = insts + it.inst;
+        float sum2 = 0.f, vmax = 0.f;
+        int bad = 0;
+        if (I->active) {   // uniform over the block
+            const Lattice L = I->L;
+            const L2F K = I->K2;
+            const int cur = I->cur;
+            const int t = threadIdx.y * BX + threadIdx.x;
+            // the item's 1024 cells of the flattened plane, 4 a thread 256 cells apart
+            for (int q = 0; q < 4; ++q) {
+                const int64_t cell = 4 * (int64_t)it.bx + 256 * q + t;
+                if (cell < (int64_t)L.nxny)
+                    check_df_column<FUSE>(L, K, I->sdf[cur], I->delta[0], I->sdf[cur ^ 1],
+                                          I->r32, 0, (int)(cell % L.nx), (int)(cell / L.nx),
+                                          it.kb, it.ke, sum2, vmax, bad);
+            }
+        }
+        double acc[NRED] = {(double)sum2, 0.0, 0.0, 0.0, 0.0, 0.0, (double)bad, (double)vmax};
         block_reduce_store(acc, partials + (int64_t)w * NRED);
     }
 }

@@ -408,7 +408,7 @@ class BatchInfo(ctypes.Structure):
                 ("grid_blocks", c_int32), ("sweep_ms", c_double), ("check_ms", c_double),
                 ("cycles", c_int64), ("time_ms", c_double), ("launches", c_int64),
                 ("graph_launches", c_int64), ("pass_stages", c_int32), ("pass_chunk", c_int32),
-                ("pass_tile_cols", c_int32), ("reserved_", c_int32)]
+                ("pass_tile_cols", c_int32), ("df_cycles", c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

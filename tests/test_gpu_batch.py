@@ -55,7 +55,7 @@ def test_small_batch_matches_oracle_and_single_solves():
 
 def test_device_driven_loop_equals_the_host_driven_cycles():
     """Without a timeout the cycles run in the device-driven loop (a conditional while
-    node; a few graph launches for the whole solve); with one, one captured cycle per
+    node; a graph launch per 64 cycles of each check precision); with one, one captured cycle per
     launch with the host in between. Both run the same cycles: bitwise the same states,
     sweep counts and residuals."""
     from paper_2502_08034_gb300 import rfb
@@ -73,7 +73,10 @@ def test_device_driven_loop_equals_the_host_driven_cycles():
                 s.close()
     (sa, ra, ia), (sb, rb, ib) = out
     assert ia["cycles"] == ib["cycles"] and ib["graph_launches"] == ib["cycles"]
-    assert ia["graph_launches"] == -(-ia["cycles"] // 64) < ia["cycles"]
+    # the double-float cycles, then (for lattices whose tol lies below the double-float
+    # floor) the FP64 ones: one device-driven launch per 64 cycles of each
+    assert ia["graph_launches"] <= -(-ia["cycles"] // 64) + 1 and ia["graph_launches"] < ia["cycles"]
+    assert ia["df_cycles"] == ib["df_cycles"] > 0
     for x, y in zip(sa, sb):
         assert np.array_equal(x, y)
     for x, y in zip(ra, rb):
@@ -95,6 +98,7 @@ def test_batched_two_sweep_pass_and_one_sweep_kernel_reach_the_oracle():
                                     [1e-10] * len(cases), fp32_kernel=kernel)
             if kernel == "blocked":
                 assert info["sweeps_per_cycle"] % 4 == 0
+            assert 0 < info["df_cycles"] <= info["cycles"]
             for c, r, sv, ref in zip(cases, res, solvers, refs):
                 assert r["residual"] <= 1e-10
                 assert np.abs(sv.get_state() - ref).max() < 1e-6, (kernel, c.name)
@@ -197,3 +201,24 @@ def test_batched_pass_64_and_128_column_tiles_are_the_same_sweeps():
     assert na == nb
     for x, y in zip(sa, sb):
         assert np.array_equal(x, y)
+
+
+def test_batch_below_the_double_float_floor_finishes_with_fp64_checks():
+    """A tolerance below what double-float defects resolve (10 x tau 2^-44 max_c d_c): the
+    batch leaves the double-float cycles at that level and finishes with FP64 checks, at
+    the oracle's steady states."""
+    from paper_2502_08034_gb300 import rfb
+    cases = _small_batch()[:2]
+    refs = [soc.steady_state(soc.assemble(problem_from_case(c, soc))) for c in cases]
+    solvers = [rfb.Solver.from_case(c) for c in cases]
+    try:
+        with rfb.Batch(solvers) as b:
+            res, info = b.solve([c.s_in for c in cases], [c.eta for c in cases],
+                                [1e-12] * len(cases))
+        assert 0 < info["df_cycles"] < info["cycles"]
+        for r, sv, ref in zip(res, solvers, refs):
+            assert r["residual"] <= 1e-12
+            assert np.abs(sv.get_state() - ref).max() < 1e-9
+    finally:
+        for s in solvers:
+            s.close()
