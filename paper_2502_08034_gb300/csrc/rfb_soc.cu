@@ -174,9 +174,52 @@ void set_err(rfb_soc_handle* h, const char* fmt, ...) {
         ++(h)->launches;                                                               \
     } while (0)
 
+// Device memory of the handles comes from a stream-ordered pool the library owns (one per
+// device): a handle created after another was destroyed reuses its memory without a
+// cudaMalloc / cudaFree, each of which synchronises the whole device. The pool keeps up to
+// 16 GB of freed memory for reuse and returns the rest to the driver at the next
+// synchronisation. Allocations are ordered on the handle's stream; every host call that
+// hands a buffer to another stream synchronises the handle's stream first.
+cudaMemPool_t handle_pool(rfb_soc_handle* h, bool renew = false) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(h->device);
+    if (it != pools.end() && !renew) return it->second;
+    if (it != pools.end()) pools.erase(it);   // lost with the context (a device reset)
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = h->device;
+    cudaMemPool_t p = nullptr;
+    CK(h, cudaMemPoolCreate(&p, &props));
+    uint64_t keep = 16ull << 30;
+    CK(h, cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[h->device] = p;
+    return p;
+}
+
+// A new buffer is zero-filled: the kernels leave cells they never update at the value they
+// find (the FP32 forcing of solid cells stays 0, and the correction sweeps multiply it by
+// the zero step of those cells), and memory the pool hands out again holds old data.
+void pool_alloc(rfb_soc_handle* h, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 1);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, handle_pool(h), h->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (e == cudaErrorMemoryAllocation) {
+            set_err(h, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+            throw Fail{RFB_ERR_OOM};
+        }
+        // the pool no longer exists (the context was reset): a new one
+        CK(h, cudaMallocFromPoolAsync(p, bytes, handle_pool(h, true), h->stream));
+    }
+    CK(h, cudaMemsetAsync(*p, 0, bytes, h->stream));
+}
+
 template <typename T>
 void dalloc(rfb_soc_handle* h, T** p, size_t n) {
-    CK(h, cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)));
+    pool_alloc(h, (void**)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
 int flat_grid(int64_t n) {
@@ -1044,8 +1087,9 @@ void free_all(rfb_soc_handle* h) {
     void* ptrs[] = {h->d_arena, h->d_m,    h->d_m32,  h->d_lam[0], h->d_lam[1], h->d_g,
                     h->d_grad,  h->d_L64,  h->d_L2F,  h->d_eta,    h->d_elec,   h->d_sdf[0],
                     h->d_sdf[1], h->d_gdf,  h->d_stage,  h->d_bv,     h->d_bvpart};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs)   // back to the pool, in the handle's stream order
+        if (p) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
     if (h->h_red) cudaFreeHost(h->h_red);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -1174,7 +1218,7 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
             auto up = [](size_t b) { return (b + 255) / 256 * 256; };
             size_t total = 0;
             for (const Part& q : parts) total += up(q.bytes);
-            CK(h, cudaMalloc((void**)&h->d_arena, total));
+            pool_alloc(h, (void**)&h->d_arena, total);
             size_t off = 0;
             for (const Part& q : parts) {
                 *q.p = h->d_arena + off;
@@ -1190,7 +1234,7 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
         std::vector<void*> tmp;
         auto stage = [&](const void* src, size_t bytes, void** dst) {
             if (kind == RFB_MEM_DEVICE) { *dst = const_cast<void*>(src); return; }
-            CK(h, cudaMalloc(dst, std::max<size_t>(bytes, 1)));
+            pool_alloc(h, dst, bytes);
             tmp.push_back(*dst);
             CK(h, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
         };
@@ -1234,7 +1278,7 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
             CK(h, cudaMemcpyAsync(h->h_red, h->d_red, NRED * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
-            for (void* p : tmp) cudaFree(p);
+            for (void* p : tmp) cudaFreeAsync(p, h->stream);
             tmp.clear();
             if (herr[0]) { set_err(nullptr, "%llu non-finite face velocities", herr[0]); throw Fail{RFB_ERR_INVALID_ARG}; }
             if (herr[1]) { set_err(nullptr, "%llu nonzero velocities on side-wall or fiber faces", herr[1]); throw Fail{RFB_ERR_INVALID_ARG}; }
@@ -1249,7 +1293,8 @@ rfb_status rfb_soc_create(const int32_t dims[3], double dx, const uint8_t* fiber
             }
             if (h->n_fluid == 0) { set_err(nullptr, "no fluid cells"); throw Fail{RFB_ERR_INVALID_ARG}; }
         } catch (...) {
-            for (void* p : tmp) cudaFree(p);
+            cudaStreamSynchronize(h->stream);
+            for (void* p : tmp) cudaFreeAsync(p, h->stream);
             throw;
         }
     } catch (Fail f) {
