@@ -80,7 +80,8 @@ def parse():
                          "five) delta stages)")
     ap.add_argument("--logpile-flow", default="potential", choices=["potential", "stokes"],
                     help="logpile workload: potential flow at the paper's 10 Pa flow rate "
-                         "(default) or the Stokes flow at 10 Pa (matrix-free MINRES)")
+                         "(default) or the Stokes flow at 10 Pa (matrix-free MINRES with a multigrid "
+                         "preconditioner)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, U_mt, e2e and CPU-baseline legs")
     return ap.parse_args()
