@@ -513,13 +513,13 @@ void tb_encode(rfb_soc_handle* h, CUtensorMap* m, CUtensorMapDataType t, size_t 
 
 void tb_prepare(rfb_soc_handle* h) {
     if (h->tm_ready) return;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[0]) {
+    // The shared-memory limit is an attribute of the kernel in the current device's
+    // context, so it is set for every handle (with its device current): a process-wide
+    // flag would leave a second device, or a context rebuilt after cudaDeviceReset, at
+    // the default 48 KB and the launches would fail.
+    {
         CK(h, cudaFuncSetAttribute(sweep32tb_kernel<false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
-        attr_set[0] = true;
-    }
-    if (!attr_set[1]) {
         CK(h, cudaFuncSetAttribute(sweep32tb_kernel<true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
         CK(h, cudaFuncSetAttribute(sweep32tbd_kernel<false, 3>,
@@ -538,7 +538,6 @@ void tb_prepare(rfb_soc_handle* h) {
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<5>()));
         CK(h, cudaFuncSetAttribute(sweep32t3_kernel<true, 5>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, t3_smem<5>()));
-        attr_set[1] = true;
     }
     for (int q = 0; q < 2; ++q) {
         tb_encode(h, &h->tm_delta[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->d_delta[q], h->nz,
@@ -2880,8 +2879,9 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
         bool tb_ok = local;
         for (int q = 0; q < n && tb_ok; ++q) tb_ok = tb_eligible(b->hs[q], true);
         if (tb_ok) {
-            static bool attr = false;
-            if (!attr) {
+            // per solve, on the batch's device (an attribute of the kernel in that
+            // device's context; see tb_prepare)
+            {
                 BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3, 128>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             tbd_smem<3>()));
@@ -2891,7 +2891,6 @@ rfb_status rfb_soc_batch_solve(rfb_batch* b, const double* s_in, const double* e
                 BCK(b, cudaFuncSetAttribute(batch_tbd_kernel<3, 64>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             tbd_smem<3, 64>()));
-                attr = true;
             }
             for (int wide = 0; wide < 2; ++wide) {   // 72- then 136-column boxes
                 const int bw = wide ? TB_BW : TBDGeom<64>::BW;
