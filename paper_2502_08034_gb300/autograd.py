@@ -3,8 +3,10 @@ reactive-area multiplier field and the velocity scale.
 
 Forward runs the steady-state solve and the U_mt solve in the CUDA library; backward runs
 its discrete adjoint (``rfb_soc_adjoint``), one adjoint solve per objective whose incoming
-gradient is nonzero. ``precision`` ("fp64" or "mixed") selects both. Only the converged states are kept (in
-the solver handle), so no activation checkpointing is involved.
+gradient is nonzero. ``precision`` ("fp64" or "mixed") selects both. Only the converged
+states are kept (in the solver handle), so no activation checkpointing is involved; for
+the same reason a backward must come before any other call that changes the solver's
+states, which it checks.
 """
 from __future__ import annotations
 
@@ -29,6 +31,7 @@ class SocObjective(torch.autograd.Function):
         r = solver.solve(s_in, eta, tol, precision=precision, velocity_scale=b)
         u_mt, _ = solver.umt(tol, precision=precision, velocity_scale=b)
         ctx.solver = solver
+        ctx.generation = solver.state_generation
         ctx.tol = tol
         ctx.precision = precision
         ctx.device = area_mult.device
@@ -41,6 +44,13 @@ class SocObjective(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_i, g_u, g_umt):
         sv = ctx.solver
+        if sv.state_generation != ctx.generation:
+            # the adjoint differentiates the handle's current states, which are no longer
+            # the ones this forward computed
+            raise RuntimeError(
+                "the solver was used again after this forward (a solve, U_mt solve, state or "
+                "area-multiplier change, upsampling or batch solve): its adjoint would "
+                "differentiate that later state; run the forward again before backward")
         grad_m = torch.zeros(ctx.n, dtype=torch.float64, device=ctx.device)
         grad_b = 0.0
         for g, obj in ((g_i, "I_tot"), (g_u, "U"), (g_umt, "U_mt")):

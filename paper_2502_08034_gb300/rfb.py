@@ -201,7 +201,11 @@ def _ptr(x, dtype, n=None, what="array"):
 
 
 class Solver:
-    """One lattice + flow field on the GPU (a ``rfb_soc_handle``)."""
+    """One lattice + flow field on the GPU (a ``rfb_soc_handle``).
+
+    ``state_generation`` counts the calls that may change what an adjoint differentiates
+    (the forward or U_mt state, the operating point, the area multipliers); the
+    autograd bridge compares it between its forward and backward."""
 
     def __init__(self, dims, dx, solid, U, V, W, D, k0, alpha=0.5, n_e=2, T=298.0, c0=20.0,
                  area_mult=None, stream=None, kinetics_mode=KIN_AFFINE):
@@ -230,6 +234,7 @@ class Solver:
         if st != RFB_OK:
             raise RfbError(st, L.rfb_soc_last_error(None).decode())
         self.h = h
+        self.state_generation = 0
         n, nf = c_int64(), c_int64()
         L.rfb_soc_info(h, byref(n), byref(nf))
         self.n_cells, self.n_fluid = n.value, nf.value
@@ -251,9 +256,15 @@ class Solver:
             raise RfbError(st, lib().rfb_soc_last_error(self.h).decode())
         return st
 
+    def _changing(self):
+        """Called before every call that may change the handle's states or operating
+        point (also when the call then fails: it may have changed them part way)."""
+        self.state_generation = getattr(self, "state_generation", 0) + 1
+
     def solve(self, s_in, eta, tol, allow_not_converged=False, **opts) -> dict:
         r = SolveResult()
         o = make_opts(**opts)
+        self._changing()
         st = lib().rfb_soc_solve(self.h, float(s_in), float(eta), float(tol), byref(o), byref(r))
         self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
         out = r.as_dict()
@@ -263,6 +274,7 @@ class Solver:
     def step(self, s_in, eta, n, **opts) -> dict:
         r = SolveResult()
         o = make_opts(**opts)
+        self._changing()
         self._check(lib().rfb_soc_step(self.h, float(s_in), float(eta), int(n), byref(o), byref(r)))
         return r.as_dict()
 
@@ -270,6 +282,7 @@ class Solver:
         """rfb_soc_solve_nernst: the SBV steady state by the Nernst model (FP64)."""
         r = SolveResult()
         o = make_opts(**opts)
+        self._changing()
         st = lib().rfb_soc_solve_nernst(self.h, float(s_in), float(eta), float(tol),
                                         float(omega), byref(o), byref(r))
         self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
@@ -285,6 +298,7 @@ class Solver:
                      int(max_cg), BV_START[start] if isinstance(start, str) else int(start), 0)
         r = BVResult()
         o = make_opts(**opts)
+        self._changing()
         st = lib().rfb_soc_solve_bv(self.h, float(s_in), float(eta), float(tol), byref(q),
                                     byref(o), byref(r))
         self._check(st, (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,))
@@ -326,6 +340,7 @@ class Solver:
         r = SolveResult()
         u = c_double()
         o = make_opts(**opts)
+        self._changing()
         self._check(lib().rfb_soc_umt(self.h, float(tol), byref(o), byref(u), byref(r)))
         return u.value, r.as_dict()
 
@@ -340,14 +355,17 @@ class Solver:
 
     def set_state(self, s):
         p, keep, kind = _ptr(s, np.float64, self.n_cells, "state")
+        self._changing()
         self._check(lib().rfb_soc_set_state(self.h, p, kind))
 
     def set_area_mult(self, m):
         """rfb_soc_set_area_mult (None = all ones)."""
         if m is None:
+            self._changing()
             self._check(lib().rfb_soc_set_area_mult(self.h, None, MEM_HOST))
             return
         p, keep, kind = _ptr(m, np.float64, self.n_cells, "area_mult")
+        self._changing()
         self._check(lib().rfb_soc_set_area_mult(self.h, p, kind))
 
     def adjoint(self, objective="I_tot", tol=1e-12, out=None, **opts):
@@ -365,9 +383,11 @@ class Solver:
 
     def upsample_from(self, coarse: "Solver"):
         """rfb_soc_upsample: this (fine) handle's state := 2x prolongation of coarse's."""
+        self._changing()
         self._check(lib().rfb_soc_upsample(coarse.h, self.h))
 
     def reset_state(self):
+        self._changing()
         self._check(lib().rfb_soc_reset_state(self.h))
 
     def set_stream(self, stream):
@@ -442,6 +462,8 @@ class Batch:
         res = (SolveResult * n)()
         info = BatchInfo()
         o = make_opts(**opts)
+        for sv in self.solvers:
+            sv._changing()
         st = lib().rfb_soc_batch_solve(self.b, D(*s_in), D(*eta), D(*tol), byref(o), res,
                                        byref(info))
         ok = (RFB_OK, RFB_ERR_NOT_CONVERGED) if allow_not_converged else (RFB_OK,)
