@@ -227,3 +227,16 @@ def test_multigrid_keeps_minres_iterations_nearly_flat_under_refinement():
         growth_j = its["jacobi", r] / its["jacobi", r // 2]
         assert growth_j > 2.0 and growth_mg < 0.75 * growth_j, its
     assert its["mg", 4] * 5 < its["jacobi", 4], its
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 1), (6, 1, 5), (8, 1, 1), (3, 4, 4)])
+def test_multigrid_minres_on_degenerate_lattices(shape):
+    """One cell across in x and/or y leaves a velocity component with no open face (an
+    empty multigrid level) and coarsening stops at extents of one; the flow still matches
+    the sparse-LU fixture."""
+    s = np.zeros(shape, dtype=bool)
+    a = synth.stokes_flow(s, 1e-6, dp=1.0)
+    b = synth.stokes_flow_minres(s, 1e-6, dp=1.0, tol=1e-12)
+    assert abs(b[3]["q_m3_s"] / a[3]["q_m3_s"] - 1.0) <= 1e-12
+    for x, y in zip(a[:3], b[:3]):
+        assert np.abs(x - y).max() <= 1e-10 * np.abs(a[2]).max()
