@@ -1,7 +1,8 @@
 """The seeded input recipe (no GPU): the project-written SplitMix64 against the reference
 generator's published output, the fiber rasteriser against a cell-by-cell distance test,
-the stopping rule of the fiber generator, and the flood fill that removes fluid pockets
-not connected to the inlet."""
+the stopping rule of the fiber generator, the flood fill that removes fluid pockets not
+connected to the inlet, and the host potential-flow solver against its discrete problem
+written out and solved by sparse LU."""
 import math
 
 import numpy as np
@@ -71,3 +72,55 @@ def test_unconnected_fluid_is_made_solid():
     blocked[2, 0, 0] = True         # no path from the inlet plane to the outlet plane
     with pytest.raises(ValueError):
         synth.remove_unconnected(blocked)
+
+
+def _potential_flow_direct(solid, u_mean):
+    """The potential-flow fixture's discrete problem written out and solved by sparse LU:
+    cell-centred phi on fluid cells, conductance 1 between fluid neighbours, 2 to the inlet
+    face (phi = 1) and the outlet face (phi = 0) of the first and last plane, none through
+    solid cells or side walls; face velocities -grad phi, scaled so that the mean of W over
+    fluid z-faces (inlet and outlet faces included) is u_mean."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    nz, ny, nx = solid.shape
+    fl = ~solid.astype(bool)
+    idx = -np.ones(solid.shape, dtype=np.int64)
+    idx[fl] = np.arange(int(fl.sum()))
+    rows, cols, vals = [], [], []
+    diag = np.zeros(int(fl.sum()))
+    b = np.zeros_like(diag)
+    for k, j, i in zip(*np.nonzero(fl)):
+        c = idx[k, j, i]
+        for dk, dj, di in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+            kk, jj, ii = k + dk, j + dj, i + di
+            if 0 <= kk < nz and 0 <= jj < ny and 0 <= ii < nx and fl[kk, jj, ii]:
+                diag[c] += 1.0
+                rows.append(c); cols.append(idx[kk, jj, ii]); vals.append(-1.0)
+        if k == 0:
+            diag[c] += 2.0
+            b[c] += 2.0
+        if k == nz - 1:
+            diag[c] += 2.0
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(diag.size, diag.size)) + sp.diags(diag)
+    phi = np.zeros(solid.shape)
+    phi[fl] = spla.spsolve(A.tocsc(), b)
+    U = np.zeros((nz, ny, nx + 1))
+    V = np.zeros((nz, ny + 1, nx))
+    W = np.zeros((nz + 1, ny, nx))
+    U[:, :, 1:nx] = np.where(fl[:, :, 1:] & fl[:, :, :-1], phi[:, :, :-1] - phi[:, :, 1:], 0.0)
+    V[:, 1:ny, :] = np.where(fl[:, 1:] & fl[:, :-1], phi[:, :-1] - phi[:, 1:], 0.0)
+    W[1:nz] = np.where(fl[1:] & fl[:-1], phi[:-1] - phi[1:], 0.0)
+    W[0] = np.where(fl[0], 2.0 * (1.0 - phi[0]), 0.0)
+    W[nz] = np.where(fl[-1], 2.0 * phi[-1], 0.0)
+    zf = np.concatenate([fl[:1], fl[1:] & fl[:-1], fl[-1:]])
+    f = u_mean / W[zf].mean()
+    return U * f, V * f, W * f
+
+
+def test_host_potential_flow_is_the_discrete_potential_problem():
+    _, solid = synth.generate_fibers(3, (14, 12, 20), 0.8, 3.0)
+    solid = synth.remove_unconnected(solid)
+    got = synth.potential_flow(solid, 1e-6, 0.004)
+    want = _potential_flow_direct(solid, 0.004)
+    for g, w in zip(got[:3], want):
+        assert np.abs(g - w).max() <= 1e-10 * 0.004
