@@ -124,3 +124,27 @@ def test_host_potential_flow_is_the_discrete_potential_problem():
     want = _potential_flow_direct(solid, 0.004)
     for g, w in zip(got[:3], want):
         assert np.abs(g - w).max() <= 1e-10 * 0.004
+
+
+def test_batched_workload_recipe():
+    """The 48-lattice batch: lattice 0 is 64^3 and lattice 1 192x192x384; the others have
+    nx = ny in {64, 80, ..., 192} and nz a multiple of 16 between nx and 2 nx (inside the
+    clipping range [64, 384]); porosity, mean velocity (log-uniform), s_in and eta
+    lie in their ranges; 187M cells in all."""
+    qs = [synth.batch_instance_params(i) for i in range(48)]
+    assert qs[0]["dims"] == (64, 64, 64) and qs[1]["dims"] == (192, 192, 384)
+    for q in qs[2:]:
+        nx, ny, nz = q["dims"]
+        assert nx == ny and nx in range(64, 193, 16)
+        assert nz % 16 == 0 and 64 <= nz <= 384
+        assert nx <= nz <= 2 * nx                       # 16 round(nx U[1, 2] / 16)
+    for i, q in enumerate(qs):
+        assert q["seed"] == 3000 + i
+        assert 0.75 <= q["porosity"] <= 0.90
+        assert 0.001 <= q["u_mean"] <= 0.05
+        assert 0.1 <= q["s_in"] <= 0.9 and -0.2 <= q["eta"] <= -0.02
+    cells = sum(np.prod(q["dims"]) for q in qs)
+    assert 180e6 < cells < 195e6, cells
+    assert len({q["dims"] for q in qs}) > 20            # uneven sizes
+    us = np.log10([q["u_mean"] for q in qs])
+    assert us.min() < -2.5 and us.max() > -1.6        # spread over the log range
