@@ -148,3 +148,44 @@ def test_batched_workload_recipe():
     assert len({q["dims"] for q in qs}) > 20            # uneven sizes
     us = np.log10([q["u_mean"] for q in qs])
     assert us.min() < -2.5 and us.max() > -1.6        # spread over the log range
+
+
+def test_multilevel_lattices_rasterise_the_same_fibers():
+    """Every level of an upsampling chain rasterises the fibers drawn once at the finest
+    level: a coarse cell is solid exactly when its centre, in finest-level units, lies
+    within a fiber's radius (before the flood fill), and the cell size doubles per level."""
+    fine = (32, 24, 48)
+    fibers, solid_f = synth.generate_fibers(9, fine, 0.85, 4.0)
+    cases = synth.multilevel_cases(fine, 3, 0.85, 4.0, 9, 0.01, -0.1, 0.5, 1e-8,
+                                   h_fine=1e-6)
+    assert [c.dims for c in cases] == [(8, 6, 12), (16, 12, 24), (32, 24, 48)]
+    assert [c.h for c in cases] == [4e-6, 2e-6, 1e-6]
+    assert np.array_equal(cases[-1].solid.astype(bool), synth.remove_unconnected(solid_f))
+    for c, f in zip(cases[:2], (4, 2)):
+        nx, ny, nz = c.dims
+        raw = np.zeros((nz, ny, nx), dtype=bool)
+        for fb in fibers:
+            for k in range(nz):
+                z = (k + 0.5) * f - fb.z0
+                for j in range(ny):
+                    y = (j + 0.5) * f
+                    x = (np.arange(nx) + 0.5) * f
+                    across = (x - fb.x0) * math.sin(fb.theta) - (y - fb.y0) * math.cos(fb.theta)
+                    raw[k, j] |= across ** 2 + z ** 2 <= (fb.d / 2) ** 2
+        assert np.array_equal(c.solid.astype(bool), synth.remove_unconnected(raw))
+
+
+def test_area_multipliers_are_lognormal_on_wall_cells_only():
+    _, solid = synth.generate_fibers(4, (40, 40, 60), 0.8, 8.0)
+    m = synth.lognormal_area_mult(solid, sigma=0.3, seed=40)
+    s = solid.astype(bool)
+    pad = np.pad(s, 1)
+    touch = (pad[1:-1, 1:-1, :-2] | pad[1:-1, 1:-1, 2:] | pad[1:-1, :-2, 1:-1] |
+             pad[1:-1, 2:, 1:-1] | pad[:-2, 1:-1, 1:-1] | pad[2:, 1:-1, 1:-1])
+    wall = touch & ~s
+    assert np.all(m[~wall] == 1.0)
+    z = np.log(m[wall]) / 0.3
+    assert z.size > 5000
+    assert np.array_equal(z, np.log(np.exp(0.3 * np.random.default_rng(40).standard_normal(
+        z.size))) / 0.3)
+    assert abs(np.median(z)) < 0.05 and abs(z.std() - 1.0) < 0.03
